@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the EPIC imaging path on GB300.
+
+One step = one integration imaged by one epic_image call: every channel,
+polarisation and time sample of the workload (unpack, calibrate, grid,
+transform, products, time sum, autocorrelation subtraction).  The metric is
+imaged spectra per second, spectra = channels x time samples x polarisations.
+
+Default workload: the LWA-station-like configuration (256 dual-pol antennas,
+64 channels of 25 kHz from 60 MHz, 1000 spectra per integration, 5x5 kernel,
+128x128 grid), seeded synthetic inputs resident in HBM.  L2 is flushed by a
+256 MiB write between timed steps.  Under torchrun each rank images its own
+band of the same shape (weak scaling, no collective on the data path).
+
+--impl reference times the FP64 CPU oracle (the correctness reference) on the
+host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "imaged spectra/s (chan x time x pol)"
+UNIT = "spectra/s"
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+# DRAM traffic of one launch of the dominant kernel from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload, with the
+# hash of the kernel source it was taken on; ignored once the source changes.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["lwa", "tiny", "uneven", "dense"], default="lwa")
+    ap.add_argument("--precision", choices=["fp32"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    from paper_2301_09662_gb300 import synth
+    return {"lwa": synth.lwa, "tiny": synth.tiny, "uneven": synth.uneven, "dense": synth.dense}[name]()
+
+
+def describe(wl, name):
+    Ns = sorted(set(int(n) for n in wl.grid_n))
+    return {
+        "workload": f"{wl.name}: {wl.A} antennas x {wl.n_pol} pol, {wl.C} channels, {wl.T} spectra per "
+                    f"integration, {wl.K}x{wl.K} kernel, grid {'/'.join(str(n) for n in Ns)}",
+        "antennas": wl.A, "pols": wl.n_pol, "channels": wl.C, "spectra_per_integration": wl.T,
+        "kernel": wl.K, "grid": Ns, "gains": wl.gains is not None,
+        "l2": "flushed between timed steps (256 MiB write)",
+        "parallelism": "one integration per GPU; ranks image independent bands",
+    }
+
+
+def fp32_flops_per_spectrum(A, K, N):
+    """Algorithmic FLOPs of one spectrum in the FP32 form: gridding 8 A K^2,
+    row-pruned radix-2 FFT 5 N log2 N (N/2 + N), products 8 N^2."""
+    return 8.0 * A * K * K + 5.0 * N * math.log2(N) * (N / 2 + N) + 8.0 * N * N
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("fp32_image.cu", "dft_small.cuh"):
+        with open(os.path.join(ROOT, "paper_2301_09662_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def cpu_baseline(wl, budget_s):
+    """Time the FP64 oracle (O1, OpenMP over channels) on a bounded sample:
+    one channel per thread, as many time samples as fit the budget."""
+    import oracle
+    threads = oracle.threads()
+    C_s = max(1, min(wl.C, threads))
+    chans = list(range(C_s))
+    # calibrate the per-spectrum cost on a short run
+    T_probe = max(1, min(wl.T, 8))
+    sub = _sub_workload(wl, chans, T_probe)
+    t0 = time.perf_counter()
+    oracle.workload_image(sub)
+    dt = time.perf_counter() - t0
+    per_t = dt / T_probe
+    T_s = int(max(1, min(wl.T, budget_s / max(per_t, 1e-9))))
+    sub = _sub_workload(wl, chans, T_s)
+    t0 = time.perf_counter()
+    oracle.workload_image(sub)
+    dt = time.perf_counter() - t0
+    spectra = T_s * C_s * wl.n_pol
+    return {"value": spectra / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"O1 (FP64 EPIC direct, own FFT) on {C_s} of {wl.C} channels x {T_s} of {wl.T} spectra "
+                      f"x {wl.n_pol} pol = {spectra} spectra in {dt:.1f} s"}
+
+
+def _sub_workload(wl, chans, T):
+    import copy
+    sub = copy.copy(wl)
+    sub.v = wl.v[:T, chans]
+    sub.gains = None if wl.gains is None else wl.gains[chans]
+    sub.freq_hz = wl.freq_hz[chans]
+    sub.grid_n = wl.grid_n[chans]
+    sub.T = T
+    return sub
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    wl = make_workload(args.workload)
+    threads = oracle.threads()
+    C_s = max(1, min(wl.C, threads))
+    chans = list(range(C_s))
+    probe = _sub_workload(wl, chans, max(1, min(wl.T, 4)))
+    t0 = time.perf_counter()
+    oracle.workload_image(probe)
+    per_t = (time.perf_counter() - t0) / probe.T
+    # each step a bounded sample sized so the whole run ends within a few minutes
+    T_s = int(max(1, min(wl.T, 150.0 / max(args.steps + args.warmup, 1) / max(per_t, 1e-9))))
+    sub = _sub_workload(wl, chans, T_s)
+    for _ in range(args.warmup):
+        oracle.workload_image(sub)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.workload_image(sub)
+        times.append(time.perf_counter() - t0)
+    spectra = T_s * C_s * wl.n_pol
+    mean = sum(times) / len(times)
+    value = spectra / mean
+    sample = (f"O1 (FP64 EPIC direct) per step on {C_s} of {wl.C} channels x {T_s} of {wl.T} spectra x "
+              f"{wl.n_pol} pol = {spectra} spectra")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(wl, args.workload),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2301_09662_gb300 import epic
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = make_workload(args.workload)
+    plan = epic.Plan.from_workload(wl)
+    v = torch.from_numpy(wl.v).cuda()
+    g = None if wl.gains is None else torch.from_numpy(wl.gains).cuda()
+    out = torch.empty(plan.out_floats // 2, dtype=torch.complex64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    spectra = wl.spectra
+
+    for _ in range(max(args.warmup, 0)):
+        plan.image(v, g, out=out)
+    torch.cuda.synchronize()
+    if plan.status() != epic.EPIC_OK:
+        raise RuntimeError("device status not OK after warm-up")
+
+    names = plan.stage_names()
+    image_stage = next(n for n in names if n.startswith("image["))
+    stage_sum = {n: 0.0 for n in names}
+    plan.set_profiling(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            plan.image(v, g, out=out)
+            ends[k].record(stream)
+            for n, ms in plan.stage_times().items():
+                stage_sum[n] += ms
+        torch.cuda.synchronize()
+        barrier()
+    plan.set_profiling(False)
+    clocks = clk.summary()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_total_ms = float(t.item())
+    ms_per_step = max_total_ms / args.steps
+    value = world * spectra / (ms_per_step / 1e3)
+    launches = len(names) * args.steps
+
+    # end to end through the host-buffer entry point: pinned inputs copied in,
+    # image copied out, every step
+    vh = torch.from_numpy(wl.v).pin_memory()
+    gh = None if wl.gains is None else torch.from_numpy(wl.gains).pin_memory()
+    oh = torch.empty(plan.out_floats // 2, dtype=torch.complex64).pin_memory()
+    for _ in range(2):
+        plan.image_host(vh, gh, out=oh)
+    e2e_times = []
+    barrier()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        plan.image_host(vh, gh, out=oh)
+        e2e_times.append(time.perf_counter() - t0)
+    barrier()
+    e2e_step = sum(e2e_times) / len(e2e_times)
+    te = torch.tensor([e2e_step], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * spectra / float(te.item())
+    h2d = vh.numel() + (gh.numel() * 8 if gh is not None else 0)
+    d2h = oh.numel() * 8
+
+    # roofline of the dominant kernel (the fused imaging kernel)
+    peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    Ns = sorted(set(int(n) for n in wl.grid_n))
+    flops = sum(fp32_flops_per_spectrum(wl.A, wl.K, int(n)) * wl.T * wl.n_pol for n in wl.grid_n
+                if int(n) == int(image_stage[8:-1]))
+    img_ms = stage_sum[image_stage] / args.steps
+    achieved = flops / (img_ms / 1e3) / 1e12
+    traffic = None
+    rec = NCU_TRAFFIC.get(args.workload)
+    if rec and rec[1] == kernel_source_hash():
+        traffic = rec[0]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded LWA-like layout, sky, noise, gains)",
+        "config": describe(wl, args.workload),
+        "roofline": {"bound": "alu", "kernel": f"fp32_image_kernel {image_stage}", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                     "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                    f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS)",
+                     "flops_per_launch": flops, "ms_per_launch": img_ms},
+        "stages_ms": {n: s / args.steps for n, s in stage_sum.items()},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * epic.h -- C ABI of libepic, a GB300 (sm_103a) implementation of the
+ * E-field Parallel Imaging Correlator's imaging path (Krishnan et al. 2023,
+ * "Optimization and Commissioning of the EPIC Commensal Radio Transient Imager
+ * for the Long Wavelength Array").
+ *
+ * What one call computes (Eq. 4 and the GPU block chain of Sec. 2.2): for every
+ * channel c and time sample t of one integration, each antenna's 4+4-bit
+ * complex voltage is calibrated (e~ = g e), gridded onto a padded N x N
+ * aperture grid through the illumination kernel W, Fourier transformed to the
+ * sky, F_p(l) = sum_k G_p(k) exp(+2 pi i k.l / N) (unnormalised), and the
+ * polarisation products F_p F_q^* (XX, YY, XY, YX; Sec. 3.2) are summed over
+ * the integration.  The autocorrelation term A_pq |W^(l)|^2 -- the a = b part
+ * of F_p F_q^*, A_pq = sum_a g_ap g_aq^* sum_t e_ap e_aq^*, W^(l) = sum_d W(d)
+ * exp(+2 pi i d.l / N) -- is subtracted (Sec. 2.2), which makes the result
+ * equal to the FX-correlator dirty image of Eq. 2-3.
+ *
+ * Conventions shared by every call:
+ *   - ci4 byte: real part in the high nibble, imaginary in the low nibble,
+ *     two's complement, values -8..7 (Sec. 2.1, "4+4 complex integers").
+ *   - complex64 = two interleaved floats (re, im), i.e. float[2*n].
+ *   - antenna -> cell map (Sec. 3.1, nearest neighbour on a regular grid of
+ *     spacing du wavelengths): per channel, per axis,
+ *       k = llround(((x - x_c) * f_c) / (c0 * du)) + N_c / 2,
+ *     x_c the centroid of the layout, c0 = 299792458 m/s.  Antenna a's
+ *     footprint covers cells k_a + (dx, dy), |dx|, |dy| <= (K-1)/2.
+ *   - kernel W: complex64 [K][K], element [dy + h][dx + h], h = (K-1)/2; one
+ *     kernel for every antenna, channel and polarisation.
+ *   - output image of channel c: complex64 [NP][N_c][N_c], NP = 4 products
+ *     (XX, YY, XY, YX) for dual polarisation, 1 (XX) for single; pixel (i, j)
+ *     holds direction l = (j - N_c/2, i - N_c/2) in cells of 1/(N_c du), i.e.
+ *     the transform is fft-shifted.  Channels are packed one after another in
+ *     channel order.
+ *   - XX and YY are real (imaginary part written as 0); YX = conj(XY).
+ *   - an integration is a sum over time; EPIC_MEAN divides by n_spectra.
+ *
+ * Ownership: the caller owns every buffer passed in; the plan owns its device
+ * tables and workspace.  A plan is used by one stream at a time.
+ *
+ * Errors: every entry point returns EPIC_OK (0) or a negative EPIC_ERR_* code.
+ * Argument errors are detected on the host before anything is launched and
+ * leave the output untouched.  Device-side errors (a bounded wait that ran
+ * out, an index check that failed) are recorded in the plan's status word and
+ * reported by epic_status.
+ */
+#ifndef EPIC_H
+#define EPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct epic_plan_s *epic_plan_t;
+
+enum {
+    EPIC_OK = 0,
+    EPIC_ERR_ARG = -1,          /* bad argument (null pointer, size, range) */
+    EPIC_ERR_OUT_OF_GRID = -2,  /* an antenna footprint leaves [0, N) */
+    EPIC_ERR_UNSUPPORTED = -3,  /* valid request this build does not implement */
+    EPIC_ERR_CUDA = -4,         /* a CUDA runtime call failed */
+    EPIC_ERR_TIMEOUT = -5,      /* a bounded device-side wait ran out */
+    EPIC_ERR_NOMEM = -6,        /* device or host allocation failed */
+    EPIC_ERR_DEVICE = -7        /* a device-side index/consistency check failed */
+};
+
+/* Arithmetic form of the gridding + transform + products stages. */
+enum {
+    EPIC_FP32 = 0,              /* FP32 SIMT: shared-memory gridding and FFT */
+    EPIC_TC_SPLIT_FP16 = 1,     /* tensor cores, split hi+lo FP16 operands, FP32 accumulate */
+    EPIC_TC_FP16 = 2,           /* tensor cores, single FP16 operands */
+    EPIC_TC_SPLIT_BF16 = 3      /* tensor cores, three-term BF16 split */
+};
+
+/* flags */
+#define EPIC_MEAN        1u     /* divide the sum over time by n_spectra */
+#define EPIC_NO_AUTOSUB  2u     /* keep the autocorrelation term (diagnostics) */
+
+/*
+ * epic_plan -- validate the array geometry and build every table the imaging
+ * calls need (Sec. 3.1 grid and antenna-to-cell map; Eq. 4 kernel image).
+ *
+ *   out            receives the plan handle (set to NULL on error)
+ *   ant_xy_m       host double [n_ant][2], antenna (x, y) positions in metres
+ *   n_ant          number of antennas A >= 1
+ *   n_pol          1 (single polarisation, product XX) or 2 (X and Y)
+ *   kernel_c64     host complex64 [K][K] illumination kernel W
+ *   K              odd kernel side, 1 <= K <= 15
+ *   grid_n         host int [n_chan], grid side N_c per channel; supported
+ *                  sides are 32, 64, 96, 128, 256 and 512
+ *   freq_hz        host double [n_chan], channel centre frequencies
+ *   n_chan         number of channels C >= 1
+ *   du_wavelengths cell size in wavelengths, 0 < du <= 0.5 (lambda/2 grid)
+ *   max_spectra    largest n_spectra an epic_image call will pass (>= 0)
+ *   precision      EPIC_FP32 or one of the EPIC_TC_* forms
+ *   flags          EPIC_MEAN | EPIC_NO_AUTOSUB
+ *
+ * Uses the current CUDA device.  Allocates device memory (tables and
+ * workspace) and returns EPIC_ERR_NOMEM if that fails.  Returns
+ * EPIC_ERR_OUT_OF_GRID when some antenna footprint k_a +- (K-1)/2 leaves
+ * [0, N_c) in some channel; EPIC_ERR_UNSUPPORTED for a grid side, precision or
+ * size this build does not provide.
+ */
+int epic_plan(epic_plan_t *out,
+              const double *ant_xy_m, int n_ant, int n_pol,
+              const float *kernel_c64, int K,
+              const int *grid_n, const double *freq_hz, int n_chan,
+              double du_wavelengths, int max_spectra, int precision,
+              unsigned flags);
+
+/*
+ * epic_image -- image one integration (Eq. 4 with autocorrelation removal,
+ * Sec. 2.2).
+ *
+ *   plan        from epic_plan
+ *   ci4         device uint8 [n_spectra][n_chan][n_ant][n_pol], packed 4+4-bit
+ *               voltages (time slowest, polarisation fastest)
+ *   gains_c64   device complex64 [n_chan][n_ant][n_pol] per-antenna gains, or
+ *               NULL for unit gains (Sec. 4 notes gains are not applied in the
+ *               deployed system; they multiply the voltages here)
+ *   n_spectra   number of time samples T, 0 <= T <= max_spectra; T = 0 gives
+ *               an all-zero image
+ *   out_c64     device complex64, epic_out_floats(plan) floats, overwritten
+ *   cuda_stream cudaStream_t to order the work on (NULL = legacy default)
+ *
+ * Asynchronous and stream-ordered; allocates nothing.  Returns EPIC_ERR_ARG
+ * (nothing launched) for null pointers or n_spectra out of range, and
+ * EPIC_ERR_CUDA if a launch fails.
+ */
+int epic_image(epic_plan_t plan, const uint8_t *ci4, const float *gains_c64,
+               int n_spectra, float *out_c64, void *cuda_stream);
+
+/*
+ * epic_image_host -- the same integration with HOST buffers: copies ci4 and
+ * gains to plan-owned device staging (allocated on the first call, reused
+ * after), runs epic_image on the given stream, copies the image back into
+ * out_c64 (host) and synchronises that stream before returning.  Pinned host
+ * memory makes the copies asynchronous DMA; pageable memory works but is
+ * slower.  Argument meanings and layouts are those of epic_image.
+ */
+int epic_image_host(epic_plan_t plan, const uint8_t *ci4_host, const float *gains_c64_host,
+                    int n_spectra, float *out_c64_host, void *cuda_stream);
+
+/* Number of floats of one epic_image output (2 per complex value), or 0 for a
+ * NULL plan. */
+size_t epic_out_floats(epic_plan_t plan);
+
+/*
+ * epic_status -- synchronise the device and return the sticky device-side
+ * status of the plan: EPIC_OK, EPIC_ERR_TIMEOUT or EPIC_ERR_DEVICE (an
+ * in-kernel consistency check failed; the output of that call is undefined),
+ * or EPIC_ERR_CUDA if the synchronisation itself reported an error.  Reading
+ * the status clears it.
+ */
+int epic_status(epic_plan_t plan);
+
+/* Free the plan and everything it owns (waits for the device first). NULL is
+ * accepted. */
+void epic_destroy(epic_plan_t plan);
+
+/*
+ * Stage timing (the per-block processing-time breakdown of Table 2, taken on
+ * the device).  epic_set_profiling(plan, 1) makes every later epic_image call
+ * record CUDA events on its stream around each of its kernel launches;
+ * epic_stage_times waits for the last such call and writes the device time in
+ * milliseconds of each launch, in launch order: [0] the auto-power kernel
+ * (absent with EPIC_NO_AUTOSUB), then for each grid side in ascending order
+ * the imaging kernel and its epilogue.  Returns the number of values written
+ * (at most max_stages), or a negative EPIC_ERR_* code (EPIC_ERR_ARG if
+ * profiling is off or no call was recorded).
+ */
+int epic_set_profiling(epic_plan_t plan, int enable);
+int epic_stage_times(epic_plan_t plan, float *ms, int max_stages);
+
+/* Static, human-readable text for an EPIC_* code. */
+const char *epic_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPIC_H */

@@ -1,0 +1,84 @@
+// Internal declarations shared by the libepic translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "epic.h"
+
+namespace epic {
+
+constexpr double kC0 = 299792458.0;
+constexpr int kThreads = 256;          // threads per CTA of the imaging kernels
+constexpr int kMaxTau = 64;            // most time chunks one channel item is split into
+constexpr int kMaxK = 15;
+constexpr int kMaxAP = 4096;           // n_ant * n_pol handled by one CTA's staging
+
+// How one grid side N is imaged by the FP32 kernel: the sky is split into
+// Q1 x Q1 pixel classes l = (Q1 m + h) and each CTA owns one class, so it grids
+// into an M x M folded aperture (M = N / Q1) and runs an M x M transform.
+struct GroupCfg {
+    int N = 0, M = 0, Q1 = 1, Q = 1;
+    int n_chan = 0;
+    std::vector<int> chans;            // plan channel indices in this group
+    int *d_chans = nullptr;            // device copy of chans
+    long long *d_out_off = nullptr;    // device: output offset (complex elements) per group channel
+    double *d_wpow = nullptr;          // device: |W^(l)|^2 on the shifted [N][N] layout
+    float2 *d_twN = nullptr;           // device: exp(+2 pi i k / N), k < N
+    int n_items = 0;                   // n_chan * Q
+    float *d_partial = nullptr;        // device: [kMaxTau][n_items][M*M][NPF] partial sums
+};
+
+struct KernelTables {
+    const short2 *cells;               // [C][A] (kx, ky)
+    const float2 *kernel;              // [K*K]
+    int A, P, C, K;
+};
+
+}  // namespace epic
+
+struct epic_plan_s {
+    int device = 0;
+    int A = 0, P = 0, NP = 0, C = 0, K = 0, max_spectra = 0, precision = 0;
+    unsigned flags = 0;
+    int sm_count = 0;
+    std::vector<int> grid_n;
+    std::vector<long long> out_off;    // complex-element offset of each channel's image
+    size_t out_floats = 0;
+    short2 *d_cells = nullptr;         // [C][A]
+    float2 *d_kernel = nullptr;        // [K*K]
+    int *d_autoint = nullptr;          // [C][A][4] exact integer auto sums
+    int *d_status = nullptr;           // sticky device status word
+    std::vector<epic::GroupCfg> groups;
+    // stage timing (epic_set_profiling)
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;   // 2 per recorded stage
+    int n_recorded = 0;
+    // host-buffer entry point staging (allocated on first use)
+    uint8_t *d_stage_v = nullptr;
+    float *d_stage_g = nullptr;
+    float *d_stage_out = nullptr;
+};
+
+namespace epic {
+
+// Stage timing helpers: no-ops unless profiling is on.
+void prof_begin(epic_plan_s *plan);
+void prof_mark(epic_plan_s *plan, cudaStream_t stream, int stage, bool start);
+
+// FP32 form: launch every kernel of one integration on `stream`.
+int image_fp32(epic_plan_s *plan, const uint8_t *v, const float2 *gains, int T,
+               float2 *out, cudaStream_t stream);
+
+// shared pieces (image_common.cu)
+int launch_autopower(epic_plan_s *plan, const uint8_t *v, int T, cudaStream_t stream);
+int launch_epilogue(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T, int n_tau,
+                    float2 *out, cudaStream_t stream);
+
+// device status bits
+constexpr int kStatusDevice = 1;
+constexpr int kStatusTimeout = 2;
+
+}  // namespace epic

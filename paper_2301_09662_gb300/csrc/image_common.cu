@@ -1,0 +1,207 @@
+// Stages shared by every arithmetic form: the exact integer auto-power (a7)
+// and the epilogue that sums the partial images, subtracts the
+// autocorrelation term and writes the shifted output (a8).
+//
+// Autocorrelation removal (Sec. 2.2): the a = b terms of F_p F_q^* are
+// e~_ap e~_aq^* |W^(l)|^2 for every antenna, so their sum over the integration
+// is A_pq |W^(l)|^2 with A_pq = sum_a g_ap g_aq^* sum_t e_ap e_aq^*.  The inner
+// time sum is exact in int32 (|e e^*| components <= 128, T <= 10^5); the
+// antenna sum and the subtraction run in FP64 because the auto term can be
+// much larger than what is left after it is removed.
+#include "epic_internal.cuh"
+
+namespace epic {
+namespace {
+
+__device__ __forceinline__ void ci4_parts(uint32_t b, int &re, int &im)
+{
+    re = static_cast<int>(static_cast<int8_t>(b & 0xF0u)) >> 4;
+    im = static_cast<int>(static_cast<int8_t>((b << 4) & 0xF0u)) >> 4;
+}
+
+// grid (C, n_chunks): per antenna, integer sums over one time chunk
+//   [0] sum |e_X|^2   [1] sum |e_Y|^2   [2] Re sum e_X e_Y^*   [3] Im sum e_X e_Y^*
+__global__ void __launch_bounds__(kThreads)
+autopower_kernel(const uint8_t *__restrict__ v, int T, int C, int A, int P, int n_chunks,
+                 int *__restrict__ autoint)
+{
+    const int c = blockIdx.x;
+    const int chunk = blockIdx.y;
+    const int t0 = static_cast<int>(static_cast<long long>(T) * chunk / n_chunks);
+    const int t1 = static_cast<int>(static_cast<long long>(T) * (chunk + 1) / n_chunks);
+    for (int a = threadIdx.x; a < A; a += blockDim.x) {
+        int sxx = 0, syy = 0, sxyr = 0, sxyi = 0;
+        for (int t = t0; t < t1; t++) {
+            const uint8_t *row = v + (static_cast<size_t>(t) * C + c) * A * P + static_cast<size_t>(a) * P;
+            int xr, xi;
+            ci4_parts(row[0], xr, xi);
+            sxx += xr * xr + xi * xi;
+            if (P == 2) {
+                int yr, yi;
+                ci4_parts(row[1], yr, yi);
+                syy += yr * yr + yi * yi;
+                sxyr += xr * yr + xi * yi;
+                sxyi += xi * yr - xr * yi;
+            }
+        }
+        int *dst = autoint + (static_cast<size_t>(c) * A + a) * 4;
+        atomicAdd(dst + 0, sxx);
+        if (P == 2) {
+            atomicAdd(dst + 1, syy);
+            atomicAdd(dst + 2, sxyr);
+            atomicAdd(dst + 3, sxyi);
+        }
+    }
+}
+
+template <int M>
+struct Digits;
+template <> struct Digits<32> { static constexpr int R1 = 8, R2 = 4; };
+template <> struct Digits<48> { static constexpr int R1 = 8, R2 = 6; };
+template <> struct Digits<64> { static constexpr int R1 = 8, R2 = 8; };
+
+// grid (pixel tiles, group channels).  Partial layout written by the imaging
+// kernels: [tau][item][pos][NPF] with item = ci * Q + (hy * Q1 + hx) and
+// pos = py * M + px, where folded frequency m sits at digit position
+// R2 (m mod R1) + m / R1.
+template <int M, int P>
+__global__ void __launch_bounds__(kThreads)
+epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N, int Q1,
+                const int *__restrict__ chans, const long long *__restrict__ out_off,
+                const double *__restrict__ wpow, const int *__restrict__ autoint,
+                const float2 *__restrict__ gains, int A, int T, unsigned flags, float2 *__restrict__ out)
+{
+    constexpr int R1 = Digits<M>::R1, R2 = Digits<M>::R2;
+    constexpr int NPF = P == 2 ? 4 : 1;
+    constexpr int NP = P == 2 ? 4 : 1;
+    const int ci = blockIdx.y;
+    const int c = chans[ci];
+    const bool autosub = !(flags & EPIC_NO_AUTOSUB);
+
+    // A_pq(c) in FP64, reduced in a fixed order (deterministic)
+    __shared__ double red[kThreads][6];
+    __shared__ double apq[6];   // XX, YY, Re XY, Im XY (YX = conj XY)
+    if (autosub) {
+        double s[6] = {0, 0, 0, 0, 0, 0};
+        for (int a = threadIdx.x; a < A; a += kThreads) {
+            const int *ia = autoint + (static_cast<size_t>(c) * A + a) * 4;
+            double gxr = 1, gxi = 0, gyr = 1, gyi = 0;
+            if (gains) {
+                const float2 gx = gains[(static_cast<size_t>(c) * A + a) * P];
+                gxr = gx.x;
+                gxi = gx.y;
+                if (P == 2) {
+                    const float2 gy = gains[(static_cast<size_t>(c) * A + a) * P + 1];
+                    gyr = gy.x;
+                    gyi = gy.y;
+                }
+            }
+            s[0] += (gxr * gxr + gxi * gxi) * static_cast<double>(ia[0]);
+            if (P == 2) {
+                s[1] += (gyr * gyr + gyi * gyi) * static_cast<double>(ia[1]);
+                // g_x g_y^* (I_re + i I_im)
+                const double pr = gxr * gyr + gxi * gyi, pi = gxi * gyr - gxr * gyi;
+                s[2] += pr * ia[2] - pi * ia[3];
+                s[3] += pr * ia[3] + pi * ia[2];
+            }
+        }
+        for (int k = 0; k < 4; k++) red[threadIdx.x][k] = s[k];
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            double tot = 0;
+            for (int i = 0; i < kThreads; i++) tot += red[i][threadIdx.x];
+            apq[threadIdx.x] = tot;
+        }
+        __syncthreads();
+    }
+
+    const double scale = ((flags & EPIC_MEAN) && T > 0) ? 1.0 / T : 1.0;
+    const int NN = N * N;
+    const int Q = Q1 * Q1;
+    float2 *oc = out + out_off[ci];
+    for (int pix = blockIdx.x * kThreads + threadIdx.x; pix < NN; pix += gridDim.x * kThreads) {
+        const int i = pix / N, j = pix % N;
+        const int ly = (i + N / 2) % N, lx = (j + N / 2) % N;   // (i - N/2) mod N
+        const int hx = lx % Q1, mx = lx / Q1, hy = ly % Q1, my = ly / Q1;
+        const int item = ci * Q + hy * Q1 + hx;
+        const int px = R2 * (mx % R1) + mx / R1, py = R2 * (my % R1) + my / R1;
+        const size_t pos = static_cast<size_t>(py) * M + px;
+        double s[4] = {0, 0, 0, 0};
+        for (int tau = 0; tau < n_tau; tau++) {
+            const float *src = partial + ((static_cast<size_t>(tau) * n_items + item) * (M * M) + pos) * NPF;
+            if constexpr (P == 2) {
+                const float4 f = *reinterpret_cast<const float4 *>(src);
+                s[0] += f.x;
+                s[1] += f.y;
+                s[2] += f.z;
+                s[3] += f.w;
+            } else {
+                s[0] += src[0];
+            }
+        }
+        if (autosub) {
+            const double w = wpow[pix];
+            s[0] -= apq[0] * w;
+            if (P == 2) {
+                s[1] -= apq[1] * w;
+                s[2] -= apq[2] * w;
+                s[3] -= apq[3] * w;
+            }
+        }
+        oc[pix] = make_float2(static_cast<float>(s[0] * scale), 0.f);
+        if constexpr (NP == 4) {
+            oc[NN + pix] = make_float2(static_cast<float>(s[1] * scale), 0.f);
+            oc[2 * NN + pix] = make_float2(static_cast<float>(s[2] * scale), static_cast<float>(s[3] * scale));
+            oc[3 * NN + pix] = make_float2(static_cast<float>(s[2] * scale), static_cast<float>(-s[3] * scale));
+        }
+    }
+}
+
+template <int M, int P>
+int launch_epi(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T, int n_tau, float2 *out,
+               cudaStream_t stream)
+{
+    const int NN = g.N * g.N;
+    const int tiles = (NN + kThreads * 4 - 1) / (kThreads * 4);
+    const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(g.n_chan));
+    epilogue_kernel<M, P><<<grid, kThreads, 0, stream>>>(g.d_partial, n_tau, g.n_items, g.N, g.Q1, g.d_chans,
+                                                         g.d_out_off, g.d_wpow, plan->d_autoint, gains, plan->A, T,
+                                                         plan->flags, out);
+    return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
+}  // namespace
+
+int launch_autopower(epic_plan_s *plan, const uint8_t *v, int T, cudaStream_t stream)
+{
+    const size_t n = static_cast<size_t>(plan->C) * plan->A * 4;
+    if (cudaMemsetAsync(plan->d_autoint, 0, n * sizeof(int), stream) != cudaSuccess) return EPIC_ERR_CUDA;
+    if (T == 0) return EPIC_OK;
+    int chunks = (4 * plan->sm_count + plan->C - 1) / plan->C;
+    if (chunks > T) chunks = T;
+    if (chunks < 1) chunks = 1;
+    const dim3 grid(static_cast<unsigned>(plan->C), static_cast<unsigned>(chunks));
+    autopower_kernel<<<grid, kThreads, 0, stream>>>(v, T, plan->C, plan->A, plan->P, chunks, plan->d_autoint);
+    return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
+int launch_epilogue(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T, int n_tau, float2 *out,
+                    cudaStream_t stream)
+{
+    if (plan->P == 2) {
+        switch (g.M) {
+        case 32: return launch_epi<32, 2>(plan, g, gains, T, n_tau, out, stream);
+        case 48: return launch_epi<48, 2>(plan, g, gains, T, n_tau, out, stream);
+        case 64: return launch_epi<64, 2>(plan, g, gains, T, n_tau, out, stream);
+        }
+    } else {
+        switch (g.M) {
+        case 32: return launch_epi<32, 1>(plan, g, gains, T, n_tau, out, stream);
+        case 48: return launch_epi<48, 1>(plan, g, gains, T, n_tau, out, stream);
+        case 64: return launch_epi<64, 1>(plan, g, gains, T, n_tau, out, stream);
+        }
+    }
+    return EPIC_ERR_UNSUPPORTED;
+}
+
+}  // namespace epic

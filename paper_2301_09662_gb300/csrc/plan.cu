@@ -1,0 +1,345 @@
+// Plan construction and the C entry points of libepic.
+//
+// epic_plan validates the geometry, maps antennas to grid cells (Sec. 3.1),
+// builds the kernel image |W^(l)|^2 used by the autocorrelation subtraction
+// (Sec. 2.2, Eq. 4), the FP32 twiddle tables, and the workspace.  Everything
+// here runs once per plan; the per-integration work is in the kernels.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+
+#include "epic_internal.cuh"
+
+using epic::GroupCfg;
+
+namespace {
+
+bool supported_n(int n) { return n == 32 || n == 64 || n == 96 || n == 128 || n == 256 || n == 512; }
+
+// Folding factor per grid side for the FP32 kernel (folded side M = N / Q1).
+int fold_for(int n)
+{
+    switch (n) {
+    case 32: return 1;    // M = 32
+    case 64: return 1;    // M = 64
+    case 96: return 2;    // M = 48
+    case 128: return 2;   // M = 64
+    case 256: return 4;   // M = 64
+    case 512: return 8;   // M = 64
+    default: return 0;
+    }
+}
+
+template <class T>
+int dev_upload(T **dst, const T *src, size_t n)
+{
+    *dst = nullptr;
+    if (n == 0) return EPIC_OK;
+    if (cudaMalloc(reinterpret_cast<void **>(dst), n * sizeof(T)) != cudaSuccess) {
+        *dst = nullptr;
+        return EPIC_ERR_NOMEM;
+    }
+    if (src && cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return EPIC_ERR_CUDA;
+    return EPIC_OK;
+}
+
+void free_plan(epic_plan_s *p)
+{
+    if (!p) return;
+    for (auto e : p->events) cudaEventDestroy(e);
+    cudaFree(p->d_cells);
+    cudaFree(p->d_kernel);
+    cudaFree(p->d_autoint);
+    cudaFree(p->d_status);
+    cudaFree(p->d_stage_v);
+    cudaFree(p->d_stage_g);
+    cudaFree(p->d_stage_out);
+    for (auto &g : p->groups) {
+        cudaFree(g.d_chans);
+        cudaFree(g.d_out_off);
+        cudaFree(g.d_wpow);
+        cudaFree(g.d_twN);
+        cudaFree(g.d_partial);
+    }
+    delete p;
+}
+
+// |W^(l)|^2, W^(l) = sum_d W(d) exp(+2 pi i d.l / N), on the shifted layout
+// out[i][j] with l = (j - N/2, i - N/2).  FP64, separable phase tables.
+void kernel_power(const float *kern, int K, int N, std::vector<double> &out)
+{
+    const int h = (K - 1) / 2;
+    std::vector<std::complex<double>> ph(static_cast<size_t>(K) * N);  // [d + h][l index]
+    for (int d = -h; d <= h; d++)
+        for (int i = 0; i < N; i++) {
+            const int l = i - N / 2;
+            const long e = (((long)d * l) % N + N) % N;
+            const double ang = 2.0 * M_PI * static_cast<double>(e) / N;
+            ph[static_cast<size_t>(d + h) * N + i] = {std::cos(ang), std::sin(ang)};
+        }
+    out.assign(static_cast<size_t>(N) * N, 0.0);
+    std::vector<std::complex<double>> rowsum(static_cast<size_t>(K) * N);  // [dy][j]
+    for (int dy = 0; dy < K; dy++)
+        for (int j = 0; j < N; j++) {
+            std::complex<double> s = 0;
+            for (int dx = 0; dx < K; dx++) {
+                std::complex<double> w(kern[2 * (dy * K + dx)], kern[2 * (dy * K + dx) + 1]);
+                s += w * ph[static_cast<size_t>(dx) * N + j];
+            }
+            rowsum[static_cast<size_t>(dy) * N + j] = s;
+        }
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            std::complex<double> s = 0;
+            for (int dy = 0; dy < K; dy++) s += rowsum[static_cast<size_t>(dy) * N + j] * ph[static_cast<size_t>(dy) * N + i];
+            out[static_cast<size_t>(i) * N + j] = std::norm(s);
+        }
+}
+
+}  // namespace
+
+namespace epic {
+
+void prof_begin(epic_plan_s *plan)
+{
+    if (plan->profiling) plan->n_recorded = 0;
+}
+
+void prof_mark(epic_plan_s *plan, cudaStream_t stream, int stage, bool start)
+{
+    if (!plan->profiling) return;
+    while (static_cast<int>(plan->events.size()) < 2 * (stage + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            plan->profiling = false;
+            return;
+        }
+        plan->events.push_back(e);
+    }
+    cudaEventRecord(plan->events[2 * stage + (start ? 0 : 1)], stream);
+    if (!start && stage + 1 > plan->n_recorded) plan->n_recorded = stage + 1;
+}
+
+}  // namespace epic
+
+extern "C" {
+
+const char *epic_strerror(int code)
+{
+    switch (code) {
+    case EPIC_OK: return "ok";
+    case EPIC_ERR_ARG: return "invalid argument";
+    case EPIC_ERR_OUT_OF_GRID: return "antenna footprint outside the grid";
+    case EPIC_ERR_UNSUPPORTED: return "unsupported configuration";
+    case EPIC_ERR_CUDA: return "CUDA runtime error";
+    case EPIC_ERR_TIMEOUT: return "device-side wait timed out";
+    case EPIC_ERR_NOMEM: return "out of memory";
+    case EPIC_ERR_DEVICE: return "device-side consistency check failed";
+    default: return "unknown error";
+    }
+}
+
+int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
+              const float *kernel_c64, int K, const int *grid_n, const double *freq_hz,
+              int n_chan, double du, int max_spectra, int precision, unsigned flags)
+{
+    if (!out) return EPIC_ERR_ARG;
+    *out = nullptr;
+    if (!ant_xy_m || !kernel_c64 || !grid_n || !freq_hz) return EPIC_ERR_ARG;
+    if (n_ant < 1 || (n_pol != 1 && n_pol != 2) || K < 1 || (K % 2) == 0 || K > epic::kMaxK ||
+        n_chan < 1 || !(du > 0.0) || du > 0.5 || max_spectra < 0)
+        return EPIC_ERR_ARG;
+    if (flags & ~(EPIC_MEAN | EPIC_NO_AUTOSUB)) return EPIC_ERR_ARG;
+    if (precision < EPIC_FP32 || precision > EPIC_TC_SPLIT_BF16) return EPIC_ERR_ARG;
+    if (precision != EPIC_FP32) return EPIC_ERR_UNSUPPORTED;
+    if (static_cast<long long>(n_ant) * n_pol > epic::kMaxAP) return EPIC_ERR_UNSUPPORTED;
+    for (int c = 0; c < n_chan; c++) {
+        if (!(freq_hz[c] > 0.0) || !std::isfinite(freq_hz[c])) return EPIC_ERR_ARG;
+        if (!supported_n(grid_n[c])) return EPIC_ERR_UNSUPPORTED;
+    }
+    for (int a = 0; a < n_ant; a++)
+        if (!std::isfinite(ant_xy_m[2 * a]) || !std::isfinite(ant_xy_m[2 * a + 1])) return EPIC_ERR_ARG;
+
+    // antenna -> cell map: per channel, per axis, llround((x - x_c) f / (c0 du)) + N/2
+    double sx = 0, sy = 0;
+    for (int a = 0; a < n_ant; a++) { sx += ant_xy_m[2 * a]; sy += ant_xy_m[2 * a + 1]; }
+    const double cx = sx / n_ant, cy = sy / n_ant;
+    const int h = (K - 1) / 2;
+    std::vector<short2> cells(static_cast<size_t>(n_chan) * n_ant);
+    for (int c = 0; c < n_chan; c++) {
+        const int N = grid_n[c];
+        for (int a = 0; a < n_ant; a++) {
+            const double x = ant_xy_m[2 * a] - cx, y = ant_xy_m[2 * a + 1] - cy;
+            const double fx = (x * freq_hz[c]) / (epic::kC0 * du);
+            const double fy = (y * freq_hz[c]) / (epic::kC0 * du);
+            if (std::fabs(fx) > 1e6 || std::fabs(fy) > 1e6) return EPIC_ERR_OUT_OF_GRID;
+            const long long kx = std::llround(fx) + N / 2;
+            const long long ky = std::llround(fy) + N / 2;
+            if (kx - h < 0 || kx + h >= N || ky - h < 0 || ky + h >= N) return EPIC_ERR_OUT_OF_GRID;
+            cells[static_cast<size_t>(c) * n_ant + a] = make_short2(static_cast<short>(kx), static_cast<short>(ky));
+        }
+    }
+
+    auto *p = new (std::nothrow) epic_plan_s();
+    if (!p) return EPIC_ERR_NOMEM;
+    if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return EPIC_ERR_CUDA; }
+    if (cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+        delete p;
+        return EPIC_ERR_CUDA;
+    }
+    p->A = n_ant;
+    p->P = n_pol;
+    p->NP = n_pol == 2 ? 4 : 1;
+    p->C = n_chan;
+    p->K = K;
+    p->max_spectra = max_spectra;
+    p->precision = precision;
+    p->flags = flags;
+    p->grid_n.assign(grid_n, grid_n + n_chan);
+    p->out_off.resize(n_chan);
+    long long off = 0;
+    for (int c = 0; c < n_chan; c++) {
+        p->out_off[c] = off;
+        off += static_cast<long long>(p->NP) * grid_n[c] * grid_n[c];
+    }
+    p->out_floats = static_cast<size_t>(off) * 2;
+
+    int rc = dev_upload(&p->d_cells, cells.data(), cells.size());
+    if (rc == EPIC_OK) rc = dev_upload(&p->d_kernel, reinterpret_cast<const float2 *>(kernel_c64), static_cast<size_t>(K) * K);
+    if (rc == EPIC_OK) rc = dev_upload(&p->d_autoint, static_cast<const int *>(nullptr), static_cast<size_t>(n_chan) * n_ant * 4);
+    if (rc == EPIC_OK) rc = dev_upload(&p->d_status, static_cast<const int *>(nullptr), 1);
+    if (rc == EPIC_OK && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) rc = EPIC_ERR_CUDA;
+
+    // channel groups by grid side
+    std::map<int, std::vector<int>> by_n;
+    for (int c = 0; c < n_chan; c++) by_n[grid_n[c]].push_back(c);
+    const int npf = n_pol == 2 ? 4 : 1;
+    for (auto &kv : by_n) {
+        if (rc != EPIC_OK) break;
+        GroupCfg g;
+        g.N = kv.first;
+        g.Q1 = fold_for(g.N);
+        g.M = g.N / g.Q1;
+        g.Q = g.Q1 * g.Q1;
+        g.chans = kv.second;
+        g.n_chan = static_cast<int>(g.chans.size());
+        g.n_items = g.n_chan * g.Q;
+        std::vector<long long> offs(g.n_chan);
+        for (int i = 0; i < g.n_chan; i++) offs[i] = p->out_off[g.chans[i]];
+        std::vector<double> wpow;
+        kernel_power(kernel_c64, K, g.N, wpow);
+        std::vector<float2> tw(g.N);
+        for (int k = 0; k < g.N; k++) {
+            const double ang = 2.0 * M_PI * k / g.N;
+            tw[k] = make_float2(static_cast<float>(std::cos(ang)), static_cast<float>(std::sin(ang)));
+        }
+        rc = dev_upload(&g.d_chans, g.chans.data(), g.chans.size());
+        if (rc == EPIC_OK) rc = dev_upload(&g.d_out_off, offs.data(), offs.size());
+        if (rc == EPIC_OK) rc = dev_upload(&g.d_wpow, wpow.data(), wpow.size());
+        if (rc == EPIC_OK) rc = dev_upload(&g.d_twN, tw.data(), tw.size());
+        if (rc == EPIC_OK)
+            rc = dev_upload(&g.d_partial, static_cast<const float *>(nullptr),
+                            static_cast<size_t>(epic::kMaxTau) * g.n_items * g.M * g.M * npf);
+        p->groups.push_back(g);
+    }
+    if (rc != EPIC_OK) {
+        free_plan(p);
+        return rc;
+    }
+    *out = p;
+    return EPIC_OK;
+}
+
+size_t epic_out_floats(epic_plan_t plan) { return plan ? plan->out_floats : 0; }
+
+int epic_image(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra,
+               float *out, void *stream)
+{
+    if (!plan || !out) return EPIC_ERR_ARG;
+    if (n_spectra < 0 || n_spectra > plan->max_spectra) return EPIC_ERR_ARG;
+    if (n_spectra > 0 && !ci4) return EPIC_ERR_ARG;
+    auto s = static_cast<cudaStream_t>(stream);
+    return epic::image_fp32(plan, ci4, reinterpret_cast<const float2 *>(gains), n_spectra,
+                            reinterpret_cast<float2 *>(out), s);
+}
+
+int epic_image_host(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra,
+                    float *out, void *stream)
+{
+    if (!plan || !out) return EPIC_ERR_ARG;
+    if (n_spectra < 0 || n_spectra > plan->max_spectra) return EPIC_ERR_ARG;
+    if (n_spectra > 0 && !ci4) return EPIC_ERR_ARG;
+    auto s = static_cast<cudaStream_t>(stream);
+    const size_t vbytes = static_cast<size_t>(plan->max_spectra) * plan->C * plan->A * plan->P;
+    const size_t gfloats = static_cast<size_t>(plan->C) * plan->A * plan->P * 2;
+    if (!plan->d_stage_out) {
+        if (cudaMalloc(&plan->d_stage_v, vbytes ? vbytes : 16) != cudaSuccess ||
+            cudaMalloc(&plan->d_stage_g, gfloats * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&plan->d_stage_out, plan->out_floats * sizeof(float)) != cudaSuccess) {
+            cudaFree(plan->d_stage_v);
+            cudaFree(plan->d_stage_g);
+            cudaFree(plan->d_stage_out);
+            plan->d_stage_v = nullptr;
+            plan->d_stage_g = nullptr;
+            plan->d_stage_out = nullptr;
+            return EPIC_ERR_NOMEM;
+        }
+    }
+    const size_t nbytes = static_cast<size_t>(n_spectra) * plan->C * plan->A * plan->P;
+    if (nbytes && cudaMemcpyAsync(plan->d_stage_v, ci4, nbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return EPIC_ERR_CUDA;
+    if (gains && cudaMemcpyAsync(plan->d_stage_g, gains, gfloats * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return EPIC_ERR_CUDA;
+    int rc = epic::image_fp32(plan, plan->d_stage_v, gains ? reinterpret_cast<const float2 *>(plan->d_stage_g) : nullptr,
+                              n_spectra, reinterpret_cast<float2 *>(plan->d_stage_out), s);
+    if (rc != EPIC_OK) return rc;
+    if (cudaMemcpyAsync(out, plan->d_stage_out, plan->out_floats * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return EPIC_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return EPIC_ERR_CUDA;
+    return EPIC_OK;
+}
+
+int epic_status(epic_plan_t plan)
+{
+    if (!plan) return EPIC_ERR_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return EPIC_ERR_CUDA;
+    int st = 0;
+    if (cudaMemcpy(&st, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return EPIC_ERR_CUDA;
+    if (cudaMemset(plan->d_status, 0, sizeof(int)) != cudaSuccess) return EPIC_ERR_CUDA;
+    if (st & epic::kStatusTimeout) return EPIC_ERR_TIMEOUT;
+    if (st & epic::kStatusDevice) return EPIC_ERR_DEVICE;
+    return EPIC_OK;
+}
+
+int epic_set_profiling(epic_plan_t plan, int enable)
+{
+    if (!plan) return EPIC_ERR_ARG;
+    plan->profiling = enable != 0;
+    plan->n_recorded = 0;
+    return EPIC_OK;
+}
+
+int epic_stage_times(epic_plan_t plan, float *ms, int max_stages)
+{
+    if (!plan || !ms || max_stages < 0) return EPIC_ERR_ARG;
+    if (!plan->profiling || plan->n_recorded == 0) return EPIC_ERR_ARG;
+    const int n = plan->n_recorded < max_stages ? plan->n_recorded : max_stages;
+    if (cudaEventSynchronize(plan->events[2 * plan->n_recorded - 1]) != cudaSuccess) return EPIC_ERR_CUDA;
+    for (int i = 0; i < n; i++)
+        if (cudaEventElapsedTime(&ms[i], plan->events[2 * i], plan->events[2 * i + 1]) != cudaSuccess)
+            return EPIC_ERR_CUDA;
+    return n;
+}
+
+void epic_destroy(epic_plan_t plan)
+{
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    free_plan(plan);
+}
+
+}  // extern "C"

@@ -1,0 +1,231 @@
+"""Thin Python binding of libepic (include/epic.h) over ctypes.
+
+Argument marshalling only: every step of the imaging path runs in the CUDA
+library.  PyTorch provides device memory and the current stream.  If the
+library has not been built, every entry point raises (there is no CPU path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libepic.so")
+
+EPIC_OK = 0
+EPIC_ERR_ARG = -1
+EPIC_ERR_OUT_OF_GRID = -2
+EPIC_ERR_UNSUPPORTED = -3
+EPIC_ERR_CUDA = -4
+EPIC_ERR_TIMEOUT = -5
+EPIC_ERR_NOMEM = -6
+EPIC_ERR_DEVICE = -7
+
+EPIC_FP32 = 0
+EPIC_TC_SPLIT_FP16 = 1
+EPIC_TC_FP16 = 2
+EPIC_TC_SPLIT_BF16 = 3
+
+EPIC_MEAN = 1
+EPIC_NO_AUTOSUB = 2
+
+PRODUCTS = ("XX", "YY", "XY", "YX")
+
+#: every symbol include/epic.h declares
+EXPORTS = ("epic_plan", "epic_image", "epic_image_host", "epic_out_floats", "epic_status",
+           "epic_set_profiling", "epic_stage_times", "epic_destroy", "epic_strerror")
+
+_lib = None
+
+
+class EpicError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = load().epic_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+def load():
+    """Load libepic.so (built by build_lib.build()); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, u = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint
+    L.epic_plan.argtypes = [ctypes.POINTER(vp), vp, i, i, vp, i, vp, vp, i, ctypes.c_double, i, i, u]
+    L.epic_plan.restype = i
+    L.epic_image.argtypes = [vp, vp, vp, i, vp, vp]
+    L.epic_image.restype = i
+    L.epic_image_host.argtypes = [vp, vp, vp, i, vp, vp]
+    L.epic_image_host.restype = i
+    L.epic_out_floats.argtypes = [vp]
+    L.epic_out_floats.restype = ctypes.c_size_t
+    L.epic_status.argtypes = [vp]
+    L.epic_status.restype = i
+    L.epic_set_profiling.argtypes = [vp, i]
+    L.epic_set_profiling.restype = i
+    L.epic_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
+    L.epic_stage_times.restype = i
+    L.epic_destroy.argtypes = [vp]
+    L.epic_destroy.restype = None
+    L.epic_strerror.argtypes = [i]
+    L.epic_strerror.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    return load().epic_strerror(code).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != EPIC_OK:
+        raise EpicError(rc, what)
+
+
+class Plan:
+    """An imaging plan: array geometry, kernel, channel grid sides (epic_plan)."""
+
+    def __init__(self, ant_xy, n_pol, kernel, grid_n, freq_hz, du=0.5, max_spectra=1000,
+                 precision=EPIC_FP32, flags=0):
+        L = load()
+        self._ant = np.ascontiguousarray(ant_xy, np.float64)
+        self._kern = np.ascontiguousarray(kernel, np.complex64)
+        self.grid_n = np.ascontiguousarray(grid_n, np.int32)
+        self._freq = np.ascontiguousarray(freq_hz, np.float64)
+        if self._ant.ndim != 2 or self._ant.shape[1] != 2:
+            raise ValueError("ant_xy must be [A][2]")
+        if self._kern.ndim != 2 or self._kern.shape[0] != self._kern.shape[1]:
+            raise ValueError("kernel must be [K][K]")
+        if self.grid_n.shape != self._freq.shape:
+            raise ValueError("grid_n and freq_hz must have one entry per channel")
+        self.A = self._ant.shape[0]
+        self.P = int(n_pol)
+        self.NP = 4 if self.P == 2 else 1
+        self.C = len(self._freq)
+        self.K = self._kern.shape[0]
+        self.max_spectra = int(max_spectra)
+        self.precision = int(precision)
+        self.flags = int(flags)
+        h = ctypes.c_void_p()
+        rc = L.epic_plan(ctypes.byref(h), self._ant.ctypes.data, self.A, self.P, self._kern.ctypes.data,
+                         self.K, self.grid_n.ctypes.data, self._freq.ctypes.data, self.C, float(du),
+                         self.max_spectra, self.precision, self.flags)
+        _check(rc, "epic_plan")
+        self._h = h
+        self.out_floats = int(L.epic_out_floats(h))
+
+    @classmethod
+    def from_workload(cls, wl, **kw):
+        kw.setdefault("max_spectra", wl.T)
+        return cls(wl.ant_xy, wl.n_pol, wl.kernel, wl.grid_n, wl.freq_hz, wl.du, **kw)
+
+    @property
+    def handle(self):
+        return self._h.value
+
+    def _stream(self, stream):
+        import torch
+        if stream is None:
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+    def _check_inputs(self, v, gains, device: bool):
+        import torch
+        if not isinstance(v, torch.Tensor) or v.dtype != torch.uint8:
+            raise TypeError("v must be a torch.uint8 tensor [T][C][A][P]")
+        if v.dim() != 4 or tuple(v.shape[1:]) != (self.C, self.A, self.P):
+            raise ValueError(f"v must be [T][{self.C}][{self.A}][{self.P}], got {tuple(v.shape)}")
+        if not v.is_contiguous():
+            raise ValueError("v must be contiguous")
+        if v.is_cuda != device:
+            raise ValueError("v is on the wrong device for this call")
+        if gains is not None:
+            if gains.dtype != torch.complex64 or tuple(gains.shape) != (self.C, self.A, self.P):
+                raise ValueError(f"gains must be complex64 [{self.C}][{self.A}][{self.P}]")
+            if not gains.is_contiguous() or gains.is_cuda != device:
+                raise ValueError("gains must be contiguous and on the same device as v")
+
+    def image(self, v, gains=None, out=None, stream=None):
+        """Image one integration of device-resident voltages; returns (or fills)
+        a flat complex64 device tensor of epic_out_floats/2 elements."""
+        import torch
+        self._check_inputs(v, gains, device=True)
+        if out is None:
+            out = torch.empty(self.out_floats // 2, dtype=torch.complex64, device=v.device)
+        elif out.dtype != torch.complex64 or out.numel() * 2 != self.out_floats or not out.is_contiguous():
+            raise ValueError("out must be a contiguous complex64 tensor of the plan's output size")
+        rc = load().epic_image(self._h, v.data_ptr(), gains.data_ptr() if gains is not None else None,
+                               int(v.shape[0]), out.data_ptr(), self._stream(stream))
+        _check(rc, "epic_image")
+        return out
+
+    def image_host(self, v, gains=None, out=None, stream=None):
+        """Host-buffer variant (epic_image_host): copies in, images, copies out."""
+        import torch
+        self._check_inputs(v, gains, device=False)
+        if out is None:
+            out = torch.empty(self.out_floats // 2, dtype=torch.complex64)
+        rc = load().epic_image_host(self._h, v.data_ptr(), gains.data_ptr() if gains is not None else None,
+                                    int(v.shape[0]), out.data_ptr(), self._stream(stream))
+        _check(rc, "epic_image_host")
+        return out
+
+    def split(self, flat):
+        """Per-channel [NP][N][N] views of a packed output."""
+        res, off = [], 0
+        for N in self.grid_n:
+            sz = self.NP * int(N) * int(N)
+            res.append(flat[off:off + sz].reshape(self.NP, int(N), int(N)))
+            off += sz
+        return res
+
+    def stage_names(self):
+        names = [] if self.flags & EPIC_NO_AUTOSUB else ["autopower"]
+        for N in sorted(set(int(n) for n in self.grid_n)):
+            names += [f"image[N={N}]", f"epilogue[N={N}]"]
+        return names
+
+    def set_profiling(self, on: bool = True):
+        _check(load().epic_set_profiling(self._h, int(bool(on))), "epic_set_profiling")
+
+    def stage_times(self):
+        """{stage name: device ms} of the last epic_image call (profiling on)."""
+        names = self.stage_names()
+        buf = (ctypes.c_float * len(names))()
+        n = load().epic_stage_times(self._h, buf, len(names))
+        if n < 0:
+            _check(n, "epic_stage_times")
+        return {names[i]: float(buf[i]) for i in range(n)}
+
+    def status(self) -> int:
+        return load().epic_status(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().epic_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_plan_raw(ant_xy, n_pol, kernel, grid_n, freq_hz, du=0.5, max_spectra=16, precision=EPIC_FP32,
+                  flags=0):
+    """Call epic_plan and return (rc, handle) without raising (for error-path tests)."""
+    L = load()
+    ant = np.ascontiguousarray(ant_xy, np.float64)
+    kern = np.ascontiguousarray(kernel, np.complex64)
+    gn = np.ascontiguousarray(grid_n, np.int32)
+    fr = np.ascontiguousarray(freq_hz, np.float64)
+    h = ctypes.c_void_p()
+    rc = L.epic_plan(ctypes.byref(h), ant.ctypes.data, ant.shape[0], int(n_pol), kern.ctypes.data, kern.shape[0],
+                     gn.ctypes.data, fr.ctypes.data, len(fr), float(du), int(max_spectra), int(precision), int(flags))
+    return rc, h

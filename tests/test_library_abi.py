@@ -1,0 +1,83 @@
+"""CPU-side checks of the C ABI: the library loads, exports every symbol that
+include/epic.h declares, and rejects bad plans on the host before any CUDA
+call.  No compute runs here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2301_09662_gb300 import build_lib, epic, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return epic.load()
+
+
+def header_symbols():
+    src = open(os.path.join(ROOT, "include", "epic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(epic_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_exports():
+    assert header_symbols() == sorted(epic.EXPORTS)
+
+
+def test_library_exports_every_header_symbol(lib):
+    for name in header_symbols():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_strerror_texts(lib):
+    for code in range(0, -8, -1):
+        assert epic.strerror(code) not in ("", "unknown error")
+    assert epic.strerror(-99) == "unknown error"
+
+
+def _geom(**kw):
+    wl = synth.random_small(A=8, P=2, C=2, T=4, N=32, K=3, seed=1)
+    args = dict(ant_xy=wl.ant_xy, n_pol=2, kernel=wl.kernel, grid_n=wl.grid_n, freq_hz=wl.freq_hz, du=0.5,
+                max_spectra=4, precision=epic.EPIC_FP32, flags=0)
+    args.update(kw)
+    return args
+
+
+@pytest.mark.parametrize("bad,code", [
+    (dict(n_pol=3), epic.EPIC_ERR_ARG),
+    (dict(kernel=np.ones((2, 2), np.complex64)), epic.EPIC_ERR_ARG),
+    (dict(du=0.0), epic.EPIC_ERR_ARG),
+    (dict(du=0.75), epic.EPIC_ERR_ARG),
+    (dict(max_spectra=-1), epic.EPIC_ERR_ARG),
+    (dict(flags=8), epic.EPIC_ERR_ARG),
+    (dict(precision=9), epic.EPIC_ERR_ARG),
+    (dict(grid_n=np.array([32, 40], np.int32)), epic.EPIC_ERR_UNSUPPORTED),
+    (dict(freq_hz=np.array([50e6, -1.0])), epic.EPIC_ERR_ARG),
+])
+def test_plan_rejects_bad_arguments_on_host(lib, bad, code):
+    rc, h = epic.make_plan_raw(**_geom(**bad))
+    assert rc == code and not h.value
+
+
+def test_plan_rejects_footprint_outside_grid(lib):
+    # 60 m baselines at 80 MHz are ~32 cells at lambda/2: too wide for N = 32
+    ant = np.array([[-60.0, 0.0], [60.0, 0.0], [0.0, 5.0]])
+    rc, h = epic.make_plan_raw(**_geom(ant_xy=ant, grid_n=np.array([32], np.int32),
+                                       freq_hz=np.array([80e6])))
+    assert rc == epic.EPIC_ERR_OUT_OF_GRID and not h.value
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.epic_image(None, None, None, 0, None, None) == epic.EPIC_ERR_ARG
+    assert lib.epic_image_host(None, None, None, 0, None, None) == epic.EPIC_ERR_ARG
+    assert lib.epic_status(None) == epic.EPIC_ERR_ARG
+    assert lib.epic_out_floats(None) == 0
+    lib.epic_destroy(None)
+    h = ctypes.c_void_p()
+    assert lib.epic_plan(ctypes.byref(h), None, 1, 1, None, 1, None, None, 1, 0.5, 1, 0, 0) == epic.EPIC_ERR_ARG
