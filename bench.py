@@ -52,13 +52,17 @@ def parse():
     ap.add_argument("--workload", choices=["lwa", "tiny", "uneven", "dense"], default="lwa")
     ap.add_argument("--precision", choices=["fp32"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
+    ap.add_argument("--channels", type=int, default=None,
+                    help="shrink the workload to this many channels (profiling captures only)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     return ap.parse_args()
 
 
-def make_workload(name):
+def make_workload(name, channels=None):
     from paper_2301_09662_gb300 import synth
-    return {"lwa": synth.lwa, "tiny": synth.tiny, "uneven": synth.uneven, "dense": synth.dense}[name]()
+    fn = {"lwa": synth.lwa, "tiny": synth.tiny, "uneven": synth.uneven, "dense": synth.dense}[name]
+    return fn() if channels is None else fn(C=channels)
 
 
 def describe(wl, name):
@@ -194,7 +198,7 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.channels)
     threads = oracle.threads()
     C_s = max(1, min(wl.C, threads))
     chans = list(range(C_s))
@@ -226,6 +230,31 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_e2e(plan, wl, args, world, barrier, spectra):
+    """Same metric through epic_image_host: every step copies the pinned host
+    voltages and gains in and the image out, inside the timed region."""
+    import torch
+    import torch.distributed as dist
+    vh = torch.from_numpy(wl.v).pin_memory()
+    gh = None if wl.gains is None else torch.from_numpy(wl.gains).pin_memory()
+    oh = torch.empty(plan.out_floats // 2, dtype=torch.complex64).pin_memory()
+    for _ in range(2):
+        plan.image_host(vh, gh, out=oh)
+    times = []
+    barrier()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        plan.image_host(vh, gh, out=oh)
+        times.append(time.perf_counter() - t0)
+    barrier()
+    te = torch.tensor([sum(times) / len(times)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    return {"value": world * spectra / float(te.item()), "unit": UNIT,
+            "h2d_bytes_per_step": vh.numel() + (gh.numel() * 8 if gh is not None else 0),
+            "d2h_bytes_per_step": oh.numel() * 8}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -244,7 +273,7 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.channels)
     plan = epic.Plan.from_workload(wl)
     v = torch.from_numpy(wl.v).cuda()
     g = None if wl.gains is None else torch.from_numpy(wl.gains).cuda()
@@ -291,25 +320,10 @@ def run_ours(args):
 
     # end to end through the host-buffer entry point: pinned inputs copied in,
     # image copied out, every step
-    vh = torch.from_numpy(wl.v).pin_memory()
-    gh = None if wl.gains is None else torch.from_numpy(wl.gains).pin_memory()
-    oh = torch.empty(plan.out_floats // 2, dtype=torch.complex64).pin_memory()
-    for _ in range(2):
-        plan.image_host(vh, gh, out=oh)
-    e2e_times = []
-    barrier()
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        plan.image_host(vh, gh, out=oh)
-        e2e_times.append(time.perf_counter() - t0)
-    barrier()
-    e2e_step = sum(e2e_times) / len(e2e_times)
-    te = torch.tensor([e2e_step], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * spectra / float(te.item())
-    h2d = vh.numel() + (gh.numel() * 8 if gh is not None else 0)
-    d2h = oh.numel() * 8
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(plan, wl, args, world, barrier, spectra)
+
 
     # roofline of the dominant kernel (the fused imaging kernel)
     peaks = measured_peaks()
@@ -337,7 +351,7 @@ def run_ours(args):
                                     f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS)",
                      "flops_per_launch": flops, "ms_per_launch": img_ms},
         "stages_ms": {n: s / args.steps for n, s in stage_sum.items()},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": launches,
     }
