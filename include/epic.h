@@ -63,7 +63,8 @@ enum {
     EPIC_ERR_CUDA = -4,         /* a CUDA runtime call failed */
     EPIC_ERR_TIMEOUT = -5,      /* a bounded device-side wait ran out */
     EPIC_ERR_NOMEM = -6,        /* device or host allocation failed */
-    EPIC_ERR_DEVICE = -7        /* a device-side index/consistency check failed */
+    EPIC_ERR_DEVICE = -7,       /* a device-side index/consistency check failed */
+    EPIC_ERR_TOO_LARGE = -8     /* request does not fit epic_image_static's fixed scratch */
 };
 
 /* Arithmetic form of the gridding + transform + products stages. */
@@ -173,6 +174,39 @@ void epic_destroy(epic_plan_t plan);
  */
 int epic_set_profiling(epic_plan_t plan, int enable);
 int epic_stage_times(epic_plan_t plan, float *ms, int max_stages);
+
+/*
+ * epic_image_static -- one integration in the FP32 form with no device
+ * allocation: no plan, no cudaMalloc/cudaFree, no allocating library call.
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot allocate device memory themselves or through the library -- a
+ * pipeline whose GPU memory is all reserved by its own pool allocator, a
+ * real-time capture loop that must not let cudaMalloc/cudaFree synchronise the
+ * device under it, a plug-in that may leave no allocations behind.
+ *
+ * The caller passes the geometry (as for epic_plan, but one grid side
+ * grid_n in {32, 64, 96, 128} for every channel), the device inputs (as for
+ * epic_image) and the device output (complex64 [n_chan][NP][grid_n][grid_n]).
+ * Tables and workspace live in one 32 MiB array in device global memory that
+ * the library declares at file scope; every GPU that loads libepic holds it
+ * until the process exits.  Requests whose tables, auto-power sums and one set
+ * of partial images do not fit it return EPIC_ERR_TOO_LARGE before any work
+ * is queued (e.g. 64 channels of 128 x 128 dual polarisation fit; 128 do not).
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the array and overwrites what the previous call
+ * left in it (what must start at zero is cleared on the call's stream), so
+ * calls whose GPU work overlaps -- different streams, different host threads
+ * -- race; order them.  The geometry tables are copied from pageable host
+ * memory on the stream, so the call may block the host briefly.  Asynchronous
+ * otherwise.  Other errors are those of epic_plan and epic_image.
+ */
+int epic_image_static(const double *ant_xy_m, int n_ant, int n_pol,
+                      const float *kernel_c64, int K, int grid_n,
+                      const double *freq_hz, int n_chan, double du_wavelengths,
+                      const uint8_t *ci4, const float *gains_c64, int n_spectra,
+                      unsigned flags, float *out_c64, void *cuda_stream);
 
 /* Static, human-readable text for an EPIC_* code. */
 const char *epic_strerror(int code);

@@ -77,6 +77,31 @@ int launch_autopower(epic_plan_s *plan, const uint8_t *v, int T, cudaStream_t st
 int launch_epilogue(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T, int n_tau,
                     float2 *out, cudaStream_t stream);
 
+// One single-grid-side FP32 imaging job on caller-provided device tables and
+// workspace (used by the static-scratch entry point).
+struct RawImage {
+    int A = 0, P = 0, C = 0, K = 0, N = 0, M = 0, Q1 = 1, n_items = 0, n_tau = 1, T = 0;
+    unsigned flags = 0;
+    const short2 *cells = nullptr;     // [C][A]
+    const float2 *kernel = nullptr;    // [K*K]
+    const int *chans = nullptr;        // [C] identity channel list
+    const long long *out_off = nullptr;  // [C]
+    const double *wpow = nullptr;      // [N][N]
+    const float2 *twN = nullptr;       // [N]
+    float *partial = nullptr;          // [n_tau][n_items][M*M][NPF]
+    int *autoint = nullptr;            // [C][A][4]
+    int *status = nullptr;
+};
+int fp32_pick_tau(int n_items, int T, int sms);
+size_t fp32_smem_bytes(int M, int P, int A, int K);
+int launch_fp32_raw(const RawImage &r, const uint8_t *v, const float2 *gains, cudaStream_t stream);
+int launch_autopower_raw(const RawImage &r, const uint8_t *v, int sm_count, cudaStream_t stream);
+int launch_epilogue_raw(const RawImage &r, const float2 *gains, float2 *out, cudaStream_t stream);
+// host tables shared by the plan and the static-scratch entry point
+int host_cell_map(const double *ant_xy_m, int n_ant, const double *freq_hz, int n_chan, const int *grid_n,
+                  double du, int K, std::vector<short2> &cells);
+void host_kernel_power(const float *kern, int K, int N, std::vector<double> &out);
+
 // device status bits
 constexpr int kStatusDevice = 1;
 constexpr int kStatusTimeout = 2;

@@ -316,7 +316,48 @@ int launch_group(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
+template <int M, int P>
+int launch_raw(const RawImage &r, const uint8_t *v, const float2 *gains, cudaStream_t stream)
+{
+    auto kfn = fp32_image_kernel<M, P>;
+    const size_t smem = smem_bytes<M, P>(r.A, r.K);
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+        return EPIC_ERR_UNSUPPORTED;
+    const dim3 grid(static_cast<unsigned>(r.n_items * r.n_tau));
+    kfn<<<grid, kThreads, smem, stream>>>(v, gains, r.cells, r.kernel, r.K, r.chans, r.twN, r.A, r.C, r.T, r.N, r.Q1,
+                                          r.n_items, r.n_tau, r.partial, r.status);
+    return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
 }  // namespace
+
+int fp32_pick_tau(int n_items, int T, int sms) { return pick_tau(n_items, T, sms); }
+
+size_t fp32_smem_bytes(int M, int P, int A, int K)
+{
+    switch (M * 4 + P) {
+    case 32 * 4 + 1: return smem_bytes<32, 1>(A, K);
+    case 32 * 4 + 2: return smem_bytes<32, 2>(A, K);
+    case 48 * 4 + 1: return smem_bytes<48, 1>(A, K);
+    case 48 * 4 + 2: return smem_bytes<48, 2>(A, K);
+    case 64 * 4 + 1: return smem_bytes<64, 1>(A, K);
+    case 64 * 4 + 2: return smem_bytes<64, 2>(A, K);
+    default: return 0;
+    }
+}
+
+int launch_fp32_raw(const RawImage &r, const uint8_t *v, const float2 *gains, cudaStream_t stream)
+{
+    switch (r.M * 4 + r.P) {
+    case 32 * 4 + 1: return launch_raw<32, 1>(r, v, gains, stream);
+    case 32 * 4 + 2: return launch_raw<32, 2>(r, v, gains, stream);
+    case 48 * 4 + 1: return launch_raw<48, 1>(r, v, gains, stream);
+    case 48 * 4 + 2: return launch_raw<48, 2>(r, v, gains, stream);
+    case 64 * 4 + 1: return launch_raw<64, 1>(r, v, gains, stream);
+    case 64 * 4 + 2: return launch_raw<64, 2>(r, v, gains, stream);
+    default: return EPIC_ERR_UNSUPPORTED;
+    }
+}
 
 int image_fp32(epic_plan_s *plan, const uint8_t *v, const float2 *gains, int T, float2 *out, cudaStream_t stream)
 {

@@ -170,7 +170,43 @@ int launch_epi(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T,
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
+template <int M, int P>
+int launch_epi_raw(const RawImage &r, const float2 *gains, float2 *out, cudaStream_t stream)
+{
+    const int NN = r.N * r.N;
+    const int tiles = (NN + kThreads * 4 - 1) / (kThreads * 4);
+    const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(r.C));
+    epilogue_kernel<M, P><<<grid, kThreads, 0, stream>>>(r.partial, r.n_tau, r.n_items, r.N, r.Q1, r.chans,
+                                                         r.out_off, r.wpow, r.autoint, gains, r.A, r.T, r.flags,
+                                                         out);
+    return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
 }  // namespace
+
+int launch_autopower_raw(const RawImage &r, const uint8_t *v, int sm_count, cudaStream_t stream)
+{
+    if (r.T == 0) return EPIC_OK;
+    int chunks = (4 * sm_count + r.C - 1) / r.C;
+    if (chunks > r.T) chunks = r.T;
+    if (chunks < 1) chunks = 1;
+    const dim3 grid(static_cast<unsigned>(r.C), static_cast<unsigned>(chunks));
+    autopower_kernel<<<grid, kThreads, 0, stream>>>(v, r.T, r.C, r.A, r.P, chunks, r.autoint);
+    return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
+int launch_epilogue_raw(const RawImage &r, const float2 *gains, float2 *out, cudaStream_t stream)
+{
+    switch (r.M * 4 + r.P) {
+    case 32 * 4 + 1: return launch_epi_raw<32, 1>(r, gains, out, stream);
+    case 32 * 4 + 2: return launch_epi_raw<32, 2>(r, gains, out, stream);
+    case 48 * 4 + 1: return launch_epi_raw<48, 1>(r, gains, out, stream);
+    case 48 * 4 + 2: return launch_epi_raw<48, 2>(r, gains, out, stream);
+    case 64 * 4 + 1: return launch_epi_raw<64, 1>(r, gains, out, stream);
+    case 64 * 4 + 2: return launch_epi_raw<64, 2>(r, gains, out, stream);
+    default: return EPIC_ERR_UNSUPPORTED;
+    }
+}
 
 int launch_autopower(epic_plan_s *plan, const uint8_t *v, int T, cudaStream_t stream)
 {

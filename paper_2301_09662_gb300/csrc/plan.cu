@@ -104,6 +104,32 @@ void kernel_power(const float *kern, int K, int N, std::vector<double> &out)
 
 namespace epic {
 
+int host_cell_map(const double *ant_xy_m, int n_ant, const double *freq_hz, int n_chan, const int *grid_n,
+                  double du, int K, std::vector<short2> &cells)
+{
+    double sx = 0, sy = 0;
+    for (int a = 0; a < n_ant; a++) { sx += ant_xy_m[2 * a]; sy += ant_xy_m[2 * a + 1]; }
+    const double cx = sx / n_ant, cy = sy / n_ant;
+    const int h = (K - 1) / 2;
+    cells.assign(static_cast<size_t>(n_chan) * n_ant, make_short2(0, 0));
+    for (int c = 0; c < n_chan; c++) {
+        const int N = grid_n[c];
+        for (int a = 0; a < n_ant; a++) {
+            const double x = ant_xy_m[2 * a] - cx, y = ant_xy_m[2 * a + 1] - cy;
+            const double fx = (x * freq_hz[c]) / (kC0 * du);
+            const double fy = (y * freq_hz[c]) / (kC0 * du);
+            if (std::fabs(fx) > 1e6 || std::fabs(fy) > 1e6) return EPIC_ERR_OUT_OF_GRID;
+            const long long kx = std::llround(fx) + N / 2;
+            const long long ky = std::llround(fy) + N / 2;
+            if (kx - h < 0 || kx + h >= N || ky - h < 0 || ky + h >= N) return EPIC_ERR_OUT_OF_GRID;
+            cells[static_cast<size_t>(c) * n_ant + a] = make_short2(static_cast<short>(kx), static_cast<short>(ky));
+        }
+    }
+    return EPIC_OK;
+}
+
+void host_kernel_power(const float *kern, int K, int N, std::vector<double> &out) { kernel_power(kern, K, N, out); }
+
 void prof_begin(epic_plan_s *plan)
 {
     if (plan->profiling) plan->n_recorded = 0;
@@ -139,6 +165,7 @@ const char *epic_strerror(int code)
     case EPIC_ERR_TIMEOUT: return "device-side wait timed out";
     case EPIC_ERR_NOMEM: return "out of memory";
     case EPIC_ERR_DEVICE: return "device-side consistency check failed";
+    case EPIC_ERR_TOO_LARGE: return "request exceeds the fixed scratch of epic_image_static";
     default: return "unknown error";
     }
 }

@@ -22,6 +22,7 @@ EPIC_ERR_CUDA = -4
 EPIC_ERR_TIMEOUT = -5
 EPIC_ERR_NOMEM = -6
 EPIC_ERR_DEVICE = -7
+EPIC_ERR_TOO_LARGE = -8
 
 EPIC_FP32 = 0
 EPIC_TC_SPLIT_FP16 = 1
@@ -35,7 +36,7 @@ PRODUCTS = ("XX", "YY", "XY", "YX")
 
 #: every symbol include/epic.h declares
 EXPORTS = ("epic_plan", "epic_image", "epic_image_host", "epic_out_floats", "epic_status",
-           "epic_set_profiling", "epic_stage_times", "epic_destroy", "epic_strerror")
+           "epic_set_profiling", "epic_stage_times", "epic_image_static", "epic_destroy", "epic_strerror")
 
 _lib = None
 
@@ -70,6 +71,8 @@ def load():
     L.epic_set_profiling.restype = i
     L.epic_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
     L.epic_stage_times.restype = i
+    L.epic_image_static.argtypes = [vp, i, i, vp, i, i, vp, i, ctypes.c_double, vp, vp, i, u, vp, vp]
+    L.epic_image_static.restype = i
     L.epic_destroy.argtypes = [vp]
     L.epic_destroy.restype = None
     L.epic_strerror.argtypes = [i]
@@ -215,6 +218,34 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def image_static(ant_xy, n_pol, kernel, grid_n, freq_hz, du, v, gains=None, flags=0, out=None, stream=None):
+    """epic_image_static: plan-free imaging with no device allocation (one grid
+    side for all channels).  v, gains, out are device tensors as for Plan.image."""
+    import torch
+    L = load()
+    ant = np.ascontiguousarray(ant_xy, np.float64)
+    kern = np.ascontiguousarray(kernel, np.complex64)
+    fr = np.ascontiguousarray(freq_hz, np.float64)
+    C, A, P = len(fr), ant.shape[0], int(n_pol)
+    if v.dtype != torch.uint8 or not v.is_cuda or not v.is_contiguous() or tuple(v.shape[1:]) != (C, A, P):
+        raise ValueError(f"v must be a contiguous CUDA uint8 tensor [T][{C}][{A}][{P}]")
+    if gains is not None and (gains.dtype != torch.complex64 or not gains.is_cuda or not gains.is_contiguous()
+                              or tuple(gains.shape) != (C, A, P)):
+        raise ValueError(f"gains must be a contiguous CUDA complex64 tensor [{C}][{A}][{P}]")
+    NP = 4 if P == 2 else 1
+    n_out = C * NP * int(grid_n) * int(grid_n)
+    if out is None:
+        out = torch.empty(n_out, dtype=torch.complex64, device=v.device)
+    elif out.dtype != torch.complex64 or out.numel() != n_out or not out.is_contiguous():
+        raise ValueError("out must be a contiguous complex64 tensor of C*NP*N*N elements")
+    s = torch.cuda.current_stream() if stream is None else stream
+    rc = L.epic_image_static(ant.ctypes.data, A, P, kern.ctypes.data, kern.shape[0], int(grid_n), fr.ctypes.data,
+                             C, float(du), v.data_ptr(), gains.data_ptr() if gains is not None else None,
+                             int(v.shape[0]), int(flags), out.data_ptr(), ctypes.c_void_p(s.cuda_stream))
+    _check(rc, "epic_image_static")
+    return out
 
 
 def make_plan_raw(ant_xy, n_pol, kernel, grid_n, freq_hz, du=0.5, max_spectra=16, precision=EPIC_FP32,

@@ -36,7 +36,7 @@ def test_library_exports_every_header_symbol(lib):
 
 
 def test_strerror_texts(lib):
-    for code in range(0, -8, -1):
+    for code in range(0, -9, -1):
         assert epic.strerror(code) not in ("", "unknown error")
     assert epic.strerror(-99) == "unknown error"
 
