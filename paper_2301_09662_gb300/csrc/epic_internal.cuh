@@ -28,7 +28,16 @@ struct GroupCfg {
     double *d_wpow = nullptr;          // device: |W^(l)|^2 on the shifted [N][N] layout
     float2 *d_twN = nullptr;           // device: exp(+2 pi i k / N), k < N
     int n_items = 0;                   // n_chan * Q
-    float *d_partial = nullptr;        // device: [kMaxTau][n_items][M*M][NPF] partial sums
+    int tau_cap = 1;                   // time chunks the partial buffer holds
+    float *d_partial = nullptr;        // device: [tau_cap][n_items][M*M][NPF] partial sums
+    // partial-sum pixel order: folded frequency m sits at R2 (m mod R1) + m / R1
+    int R1 = 1, R2 = 1;
+    // M = 64 register-transform kernel: gridding schedule and samples per iteration
+    bool reg64 = false;
+    int ts = 1;
+    int rmax = 0;
+    uint32_t *d_sched = nullptr;       // device: [n_chan][8 warps][rmax][32] segment descriptors
+    int *d_nrounds = nullptr;          // device: [n_chan][8] rounds per warp
 };
 
 struct KernelTables {
@@ -76,6 +85,14 @@ int image_fp32(epic_plan_s *plan, const uint8_t *v, const float2 *gains, int T,
 int launch_autopower(epic_plan_s *plan, const uint8_t *v, int T, cudaStream_t stream);
 int launch_epilogue(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T, int n_tau,
                     float2 *out, cudaStream_t stream);
+
+// M = 64 register-transform kernel (fp32_reg64.cu)
+size_t reg64_smem_bytes(int P, int TS, int A, int K);
+int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
+                 cudaStream_t stream);
+// Gridding schedule of the M = 64 kernel for the channels of one group (plan.cu).
+int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
+                         std::vector<uint32_t> &desc, std::vector<int> &nrounds, int &rmax);
 
 // One single-grid-side FP32 imaging job on caller-provided device tables and
 // workspace (used by the static-scratch entry point).

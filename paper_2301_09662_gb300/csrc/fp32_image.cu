@@ -307,7 +307,8 @@ int launch_group(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, smem) != cudaSuccess || per_sm < 1)
         return EPIC_ERR_UNSUPPORTED;
-    const int n_tau = pick_tau(g.n_items, T, plan->sm_count);
+    int n_tau = pick_tau(g.n_items, T, plan->sm_count);
+    if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));
     kfn<<<grid, kThreads, smem, stream>>>(v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN,
@@ -377,7 +378,9 @@ int image_fp32(epic_plan_s *plan, const uint8_t *v, const float2 *gains, int T, 
         if (rc != EPIC_OK) return rc;
         int n_tau = 1;
         prof_mark(plan, stream, stage, true);
-        if (plan->P == 2) {
+        if (g.reg64) {
+            rc = launch_reg64(plan, g, v, gains, T, &n_tau, stream);
+        } else if (plan->P == 2) {
             switch (g.M) {
             case 32: rc = launch_group<32, 2>(plan, g, v, gains, T, &n_tau, stream); break;
             case 48: rc = launch_group<48, 2>(plan, g, v, gains, T, &n_tau, stream); break;

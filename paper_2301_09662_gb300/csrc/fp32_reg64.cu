@@ -1,0 +1,263 @@
+// FP32 form, folded side M = 64: the imaging kernel used for grid sides 64,
+// 128, 256 and 512 (one pixel class of one channel per CTA, as in
+// fp32_image.cu; see the derivation there).
+//
+// What differs from the general kernel, and why (measured: the general kernel
+// is bound by the shared-memory pipe, ~17 000 wavefronts per CTA and sample):
+//  * gridding without atomics: the plan splits every antenna footprint into K
+//    row segments and packs them into rounds of 32 lanes in which no two
+//    segments touch the same cell and no two lanes of a half-warp hit the same
+//    bank; warp w owns the grid rows y = w (mod 8), so a round is a plain
+//    read-add-write of K cells per lane with no inter-warp race;
+//  * the 64-point transforms run in registers (one row or column per thread),
+//    so each axis costs one shared-memory read and one write;
+//  * two time samples per iteration share the schedule, the twiddles and the
+//    synchronisation.
+#include "epic_internal.cuh"
+#include "fft64.cuh"
+
+namespace epic {
+namespace {
+
+constexpr int M64 = 64;
+constexpr int S64 = 65;                       // padded row stride (float2)
+
+__device__ __forceinline__ float2 ci4_f2(uint32_t b)
+{
+    const int re = static_cast<int>(static_cast<int8_t>(b & 0xF0u)) >> 4;
+    const int im = static_cast<int>(static_cast<int8_t>((b << 4) & 0xF0u)) >> 4;
+    return make_float2(static_cast<float>(re), static_cast<float>(im));
+}
+
+template <int P>
+struct Acc64;
+template <> struct Acc64<1> { using T = float; };
+template <> struct Acc64<2> { using T = float4; };
+
+// Grid buffers: G[ts][p][y][x] with x < 64 at stride S64.
+template <int P, int TS>
+__global__ void __launch_bounds__(kThreads, 1)
+fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
+                  const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K,
+                  const int *__restrict__ chans, const float2 *__restrict__ twN,
+                  const uint32_t *__restrict__ sched, const int *__restrict__ nrounds, int rmax,
+                  int A, int C, int T, int N, int Q1, int n_items, int n_tau,
+                  float *__restrict__ partial, int *__restrict__ status)
+{
+    constexpr int NPOS = M64 * M64 / kThreads;   // 16 pixels per thread
+    constexpr int BUF = M64 * S64;               // one [y][x] plane
+    extern __shared__ float4 smem_raw[];
+    const int AP = A * P, KK = K * K, hk = (K - 1) / 2;
+    const int APW = (AP + 3) >> 2;
+    float2 *G = reinterpret_cast<float2 *>(smem_raw);          // [TS][P][64][65]
+    float2 *es = G + TS * P * BUF;                             // [TS][A*P]
+    float2 *gp = es + TS * AP;                                 // [A*P]
+    float2 *tapw = gp + AP;                                    // [K*K]
+    uint32_t *stage = reinterpret_cast<uint32_t *>(tapw + KK); // [TS][APW]
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int item = blockIdx.x % n_items;
+    const int tau = blockIdx.x / n_items;
+    const int Q = Q1 * Q1;
+    const int ci = item / Q, h = item % Q, hx = h % Q1, hy = h / Q1;
+    const int c = chans[ci];
+    const int t0 = static_cast<int>(static_cast<long long>(T) * tau / n_tau);
+    const int t1 = static_cast<int>(static_cast<long long>(T) * (tau + 1) / n_tau);
+    const uint32_t *my_sched = sched + (static_cast<size_t>(ci) * 8 + warp) * rmax * 32;
+    const int my_rounds = nrounds[ci * 8 + warp];
+
+    // ---- set-up: phase-folded gains and taps (class phase w_N^{k.h})
+    for (int a = tid; a < A; a += kThreads) {
+        const short2 k = cells[static_cast<size_t>(c) * A + a];
+        if (k.x < hk || k.x >= N - hk || k.y < hk || k.y >= N - hk) atomicOr(status, kStatusDevice);
+        const float2 ph = twN[((k.x * hx + k.y * hy) % N + N) % N];
+        for (int p = 0; p < P; p++) {
+            const float2 g = gains ? gains[(static_cast<size_t>(c) * A + a) * P + p] : make_float2(1.f, 0.f);
+            gp[a * P + p] = cmul(g, ph);
+        }
+    }
+    for (int i = tid; i < KK; i += kThreads) {
+        const int dy = i / K - hk, dx = i % K - hk;
+        tapw[i] = cmul(kern[i], twN[((dx * hx + dy * hy) % N + N) % N]);
+    }
+    for (int i = tid; i < TS * P * BUF; i += kThreads) G[i] = make_float2(0.f, 0.f);
+    for (int ts = 0; ts < TS; ts++) {
+        if (t0 + ts < t1) {
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(t0 + ts) * C + c) * AP);
+            for (int w = tid; w < APW; w += kThreads) stage[ts * APW + w] = row[w];
+        }
+    }
+
+    typename Acc64<P>::T acc[NPOS];
+#pragma unroll
+    for (int r = 0; r < NPOS; r++) {
+        if constexpr (P == 2) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        else acc[r] = 0.f;
+    }
+    __syncthreads();
+
+    constexpr int kPreW = kMaxAP / 4 / kThreads;
+    for (int t = t0; t < t1; t += TS) {
+        // ---- a1, a2: unpack and calibrate TS samples (an absent sample grids zeros)
+#pragma unroll
+        for (int ts = 0; ts < TS; ts++) {
+            const bool ok = t + ts < t1;
+            for (int i = tid; i < AP; i += kThreads) {
+                const uint32_t b = reinterpret_cast<const uint8_t *>(stage + ts * APW)[i];
+                es[ts * AP + i] = ok ? cmul(gp[i], ci4_f2(b)) : make_float2(0.f, 0.f);
+            }
+        }
+        // prefetch the next TS samples while this group is gridded and transformed
+        uint32_t pre[TS][kPreW];
+#pragma unroll
+        for (int ts = 0; ts < TS; ts++) {
+            const int tn = t + TS + ts;
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(tn) * C + c) * AP);
+#pragma unroll
+            for (int r = 0; r < kPreW; r++) {
+                const int w = tid + r * kThreads;
+                pre[ts][r] = (tn < t1 && w < APW) ? __ldg(row + w) : 0u;
+            }
+        }
+        __syncthreads();
+
+        // ---- a3: scheduled gridding, warp w owns rows y = w (mod 8)
+        for (int r = 0; r < my_rounds; r++) {
+            const uint32_t d = __ldg(my_sched + r * 32 + lane);
+            if (d >> 31) {
+                const int a = static_cast<int>(d & 0xFFFu);
+                const int dyi = static_cast<int>((d >> 12) & 0xFu);
+                const int y = static_cast<int>((d >> 16) & 0x3Fu);
+                const int x0 = static_cast<int>((d >> 22) & 0x3Fu);
+                float2 e[TS][P];
+#pragma unroll
+                for (int ts = 0; ts < TS; ts++)
+#pragma unroll
+                    for (int p = 0; p < P; p++) e[ts][p] = es[ts * AP + a * P + p];
+                const float2 *wrow = tapw + dyi * K;
+                for (int dx = 0; dx < K; dx++) {
+                    const float2 w = wrow[dx];
+                    const int x = (x0 + dx) & (M64 - 1);
+#pragma unroll
+                    for (int ts = 0; ts < TS; ts++)
+#pragma unroll
+                        for (int p = 0; p < P; p++) {
+                            float2 *cell = G + (ts * P + p) * BUF + y * S64 + x;
+                            const float2 cv = cmul(w, e[ts][p]);
+                            float2 old = *cell;
+                            old.x += cv.x;
+                            old.y += cv.y;
+                            *cell = old;
+                        }
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+
+        // ---- a4: rows then columns, one 64-point transform per thread
+        for (int q = tid; q < TS * P * M64; q += kThreads) {
+            float2 *line = G + (q / M64) * BUF + (q % M64) * S64;
+            float2 x[64];
+#pragma unroll
+            for (int i = 0; i < 64; i++) x[i] = line[i];
+            fft64_stage1(x);
+            fft64_stage2(x, [&](int k, float2 val) { line[k] = val; });
+        }
+        __syncthreads();
+        for (int q = tid; q < TS * P * M64; q += kThreads) {
+            float2 *col = G + (q / M64) * BUF + (q % M64);
+            float2 x[64];
+#pragma unroll
+            for (int i = 0; i < 64; i++) x[i] = col[i * S64];
+            fft64_stage1(x);
+            fft64_stage2(x, [&](int k, float2 val) { col[k * S64] = val; });
+        }
+        __syncthreads();
+
+        // ---- a5, a6: products summed over time; clear the grids for the next group
+#pragma unroll
+        for (int r = 0; r < NPOS; r++) {
+            const int pos = tid + r * kThreads;
+            const int idx = (pos >> 6) * S64 + (pos & 63);
+#pragma unroll
+            for (int ts = 0; ts < TS; ts++) {
+                const float2 f0 = G[(ts * P) * BUF + idx];
+                G[(ts * P) * BUF + idx] = make_float2(0.f, 0.f);
+                if constexpr (P == 2) {
+                    const float2 f1 = G[(ts * P + 1) * BUF + idx];
+                    G[(ts * P + 1) * BUF + idx] = make_float2(0.f, 0.f);
+                    acc[r].x = fmaf(f0.x, f0.x, fmaf(f0.y, f0.y, acc[r].x));
+                    acc[r].y = fmaf(f1.x, f1.x, fmaf(f1.y, f1.y, acc[r].y));
+                    acc[r].z = fmaf(f0.x, f1.x, fmaf(f0.y, f1.y, acc[r].z));
+                    acc[r].w = fmaf(f0.y, f1.x, fmaf(-f0.x, f1.y, acc[r].w));
+                } else {
+                    acc[r] = fmaf(f0.x, f0.x, fmaf(f0.y, f0.y, acc[r]));
+                }
+            }
+        }
+#pragma unroll
+        for (int ts = 0; ts < TS; ts++)
+#pragma unroll
+            for (int r = 0; r < kPreW; r++) {
+                const int w = tid + r * kThreads;
+                if (w < APW) stage[ts * APW + w] = pre[ts][r];
+            }
+        __syncthreads();
+    }
+
+    float *dst = partial + (static_cast<size_t>(tau) * n_items + item) * (M64 * M64) * (P == 2 ? 4 : 1);
+#pragma unroll
+    for (int r = 0; r < NPOS; r++) {
+        const int pos = tid + r * kThreads;
+        if constexpr (P == 2) reinterpret_cast<float4 *>(dst)[pos] = acc[r];
+        else dst[pos] = acc[r];
+    }
+}
+
+template <int P, int TS>
+size_t reg64_smem(int A, int K)
+{
+    const int AP = A * P;
+    size_t b = sizeof(float2) * (static_cast<size_t>(TS) * P * M64 * S64 + static_cast<size_t>(TS) * AP + AP + K * K);
+    b += sizeof(uint32_t) * TS * ((AP + 3) / 4);
+    return (b + 15) & ~static_cast<size_t>(15);
+}
+
+template <int P, int TS>
+int launch_reg64_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau_out,
+                   cudaStream_t stream)
+{
+    auto kfn = fp32_reg64_kernel<P, TS>;
+    const size_t smem = reg64_smem<P, TS>(plan->A, plan->K);
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+        return EPIC_ERR_UNSUPPORTED;
+    int n_tau = fp32_pick_tau(g.n_items, T, plan->sm_count);
+    if (n_tau > g.tau_cap) n_tau = g.tau_cap;
+    *n_tau_out = n_tau;
+    const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));
+    kfn<<<grid, kThreads, smem, stream>>>(v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN,
+                                          g.d_sched, g.d_nrounds, g.rmax, plan->A, plan->C, T, g.N, g.Q1, g.n_items,
+                                          n_tau, g.d_partial, plan->d_status);
+    return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
+}  // namespace
+
+size_t reg64_smem_bytes(int P, int TS, int A, int K)
+{
+    if (P == 2) return TS == 2 ? reg64_smem<2, 2>(A, K) : reg64_smem<2, 1>(A, K);
+    return TS == 2 ? reg64_smem<1, 2>(A, K) : reg64_smem<1, 1>(A, K);
+}
+
+int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
+                 cudaStream_t stream)
+{
+    if (plan->P == 2)
+        return g.ts == 2 ? launch_reg64_t<2, 2>(plan, g, v, gains, T, n_tau, stream)
+                         : launch_reg64_t<2, 1>(plan, g, v, gains, T, n_tau, stream);
+    return g.ts == 2 ? launch_reg64_t<1, 2>(plan, g, v, gains, T, n_tau, stream)
+                     : launch_reg64_t<1, 1>(plan, g, v, gains, T, n_tau, stream);
+}
+
+}  // namespace epic

@@ -54,24 +54,17 @@ autopower_kernel(const uint8_t *__restrict__ v, int T, int C, int A, int P, int 
     }
 }
 
-template <int M>
-struct Digits;
-template <> struct Digits<32> { static constexpr int R1 = 8, R2 = 4; };
-template <> struct Digits<48> { static constexpr int R1 = 8, R2 = 6; };
-template <> struct Digits<64> { static constexpr int R1 = 8, R2 = 8; };
-
 // grid (pixel tiles, group channels).  Partial layout written by the imaging
 // kernels: [tau][item][pos][NPF] with item = ci * Q + (hy * Q1 + hx) and
 // pos = py * M + px, where folded frequency m sits at digit position
-// R2 (m mod R1) + m / R1.
+// R2 (m mod R1) + m / R1 (R1 = 1, R2 = M for natural order).
 template <int M, int P>
 __global__ void __launch_bounds__(kThreads)
-epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N, int Q1,
+epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N, int Q1, int R1, int R2,
                 const int *__restrict__ chans, const long long *__restrict__ out_off,
                 const double *__restrict__ wpow, const int *__restrict__ autoint,
                 const float2 *__restrict__ gains, int A, int T, unsigned flags, float2 *__restrict__ out)
 {
-    constexpr int R1 = Digits<M>::R1, R2 = Digits<M>::R2;
     constexpr int NPF = P == 2 ? 4 : 1;
     constexpr int NP = P == 2 ? 4 : 1;
     const int ci = blockIdx.y;
@@ -164,7 +157,8 @@ int launch_epi(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T,
     const int NN = g.N * g.N;
     const int tiles = (NN + kThreads * 4 - 1) / (kThreads * 4);
     const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(g.n_chan));
-    epilogue_kernel<M, P><<<grid, kThreads, 0, stream>>>(g.d_partial, n_tau, g.n_items, g.N, g.Q1, g.d_chans,
+    epilogue_kernel<M, P><<<grid, kThreads, 0, stream>>>(g.d_partial, n_tau, g.n_items, g.N, g.Q1, g.R1, g.R2,
+                                                         g.d_chans,
                                                          g.d_out_off, g.d_wpow, plan->d_autoint, gains, plan->A, T,
                                                          plan->flags, out);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
@@ -176,7 +170,8 @@ int launch_epi_raw(const RawImage &r, const float2 *gains, float2 *out, cudaStre
     const int NN = r.N * r.N;
     const int tiles = (NN + kThreads * 4 - 1) / (kThreads * 4);
     const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(r.C));
-    epilogue_kernel<M, P><<<grid, kThreads, 0, stream>>>(r.partial, r.n_tau, r.n_items, r.N, r.Q1, r.chans,
+    epilogue_kernel<M, P><<<grid, kThreads, 0, stream>>>(r.partial, r.n_tau, r.n_items, r.N, r.Q1, 8, M / 8,
+                                                         r.chans,
                                                          r.out_off, r.wpow, r.autoint, gains, r.A, r.T, r.flags,
                                                          out);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;

@@ -8,6 +8,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <new>
 
@@ -64,6 +65,8 @@ void free_plan(epic_plan_s *p)
         cudaFree(g.d_wpow);
         cudaFree(g.d_twN);
         cudaFree(g.d_partial);
+        cudaFree(g.d_sched);
+        cudaFree(g.d_nrounds);
     }
     delete p;
 }
@@ -129,6 +132,76 @@ int host_cell_map(const double *ant_xy_m, int n_ant, const double *freq_hz, int 
 }
 
 void host_kernel_power(const float *kern, int K, int N, std::vector<double> &out) { kernel_power(kern, K, N, out); }
+
+// Gridding schedule of the M = 64 kernel.  Each antenna footprint is cut into
+// K row segments (one per dy) of K cells on the folded 64 x 64 grid.  Warp w
+// owns rows y = w (mod 8); its segments are packed greedily into rounds of 32
+// lanes such that (a) no two segments of a round share a cell, so a round can
+// read-add-write without atomics, and (b) the 16 lanes of each half-warp start
+// at distinct (y + x) mod 16, which with the 65-float2 row stride puts every
+// lane of a half-warp on its own pair of banks for each of the K cells.
+int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
+                         std::vector<uint32_t> &desc, std::vector<int> &nrounds, int &rmax)
+{
+    constexpr int M = 64, W = 8;
+    const int h = (K - 1) / 2;
+    if (A > 4096 || K > 15) return EPIC_ERR_UNSUPPORTED;
+    struct Round {
+        uint32_t lane[32];
+        uint64_t rowmask[M / W];
+    };
+    const int nc = static_cast<int>(chans.size());
+    std::vector<std::vector<std::vector<Round>>> all(nc, std::vector<std::vector<Round>>(W));
+    rmax = 0;
+    for (int ci = 0; ci < nc; ci++) {
+        const int c = chans[ci];
+        for (int a = 0; a < A; a++) {
+            const short2 k = cells[static_cast<size_t>(c) * A + a];
+            const int jx = k.x % M, jy = k.y % M;
+            const int x0 = ((jx - h) % M + M) % M;
+            uint64_t mask = 0;
+            for (int dx = 0; dx < K; dx++) mask |= 1ull << ((x0 + dx) & (M - 1));
+            for (int dyi = 0; dyi < K; dyi++) {
+                const int y = ((jy + dyi - h) % M + M) % M;
+                const int w = y % W, res = (y + x0) % 16;
+                const uint32_t d = (1u << 31) | (static_cast<uint32_t>(x0) << 22) | (static_cast<uint32_t>(y) << 16) |
+                                   (static_cast<uint32_t>(dyi) << 12) | static_cast<uint32_t>(a);
+                auto &rounds = all[ci][w];
+                bool placed = false;
+                for (auto &r : rounds) {
+                    if (r.rowmask[y / W] & mask) continue;
+                    int ln = -1;
+                    if (!r.lane[res]) ln = res;
+                    else if (!r.lane[16 + res]) ln = 16 + res;
+                    if (ln < 0) continue;
+                    r.lane[ln] = d;
+                    r.rowmask[y / W] |= mask;
+                    placed = true;
+                    break;
+                }
+                if (!placed) {
+                    Round r{};
+                    r.lane[res] = d;
+                    r.rowmask[y / W] = mask;
+                    rounds.push_back(r);
+                }
+            }
+        }
+        for (int w = 0; w < W; w++) rmax = std::max(rmax, static_cast<int>(all[ci][w].size()));
+    }
+    if (rmax == 0) rmax = 1;
+    desc.assign(static_cast<size_t>(nc) * W * rmax * 32, 0u);
+    nrounds.assign(static_cast<size_t>(nc) * W, 0);
+    for (int ci = 0; ci < nc; ci++)
+        for (int w = 0; w < W; w++) {
+            const auto &rounds = all[ci][w];
+            nrounds[ci * W + w] = static_cast<int>(rounds.size());
+            for (size_t r = 0; r < rounds.size(); r++)
+                for (int l = 0; l < 32; l++)
+                    desc[((static_cast<size_t>(ci) * W + w) * rmax + r) * 32 + l] = rounds[r].lane[l];
+        }
+    return EPIC_OK;
+}
 
 void prof_begin(epic_plan_s *plan)
 {
@@ -235,6 +308,11 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     }
     p->out_floats = static_cast<size_t>(off) * 2;
 
+    int smem_optin = 0;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device) != cudaSuccess) {
+        delete p;
+        return EPIC_ERR_CUDA;
+    }
     int rc = dev_upload(&p->d_cells, cells.data(), cells.size());
     if (rc == EPIC_OK) rc = dev_upload(&p->d_kernel, reinterpret_cast<const float2 *>(kernel_c64), static_cast<size_t>(K) * K);
     if (rc == EPIC_OK) rc = dev_upload(&p->d_autoint, static_cast<const int *>(nullptr), static_cast<size_t>(n_chan) * n_ant * 4);
@@ -264,13 +342,35 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
             const double ang = 2.0 * M_PI * k / g.N;
             tw[k] = make_float2(static_cast<float>(std::cos(ang)), static_cast<float>(std::sin(ang)));
         }
-        rc = dev_upload(&g.d_chans, g.chans.data(), g.chans.size());
+        g.tau_cap = epic::fp32_pick_tau(g.n_items, max_spectra, p->sm_count);
+        if (g.tau_cap < 1) g.tau_cap = 1;
+        g.R1 = 8;
+        g.R2 = g.M / 8;
+        const int ap = n_ant * n_pol;
+        if (g.M == 64 && (ap % 4) == 0) {
+            for (int ts = 2; ts >= 1 && !g.reg64; ts--) {
+                if (epic::reg64_smem_bytes(n_pol, ts, n_ant, K) <= static_cast<size_t>(smem_optin)) {
+                    g.reg64 = true;
+                    g.ts = ts;
+                }
+            }
+        }
+        if (g.reg64) {
+            g.R1 = 1;
+            g.R2 = 64;
+            std::vector<uint32_t> desc;
+            std::vector<int> nr;
+            rc = epic::build_reg64_schedule(cells, n_ant, K, g.chans, desc, nr, g.rmax);
+            if (rc == EPIC_OK) rc = dev_upload(&g.d_sched, desc.data(), desc.size());
+            if (rc == EPIC_OK) rc = dev_upload(&g.d_nrounds, nr.data(), nr.size());
+        }
+        if (rc == EPIC_OK) rc = dev_upload(&g.d_chans, g.chans.data(), g.chans.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_out_off, offs.data(), offs.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_wpow, wpow.data(), wpow.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_twN, tw.data(), tw.size());
         if (rc == EPIC_OK)
             rc = dev_upload(&g.d_partial, static_cast<const float *>(nullptr),
-                            static_cast<size_t>(epic::kMaxTau) * g.n_items * g.M * g.M * npf);
+                            static_cast<size_t>(g.tau_cap) * g.n_items * g.M * g.M * npf);
         p->groups.push_back(g);
     }
     if (rc != EPIC_OK) {
