@@ -65,6 +65,17 @@ struct epic_plan_s {
     bool profiling = false;
     std::vector<cudaEvent_t> events;   // 2 per recorded stage
     int n_recorded = 0;
+    // CUDA graph of one integration, re-captured when T, pointers or profiling change
+    bool use_graph = true;
+    cudaStream_t cap = nullptr;        // capture stream
+    std::vector<cudaStream_t> side;    // one branch per grid side
+    cudaEvent_t ev_fork = nullptr, ev_auto = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+    cudaGraphExec_t gexec = nullptr;
+    const void *g_v = nullptr, *g_gains = nullptr;
+    void *g_out = nullptr;
+    int g_T = -1;
+    bool g_prof = false;
     // host-buffer entry point staging (allocated on first use)
     uint8_t *d_stage_v = nullptr;
     float *d_stage_g = nullptr;
@@ -77,9 +88,15 @@ namespace epic {
 void prof_begin(epic_plan_s *plan);
 void prof_mark(epic_plan_s *plan, cudaStream_t stream, int stage, bool start);
 
-// FP32 form: launch every kernel of one integration on `stream`.
+// FP32 form: launch every kernel of one integration on `stream` (with fork,
+// the grid sides run on the plan's side streams and join back).
 int image_fp32(epic_plan_s *plan, const uint8_t *v, const float2 *gains, int T,
-               float2 *out, cudaStream_t stream);
+               float2 *out, cudaStream_t stream, bool fork);
+// one integration through the plan's CUDA graph (or direct launches)
+int run_image(epic_plan_s *plan, const uint8_t *v, const float2 *gains, int T, float2 *out, cudaStream_t stream);
+// per-group kernel attributes (dynamic shared memory), set once at plan time
+int prepare_fp32(const epic_plan_s *plan, const GroupCfg &g);
+int prepare_reg64(const epic_plan_s *plan, const GroupCfg &g);
 
 // shared pieces (image_common.cu)
 int launch_autopower(epic_plan_s *plan, const uint8_t *v, int T, cudaStream_t stream);

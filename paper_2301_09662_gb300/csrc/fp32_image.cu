@@ -302,11 +302,6 @@ int launch_group(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
 {
     auto kfn = fp32_image_kernel<M, P>;
     const size_t smem = smem_bytes<M, P>(plan->A, plan->K);
-    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
-        return EPIC_ERR_UNSUPPORTED;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, smem) != cudaSuccess || per_sm < 1)
-        return EPIC_ERR_UNSUPPORTED;
     int n_tau = pick_tau(g.n_items, T, plan->sm_count);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
@@ -315,6 +310,19 @@ int launch_group(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
                                           plan->A, plan->C, T, g.N, g.Q1, g.n_items, n_tau, g.d_partial,
                                           plan->d_status);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
+template <int M, int P>
+int prepare_group(const epic_plan_s *plan)
+{
+    auto kfn = fp32_image_kernel<M, P>;
+    const size_t smem = smem_bytes<M, P>(plan->A, plan->K);
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
+        return EPIC_ERR_UNSUPPORTED;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, smem) != cudaSuccess || per_sm < 1)
+        return EPIC_ERR_UNSUPPORTED;
+    return EPIC_OK;
 }
 
 template <int M, int P>
@@ -360,46 +368,79 @@ int launch_fp32_raw(const RawImage &r, const uint8_t *v, const float2 *gains, cu
     }
 }
 
-int image_fp32(epic_plan_s *plan, const uint8_t *v, const float2 *gains, int T, float2 *out, cudaStream_t stream)
+int prepare_fp32(const epic_plan_s *plan, const GroupCfg &g)
+{
+    if (g.reg64) return prepare_reg64(plan, g);
+    switch (g.M * 4 + plan->P) {
+    case 32 * 4 + 1: return prepare_group<32, 1>(plan);
+    case 32 * 4 + 2: return prepare_group<32, 2>(plan);
+    case 48 * 4 + 1: return prepare_group<48, 1>(plan);
+    case 48 * 4 + 2: return prepare_group<48, 2>(plan);
+    case 64 * 4 + 1: return prepare_group<64, 1>(plan);
+    case 64 * 4 + 2: return prepare_group<64, 2>(plan);
+    default: return EPIC_ERR_UNSUPPORTED;
+    }
+}
+
+// Launch every kernel of one integration.  With fork, the auto-power kernel
+// runs on `stream` while each grid side's imaging kernel runs on its own side
+// stream; each epilogue waits for its imaging kernel and for the auto-power,
+// and `stream` joins all branches at the end (the shape captured into the
+// plan's CUDA graph).
+int image_fp32(epic_plan_s *plan, const uint8_t *v, const float2 *gains, int T, float2 *out, cudaStream_t stream,
+               bool fork)
 {
     if (T == 0) {
         return cudaMemsetAsync(out, 0, plan->out_floats * sizeof(float), stream) == cudaSuccess ? EPIC_OK
                                                                                                 : EPIC_ERR_CUDA;
     }
+    const bool autosub = !(plan->flags & EPIC_NO_AUTOSUB);
+    fork = fork && !plan->side.empty();
     int rc = EPIC_OK;
     int stage = 0;
     prof_begin(plan);
-    if (!(plan->flags & EPIC_NO_AUTOSUB)) {
+    if (fork && cudaEventRecord(plan->ev_fork, stream) != cudaSuccess) return EPIC_ERR_CUDA;
+    if (autosub) {
         prof_mark(plan, stream, stage, true);
         rc = launch_autopower(plan, v, T, stream);
         prof_mark(plan, stream, stage++, false);
-    }
-    for (const auto &g : plan->groups) {
         if (rc != EPIC_OK) return rc;
+        if (fork && cudaEventRecord(plan->ev_auto, stream) != cudaSuccess) return EPIC_ERR_CUDA;
+    }
+    for (size_t gi = 0; gi < plan->groups.size(); gi++) {
+        const GroupCfg &g = plan->groups[gi];
+        cudaStream_t s = fork ? plan->side[gi] : stream;
+        if (fork && cudaStreamWaitEvent(s, plan->ev_fork, 0) != cudaSuccess) return EPIC_ERR_CUDA;
         int n_tau = 1;
-        prof_mark(plan, stream, stage, true);
+        prof_mark(plan, s, stage, true);
         if (g.reg64) {
-            rc = launch_reg64(plan, g, v, gains, T, &n_tau, stream);
+            rc = launch_reg64(plan, g, v, gains, T, &n_tau, s);
         } else if (plan->P == 2) {
             switch (g.M) {
-            case 32: rc = launch_group<32, 2>(plan, g, v, gains, T, &n_tau, stream); break;
-            case 48: rc = launch_group<48, 2>(plan, g, v, gains, T, &n_tau, stream); break;
-            case 64: rc = launch_group<64, 2>(plan, g, v, gains, T, &n_tau, stream); break;
+            case 32: rc = launch_group<32, 2>(plan, g, v, gains, T, &n_tau, s); break;
+            case 48: rc = launch_group<48, 2>(plan, g, v, gains, T, &n_tau, s); break;
+            case 64: rc = launch_group<64, 2>(plan, g, v, gains, T, &n_tau, s); break;
             default: rc = EPIC_ERR_UNSUPPORTED;
             }
         } else {
             switch (g.M) {
-            case 32: rc = launch_group<32, 1>(plan, g, v, gains, T, &n_tau, stream); break;
-            case 48: rc = launch_group<48, 1>(plan, g, v, gains, T, &n_tau, stream); break;
-            case 64: rc = launch_group<64, 1>(plan, g, v, gains, T, &n_tau, stream); break;
+            case 32: rc = launch_group<32, 1>(plan, g, v, gains, T, &n_tau, s); break;
+            case 48: rc = launch_group<48, 1>(plan, g, v, gains, T, &n_tau, s); break;
+            case 64: rc = launch_group<64, 1>(plan, g, v, gains, T, &n_tau, s); break;
             default: rc = EPIC_ERR_UNSUPPORTED;
             }
         }
-        prof_mark(plan, stream, stage++, false);
+        prof_mark(plan, s, stage++, false);
         if (rc != EPIC_OK) return rc;
-        prof_mark(plan, stream, stage, true);
-        rc = launch_epilogue(plan, g, gains, T, n_tau, out, stream);
-        prof_mark(plan, stream, stage++, false);
+        if (fork && autosub && cudaStreamWaitEvent(s, plan->ev_auto, 0) != cudaSuccess) return EPIC_ERR_CUDA;
+        prof_mark(plan, s, stage, true);
+        rc = launch_epilogue(plan, g, gains, T, n_tau, out, s);
+        prof_mark(plan, s, stage++, false);
+        if (rc != EPIC_OK) return rc;
+        if (fork) {
+            if (cudaEventRecord(plan->ev_join[gi], s) != cudaSuccess) return EPIC_ERR_CUDA;
+            if (cudaStreamWaitEvent(stream, plan->ev_join[gi], 0) != cudaSuccess) return EPIC_ERR_CUDA;
+        }
     }
     return rc;
 }

@@ -230,8 +230,6 @@ int launch_reg64_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
 {
     auto kfn = fp32_reg64_kernel<P, TS>;
     const size_t smem = reg64_smem<P, TS>(plan->A, plan->K);
-    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
-        return EPIC_ERR_UNSUPPORTED;
     int n_tau = fp32_pick_tau(g.n_items, T, plan->sm_count);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
@@ -242,7 +240,24 @@ int launch_reg64_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
+template <int P, int TS>
+int prepare_reg64_t(const epic_plan_s *plan)
+{
+    auto kfn = fp32_reg64_kernel<P, TS>;
+    const size_t smem = reg64_smem<P, TS>(plan->A, plan->K);
+    return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) ==
+                   cudaSuccess
+               ? EPIC_OK
+               : EPIC_ERR_UNSUPPORTED;
+}
+
 }  // namespace
+
+int prepare_reg64(const epic_plan_s *plan, const GroupCfg &g)
+{
+    if (plan->P == 2) return g.ts == 2 ? prepare_reg64_t<2, 2>(plan) : prepare_reg64_t<2, 1>(plan);
+    return g.ts == 2 ? prepare_reg64_t<1, 2>(plan) : prepare_reg64_t<1, 1>(plan);
+}
 
 size_t reg64_smem_bytes(int P, int TS, int A, int K)
 {

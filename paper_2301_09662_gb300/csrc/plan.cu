@@ -7,6 +7,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <map>
@@ -52,6 +53,12 @@ void free_plan(epic_plan_s *p)
 {
     if (!p) return;
     for (auto e : p->events) cudaEventDestroy(e);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    for (auto st : p->side) cudaStreamDestroy(st);
+    for (auto e : p->ev_join) cudaEventDestroy(e);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_auto) cudaEventDestroy(p->ev_auto);
+    if (p->cap) cudaStreamDestroy(p->cap);
     cudaFree(p->d_cells);
     cudaFree(p->d_kernel);
     cudaFree(p->d_autoint);
@@ -219,8 +226,52 @@ void prof_mark(epic_plan_s *plan, cudaStream_t stream, int stage, bool start)
         }
         plan->events.push_back(e);
     }
-    cudaEventRecord(plan->events[2 * stage + (start ? 0 : 1)], stream);
+    // External records become event-record nodes when the stream is being
+    // captured (a plain record would only mark a dependency)
+    cudaEventRecordWithFlags(plan->events[2 * stage + (start ? 0 : 1)], stream, cudaEventRecordExternal);
     if (!start && stage + 1 > plan->n_recorded) plan->n_recorded = stage + 1;
+}
+
+// One integration on `stream`: replay the plan's CUDA graph (captured on the
+// first call and again whenever T, a pointer or the profiling state changes),
+// or launch directly when graphs are disabled.
+int run_image(epic_plan_s *p, const uint8_t *v, const float2 *gains, int T, float2 *out, cudaStream_t stream)
+{
+    if (!p->use_graph) return image_fp32(p, v, gains, T, out, stream, false);
+    if (!p->gexec || p->g_v != v || p->g_gains != gains || p->g_out != out || p->g_T != T ||
+        p->g_prof != p->profiling) {
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return EPIC_ERR_CUDA;
+        const int rc = image_fp32(p, v, gains, T, out, p->cap, true);
+        const cudaError_t ce = cudaStreamEndCapture(p->cap, &graph);
+        if (rc != EPIC_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (ce != cudaSuccess || !graph) return EPIC_ERR_CUDA;
+        bool updated = false;
+        if (p->gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            updated = cudaGraphExecUpdate(p->gexec, graph, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(p->gexec);
+                p->gexec = nullptr;
+            }
+        }
+        if (!updated && cudaGraphInstantiate(&p->gexec, graph, 0) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            p->gexec = nullptr;
+            return EPIC_ERR_CUDA;
+        }
+        cudaGraphDestroy(graph);
+        p->g_v = v;
+        p->g_gains = gains;
+        p->g_out = out;
+        p->g_T = T;
+        p->g_prof = p->profiling;
+    }
+    return cudaGraphLaunch(p->gexec, stream) == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
 }  // namespace epic
@@ -373,6 +424,34 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                             static_cast<size_t>(g.tau_cap) * g.n_items * g.M * g.M * npf);
         p->groups.push_back(g);
     }
+    for (const auto &g : p->groups) {
+        if (rc != EPIC_OK) break;
+        rc = epic::prepare_fp32(p, g);
+    }
+    if (rc == EPIC_OK) {
+        const char *env = std::getenv("EPIC_NO_GRAPH");
+        p->use_graph = !(env && env[0] == '1');
+        if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_auto, cudaEventDisableTiming) != cudaSuccess)
+            rc = EPIC_ERR_CUDA;
+        if (p->groups.size() > 1) {
+            for (size_t i = 0; i < p->groups.size() && rc == EPIC_OK; i++) {
+                cudaStream_t st;
+                cudaEvent_t ev;
+                if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+                    rc = EPIC_ERR_CUDA;
+                    break;
+                }
+                p->side.push_back(st);
+                if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+                    rc = EPIC_ERR_CUDA;
+                    break;
+                }
+                p->ev_join.push_back(ev);
+            }
+        }
+    }
     if (rc != EPIC_OK) {
         free_plan(p);
         return rc;
@@ -390,8 +469,8 @@ int epic_image(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_s
     if (n_spectra < 0 || n_spectra > plan->max_spectra) return EPIC_ERR_ARG;
     if (n_spectra > 0 && !ci4) return EPIC_ERR_ARG;
     auto s = static_cast<cudaStream_t>(stream);
-    return epic::image_fp32(plan, ci4, reinterpret_cast<const float2 *>(gains), n_spectra,
-                            reinterpret_cast<float2 *>(out), s);
+    return epic::run_image(plan, ci4, reinterpret_cast<const float2 *>(gains), n_spectra,
+                           reinterpret_cast<float2 *>(out), s);
 }
 
 int epic_image_host(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra,
@@ -421,8 +500,8 @@ int epic_image_host(epic_plan_t plan, const uint8_t *ci4, const float *gains, in
         return EPIC_ERR_CUDA;
     if (gains && cudaMemcpyAsync(plan->d_stage_g, gains, gfloats * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return EPIC_ERR_CUDA;
-    int rc = epic::image_fp32(plan, plan->d_stage_v, gains ? reinterpret_cast<const float2 *>(plan->d_stage_g) : nullptr,
-                              n_spectra, reinterpret_cast<float2 *>(plan->d_stage_out), s);
+    int rc = epic::run_image(plan, plan->d_stage_v, gains ? reinterpret_cast<const float2 *>(plan->d_stage_g) : nullptr,
+                             n_spectra, reinterpret_cast<float2 *>(plan->d_stage_out), s);
     if (rc != EPIC_OK) return rc;
     if (cudaMemcpyAsync(out, plan->d_stage_out, plan->out_floats * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return EPIC_ERR_CUDA;
@@ -455,7 +534,8 @@ int epic_stage_times(epic_plan_t plan, float *ms, int max_stages)
     if (!plan || !ms || max_stages < 0) return EPIC_ERR_ARG;
     if (!plan->profiling || plan->n_recorded == 0) return EPIC_ERR_ARG;
     const int n = plan->n_recorded < max_stages ? plan->n_recorded : max_stages;
-    if (cudaEventSynchronize(plan->events[2 * plan->n_recorded - 1]) != cudaSuccess) return EPIC_ERR_CUDA;
+    for (int i = 0; i < plan->n_recorded; i++)
+        if (cudaEventSynchronize(plan->events[2 * i + 1]) != cudaSuccess) return EPIC_ERR_CUDA;
     for (int i = 0; i < n; i++)
         if (cudaEventElapsedTime(&ms[i], plan->events[2 * i], plan->events[2 * i + 1]) != cudaSuccess)
             return EPIC_ERR_CUDA;

@@ -210,22 +210,23 @@ def tiny(T: int = 64, seed_cfg: int = 1) -> Workload:
                     {"src_lm": lm, "src_flux": [1.0]})
 
 
-def lwa(T: int = 1000, C: int = 64, seed_cfg: int = 2, with_gains: bool = True) -> Workload:
+def lwa(T: int = 1000, C: int = 64, seed_cfg: int = 2, with_gains: bool = True,
+        first_channel: int = 0) -> Workload:
     """LWA-station-like: 256 dual-pol antennas in a 110x100 m ellipse (min spacing
     4 m; random sequential packing jams below 256 dipoles at 5 m), C channels of 25 kHz from 60 MHz, 5x5 kernel, 128x128 grid, three point
     sources (1.0/0.3/0.1) plus a diffuse Gaussian sky (256 components, sigma 0.3,
     total flux 0.5), noise sigma 2, random per-(c,a,p) gains."""
     s = seeds(seed_cfg)
     ant = layout_ellipse(256, 55.0, 50.0, np.random.default_rng(s["layout"]), LWA_MIN_SPACING_M)
-    freq = 60.0e6 + 25.0e3 * np.arange(C)
+    freq = 60.0e6 + 25.0e3 * (first_channel + np.arange(C))
     rs = np.random.default_rng(s["sky"])
     lm_pts = _lm_uniform_disc(3, 0.7, rs)
     lm_diff = rs.normal(0.0, 0.3, size=(256, 2))
     lm_diff = lm_diff[np.hypot(lm_diff[:, 0], lm_diff[:, 1]) < 0.95][:256]
     lm = np.vstack([lm_pts, lm_diff])
     flux = np.concatenate([[1.0, 0.3, 0.1], np.full(len(lm_diff), 0.5 / len(lm_diff))])
-    v = sky_voltages(ant, freq, T, 2, lm, flux, 2.0, np.random.default_rng(s["voltages"]))
-    g = random_gains(C, 256, 2, np.random.default_rng(s["gains"])) if with_gains else None
+    v = sky_voltages(ant, freq, T, 2, lm, flux, 2.0, np.random.default_rng(s["voltages"] + 7919 * first_channel))
+    g = random_gains(C, 256, 2, np.random.default_rng(s["gains"] + 7919 * first_channel)) if with_gains else None
     return Workload(f"lwa-256ant-{C}ch-128grid-{T}t", ant, 2, gaussian_kernel(5),
                     np.full(C, 128, np.int32), freq, 0.5, T, v, g,
                     {"src_lm": lm_pts, "src_flux": [1.0, 0.3, 0.1]})
