@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--precision", choices=["fp32"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
+    ap.add_argument("--no-variants", action="store_true", help="skip timing the other forms")
     ap.add_argument("--channels", type=int, default=None,
                     help="shrink the workload to this many channels (profiling captures only)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
@@ -235,6 +236,66 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_variants(wl, v, g, out, flush, args, stream):
+    """Other forms of the same integration, timed the same way (device events
+    per step, L2 flushed between steps); same output up to rounding."""
+    import torch
+
+    from paper_2301_09662_gb300 import epic
+    res = {}
+    forms = {"kernel_taper": dict(flags=epic.EPIC_KERNEL_TAPER),
+             "tc_split_fp16": dict(precision=epic.EPIC_TC_SPLIT_FP16),
+             "tc_fp16": dict(precision=epic.EPIC_TC_FP16),
+             "tc_split_bf16": dict(precision=epic.EPIC_TC_SPLIT_BF16),
+             "tc_split_fp16_taper": dict(precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_KERNEL_TAPER)}
+    notes = {"kernel_taper": "FP32; image-domain |W^|^2 taper with point gridding (exact for one shared kernel)",
+             "tc_split_fp16": "column DFT on tcgen05, FP16 hi+lo operands (3 MMAs), FP32 accumulate in TMEM",
+             "tc_fp16": "column DFT on tcgen05, single FP16 operands",
+             "tc_split_bf16": "column DFT on tcgen05, BF16 hi+lo operands (3 MMAs)",
+             "tc_split_fp16_taper": "tc_split_fp16 with the image-domain kernel taper"}
+    peaks = measured_peaks()
+    for name, kw in forms.items():
+        try:
+            p = epic.Plan.from_workload(wl, **kw)
+        except epic.EpicError as e:
+            res[name] = {"unavailable": str(e)}
+            continue
+        p.set_profiling(True)
+        o = torch.empty_like(out)
+        for _ in range(max(args.warmup, 1)):
+            p.image(v, g, out=o)
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            p.image(v, g, out=o)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        stages = p.stage_times()
+        step = sum(ms) / len(ms)
+        entry = {"value": wl.spectra / (step / 1e3), "unit": UNIT, "ms_per_step": step, "note": notes[name],
+                 "stages_ms_last": stages}
+        if name.startswith("tc_"):
+            # executed tensor FLOPs: per CTA and sample, 8 k-blocks x terms MMAs of 128 x 128 x 16
+            terms = 1 if name == "tc_fp16" else 3
+            n_items = sum((int(n) // 64) ** 2 for n in wl.grid_n)
+            flops = n_items * wl.T * 8 * terms * 2.0 * 128 * 128 * 16
+            img = max((v for k, v in stages.items() if k.startswith("image[")), default=None)
+            if img:
+                ach = flops / (img / 1e3) / 1e12
+                peak = float(peaks.get("bf16_tflops", 1892.1))
+                entry["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                     "frac": ach / peak, "executed_flops_per_launch": flops,
+                                     "peak_source": "MEASURED_PEAKS bf16_tflops (dense FP16 rate = BF16 rate)"}
+        res[name] = entry
+        p.close()
+    return res
+
+
 def run_e2e(plan, wl, args, world, barrier, spectra):
     """Same metric through epic_image_host: every step copies the pinned host
     voltages and gains in and the image out, inside the timed region."""
@@ -355,6 +416,8 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": launches,
     }
+    if not args.no_variants:
+        line["variants"] = time_variants(wl, v, g, out, flush, args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     if rank == 0:

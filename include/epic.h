@@ -78,6 +78,13 @@ enum {
 /* flags */
 #define EPIC_MEAN        1u     /* divide the sum over time by n_spectra */
 #define EPIC_NO_AUTOSUB  2u     /* keep the autocorrelation term (diagnostics) */
+/* Apply the illumination kernel in the image domain: grid each calibrated
+ * voltage into its single cell and multiply the finished image by |W^(l)|^2
+ * (FP64).  Because every antenna shares one kernel, gridding through W is a
+ * convolution and F(l) = W^(l) sum_a e~_a exp(+2 pi i k_a.l / N); the result
+ * equals the default (literal gridding) form up to rounding, with K^2 times
+ * fewer gridding operations. */
+#define EPIC_KERNEL_TAPER 4u
 
 /*
  * epic_plan -- validate the array geometry and build every table the imaging
@@ -96,7 +103,7 @@ enum {
  *   du_wavelengths cell size in wavelengths, 0 < du <= 0.5 (lambda/2 grid)
  *   max_spectra    largest n_spectra an epic_image call will pass (>= 0)
  *   precision      EPIC_FP32 or one of the EPIC_TC_* forms
- *   flags          EPIC_MEAN | EPIC_NO_AUTOSUB
+ *   flags          EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER
  *
  * Uses the current CUDA device.  Allocates device memory (tables and
  * workspace) and returns EPIC_ERR_NOMEM if that fails.  Returns

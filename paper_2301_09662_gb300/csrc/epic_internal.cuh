@@ -56,6 +56,7 @@ struct epic_plan_s {
     std::vector<int> grid_n;
     std::vector<long long> out_off;    // complex-element offset of each channel's image
     size_t out_floats = 0;
+    uint8_t *d_dft = nullptr;          // tensor form: column-DFT operand (hi, lo parts)
     short2 *d_cells = nullptr;         // [C][A]
     float2 *d_kernel = nullptr;        // [K*K]
     int *d_autoint = nullptr;          // [C][A][4] exact integer auto sums
@@ -102,6 +103,13 @@ int prepare_reg64(const epic_plan_s *plan, const GroupCfg &g);
 int launch_autopower(epic_plan_s *plan, const uint8_t *v, int T, cudaStream_t stream);
 int launch_epilogue(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T, int n_tau,
                     float2 *out, cudaStream_t stream);
+
+// tensor-core form (tc_col64.cu)
+size_t tc_smem_bytes(int A, int K);
+int prepare_tc(const epic_plan_s *plan);
+int launch_tc(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
+              cudaStream_t stream);
+void build_dft_operand(bool bf16, std::vector<uint16_t> &words);
 
 // M = 64 register-transform kernel (fp32_reg64.cu)
 size_t reg64_smem_bytes(int P, int TS, int A, int K);

@@ -413,7 +413,9 @@ int image_fp32(epic_plan_s *plan, const uint8_t *v, const float2 *gains, int T, 
         if (fork && cudaStreamWaitEvent(s, plan->ev_fork, 0) != cudaSuccess) return EPIC_ERR_CUDA;
         int n_tau = 1;
         prof_mark(plan, s, stage, true);
-        if (g.reg64) {
+        if (plan->precision != EPIC_FP32) {
+            rc = launch_tc(plan, g, v, gains, T, &n_tau, s);
+        } else if (g.reg64) {
             rc = launch_reg64(plan, g, v, gains, T, &n_tau, s);
         } else if (plan->P == 2) {
             switch (g.M) {

@@ -132,8 +132,11 @@ epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N
                 s[0] += src[0];
             }
         }
-        if (autosub) {
-            const double w = wpow[pix];
+        const double w = wpow[pix];
+        if (flags & EPIC_KERNEL_TAPER) {
+            // point-gridded sums: subtract the bare autos, then apply |W^(l)|^2
+            for (int k = 0; k < (P == 2 ? 4 : 1); k++) s[k] = (s[k] - (autosub ? apq[k] : 0.0)) * w;
+        } else if (autosub) {
             s[0] -= apq[0] * w;
             if (P == 2) {
                 s[1] -= apq[1] * w;

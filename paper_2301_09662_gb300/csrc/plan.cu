@@ -61,6 +61,7 @@ void free_plan(epic_plan_s *p)
     if (p->cap) cudaStreamDestroy(p->cap);
     cudaFree(p->d_cells);
     cudaFree(p->d_kernel);
+    cudaFree(p->d_dft);
     cudaFree(p->d_autoint);
     cudaFree(p->d_status);
     cudaFree(p->d_stage_v);
@@ -304,9 +305,15 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     if (n_ant < 1 || (n_pol != 1 && n_pol != 2) || K < 1 || (K % 2) == 0 || K > epic::kMaxK ||
         n_chan < 1 || !(du > 0.0) || du > 0.5 || max_spectra < 0)
         return EPIC_ERR_ARG;
-    if (flags & ~(EPIC_MEAN | EPIC_NO_AUTOSUB)) return EPIC_ERR_ARG;
+    if (flags & ~(EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER)) return EPIC_ERR_ARG;
     if (precision < EPIC_FP32 || precision > EPIC_TC_SPLIT_BF16) return EPIC_ERR_ARG;
-    if (precision != EPIC_FP32) return EPIC_ERR_UNSUPPORTED;
+    const bool tensor = precision != EPIC_FP32;
+    if (tensor) {
+        // the tensor form exists for dual polarisation on folded side 64
+        if (n_pol != 2 || (n_ant * n_pol) % 4 != 0) return EPIC_ERR_UNSUPPORTED;
+        for (int c = 0; c < n_chan; c++)
+            if (grid_n[c] == 32 || grid_n[c] == 96) return EPIC_ERR_UNSUPPORTED;
+    }
     if (static_cast<long long>(n_ant) * n_pol > epic::kMaxAP) return EPIC_ERR_UNSUPPORTED;
     for (int c = 0; c < n_chan; c++) {
         if (!(freq_hz[c] > 0.0) || !std::isfinite(freq_hz[c])) return EPIC_ERR_ARG;
@@ -346,7 +353,11 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     p->P = n_pol;
     p->NP = n_pol == 2 ? 4 : 1;
     p->C = n_chan;
-    p->K = K;
+    // gridding kernel: the caller's W, or a single unit tap when W is applied
+    // as an image-domain taper
+    const bool taper = (flags & EPIC_KERNEL_TAPER) != 0;
+    p->K = taper ? 1 : K;
+    const float unit_tap[2] = {1.f, 0.f};
     p->max_spectra = max_spectra;
     p->precision = precision;
     p->flags = flags;
@@ -365,7 +376,9 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         return EPIC_ERR_CUDA;
     }
     int rc = dev_upload(&p->d_cells, cells.data(), cells.size());
-    if (rc == EPIC_OK) rc = dev_upload(&p->d_kernel, reinterpret_cast<const float2 *>(kernel_c64), static_cast<size_t>(K) * K);
+    if (rc == EPIC_OK)
+        rc = taper ? dev_upload(&p->d_kernel, reinterpret_cast<const float2 *>(unit_tap), 1)
+                   : dev_upload(&p->d_kernel, reinterpret_cast<const float2 *>(kernel_c64), static_cast<size_t>(K) * K);
     if (rc == EPIC_OK) rc = dev_upload(&p->d_autoint, static_cast<const int *>(nullptr), static_cast<size_t>(n_chan) * n_ant * 4);
     if (rc == EPIC_OK) rc = dev_upload(&p->d_status, static_cast<const int *>(nullptr), 1);
     if (rc == EPIC_OK && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) rc = EPIC_ERR_CUDA;
@@ -398,9 +411,14 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         g.R1 = 8;
         g.R2 = g.M / 8;
         const int ap = n_ant * n_pol;
-        if (g.M == 64 && (ap % 4) == 0) {
+        if (tensor) {
+            // + static shared memory of the kernel (barriers, TMEM slot, alignment)
+            if (epic::tc_smem_bytes(n_ant, p->K) + 2048 > static_cast<size_t>(smem_optin)) rc = EPIC_ERR_UNSUPPORTED;
+            g.reg64 = true;   // same gridding schedule and natural pixel order
+            g.ts = 1;
+        } else if (g.M == 64 && (ap % 4) == 0) {
             for (int ts = 2; ts >= 1 && !g.reg64; ts--) {
-                if (epic::reg64_smem_bytes(n_pol, ts, n_ant, K) <= static_cast<size_t>(smem_optin)) {
+                if (epic::reg64_smem_bytes(n_pol, ts, n_ant, p->K) <= static_cast<size_t>(smem_optin)) {
                     g.reg64 = true;
                     g.ts = ts;
                 }
@@ -411,7 +429,7 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
             g.R2 = 64;
             std::vector<uint32_t> desc;
             std::vector<int> nr;
-            rc = epic::build_reg64_schedule(cells, n_ant, K, g.chans, desc, nr, g.rmax);
+            rc = epic::build_reg64_schedule(cells, n_ant, p->K, g.chans, desc, nr, g.rmax);
             if (rc == EPIC_OK) rc = dev_upload(&g.d_sched, desc.data(), desc.size());
             if (rc == EPIC_OK) rc = dev_upload(&g.d_nrounds, nr.data(), nr.size());
         }
@@ -424,8 +442,14 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                             static_cast<size_t>(g.tau_cap) * g.n_items * g.M * g.M * npf);
         p->groups.push_back(g);
     }
+    if (rc == EPIC_OK && tensor) {
+        std::vector<uint16_t> ops;
+        epic::build_dft_operand(precision == EPIC_TC_SPLIT_BF16, ops);
+        rc = dev_upload(&p->d_dft, reinterpret_cast<const uint8_t *>(ops.data()), ops.size() * 2);
+        if (rc == EPIC_OK) rc = epic::prepare_tc(p);
+    }
     for (const auto &g : p->groups) {
-        if (rc != EPIC_OK) break;
+        if (rc != EPIC_OK || tensor) break;
         rc = epic::prepare_fp32(p, g);
     }
     if (rc == EPIC_OK) {

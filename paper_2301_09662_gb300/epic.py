@@ -31,6 +31,7 @@ EPIC_TC_SPLIT_BF16 = 3
 
 EPIC_MEAN = 1
 EPIC_NO_AUTOSUB = 2
+EPIC_KERNEL_TAPER = 4
 
 PRODUCTS = ("XX", "YY", "XY", "YX")
 

@@ -170,3 +170,40 @@ def test_uneven_workload_full_size_sampled_channels():
     got = np.concatenate([p.split(gpu)[c].ravel() for c in chans])
     err = peak_rel_err(got, ref, wl.grid_n[chans], 2)
     assert err.max() < FP32_TOL, err
+
+
+TAPER_CASES = [
+    # A,   P, C, T,  N,   K
+    (37, 2, 2, 13, 32, 3),
+    (101, 2, 2, 11, 96, 5),
+    (256, 2, 2, 6, 128, 5),
+    (300, 1, 1, 5, 128, 7),
+    (120, 2, 1, 3, 512, 7),
+]
+
+
+@pytest.mark.parametrize("A,P,C,T,N,K", TAPER_CASES)
+def test_kernel_taper_form_matches_oracle(A, P, C, T, N, K):
+    """EPIC_KERNEL_TAPER (point gridding, |W^|^2 applied to the image) equals the
+    literal gridding of the oracle for a shared, non-symmetric complex kernel."""
+    wl = synth.random_small(A=A, P=P, C=C, T=T, N=N, K=K, seed=A * 5 + N + K)
+    gpu, _ = run_gpu(wl, flags=epic.EPIC_KERNEL_TAPER)
+    ref = _oracle(wl)
+    assert peak_rel_err(gpu, ref, wl.grid_n, P).max() < FP32_TOL
+
+
+@pytest.mark.parametrize("flags", [epic.EPIC_MEAN, epic.EPIC_NO_AUTOSUB])
+def test_kernel_taper_with_flags(flags):
+    wl = synth.random_small(A=40, P=2, C=2, T=9, N=64, K=5, seed=55)
+    gpu, _ = run_gpu(wl, flags=flags | epic.EPIC_KERNEL_TAPER)
+    ref = _oracle(wl, flags=flags)
+    assert peak_rel_err(gpu, ref, wl.grid_n, 2).max() < FP32_TOL
+
+
+def test_kernel_taper_lwa_full_size_sampled_channels():
+    wl = synth.lwa()
+    gpu, p = run_gpu(wl, flags=epic.EPIC_KERNEL_TAPER)
+    chans = [5, 40]
+    ref = _oracle(wl, channels=chans)
+    got = np.concatenate([p.split(gpu)[c].ravel() for c in chans])
+    assert peak_rel_err(got, ref, wl.grid_n[chans], 2).max() < FP32_TOL

@@ -1,0 +1,60 @@
+"""Parity of the tensor-core form (tcgen05 column DFT-as-GEMM) with the FP64
+oracle, per operand precision: split FP16 within 1e-5 of the channel peak,
+single FP16 within 2e-3; the BF16 two-part split is reported and bounded."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2301_09662_gb300 import epic, synth
+
+from gpu_helpers import peak_rel_err, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+SPLIT_TOL = 1e-5
+FP16_TOL = 2e-3
+BF16_TOL = 1e-4
+
+
+def _cmp(wl, precision, flags=0, channels=None):
+    gpu, p = run_gpu(wl, precision=precision, flags=flags)
+    ref = oracle.workload_image(wl, flags=flags, channels=channels)
+    if channels is not None:
+        gpu = np.concatenate([p.split(gpu)[c].ravel() for c in channels])
+        return peak_rel_err(gpu, ref, wl.grid_n[channels], 2)
+    return peak_rel_err(gpu, ref, wl.grid_n, 2)
+
+
+def test_tensor_split_fp16_smallest_case():
+    wl = synth.random_small(A=24, P=2, C=1, T=2, N=64, K=3, seed=301)
+    assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16).max() < SPLIT_TOL
+
+
+@pytest.mark.parametrize("A,C,T,N,K", [(64, 2, 7, 64, 5), (256, 2, 6, 128, 5), (300, 1, 5, 128, 7),
+                                       (80, 1, 4, 256, 5)])
+def test_tensor_split_fp16(A, C, T, N, K):
+    wl = synth.random_small(A=A, P=2, C=C, T=T, N=N, K=K, seed=302 + A + N)
+    assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16).max() < SPLIT_TOL
+
+
+def test_tensor_single_fp16():
+    wl = synth.random_small(A=256, P=2, C=2, T=6, N=128, K=5, seed=310)
+    err = _cmp(wl, epic.EPIC_TC_FP16).max()
+    assert err < FP16_TOL
+    assert err > SPLIT_TOL        # the split is what buys the accuracy
+
+
+def test_tensor_split_bf16():
+    wl = synth.random_small(A=256, P=2, C=2, T=6, N=128, K=5, seed=311)
+    assert _cmp(wl, epic.EPIC_TC_SPLIT_BF16).max() < BF16_TOL
+
+
+def test_tensor_split_fp16_with_taper_and_flags():
+    wl = synth.random_small(A=120, P=2, C=2, T=9, N=128, K=5, seed=312)
+    for flags in (epic.EPIC_KERNEL_TAPER, epic.EPIC_MEAN, epic.EPIC_NO_AUTOSUB):
+        assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16, flags=flags).max() < SPLIT_TOL
+
+
+def test_tensor_lwa_full_size_sampled_channels():
+    wl = synth.lwa()
+    assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16, channels=[3, 60]).max() < SPLIT_TOL
