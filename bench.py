@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["lwa", "tiny", "uneven", "dense"], default="lwa")
-    ap.add_argument("--precision", choices=["fp32"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "tc_split_fp16", "tc_fp16", "tc_split_bf16"], default="fp32",
+                    help="arithmetic form of the timed plan (default: the FP32 form)")
+    ap.add_argument("--taper", action="store_true", help="apply the kernel as an image-domain taper")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     ap.add_argument("--no-variants", action="store_true", help="skip timing the other forms")
@@ -236,6 +238,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def tensor_roofline(wl, form, img_ms, peaks):
+    """Executed tensor FLOPs of the tensor-core imaging launch over its time:
+    per CTA (pixel class) and sample, 8 k-blocks x terms MMAs of 128 x 128 x 16."""
+    terms = 1 if form == "tc_fp16" else 3
+    n_items = sum((int(n) // 64) ** 2 for n in wl.grid_n)
+    flops = n_items * wl.T * 8 * terms * 2.0 * 128 * 128 * 16
+    ach = flops / (img_ms / 1e3) / 1e12
+    peak = float(peaks.get("bf16_tflops", 1892.1))
+    return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "executed_flops_per_launch": flops, "ms_per_launch": img_ms,
+            "peak_source": "MEASURED_PEAKS bf16_tflops burst (dense FP16 rate equals BF16)"}
+
+
 def time_variants(wl, v, g, out, flush, args, stream):
     """Other forms of the same integration, timed the same way (device events
     per step, L2 flushed between steps); same output up to rounding."""
@@ -280,17 +295,9 @@ def time_variants(wl, v, g, out, flush, args, stream):
         entry = {"value": wl.spectra / (step / 1e3), "unit": UNIT, "ms_per_step": step, "note": notes[name],
                  "stages_ms_last": stages}
         if name.startswith("tc_"):
-            # executed tensor FLOPs: per CTA and sample, 8 k-blocks x terms MMAs of 128 x 128 x 16
-            terms = 1 if name == "tc_fp16" else 3
-            n_items = sum((int(n) // 64) ** 2 for n in wl.grid_n)
-            flops = n_items * wl.T * 8 * terms * 2.0 * 128 * 128 * 16
             img = max((v for k, v in stages.items() if k.startswith("image[")), default=None)
             if img:
-                ach = flops / (img / 1e3) / 1e12
-                peak = float(peaks.get("bf16_tflops", 1892.1))
-                entry["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                                     "frac": ach / peak, "executed_flops_per_launch": flops,
-                                     "peak_source": "MEASURED_PEAKS bf16_tflops (dense FP16 rate = BF16 rate)"}
+                entry["roofline"] = tensor_roofline(wl, name.replace("_taper", ""), img, peaks)
         res[name] = entry
         p.close()
     return res
@@ -339,7 +346,9 @@ def run_ours(args):
             dist.barrier()
 
     wl = make_workload(args.workload, args.channels, rank)
-    plan = epic.Plan.from_workload(wl)
+    precision = {"fp32": epic.EPIC_FP32, "tc_split_fp16": epic.EPIC_TC_SPLIT_FP16, "tc_fp16": epic.EPIC_TC_FP16,
+                 "tc_split_bf16": epic.EPIC_TC_SPLIT_BF16}[args.precision]
+    plan = epic.Plan.from_workload(wl, precision=precision, flags=epic.EPIC_KERNEL_TAPER if args.taper else 0)
     v = torch.from_numpy(wl.v).cuda()
     g = None if wl.gains is None else torch.from_numpy(wl.gains).cuda()
     out = torch.empty(plan.out_floats // 2, dtype=torch.complex64, device="cuda")
@@ -401,16 +410,22 @@ def run_ours(args):
     if rec and rec[1] == kernel_source_hash():
         traffic = rec[0]
 
+    config = describe(wl, args.workload)
+    config["form"] = args.precision + (" + image-domain kernel taper" if args.taper else " (literal gridding)")
+    roofline = {"bound": "alu", "kernel": f"FP32 imaging kernel {image_stage}", "achieved": achieved,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                               f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS)",
+                "flops_per_launch": flops, "ms_per_launch": img_ms}
+    if args.precision != "fp32":
+        roofline = tensor_roofline(wl, args.precision, img_ms, peaks)
+        roofline["kernel"] = f"tensor-core imaging kernel {image_stage}"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded LWA-like layout, sky, noise, gains)",
-        "config": describe(wl, args.workload),
-        "roofline": {"bound": "alu", "kernel": f"FP32 imaging kernel {image_stage}", "achieved": achieved,
-                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                     "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
-                                    f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS)",
-                     "flops_per_launch": flops, "ms_per_launch": img_ms},
+        "config": config,
+        "roofline": roofline,
         "stages_ms": {n: s / args.steps for n, s in stage_sum.items()},
         "e2e": e2e,
         "clocks": clocks,

@@ -85,6 +85,10 @@ enum {
  * equals the default (literal gridding) form up to rounding, with K^2 times
  * fewer gridding operations. */
 #define EPIC_KERNEL_TAPER 4u
+/* Dual polarisation only: write Stokes I = XX + YY, Q = XX - YY, U = 2 Re XY,
+ * V = 2 Im XY (XY = F_X F_Y^*) as the four real images instead of the
+ * polarisation products. */
+#define EPIC_STOKES      8u
 
 /*
  * epic_plan -- validate the array geometry and build every table the imaging
@@ -103,7 +107,7 @@ enum {
  *   du_wavelengths cell size in wavelengths, 0 < du <= 0.5 (lambda/2 grid)
  *   max_spectra    largest n_spectra an epic_image call will pass (>= 0)
  *   precision      EPIC_FP32 or one of the EPIC_TC_* forms
- *   flags          EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER
+ *   flags          EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER | EPIC_STOKES
  *
  * Uses the current CUDA device.  Allocates device memory (tables and
  * workspace) and returns EPIC_ERR_NOMEM if that fails.  Returns
@@ -150,6 +154,21 @@ int epic_image(epic_plan_t plan, const uint8_t *ci4, const float *gains_c64,
  */
 int epic_image_host(epic_plan_t plan, const uint8_t *ci4_host, const float *gains_c64_host,
                     int n_spectra, float *out_c64_host, void *cuda_stream);
+
+/*
+ * epic_image_series -- time-resolved imaging for transient searches (the
+ * millisecond imaging of Sec. 1 and Sec. 4): n_spectra = n_img *
+ * spectra_per_image, and image i is the integration of spectra
+ * [i * spectra_per_image, (i + 1) * spectra_per_image) with its own
+ * autocorrelation subtraction (flags as for the plan; EPIC_MEAN divides by
+ * spectra_per_image).  out_c64 holds n_img consecutive outputs of
+ * epic_out_floats(plan) floats each.  Other arguments as for epic_image.
+ * Returns EPIC_ERR_ARG if n_spectra is not a multiple of spectra_per_image or
+ * exceeds max_spectra.  Asynchronous; allocates nothing; runs as direct
+ * launches (no graph).
+ */
+int epic_image_series(epic_plan_t plan, const uint8_t *ci4, const float *gains_c64,
+                      int n_spectra, int spectra_per_image, float *out_c64, void *cuda_stream);
 
 /* Number of floats of one epic_image output (2 per complex value), or 0 for a
  * NULL plan. */

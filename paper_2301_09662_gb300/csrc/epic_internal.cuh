@@ -38,6 +38,7 @@ struct GroupCfg {
     int rmax = 0;
     uint32_t *d_sched = nullptr;       // device: [n_chan][8 warps][rmax][32] segment descriptors
     int *d_nrounds = nullptr;          // device: [n_chan][8] rounds per warp
+    unsigned long long *d_rowmask = nullptr;  // device: [n_chan] folded rows touched by any footprint
 };
 
 struct KernelTables {
@@ -62,6 +63,8 @@ struct epic_plan_s {
     int *d_autoint = nullptr;          // [C][A][4] exact integer auto sums
     int *d_status = nullptr;           // sticky device status word
     std::vector<epic::GroupCfg> groups;
+    int force_tau = 0;                 // > 0: time chunks of the next launches (image series)
+    int series_cap = 1;                // images one series batch can hold (partials, auto sums)
     // stage timing (epic_set_profiling)
     bool profiling = false;
     std::vector<cudaEvent_t> events;   // 2 per recorded stage
@@ -103,6 +106,13 @@ int prepare_reg64(const epic_plan_s *plan, const GroupCfg &g);
 int launch_autopower(epic_plan_s *plan, const uint8_t *v, int T, cudaStream_t stream);
 int launch_epilogue(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T, int n_tau,
                     float2 *out, cudaStream_t stream);
+// image series: per-image auto sums and one epilogue image per time chunk
+int launch_autopower_series(epic_plan_s *plan, const uint8_t *v, int spi, int n_img, cudaStream_t stream);
+int launch_epilogue_series(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int spi, int n_img,
+                           float2 *out, cudaStream_t stream);
+// imaging kernel of one group (FP32 or tensor form as the plan says)
+int launch_imaging(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
+                   cudaStream_t stream);
 
 // tensor-core form (tc_col64.cu)
 size_t tc_smem_bytes(int A, int K);
@@ -117,7 +127,8 @@ int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
                  cudaStream_t stream);
 // Gridding schedule of the M = 64 kernel for the channels of one group (plan.cu).
 int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
-                         std::vector<uint32_t> &desc, std::vector<int> &nrounds, int &rmax);
+                         std::vector<uint32_t> &desc, std::vector<int> &nrounds, int &rmax,
+                         std::vector<unsigned long long> &rowmask);
 
 // One single-grid-side FP32 imaging job on caller-provided device tables and
 // workspace (used by the static-scratch entry point).

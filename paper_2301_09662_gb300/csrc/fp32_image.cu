@@ -302,7 +302,7 @@ int launch_group(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
 {
     auto kfn = fp32_image_kernel<M, P>;
     const size_t smem = smem_bytes<M, P>(plan->A, plan->K);
-    int n_tau = pick_tau(g.n_items, T, plan->sm_count);
+    int n_tau = plan->force_tau > 0 ? plan->force_tau : pick_tau(g.n_items, T, plan->sm_count);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));
@@ -382,6 +382,22 @@ int prepare_fp32(const epic_plan_s *plan, const GroupCfg &g)
     }
 }
 
+int launch_imaging(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
+                   cudaStream_t s)
+{
+    if (plan->precision != EPIC_FP32) return launch_tc(plan, g, v, gains, T, n_tau, s);
+    if (g.reg64) return launch_reg64(plan, g, v, gains, T, n_tau, s);
+    switch (g.M * 4 + plan->P) {
+    case 32 * 4 + 2: return launch_group<32, 2>(plan, g, v, gains, T, n_tau, s);
+    case 48 * 4 + 2: return launch_group<48, 2>(plan, g, v, gains, T, n_tau, s);
+    case 64 * 4 + 2: return launch_group<64, 2>(plan, g, v, gains, T, n_tau, s);
+    case 32 * 4 + 1: return launch_group<32, 1>(plan, g, v, gains, T, n_tau, s);
+    case 48 * 4 + 1: return launch_group<48, 1>(plan, g, v, gains, T, n_tau, s);
+    case 64 * 4 + 1: return launch_group<64, 1>(plan, g, v, gains, T, n_tau, s);
+    default: return EPIC_ERR_UNSUPPORTED;
+    }
+}
+
 // Launch every kernel of one integration.  With fork, the auto-power kernel
 // runs on `stream` while each grid side's imaging kernel runs on its own side
 // stream; each epilogue waits for its imaging kernel and for the auto-power,
@@ -413,25 +429,7 @@ int image_fp32(epic_plan_s *plan, const uint8_t *v, const float2 *gains, int T, 
         if (fork && cudaStreamWaitEvent(s, plan->ev_fork, 0) != cudaSuccess) return EPIC_ERR_CUDA;
         int n_tau = 1;
         prof_mark(plan, s, stage, true);
-        if (plan->precision != EPIC_FP32) {
-            rc = launch_tc(plan, g, v, gains, T, &n_tau, s);
-        } else if (g.reg64) {
-            rc = launch_reg64(plan, g, v, gains, T, &n_tau, s);
-        } else if (plan->P == 2) {
-            switch (g.M) {
-            case 32: rc = launch_group<32, 2>(plan, g, v, gains, T, &n_tau, s); break;
-            case 48: rc = launch_group<48, 2>(plan, g, v, gains, T, &n_tau, s); break;
-            case 64: rc = launch_group<64, 2>(plan, g, v, gains, T, &n_tau, s); break;
-            default: rc = EPIC_ERR_UNSUPPORTED;
-            }
-        } else {
-            switch (g.M) {
-            case 32: rc = launch_group<32, 1>(plan, g, v, gains, T, &n_tau, s); break;
-            case 48: rc = launch_group<48, 1>(plan, g, v, gains, T, &n_tau, s); break;
-            case 64: rc = launch_group<64, 1>(plan, g, v, gains, T, &n_tau, s); break;
-            default: rc = EPIC_ERR_UNSUPPORTED;
-            }
-        }
+        rc = launch_imaging(plan, g, v, gains, T, &n_tau, s);
         prof_mark(plan, s, stage++, false);
         if (rc != EPIC_OK) return rc;
         if (fork && autosub && cudaStreamWaitEvent(s, plan->ev_auto, 0) != cudaSuccess) return EPIC_ERR_CUDA;

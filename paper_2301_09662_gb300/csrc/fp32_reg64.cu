@@ -13,6 +13,8 @@
 //    so each axis costs one shared-memory read and one write;
 //  * two time samples per iteration share the schedule, the twiddles and the
 //    synchronisation.
+#include <type_traits>
+
 #include "epic_internal.cuh"
 #include "fft64.cuh"
 
@@ -34,16 +36,21 @@ struct Acc64;
 template <> struct Acc64<1> { using T = float; };
 template <> struct Acc64<2> { using T = float4; };
 
-// Grid buffers: G[ts][p][y][x] with x < 64 at stride S64.
-template <int P, int TS>
+// Grid buffers: G[ts][p][y][x] with x < 64 at stride S64.  KC > 0 fixes the
+// kernel side at compile time (the gridding loop then unrolls fully); KC = 0
+// takes it from K.  rowmask[ci] marks the folded rows any footprint touches:
+// the others stay zero and their row transforms are skipped.
+template <int P, int TS, int KC>
 __global__ void __launch_bounds__(kThreads, 1)
 fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
-                  const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K,
+                  const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K_rt,
                   const int *__restrict__ chans, const float2 *__restrict__ twN,
                   const uint32_t *__restrict__ sched, const int *__restrict__ nrounds, int rmax,
+                  const unsigned long long *__restrict__ rowmask,
                   int A, int C, int T, int N, int Q1, int n_items, int n_tau,
                   float *__restrict__ partial, int *__restrict__ status)
 {
+    const int K = KC > 0 ? KC : K_rt;
     constexpr int NPOS = M64 * M64 / kThreads;   // 16 pixels per thread
     constexpr int BUF = M64 * S64;               // one [y][x] plane
     extern __shared__ float4 smem_raw[];
@@ -65,6 +72,7 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     const int t1 = static_cast<int>(static_cast<long long>(T) * (tau + 1) / n_tau);
     const uint32_t *my_sched = sched + (static_cast<size_t>(ci) * 8 + warp) * rmax * 32;
     const int my_rounds = nrounds[ci * 8 + warp];
+    const unsigned long long rows_used = rowmask[ci];
 
     // ---- set-up: phase-folded gains and taps (class phase w_N^{k.h})
     for (int a = tid; a < A; a += kThreads) {
@@ -135,7 +143,8 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
 #pragma unroll
                     for (int p = 0; p < P; p++) e[ts][p] = es[ts * AP + a * P + p];
                 const float2 *wrow = tapw + dyi * K;
-                for (int dx = 0; dx < K; dx++) {
+#pragma unroll
+                for (int dx = 0; dx < (KC > 0 ? KC : K); dx++) {
                     const float2 w = wrow[dx];
                     const int x = (x0 + dx) & (M64 - 1);
 #pragma unroll
@@ -157,6 +166,7 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
 
         // ---- a4: rows then columns, one 64-point transform per thread
         for (int q = tid; q < TS * P * M64; q += kThreads) {
+            if (!((rows_used >> (q % M64)) & 1ull)) continue;   // empty row: stays zero
             float2 *line = G + (q / M64) * BUF + (q % M64) * S64;
             float2 x[64];
 #pragma unroll
@@ -224,26 +234,26 @@ size_t reg64_smem(int A, int K)
     return (b + 15) & ~static_cast<size_t>(15);
 }
 
-template <int P, int TS>
+template <int P, int TS, int KC>
 int launch_reg64_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau_out,
                    cudaStream_t stream)
 {
-    auto kfn = fp32_reg64_kernel<P, TS>;
+    auto kfn = fp32_reg64_kernel<P, TS, KC>;
     const size_t smem = reg64_smem<P, TS>(plan->A, plan->K);
-    int n_tau = fp32_pick_tau(g.n_items, T, plan->sm_count);
+    int n_tau = plan->force_tau > 0 ? plan->force_tau : fp32_pick_tau(g.n_items, T, plan->sm_count);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));
     kfn<<<grid, kThreads, smem, stream>>>(v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN,
-                                          g.d_sched, g.d_nrounds, g.rmax, plan->A, plan->C, T, g.N, g.Q1, g.n_items,
-                                          n_tau, g.d_partial, plan->d_status);
+                                          g.d_sched, g.d_nrounds, g.rmax, g.d_rowmask, plan->A, plan->C, T, g.N, g.Q1,
+                                          g.n_items, n_tau, g.d_partial, plan->d_status);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
-template <int P, int TS>
+template <int P, int TS, int KC>
 int prepare_reg64_t(const epic_plan_s *plan)
 {
-    auto kfn = fp32_reg64_kernel<P, TS>;
+    auto kfn = fp32_reg64_kernel<P, TS, KC>;
     const size_t smem = reg64_smem<P, TS>(plan->A, plan->K);
     return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) ==
                    cudaSuccess
@@ -251,12 +261,51 @@ int prepare_reg64_t(const epic_plan_s *plan)
                : EPIC_ERR_UNSUPPORTED;
 }
 
+// Which instantiation serves a plan: dual polarisation gets kernels specialised
+// for the kernel sides in use here (1: image-domain taper, 5: LWA-like,
+// 7: dense); anything else runs the generic loop.
+struct Reg64Key {
+    int P, TS, KC;
+};
+
+Reg64Key reg64_key(const epic_plan_s *plan, const GroupCfg &g)
+{
+    int kc = 0;
+    if (plan->P == 2 && (plan->K == 1 || plan->K == 5 || plan->K == 7)) kc = plan->K;
+    return {plan->P, g.ts, kc};
+}
+
+template <class F>
+int reg64_dispatch(const Reg64Key &k, F &&f)
+{
+    if (k.P == 2) {
+        if (k.TS == 2) {
+            switch (k.KC) {
+            case 1: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{}, std::integral_constant<int, 1>{});
+            case 5: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{}, std::integral_constant<int, 5>{});
+            case 7: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{}, std::integral_constant<int, 7>{});
+            default: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{}, std::integral_constant<int, 0>{});
+            }
+        }
+        switch (k.KC) {
+        case 1: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 1>{}, std::integral_constant<int, 1>{});
+        case 5: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 1>{}, std::integral_constant<int, 5>{});
+        case 7: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 1>{}, std::integral_constant<int, 7>{});
+        default: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 1>{}, std::integral_constant<int, 0>{});
+        }
+    }
+    if (k.TS == 2)
+        return f(std::integral_constant<int, 1>{}, std::integral_constant<int, 2>{}, std::integral_constant<int, 0>{});
+    return f(std::integral_constant<int, 1>{}, std::integral_constant<int, 1>{}, std::integral_constant<int, 0>{});
+}
+
 }  // namespace
 
 int prepare_reg64(const epic_plan_s *plan, const GroupCfg &g)
 {
-    if (plan->P == 2) return g.ts == 2 ? prepare_reg64_t<2, 2>(plan) : prepare_reg64_t<2, 1>(plan);
-    return g.ts == 2 ? prepare_reg64_t<1, 2>(plan) : prepare_reg64_t<1, 1>(plan);
+    return reg64_dispatch(reg64_key(plan, g), [&](auto p_, auto ts_, auto kc_) {
+        return prepare_reg64_t<decltype(p_)::value, decltype(ts_)::value, decltype(kc_)::value>(plan);
+    });
 }
 
 size_t reg64_smem_bytes(int P, int TS, int A, int K)
@@ -268,11 +317,10 @@ size_t reg64_smem_bytes(int P, int TS, int A, int K)
 int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                  cudaStream_t stream)
 {
-    if (plan->P == 2)
-        return g.ts == 2 ? launch_reg64_t<2, 2>(plan, g, v, gains, T, n_tau, stream)
-                         : launch_reg64_t<2, 1>(plan, g, v, gains, T, n_tau, stream);
-    return g.ts == 2 ? launch_reg64_t<1, 2>(plan, g, v, gains, T, n_tau, stream)
-                     : launch_reg64_t<1, 1>(plan, g, v, gains, T, n_tau, stream);
+    return reg64_dispatch(reg64_key(plan, g), [&](auto p_, auto ts_, auto kc_) {
+        return launch_reg64_t<decltype(p_)::value, decltype(ts_)::value, decltype(kc_)::value>(plan, g, v, gains, T,
+                                                                                                 n_tau, stream);
+    });
 }
 
 }  // namespace epic

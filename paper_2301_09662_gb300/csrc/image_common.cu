@@ -23,7 +23,7 @@ __device__ __forceinline__ void ci4_parts(uint32_t b, int &re, int &im)
 //   [0] sum |e_X|^2   [1] sum |e_Y|^2   [2] Re sum e_X e_Y^*   [3] Im sum e_X e_Y^*
 __global__ void __launch_bounds__(kThreads)
 autopower_kernel(const uint8_t *__restrict__ v, int T, int C, int A, int P, int n_chunks,
-                 int *__restrict__ autoint)
+                 size_t chunk_stride, int *__restrict__ autoint)
 {
     const int c = blockIdx.x;
     const int chunk = blockIdx.y;
@@ -44,7 +44,8 @@ autopower_kernel(const uint8_t *__restrict__ v, int T, int C, int A, int P, int 
                 sxyi += xi * yr - xr * yi;
             }
         }
-        int *dst = autoint + (static_cast<size_t>(c) * A + a) * 4;
+        // chunk_stride 0: every chunk adds into one sum; else one sum per chunk (image series)
+        int *dst = autoint + chunk * chunk_stride + (static_cast<size_t>(c) * A + a) * 4;
         atomicAdd(dst + 0, sxx);
         if (P == 2) {
             atomicAdd(dst + 1, syy);
@@ -63,8 +64,15 @@ __global__ void __launch_bounds__(kThreads)
 epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N, int Q1, int R1, int R2,
                 const int *__restrict__ chans, const long long *__restrict__ out_off,
                 const double *__restrict__ wpow, const int *__restrict__ autoint,
-                const float2 *__restrict__ gains, int A, int T, unsigned flags, float2 *__restrict__ out)
+                const float2 *__restrict__ gains, int A, int T, unsigned flags, float2 *__restrict__ out,
+                size_t auto_stride, long long out_stride)
 {
+    // blockIdx.z = image: it sums time chunks [z n_tau, (z + 1) n_tau) and uses
+    // the auto sums and output block of index z (one image unless a series)
+    const int img = blockIdx.z;
+    partial += static_cast<size_t>(img) * n_tau * n_items * (M * M) * (P == 2 ? 4 : 1);
+    autoint += img * auto_stride;
+    out += img * out_stride;
     constexpr int NPF = P == 2 ? 4 : 1;
     constexpr int NP = P == 2 ? 4 : 1;
     const int ci = blockIdx.y;
@@ -144,6 +152,12 @@ epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N
                 s[3] -= apq[3] * w;
             }
         }
+        if (P == 2 && (flags & EPIC_STOKES)) {
+            // I = XX + YY, Q = XX - YY, U = 2 Re XY, V = 2 Im XY
+            const double st[4] = {s[0] + s[1], s[0] - s[1], 2.0 * s[2], 2.0 * s[3]};
+            for (int k = 0; k < 4; k++) oc[k * NN + pix] = make_float2(static_cast<float>(st[k] * scale), 0.f);
+            continue;
+        }
         oc[pix] = make_float2(static_cast<float>(s[0] * scale), 0.f);
         if constexpr (NP == 4) {
             oc[NN + pix] = make_float2(static_cast<float>(s[1] * scale), 0.f);
@@ -163,7 +177,7 @@ int launch_epi(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T,
     epilogue_kernel<M, P><<<grid, kThreads, 0, stream>>>(g.d_partial, n_tau, g.n_items, g.N, g.Q1, g.R1, g.R2,
                                                          g.d_chans,
                                                          g.d_out_off, g.d_wpow, plan->d_autoint, gains, plan->A, T,
-                                                         plan->flags, out);
+                                                         plan->flags, out, 0, 0);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -176,7 +190,7 @@ int launch_epi_raw(const RawImage &r, const float2 *gains, float2 *out, cudaStre
     epilogue_kernel<M, P><<<grid, kThreads, 0, stream>>>(r.partial, r.n_tau, r.n_items, r.N, r.Q1, 8, M / 8,
                                                          r.chans,
                                                          r.out_off, r.wpow, r.autoint, gains, r.A, r.T, r.flags,
-                                                         out);
+                                                         out, 0, 0);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -189,7 +203,7 @@ int launch_autopower_raw(const RawImage &r, const uint8_t *v, int sm_count, cuda
     if (chunks > r.T) chunks = r.T;
     if (chunks < 1) chunks = 1;
     const dim3 grid(static_cast<unsigned>(r.C), static_cast<unsigned>(chunks));
-    autopower_kernel<<<grid, kThreads, 0, stream>>>(v, r.T, r.C, r.A, r.P, chunks, r.autoint);
+    autopower_kernel<<<grid, kThreads, 0, stream>>>(v, r.T, r.C, r.A, r.P, chunks, 0, r.autoint);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -206,6 +220,45 @@ int launch_epilogue_raw(const RawImage &r, const float2 *gains, float2 *out, cud
     }
 }
 
+template <int M, int P>
+int launch_epi_series(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int spi, int n_img, float2 *out,
+                      cudaStream_t stream)
+{
+    const int NN = g.N * g.N;
+    const int tiles = (NN + kThreads * 4 - 1) / (kThreads * 4);
+    const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(g.n_chan), static_cast<unsigned>(n_img));
+    epilogue_kernel<M, P><<<grid, kThreads, 0, stream>>>(g.d_partial, 1, g.n_items, g.N, g.Q1, g.R1, g.R2, g.d_chans,
+                                                         g.d_out_off, g.d_wpow, plan->d_autoint, gains, plan->A, spi,
+                                                         plan->flags, out,
+                                                         static_cast<size_t>(plan->C) * plan->A * 4,
+                                                         static_cast<long long>(plan->out_floats / 2));
+    return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
+int launch_autopower_series(epic_plan_s *plan, const uint8_t *v, int spi, int n_img, cudaStream_t stream)
+{
+    const size_t stride = static_cast<size_t>(plan->C) * plan->A * 4;
+    if (cudaMemsetAsync(plan->d_autoint, 0, stride * n_img * sizeof(int), stream) != cudaSuccess) return EPIC_ERR_CUDA;
+    const dim3 grid(static_cast<unsigned>(plan->C), static_cast<unsigned>(n_img));
+    autopower_kernel<<<grid, kThreads, 0, stream>>>(v, spi * n_img, plan->C, plan->A, plan->P, n_img, stride,
+                                                    plan->d_autoint);
+    return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
+int launch_epilogue_series(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int spi, int n_img,
+                           float2 *out, cudaStream_t stream)
+{
+    switch (g.M * 4 + plan->P) {
+    case 32 * 4 + 1: return launch_epi_series<32, 1>(plan, g, gains, spi, n_img, out, stream);
+    case 32 * 4 + 2: return launch_epi_series<32, 2>(plan, g, gains, spi, n_img, out, stream);
+    case 48 * 4 + 1: return launch_epi_series<48, 1>(plan, g, gains, spi, n_img, out, stream);
+    case 48 * 4 + 2: return launch_epi_series<48, 2>(plan, g, gains, spi, n_img, out, stream);
+    case 64 * 4 + 1: return launch_epi_series<64, 1>(plan, g, gains, spi, n_img, out, stream);
+    case 64 * 4 + 2: return launch_epi_series<64, 2>(plan, g, gains, spi, n_img, out, stream);
+    default: return EPIC_ERR_UNSUPPORTED;
+    }
+}
+
 int launch_autopower(epic_plan_s *plan, const uint8_t *v, int T, cudaStream_t stream)
 {
     const size_t n = static_cast<size_t>(plan->C) * plan->A * 4;
@@ -215,7 +268,7 @@ int launch_autopower(epic_plan_s *plan, const uint8_t *v, int T, cudaStream_t st
     if (chunks > T) chunks = T;
     if (chunks < 1) chunks = 1;
     const dim3 grid(static_cast<unsigned>(plan->C), static_cast<unsigned>(chunks));
-    autopower_kernel<<<grid, kThreads, 0, stream>>>(v, T, plan->C, plan->A, plan->P, chunks, plan->d_autoint);
+    autopower_kernel<<<grid, kThreads, 0, stream>>>(v, T, plan->C, plan->A, plan->P, chunks, 0, plan->d_autoint);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 

@@ -75,6 +75,7 @@ void free_plan(epic_plan_s *p)
         cudaFree(g.d_partial);
         cudaFree(g.d_sched);
         cudaFree(g.d_nrounds);
+        cudaFree(g.d_rowmask);
     }
     delete p;
 }
@@ -149,7 +150,8 @@ void host_kernel_power(const float *kern, int K, int N, std::vector<double> &out
 // at distinct (y + x) mod 16, which with the 65-float2 row stride puts every
 // lane of a half-warp on its own pair of banks for each of the K cells.
 int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
-                         std::vector<uint32_t> &desc, std::vector<int> &nrounds, int &rmax)
+                         std::vector<uint32_t> &desc, std::vector<int> &nrounds, int &rmax,
+                         std::vector<unsigned long long> &rowmask)
 {
     constexpr int M = 64, W = 8;
     const int h = (K - 1) / 2;
@@ -160,6 +162,7 @@ int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, const s
     };
     const int nc = static_cast<int>(chans.size());
     std::vector<std::vector<std::vector<Round>>> all(nc, std::vector<std::vector<Round>>(W));
+    rowmask.assign(nc, 0ull);
     rmax = 0;
     for (int ci = 0; ci < nc; ci++) {
         const int c = chans[ci];
@@ -172,6 +175,7 @@ int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, const s
             for (int dyi = 0; dyi < K; dyi++) {
                 const int y = ((jy + dyi - h) % M + M) % M;
                 const int w = y % W, res = (y + x0) % 16;
+                rowmask[ci] |= 1ull << y;
                 const uint32_t d = (1u << 31) | (static_cast<uint32_t>(x0) << 22) | (static_cast<uint32_t>(y) << 16) |
                                    (static_cast<uint32_t>(dyi) << 12) | static_cast<uint32_t>(a);
                 auto &rounds = all[ci][w];
@@ -305,7 +309,8 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     if (n_ant < 1 || (n_pol != 1 && n_pol != 2) || K < 1 || (K % 2) == 0 || K > epic::kMaxK ||
         n_chan < 1 || !(du > 0.0) || du > 0.5 || max_spectra < 0)
         return EPIC_ERR_ARG;
-    if (flags & ~(EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER)) return EPIC_ERR_ARG;
+    if (flags & ~(EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER | EPIC_STOKES)) return EPIC_ERR_ARG;
+    if ((flags & EPIC_STOKES) && n_pol != 2) return EPIC_ERR_ARG;
     if (precision < EPIC_FP32 || precision > EPIC_TC_SPLIT_BF16) return EPIC_ERR_ARG;
     const bool tensor = precision != EPIC_FP32;
     if (tensor) {
@@ -379,7 +384,7 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     if (rc == EPIC_OK)
         rc = taper ? dev_upload(&p->d_kernel, reinterpret_cast<const float2 *>(unit_tap), 1)
                    : dev_upload(&p->d_kernel, reinterpret_cast<const float2 *>(kernel_c64), static_cast<size_t>(K) * K);
-    if (rc == EPIC_OK) rc = dev_upload(&p->d_autoint, static_cast<const int *>(nullptr), static_cast<size_t>(n_chan) * n_ant * 4);
+
     if (rc == EPIC_OK) rc = dev_upload(&p->d_status, static_cast<const int *>(nullptr), 1);
     if (rc == EPIC_OK && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) rc = EPIC_ERR_CUDA;
 
@@ -429,9 +434,11 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
             g.R2 = 64;
             std::vector<uint32_t> desc;
             std::vector<int> nr;
-            rc = epic::build_reg64_schedule(cells, n_ant, p->K, g.chans, desc, nr, g.rmax);
+            std::vector<unsigned long long> rows;
+            rc = epic::build_reg64_schedule(cells, n_ant, p->K, g.chans, desc, nr, g.rmax, rows);
             if (rc == EPIC_OK) rc = dev_upload(&g.d_sched, desc.data(), desc.size());
             if (rc == EPIC_OK) rc = dev_upload(&g.d_nrounds, nr.data(), nr.size());
+            if (rc == EPIC_OK) rc = dev_upload(&g.d_rowmask, rows.data(), rows.size());
         }
         if (rc == EPIC_OK) rc = dev_upload(&g.d_chans, g.chans.data(), g.chans.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_out_off, offs.data(), offs.size());
@@ -442,6 +449,13 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                             static_cast<size_t>(g.tau_cap) * g.n_items * g.M * g.M * npf);
         p->groups.push_back(g);
     }
+    // exact auto sums: one set per image of a series batch (slot 0 for epic_image)
+    p->series_cap = epic::kMaxTau;
+    for (const auto &g : p->groups) p->series_cap = std::min(p->series_cap, g.tau_cap);
+    p->series_cap = std::max(p->series_cap, 1);
+    if (rc == EPIC_OK)
+        rc = dev_upload(&p->d_autoint, static_cast<const int *>(nullptr),
+                        static_cast<size_t>(p->series_cap) * n_chan * n_ant * 4);
     if (rc == EPIC_OK && tensor) {
         std::vector<uint16_t> ops;
         epic::build_dft_operand(precision == EPIC_TC_SPLIT_BF16, ops);
@@ -495,6 +509,36 @@ int epic_image(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_s
     auto s = static_cast<cudaStream_t>(stream);
     return epic::run_image(plan, ci4, reinterpret_cast<const float2 *>(gains), n_spectra,
                            reinterpret_cast<float2 *>(out), s);
+}
+
+int epic_image_series(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra, int spi, float *out,
+                      void *stream)
+{
+    if (!plan || !out || spi < 1) return EPIC_ERR_ARG;
+    if (n_spectra < 0 || n_spectra > plan->max_spectra || n_spectra % spi != 0) return EPIC_ERR_ARG;
+    if (n_spectra > 0 && !ci4) return EPIC_ERR_ARG;
+    auto s = static_cast<cudaStream_t>(stream);
+    const int n_img = n_spectra / spi;
+    const size_t img_floats = plan->out_floats;
+    const size_t row_bytes = static_cast<size_t>(plan->C) * plan->A * plan->P;
+    auto *out2 = reinterpret_cast<float2 *>(out);
+    const auto *g2 = reinterpret_cast<const float2 *>(gains);
+    int rc = EPIC_OK;
+    for (int i0 = 0; i0 < n_img && rc == EPIC_OK; i0 += plan->series_cap) {
+        const int b = std::min(plan->series_cap, n_img - i0);
+        const uint8_t *vb = ci4 + static_cast<size_t>(i0) * spi * row_bytes;
+        float2 *ob = out2 + static_cast<size_t>(i0) * (img_floats / 2);
+        if (!(plan->flags & EPIC_NO_AUTOSUB)) rc = epic::launch_autopower_series(plan, vb, spi, b, s);
+        plan->force_tau = b;   // one time chunk per image
+        for (const auto &g : plan->groups) {
+            if (rc != EPIC_OK) break;
+            int n_tau = 0;
+            rc = epic::launch_imaging(plan, g, vb, g2, spi * b, &n_tau, s);
+            if (rc == EPIC_OK) rc = epic::launch_epilogue_series(plan, g, g2, spi, b, ob, s);
+        }
+        plan->force_tau = 0;
+    }
+    return rc;
 }
 
 int epic_image_host(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra,

@@ -155,8 +155,9 @@ tc_col64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
         float wsum = 0.f;
         for (int i = 0; i < KK; i++) wsum += sqrtf(tapw[i].x * tapw[i].x + tapw[i].y * tapw[i].y);
         const float bound = 2.f * static_cast<float>(A) * 11.3137085f * gm * wsum;
-        if (bound > 0.f) scale = exp2f(floorf(log2f(16384.f / bound)));
-        scale = fminf(fmaxf(scale, 0x1p-40f), 0x1p40f);
+        int e2 = 0;
+        if (bound > 0.f) e2 = static_cast<int>(floorf(log2f(16384.f / bound)));
+        scale = ldexpf(1.f, max(-40, min(40, e2)));   // an exact power of two
     }
     for (int i = tid; i < AP; i += kThreads) gp[i] = cscale(gp[i], scale);
     if (tid == 0) {
@@ -390,7 +391,7 @@ template <int VAR>
 int launch_tc_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau_out,
                 cudaStream_t stream)
 {
-    int n_tau = fp32_pick_tau(g.n_items, T, plan->sm_count);
+    int n_tau = plan->force_tau > 0 ? plan->force_tau : fp32_pick_tau(g.n_items, T, plan->sm_count);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));

@@ -32,12 +32,15 @@ EPIC_TC_SPLIT_BF16 = 3
 EPIC_MEAN = 1
 EPIC_NO_AUTOSUB = 2
 EPIC_KERNEL_TAPER = 4
+EPIC_STOKES = 8
+STOKES = ("I", "Q", "U", "V")
 
 PRODUCTS = ("XX", "YY", "XY", "YX")
 
 #: every symbol include/epic.h declares
 EXPORTS = ("epic_plan", "epic_image", "epic_image_host", "epic_out_floats", "epic_status",
-           "epic_set_profiling", "epic_stage_times", "epic_image_static", "epic_destroy", "epic_strerror")
+           "epic_set_profiling", "epic_stage_times", "epic_image_static", "epic_image_series", "epic_destroy",
+           "epic_strerror")
 
 _lib = None
 
@@ -63,6 +66,8 @@ def load():
     L.epic_image.argtypes = [vp, vp, vp, i, vp, vp]
     L.epic_image.restype = i
     L.epic_image_host.argtypes = [vp, vp, vp, i, vp, vp]
+    L.epic_image_series.argtypes = [vp, vp, vp, i, i, vp, vp]
+    L.epic_image_series.restype = i
     L.epic_image_host.restype = i
     L.epic_out_floats.argtypes = [vp]
     L.epic_out_floats.restype = ctypes.c_size_t
@@ -166,6 +171,22 @@ class Plan:
         rc = load().epic_image(self._h, v.data_ptr(), gains.data_ptr() if gains is not None else None,
                                int(v.shape[0]), out.data_ptr(), self._stream(stream))
         _check(rc, "epic_image")
+        return out
+
+    def image_series(self, v, spectra_per_image, gains=None, out=None, stream=None):
+        """Time-resolved images: one image per block of spectra_per_image spectra
+        (epic_image_series); returns a [n_img, out_floats/2] complex64 tensor."""
+        import torch
+        self._check_inputs(v, gains, device=True)
+        T = int(v.shape[0])
+        if spectra_per_image < 1 or T % spectra_per_image:
+            raise ValueError("n_spectra must be a positive multiple of spectra_per_image")
+        n_img = T // spectra_per_image
+        if out is None:
+            out = torch.empty((n_img, self.out_floats // 2), dtype=torch.complex64, device=v.device)
+        rc = load().epic_image_series(self._h, v.data_ptr(), gains.data_ptr() if gains is not None else None, T,
+                                      int(spectra_per_image), out.data_ptr(), self._stream(stream))
+        _check(rc, "epic_image_series")
         return out
 
     def image_host(self, v, gains=None, out=None, stream=None):

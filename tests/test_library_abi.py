@@ -55,7 +55,8 @@ def _geom(**kw):
     (dict(du=0.0), epic.EPIC_ERR_ARG),
     (dict(du=0.75), epic.EPIC_ERR_ARG),
     (dict(max_spectra=-1), epic.EPIC_ERR_ARG),
-    (dict(flags=8), epic.EPIC_ERR_ARG),
+    (dict(flags=64), epic.EPIC_ERR_ARG),
+    (dict(flags=epic.EPIC_STOKES, n_pol=1), epic.EPIC_ERR_ARG),
     (dict(precision=9), epic.EPIC_ERR_ARG),
     (dict(grid_n=np.array([32, 40], np.int32)), epic.EPIC_ERR_UNSUPPORTED),
     (dict(freq_hz=np.array([50e6, -1.0])), epic.EPIC_ERR_ARG),
