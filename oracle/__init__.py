@@ -12,6 +12,7 @@ readings of points the paper leaves open):
   fft1d / ifft2   the oracle's own mixed-radix FFT (Eq. 4's FT^-1)
   epic_direct     O1, Eq. 4 with the block chain of Sec. 2.2
   epic_fx         O2, Eq. 1-3 (FX correlator + gridding with W (x) W^*)
+                  (both take one [K][K] kernel or per-antenna [A][K][K] kernels, Eq. 3)
   grid_energy     sum_t sum_k |G_p(k, t)|^2 with O1's gridding (Parseval pin)
 """
 from __future__ import annotations
@@ -59,9 +60,9 @@ def lib():
             L.oracle_ifft2.argtypes = [P, i]
             for name in ("oracle_epic_direct", "oracle_epic_fx"):
                 f = getattr(L, name)
-                f.argtypes = [P, P, i, i, i, i, P, P, P, i, ctypes.c_uint, P]
+                f.argtypes = [P, P, i, i, i, i, P, P, P, i, i, ctypes.c_uint, P]
                 f.restype = i
-            L.oracle_grid_energy.argtypes = [P, P, i, i, i, i, P, P, P, i, P]
+            L.oracle_grid_energy.argtypes = [P, P, i, i, i, i, P, P, P, i, i, P]
             L.oracle_grid_energy.restype = i
             L.oracle_threads.restype = i
             _lib = L
@@ -113,12 +114,15 @@ def ifft2(g) -> np.ndarray:
 
 
 def _common(v, gains, cells, grid_n, W):
+    """W is [K][K] (one kernel) or [A][K][K] (one kernel per antenna)."""
     v = np.ascontiguousarray(v, np.uint8)
     T, C, A, P = v.shape
     g = None if gains is None else np.ascontiguousarray(gains, np.complex128)
     cells = np.ascontiguousarray(cells, np.int32)
     n = np.ascontiguousarray(grid_n, np.int32)
     w = np.ascontiguousarray(W, np.complex128)
+    if w.ndim == 3 and w.shape[0] != A:
+        raise ValueError("per-antenna kernels must be [A][K][K]")
     return v, g, cells, n, w, T, C, A, P
 
 
@@ -142,7 +146,7 @@ def _run(name, v, gains, cells, grid_n, W, flags):
     v, g, cells, n, w, T, C, A, P = _common(v, gains, cells, grid_n, W)
     out = np.zeros(out_size(n, P), np.complex128)
     rc = getattr(lib(), name)(_ptr(v), _ptr(g), T, C, A, P, _ptr(cells), _ptr(n), _ptr(w),
-                              w.shape[0], int(flags), _ptr(out))
+                              w.shape[-1], int(w.ndim == 3), int(flags), _ptr(out))
     if rc:
         raise ValueError(f"{name}: bad arguments")
     return out
@@ -162,7 +166,7 @@ def grid_energy(v, gains, cells, grid_n, W) -> np.ndarray:
     v, g, cells, n, w, T, C, A, P = _common(v, gains, cells, grid_n, W)
     out = np.zeros((C, P), np.float64)
     rc = lib().oracle_grid_energy(_ptr(v), _ptr(g), T, C, A, P, _ptr(cells), _ptr(n), _ptr(w),
-                                  w.shape[0], _ptr(out))
+                                  w.shape[-1], int(w.ndim == 3), _ptr(out))
     if rc:
         raise ValueError("oracle_grid_energy: bad arguments")
     return out

@@ -41,6 +41,10 @@
  *   - antenna -> cell map (Sec. 3.1, nearest neighbour on a grid of spacing
  *     du wavelengths): k = llround(((x - x_c) f) / (c0 du)) + N/2 per axis,
  *     x_c the centroid of the layout.
+ *   - per-antenna kernels (Eq. 3 writes W_a; Sec. 3.1 A-projection): with
+ *     kernels_per_antenna != 0 the kernel array is [A][K][K] and antenna a
+ *     grids through W_a; the auto term becomes sum_a A_a,pq |W^_a(l)|^2 and
+ *     the FX route grids pair (a, b) with B_ab(rho) = sum_d W_a(d) W_b^*(d - rho).
  */
 #include <complex.h>
 #include <math.h>
@@ -248,6 +252,52 @@ static void auto_power(const uint8_t *v, const cplx *g, int T, int C, int A, int
     }
 }
 
+/* kernel tap of antenna a at offset (dy, dx) */
+static inline cplx wtap(const cplx *W, int K, int per_antenna, int a, int dy, int dx)
+{
+    int h = (K - 1) / 2;
+    return W[((size_t)(per_antenna ? a : 0) * K + (dy + h)) * K + (dx + h)];
+}
+
+/* per-antenna auto sums A_a,pq = g_ap g_aq^* sum_t e_ap e_aq^* (inner sum exact in int64) */
+static void auto_power_antenna(const uint8_t *v, const cplx *g, int T, int C, int A, int P, int c, int a,
+                               cplx *Apq /* [P][P] */)
+{
+    for (int p = 0; p < P; p++)
+        for (int q = 0; q < P; q++) {
+            long long sre = 0, sim = 0;
+            for (int t = 0; t < T; t++) {
+                int rp, ip, rq, iq;
+                oracle_ci4_unpack(v[(((size_t)t * C + c) * A + a) * P + p], &rp, &ip);
+                oracle_ci4_unpack(v[(((size_t)t * C + c) * A + a) * P + q], &rq, &iq);
+                sre += (long long)rp * rq + (long long)ip * iq;
+                sim += (long long)ip * rq - (long long)rp * iq;
+            }
+            cplx gp = g ? g[((size_t)c * A + a) * P + p] : 1.0;
+            cplx gq = g ? g[((size_t)c * A + a) * P + q] : 1.0;
+            Apq[p * P + q] = gp * conj(gq) * ((double)sre + I * (double)sim);
+        }
+}
+
+/* auto image sum_a A_a,pq |W^_a(l)|^2 on the shifted layout, per product */
+static void auto_image(const uint8_t *v, const cplx *g, int T, int C, int A, int P, int c,
+                       const double *W_il, int K, int per_antenna, int N, int NP, cplx *out /* [NP][N][N] */)
+{
+    static const int PQP[4] = {0, 1, 0, 1}, PQQ[4] = {0, 1, 1, 0};
+    size_t NN = (size_t)N * N;
+    double *Wp = malloc(sizeof(double) * NN);
+    for (size_t i = 0; i < (size_t)NP * NN; i++) out[i] = 0;
+    for (int a = 0; a < (per_antenna ? A : 1); a++) {
+        cplx Apq[4];
+        if (per_antenna) auto_power_antenna(v, g, T, C, A, P, c, a, Apq);
+        else auto_power(v, g, T, C, A, P, c, Apq);
+        oracle_kernel_power(W_il + (size_t)(per_antenna ? a : 0) * K * K * 2, K, N, Wp);
+        for (int pq = 0; pq < NP; pq++)
+            for (size_t i = 0; i < NN; i++) out[(size_t)pq * NN + i] += Apq[PQP[pq] * P + PQQ[pq]] * Wp[i];
+    }
+    free(Wp);
+}
+
 /* product index -> (p, q): XX, YY, XY, YX */
 static const int PQ_P[4] = {0, 1, 0, 1};
 static const int PQ_Q[4] = {0, 1, 1, 0};
@@ -256,7 +306,7 @@ static const int PQ_Q[4] = {0, 1, 1, 0};
 
 int oracle_epic_direct(const uint8_t *v, const double *gains_il, int T, int C, int A, int P,
                        const int *cells, const int *grid_n, const double *W_il, int K,
-                       unsigned flags, double *out_il)
+                       int per_antenna, unsigned flags, double *out_il)
 {
     if (check_args(T, C, A, P, K, grid_n)) return -1;
     const cplx *g = (const cplx *)gains_il;
@@ -287,7 +337,7 @@ int oracle_epic_direct(const uint8_t *v, const double *gains_il, int T, int C, i
                     int ky = cells[((size_t)c * A + a) * 2 + 1];
                     for (int dy = -h; dy <= h; dy++)
                         for (int dx = -h; dx <= h; dx++)
-                            Gp[(size_t)wrap(ky + dy, N) * N + wrap(kx + dx, N)] += W[(dy + h) * K + (dx + h)] * e;
+                            Gp[(size_t)wrap(ky + dy, N) * N + wrap(kx + dx, N)] += wtap(W, K, per_antenna, a, dy, dx) * e;
                 }
                 /* a4: inverse transform to the sky */
                 ifft2(&ctx, Gp, buf);
@@ -301,21 +351,20 @@ int oracle_epic_direct(const uint8_t *v, const double *gains_il, int T, int C, i
             }
         }
         /* a7-a8: autocorrelation term and shifted output */
-        cplx Apq[4];
-        auto_power(v, g, T, C, A, P, c, Apq);
-        oracle_kernel_power(W_il, K, N, Wp);
+        cplx *autos = malloc(sizeof(cplx) * (size_t)NP * NN);
+        auto_image(v, g, T, C, A, P, c, W_il, K, per_antenna, N, NP, autos);
         cplx *oc = out + channel_offset(grid_n, c, NP);
         double scale = ((flags & ORACLE_MEAN) && T > 0) ? 1.0 / T : 1.0;
         for (int pq = 0; pq < NP; pq++) {
-            cplx a = Apq[PQ_P[pq] * P + PQ_Q[pq]];
             for (int i = 0; i < N; i++)
                 for (int j = 0; j < N; j++) {
                     int fy = wrap(i - N / 2, N), fx = wrap(j - N / 2, N);
                     cplx val = S[(size_t)pq * NN + (size_t)fy * N + fx];
-                    if (!(flags & ORACLE_NO_AUTOSUB)) val -= a * Wp[(size_t)i * N + j];
+                    if (!(flags & ORACLE_NO_AUTOSUB)) val -= autos[(size_t)pq * NN + (size_t)i * N + j];
                     oc[(size_t)pq * NN + (size_t)i * N + j] = val * scale;
                 }
         }
+        free(autos);
         free(G); free(S); free(buf); free(Wp); free(tw);
     }
     return 0;
@@ -325,7 +374,7 @@ int oracle_epic_direct(const uint8_t *v, const double *gains_il, int T, int C, i
  * the Parseval pin. */
 int oracle_grid_energy(const uint8_t *v, const double *gains_il, int T, int C, int A, int P,
                        const int *cells, const int *grid_n, const double *W_il, int K,
-                       double *energy /* [C][P] */)
+                       int per_antenna, double *energy /* [C][P] */)
 {
     if (check_args(T, C, A, P, K, grid_n)) return -1;
     const cplx *g = (const cplx *)gains_il;
@@ -346,7 +395,7 @@ int oracle_grid_energy(const uint8_t *v, const double *gains_il, int T, int C, i
                     int ky = cells[((size_t)c * A + a) * 2 + 1];
                     for (int dy = -h; dy <= h; dy++)
                         for (int dx = -h; dx <= h; dx++)
-                            G[(size_t)wrap(ky + dy, N) * N + wrap(kx + dx, N)] += W[(dy + h) * K + (dx + h)] * e;
+                            G[(size_t)wrap(ky + dy, N) * N + wrap(kx + dx, N)] += wtap(W, K, per_antenna, a, dy, dx) * e;
                 }
                 for (size_t i = 0; i < NN; i++) e_sum += creal(G[i]) * creal(G[i]) + cimag(G[i]) * cimag(G[i]);
             }
@@ -361,7 +410,7 @@ int oracle_grid_energy(const uint8_t *v, const double *gains_il, int T, int C, i
 
 int oracle_epic_fx(const uint8_t *v, const double *gains_il, int T, int C, int A, int P,
                    const int *cells, const int *grid_n, const double *W_il, int K,
-                   unsigned flags, double *out_il)
+                   int per_antenna, unsigned flags, double *out_il)
 {
     if (check_args(T, C, A, P, K, grid_n)) return -1;
     const cplx *g = (const cplx *)gains_il;
@@ -371,19 +420,22 @@ int oracle_epic_fx(const uint8_t *v, const double *gains_il, int T, int C, int A
     int h = (K - 1) / 2;
     int R = 2 * K - 1;              /* baseline kernel support, rho in [-(K-1), K-1]^2 */
 
-    /* baseline kernel B(rho) = sum_d W(d) W^*(d - rho) */
-    cplx *B = calloc((size_t)R * R, sizeof(cplx));
-    for (int ry = -(K - 1); ry <= K - 1; ry++)
-        for (int rx = -(K - 1); rx <= K - 1; rx++) {
-            cplx s = 0;
-            for (int dy = -h; dy <= h; dy++)
-                for (int dx = -h; dx <= h; dx++) {
-                    int ey = dy - ry, ex = dx - rx;
-                    if (ey < -h || ey > h || ex < -h || ex > h) continue;
-                    s += W[(dy + h) * K + (dx + h)] * conj(W[(ey + h) * K + (ex + h)]);
+    /* baseline kernel B_ab(rho) = sum_d W_a(d) W_b^*(d - rho); one kernel for all pairs unless per antenna */
+    int nk = per_antenna ? A : 1;
+    cplx *B = calloc((size_t)nk * nk * R * R, sizeof(cplx));
+    for (int ka = 0; ka < nk; ka++)
+        for (int kb = 0; kb < nk; kb++)
+            for (int ry = -(K - 1); ry <= K - 1; ry++)
+                for (int rx = -(K - 1); rx <= K - 1; rx++) {
+                    cplx s = 0;
+                    for (int dy = -h; dy <= h; dy++)
+                        for (int dx = -h; dx <= h; dx++) {
+                            int ey = dy - ry, ex = dx - rx;
+                            if (ey < -h || ey > h || ex < -h || ex > h) continue;
+                            s += wtap(W, K, 1, ka, dy, dx) * conj(wtap(W, K, 1, kb, ey, ex));
+                        }
+                    B[(((size_t)ka * nk + kb) * R + (ry + K - 1)) * R + (rx + K - 1)] = s;
                 }
-            B[(ry + K - 1) * R + (rx + K - 1)] = s;
-        }
 
 #pragma omp parallel for schedule(dynamic, 1)
     for (int c = 0; c < C; c++) {
@@ -423,10 +475,11 @@ int oracle_epic_fx(const uint8_t *v, const double *gains_il, int T, int C, int A
                     cplx gb = g ? g[((size_t)c * A + b) * P + q] : 1.0;
                     cplx Vc = ga * conj(gb) * Vab;
                     cplx *Vp = Vg + (size_t)pq * NN;
+                    const cplx *Bab = B + ((size_t)(per_antenna ? a : 0) * nk + (per_antenna ? b : 0)) * R * R;
                     for (int ry = -(K - 1); ry <= K - 1; ry++)
                         for (int rx = -(K - 1); rx <= K - 1; rx++)
                             Vp[(size_t)wrap(dy0 + ry, N) * N + wrap(dx0 + rx, N)] +=
-                                Vc * B[(ry + K - 1) * R + (rx + K - 1)];
+                                Vc * Bab[(ry + K - 1) * R + (rx + K - 1)];
                 }
             }
         /* inverse transform by direct separable DFT with an exact-index twiddle table */
@@ -438,14 +491,11 @@ int oracle_epic_fx(const uint8_t *v, const double *gains_il, int T, int C, int A
         cplx *tmp = malloc(sizeof(cplx) * NN);
         cplx *oc = out + channel_offset(grid_n, c, NP);
         double scale = ((flags & ORACLE_MEAN) && T > 0) ? 1.0 / T : 1.0;
-        cplx *Apq = NULL;
-        double *Wp = NULL;
+        cplx *autos = NULL;
         if (flags & ORACLE_NO_AUTOSUB) {
             /* put the autos back (the direct form keeps them without subtraction) */
-            Apq = malloc(sizeof(cplx) * 4);
-            Wp = malloc(sizeof(double) * NN);
-            auto_power(v, g, T, C, A, P, c, Apq);
-            oracle_kernel_power(W_il, K, N, Wp);
+            autos = malloc(sizeof(cplx) * (size_t)NP * NN);
+            auto_image(v, g, T, C, A, P, c, W_il, K, per_antenna, N, NP, autos);
         }
         for (int pq = 0; pq < NP; pq++) {
             const cplx *Vp = Vg + (size_t)pq * NN;
@@ -463,12 +513,12 @@ int oracle_epic_fx(const uint8_t *v, const double *gains_il, int T, int C, int A
                     int lx = wrap(j - N / 2, N);
                     cplx s = 0;
                     for (int ky = 0; ky < N; ky++) s += tmp[(size_t)ky * N + lx] * tw[((long)ky * ly) % N];
-                    if (Apq) s += Apq[PQ_P[pq] * P + PQ_Q[pq]] * Wp[(size_t)i * N + j];
+                    if (autos) s += autos[(size_t)pq * NN + (size_t)i * N + j];
                     oc[(size_t)pq * NN + (size_t)i * N + j] = s * scale;
                 }
             }
         }
-        free(Apq); free(Wp);
+        free(autos);
         free(Vre); free(Vim); free(er); free(ei); free(Vg); free(tw); free(tmp);
     }
     free(B);

@@ -102,6 +102,22 @@ def gaussian_kernel(K: int) -> np.ndarray:
     return w.astype(np.complex64)
 
 
+def antenna_kernels(A: int, K: int, rng: np.random.Generator) -> np.ndarray:
+    """Per-antenna kernels complex64 [A][K][K]: Gaussians whose width varies by
+    +-20 % between antennas, with a small random phase gradient (heterogeneous
+    beams / A-projection), each normalised to sum 1 in amplitude."""
+    h = (K - 1) // 2
+    d = np.arange(-h, h + 1, dtype=np.float64)
+    out = np.empty((A, K, K), np.complex64)
+    for a in range(A):
+        sigma = max((K - 1) / 4.0, 0.5) * rng.uniform(0.8, 1.2)
+        w = np.exp(-(d[:, None] ** 2 + d[None, :] ** 2) / (2 * sigma ** 2))
+        w /= w.sum()
+        gx, gy = rng.uniform(-0.3, 0.3, 2)
+        out[a] = w * np.exp(1j * (gx * d[None, :] + gy * d[:, None]))
+    return out
+
+
 def random_gains(C: int, A: int, P: int, rng: np.random.Generator) -> np.ndarray:
     """complex64 [C][A][P] with |g| ~ U[0.8, 1.2] and arg g ~ U[0, 2 pi)."""
     amp = rng.uniform(0.8, 1.2, size=(C, A, P))

@@ -291,3 +291,64 @@ def test_p8_mean_flag_and_empty(base_case):
     assert rel_err(om * wl.T, o) < 1e-14
     oe = oracle.epic_direct(wl.v[:0], wl.gains, cells, wl.grid_n, wl.kernel)
     assert np.all(oe == 0)
+
+
+# ------------------------------------------------------------------ per-antenna kernels (Eq. 3, W_a)
+
+def beamformer_image_ak(v, g, cells, N, Wa):
+    """Brute-force Eq. 4 with one kernel per antenna:
+    F(l) = sum_a e~_a W^_a(l) exp(2 pi i k_a.l/N); autos = sum_a |e~_a|^2 |W^_a|^2."""
+    T, A, P = v.shape
+    e = unpack_np(v) * g[None]
+    l = np.arange(N) - N // 2
+    ph_x = np.exp(2j * np.pi * np.outer(cells[:, 0], l) / N)
+    ph_y = np.exp(2j * np.pi * np.outer(cells[:, 1], l) / N)
+    Wh = np.array([what(Wa[a], N) for a in range(A)])                 # [a][i][j]
+    F = np.einsum("tap,ai,aj,aij->tpij", e, ph_y, ph_x, Wh)
+    out = []
+    for p, q in [(0, 0), (1, 1), (0, 1), (1, 0)]:
+        s = np.sum(F[:, p] * np.conj(F[:, q]), axis=0)
+        auto = np.einsum("ta,aij->ij", e[:, :, p] * np.conj(e[:, :, q]), np.abs(Wh) ** 2)
+        out.append(s - auto)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("A,K,N", [(3, 3, 16), (5, 5, 16), (7, 3, 32)])
+def test_antenna_kernels_direct_equals_fx(A, K, N):
+    wl = synth.random_small(A=A, P=2, C=2, T=5, N=N, K=K, seed=900 + A)
+    Wa = synth.antenna_kernels(A, K, np.random.default_rng(A))
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    o1 = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, Wa)
+    o2 = oracle.epic_fx(wl.v, wl.gains, cells, wl.grid_n, Wa)
+    assert rel_err(o1, o2) < 1e-12
+    raw1 = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, Wa, oracle.NO_AUTOSUB)
+    raw2 = oracle.epic_fx(wl.v, wl.gains, cells, wl.grid_n, Wa, oracle.NO_AUTOSUB)
+    assert rel_err(raw1, raw2) < 1e-12
+
+
+def test_antenna_kernels_brute_force_beamformer():
+    A, K, N = 6, 5, 32
+    wl = synth.random_small(A=A, P=2, C=1, T=4, N=N, K=K, seed=910)
+    Wa = synth.antenna_kernels(A, K, np.random.default_rng(1))
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    o = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, Wa).reshape(4, N, N)
+    ref = beamformer_image_ak(wl.v[:, 0], wl.gains[0], cells[0], N, Wa)
+    assert rel_err(o, ref) < 1e-12
+
+
+def test_antenna_kernels_identical_reduce_to_shared_kernel():
+    wl = synth.random_small(A=8, P=2, C=2, T=5, N=16, K=3, seed=920)
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    Wa = np.repeat(wl.kernel[None], wl.A, axis=0)
+    o_shared = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, wl.kernel)
+    o_each = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, Wa)
+    assert rel_err(o_each, o_shared) < 1e-13
+
+
+def test_antenna_kernels_single_antenna_is_zero():
+    wl = synth.random_small(A=1, P=2, C=1, T=6, N=16, K=5, seed=930)
+    Wa = synth.antenna_kernels(1, 5, np.random.default_rng(2))
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    o = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, Wa)
+    raw = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, Wa, oracle.NO_AUTOSUB)
+    assert np.max(np.abs(o)) <= 1e-12 * np.max(np.abs(raw))
