@@ -89,6 +89,13 @@ enum {
  * V = 2 Im XY (XY = F_X F_Y^*) as the four real images instead of the
  * polarisation products. */
 #define EPIC_STOKES      8u
+/* kernel_c64 holds one kernel per antenna, complex64 [n_ant][K][K] (Eq. 3
+ * writes the gridding kernel W_a per antenna: heterogeneous beams,
+ * A-projection, Sec. 3.1).  The autocorrelation term becomes
+ * sum_a A_a,pq |W^_a(l)|^2, evaluated from the auto-correlation grid
+ * sum_a A_a,pq (W_a (x) W_a^*) in FP64.  FP32 form only; not with
+ * EPIC_KERNEL_TAPER (which needs one shared kernel) or epic_image_series. */
+#define EPIC_ANTENNA_KERNELS 16u
 
 /*
  * epic_plan -- validate the array geometry and build every table the imaging
@@ -98,7 +105,8 @@ enum {
  *   ant_xy_m       host double [n_ant][2], antenna (x, y) positions in metres
  *   n_ant          number of antennas A >= 1
  *   n_pol          1 (single polarisation, product XX) or 2 (X and Y)
- *   kernel_c64     host complex64 [K][K] illumination kernel W
+ *   kernel_c64     host complex64 [K][K] illumination kernel W, or [n_ant][K][K]
+ *                  with EPIC_ANTENNA_KERNELS
  *   K              odd kernel side, 1 <= K <= 15
  *   grid_n         host int [n_chan], grid side N_c per channel; supported
  *                  sides are 32, 64, 96, 128, 256 and 512
@@ -107,7 +115,8 @@ enum {
  *   du_wavelengths cell size in wavelengths, 0 < du <= 0.5 (lambda/2 grid)
  *   max_spectra    largest n_spectra an epic_image call will pass (>= 0)
  *   precision      EPIC_FP32 or one of the EPIC_TC_* forms
- *   flags          EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER | EPIC_STOKES
+ *   flags          EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER | EPIC_STOKES |
+ *                  EPIC_ANTENNA_KERNELS
  *
  * Uses the current CUDA device.  Allocates device memory (tables and
  * workspace) and returns EPIC_ERR_NOMEM if that fails.  Returns

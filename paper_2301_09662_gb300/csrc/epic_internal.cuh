@@ -26,6 +26,8 @@ struct GroupCfg {
     int *d_chans = nullptr;            // device copy of chans
     long long *d_out_off = nullptr;    // device: output offset (complex elements) per group channel
     double *d_wpow = nullptr;          // device: |W^(l)|^2 on the shifted [N][N] layout
+    double2 *d_tw64 = nullptr;         // per-antenna kernels: exp(+2 pi i k / N) in FP64
+    double2 *d_Y = nullptr;            // per-antenna kernels: [n_chan][3][2K-1][N] partial auto images
     float2 *d_twN = nullptr;           // device: exp(+2 pi i k / N), k < N
     int n_items = 0;                   // n_chan * Q
     int tau_cap = 1;                   // time chunks the partial buffer holds
@@ -52,6 +54,8 @@ struct KernelTables {
 struct epic_plan_s {
     int device = 0;
     int A = 0, P = 0, NP = 0, C = 0, K = 0, max_spectra = 0, precision = 0;
+    int nker = 1;                      // kernels: 1 shared, or A (one per antenna)
+    double2 *d_bauto = nullptr;        // per-antenna kernels: [A][(2K-1)^2] B_aa(rho) = W_a (x) W_a^*
     unsigned flags = 0;
     int sm_count = 0;
     std::vector<int> grid_n;
@@ -106,6 +110,8 @@ int prepare_reg64(const epic_plan_s *plan, const GroupCfg &g);
 int launch_autopower(epic_plan_s *plan, const uint8_t *v, int T, cudaStream_t stream);
 int launch_epilogue(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T, int n_tau,
                     float2 *out, cudaStream_t stream);
+// per-antenna kernels: auto-correlation grid X(rho) -> Y(rho_y, l_x) per channel and product
+int launch_auto_rho(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, cudaStream_t stream);
 // image series: per-image auto sums and one epilogue image per time chunk
 int launch_autopower_series(epic_plan_s *plan, const uint8_t *v, int spi, int n_img, cudaStream_t stream);
 int launch_epilogue_series(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int spi, int n_img,
@@ -122,7 +128,7 @@ int launch_tc(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const floa
 void build_dft_operand(bool bf16, std::vector<uint16_t> &words);
 
 // M = 64 register-transform kernel (fp32_reg64.cu)
-size_t reg64_smem_bytes(int P, int TS, int A, int K);
+size_t reg64_smem_bytes(int P, int TS, int A, int K, int nker);
 int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                  cudaStream_t stream);
 // Gridding schedule of the M = 64 kernel for the channels of one group (plan.cu).

@@ -96,7 +96,7 @@ fp32_image_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                   const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K,
                   const int *__restrict__ chans, const float2 *__restrict__ twN,
                   int A, int C, int T, int N, int Q1, int n_items, int n_tau,
-                  float *__restrict__ partial, int *__restrict__ status)
+                  float *__restrict__ partial, int *__restrict__ status, int nker)
 {
     constexpr int S = M + 1;
     constexpr int NPOS = (M * M + kThreads - 1) / kThreads;
@@ -105,8 +105,8 @@ fp32_image_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     float2 *Gf = reinterpret_cast<float2 *>(smem_raw);   // [P][M][S]
     float2 *es = Gf + P * M * S;                          // [A*P] calibrated voltages
     float2 *gp = es + AP;                                 // [A*P] gains x class phase
-    float2 *tapw = gp + AP;                               // [K*K] kernel x class phase
-    float2 *twM = tapw + KK;                              // [M]
+    float2 *tapw = gp + AP;                               // [nker][K*K] kernel(s) x class phase
+    float2 *twM = tapw + nker * KK;                       // [M]
     uint32_t *antj = reinterpret_cast<uint32_t *>(twM + M);  // [A] folded cell
     uint32_t *tapd = antj + A;                            // [K*K] packed offsets
     uint32_t *stage = tapd + KK;                          // [ceil(AP/4)] ci4 words
@@ -137,11 +137,12 @@ fp32_image_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             gp[a * P + p] = cmul(g, ph);
         }
     }
-    for (int i = tid; i < KK; i += kThreads) {
-        const int dy = i / K - hk, dx = i % K - hk;
+    for (int i = tid; i < nker * KK; i += kThreads) {
+        const int tap = i % KK;
+        const int dy = tap / K - hk, dx = tap % K - hk;
         const int e = ((dx * hx + dy * hy) % N + N) % N;
         tapw[i] = cmul(kern[i], twN[e]);
-        tapd[i] = static_cast<uint32_t>(dx + 16) | (static_cast<uint32_t>(dy + 16) << 8);
+        if (i < KK) tapd[i] = static_cast<uint32_t>(dx + 16) | (static_cast<uint32_t>(dy + 16) << 8);
     }
     for (int k = tid; k < M; k += kThreads) twM[k] = twN[k * Q1];
     for (int i = tid; i < P * M * S; i += kThreads) Gf[i] = make_float2(0.f, 0.f);
@@ -195,7 +196,7 @@ fp32_image_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 x -= x >= M ? M : 0;
                 y += y < 0 ? M : 0;
                 y -= y >= M ? M : 0;
-                const float2 w = tapw[i];
+                const float2 w = tapw[(nker > 1 ? a * KK : 0) + i];
                 float2 *cell = Gf + y * S + x;
                 const float2 c0 = cmul(w, e0);
                 atomicAdd(&cell->x, c0.x);
@@ -266,10 +267,10 @@ fp32_image_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
 }
 
 template <int M, int P>
-size_t smem_bytes(int A, int K)
+size_t smem_bytes(int A, int K, int nker = 1)
 {
     const int AP = A * P, KK = K * K;
-    size_t b = sizeof(float2) * (static_cast<size_t>(P) * M * (M + 1) + 2 * AP + KK + M);
+    size_t b = sizeof(float2) * (static_cast<size_t>(P) * M * (M + 1) + 2 * AP + static_cast<size_t>(nker) * KK + M);
     b += sizeof(uint32_t) * (A + KK + (AP + 3) / 4);
     return (b + 15) & ~static_cast<size_t>(15);
 }
@@ -301,14 +302,14 @@ int launch_group(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
                  int *n_tau_out, cudaStream_t stream)
 {
     auto kfn = fp32_image_kernel<M, P>;
-    const size_t smem = smem_bytes<M, P>(plan->A, plan->K);
+    const size_t smem = smem_bytes<M, P>(plan->A, plan->K, plan->nker);
     int n_tau = plan->force_tau > 0 ? plan->force_tau : pick_tau(g.n_items, T, plan->sm_count);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));
     kfn<<<grid, kThreads, smem, stream>>>(v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN,
                                           plan->A, plan->C, T, g.N, g.Q1, g.n_items, n_tau, g.d_partial,
-                                          plan->d_status);
+                                          plan->d_status, plan->nker);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -316,7 +317,7 @@ template <int M, int P>
 int prepare_group(const epic_plan_s *plan)
 {
     auto kfn = fp32_image_kernel<M, P>;
-    const size_t smem = smem_bytes<M, P>(plan->A, plan->K);
+    const size_t smem = smem_bytes<M, P>(plan->A, plan->K, plan->nker);
     if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
         return EPIC_ERR_UNSUPPORTED;
     int per_sm = 0;
@@ -334,7 +335,7 @@ int launch_raw(const RawImage &r, const uint8_t *v, const float2 *gains, cudaStr
         return EPIC_ERR_UNSUPPORTED;
     const dim3 grid(static_cast<unsigned>(r.n_items * r.n_tau));
     kfn<<<grid, kThreads, smem, stream>>>(v, gains, r.cells, r.kernel, r.K, r.chans, r.twN, r.A, r.C, r.T, r.N, r.Q1,
-                                          r.n_items, r.n_tau, r.partial, r.status);
+                                          r.n_items, r.n_tau, r.partial, r.status, 1);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -434,7 +435,8 @@ int image_fp32(epic_plan_s *plan, const uint8_t *v, const float2 *gains, int T, 
         if (rc != EPIC_OK) return rc;
         if (fork && autosub && cudaStreamWaitEvent(s, plan->ev_auto, 0) != cudaSuccess) return EPIC_ERR_CUDA;
         prof_mark(plan, s, stage, true);
-        rc = launch_epilogue(plan, g, gains, T, n_tau, out, s);
+        if (autosub && plan->nker > 1) rc = launch_auto_rho(plan, g, gains, s);
+        if (rc == EPIC_OK) rc = launch_epilogue(plan, g, gains, T, n_tau, out, s);
         prof_mark(plan, s, stage++, false);
         if (rc != EPIC_OK) return rc;
         if (fork) {

@@ -48,7 +48,7 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                   const uint32_t *__restrict__ sched, const int *__restrict__ nrounds, int rmax,
                   const unsigned long long *__restrict__ rowmask,
                   int A, int C, int T, int N, int Q1, int n_items, int n_tau,
-                  float *__restrict__ partial, int *__restrict__ status)
+                  float *__restrict__ partial, int *__restrict__ status, int nker)
 {
     const int K = KC > 0 ? KC : K_rt;
     constexpr int NPOS = M64 * M64 / kThreads;   // 16 pixels per thread
@@ -59,8 +59,8 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     float2 *G = reinterpret_cast<float2 *>(smem_raw);          // [TS][P][64][65]
     float2 *es = G + TS * P * BUF;                             // [TS][A*P]
     float2 *gp = es + TS * AP;                                 // [A*P]
-    float2 *tapw = gp + AP;                                    // [K*K]
-    uint32_t *stage = reinterpret_cast<uint32_t *>(tapw + KK); // [TS][APW]
+    float2 *tapw = gp + AP;                                    // [nker][K*K]
+    uint32_t *stage = reinterpret_cast<uint32_t *>(tapw + nker * KK); // [TS][APW]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int item = blockIdx.x % n_items;
@@ -84,8 +84,9 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             gp[a * P + p] = cmul(g, ph);
         }
     }
-    for (int i = tid; i < KK; i += kThreads) {
-        const int dy = i / K - hk, dx = i % K - hk;
+    for (int i = tid; i < nker * KK; i += kThreads) {
+        const int tap = i % KK;
+        const int dy = tap / K - hk, dx = tap % K - hk;
         tapw[i] = cmul(kern[i], twN[((dx * hx + dy * hy) % N + N) % N]);
     }
     for (int i = tid; i < TS * P * BUF; i += kThreads) G[i] = make_float2(0.f, 0.f);
@@ -142,7 +143,7 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 for (int ts = 0; ts < TS; ts++)
 #pragma unroll
                     for (int p = 0; p < P; p++) e[ts][p] = es[ts * AP + a * P + p];
-                const float2 *wrow = tapw + dyi * K;
+                const float2 *wrow = tapw + (nker > 1 ? a * KK : 0) + dyi * K;
 #pragma unroll
                 for (int dx = 0; dx < (KC > 0 ? KC : K); dx++) {
                     const float2 w = wrow[dx];
@@ -226,10 +227,11 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
 }
 
 template <int P, int TS>
-size_t reg64_smem(int A, int K)
+size_t reg64_smem(int A, int K, int nker)
 {
     const int AP = A * P;
-    size_t b = sizeof(float2) * (static_cast<size_t>(TS) * P * M64 * S64 + static_cast<size_t>(TS) * AP + AP + K * K);
+    size_t b = sizeof(float2) * (static_cast<size_t>(TS) * P * M64 * S64 + static_cast<size_t>(TS) * AP + AP +
+                                 static_cast<size_t>(nker) * K * K);
     b += sizeof(uint32_t) * TS * ((AP + 3) / 4);
     return (b + 15) & ~static_cast<size_t>(15);
 }
@@ -239,14 +241,14 @@ int launch_reg64_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
                    cudaStream_t stream)
 {
     auto kfn = fp32_reg64_kernel<P, TS, KC>;
-    const size_t smem = reg64_smem<P, TS>(plan->A, plan->K);
+    const size_t smem = reg64_smem<P, TS>(plan->A, plan->K, plan->nker);
     int n_tau = plan->force_tau > 0 ? plan->force_tau : fp32_pick_tau(g.n_items, T, plan->sm_count);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));
     kfn<<<grid, kThreads, smem, stream>>>(v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN,
                                           g.d_sched, g.d_nrounds, g.rmax, g.d_rowmask, plan->A, plan->C, T, g.N, g.Q1,
-                                          g.n_items, n_tau, g.d_partial, plan->d_status);
+                                          g.n_items, n_tau, g.d_partial, plan->d_status, plan->nker);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -254,7 +256,7 @@ template <int P, int TS, int KC>
 int prepare_reg64_t(const epic_plan_s *plan)
 {
     auto kfn = fp32_reg64_kernel<P, TS, KC>;
-    const size_t smem = reg64_smem<P, TS>(plan->A, plan->K);
+    const size_t smem = reg64_smem<P, TS>(plan->A, plan->K, plan->nker);
     return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) ==
                    cudaSuccess
                ? EPIC_OK
@@ -308,10 +310,10 @@ int prepare_reg64(const epic_plan_s *plan, const GroupCfg &g)
     });
 }
 
-size_t reg64_smem_bytes(int P, int TS, int A, int K)
+size_t reg64_smem_bytes(int P, int TS, int A, int K, int nker)
 {
-    if (P == 2) return TS == 2 ? reg64_smem<2, 2>(A, K) : reg64_smem<2, 1>(A, K);
-    return TS == 2 ? reg64_smem<1, 2>(A, K) : reg64_smem<1, 1>(A, K);
+    if (P == 2) return TS == 2 ? reg64_smem<2, 2>(A, K, nker) : reg64_smem<2, 1>(A, K, nker);
+    return TS == 2 ? reg64_smem<1, 2>(A, K, nker) : reg64_smem<1, 1>(A, K, nker);
 }
 
 int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,

@@ -65,7 +65,8 @@ epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N
                 const int *__restrict__ chans, const long long *__restrict__ out_off,
                 const double *__restrict__ wpow, const int *__restrict__ autoint,
                 const float2 *__restrict__ gains, int A, int T, unsigned flags, float2 *__restrict__ out,
-                size_t auto_stride, long long out_stride)
+                size_t auto_stride, long long out_stride,
+                const double2 *__restrict__ Yauto, const double2 *__restrict__ tw64, int K)
 {
     // blockIdx.z = image: it sums time chunks [z n_tau, (z + 1) n_tau) and uses
     // the auto sums and output block of index z (one image unless a series)
@@ -82,7 +83,8 @@ epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N
     // A_pq(c) in FP64, reduced in a fixed order (deterministic)
     __shared__ double red[kThreads][6];
     __shared__ double apq[6];   // XX, YY, Re XY, Im XY (YX = conj XY)
-    if (autosub) {
+    const bool ant_kernels = Yauto != nullptr;   // auto image from the per-antenna auto-correlation grid
+    if (autosub && !ant_kernels) {
         double s[6] = {0, 0, 0, 0, 0, 0};
         for (int a = threadIdx.x; a < A; a += kThreads) {
             const int *ia = autoint + (static_cast<size_t>(c) * A + a) * 4;
@@ -141,7 +143,33 @@ epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N
             }
         }
         const double w = wpow[pix];
-        if (flags & EPIC_KERNEL_TAPER) {
+        if (ant_kernels) {
+            if (autosub) {
+                // auto_pq(l) = sum_{rho_y} Y_pq(rho_y, l_x) exp(+2 pi i rho_y l_y / N)
+                const int R = 2 * K - 1;
+                const int lyv = i - N / 2;
+                double ax = 0, ay = 0, axr = 0, axi = 0;
+                for (int ry = 0; ry < R; ry++) {
+                    const int m = (((ry - (K - 1)) * lyv) % N + N) % N;
+                    const double2 tw = tw64[m];
+                    const double2 y0 = Yauto[(static_cast<size_t>(ci) * 3 * R + ry) * N + j];
+                    ax += y0.x * tw.x - y0.y * tw.y;
+                    if (P == 2) {
+                        const double2 y1 = Yauto[(static_cast<size_t>(ci) * 3 * R + R + ry) * N + j];
+                        const double2 y2 = Yauto[(static_cast<size_t>(ci) * 3 * R + 2 * R + ry) * N + j];
+                        ay += y1.x * tw.x - y1.y * tw.y;
+                        axr += y2.x * tw.x - y2.y * tw.y;
+                        axi += y2.x * tw.y + y2.y * tw.x;
+                    }
+                }
+                s[0] -= ax;
+                if (P == 2) {
+                    s[1] -= ay;
+                    s[2] -= axr;
+                    s[3] -= axi;
+                }
+            }
+        } else if (flags & EPIC_KERNEL_TAPER) {
             // point-gridded sums: subtract the bare autos, then apply |W^(l)|^2
             for (int k = 0; k < (P == 2 ? 4 : 1); k++) s[k] = (s[k] - (autosub ? apq[k] : 0.0)) * w;
         } else if (autosub) {
@@ -167,6 +195,71 @@ epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N
     }
 }
 
+// Per-antenna kernels (Eq. 3's W_a): the a = b terms of F_p F_q^* sum to
+// sum_a A_a,pq |W^_a(l)|^2 = sum_rho X_pq(rho) exp(+2 pi i rho.l / N) with the
+// auto-correlation grid X_pq(rho) = sum_a A_a,pq B_aa(rho),
+// B_aa = W_a (x) W_a^* on the (2K-1)^2 offsets rho (Sec. 2.2's "auto-correlation
+// grids from individual antenna voltages").  One block per (channel, product):
+// X in FP64, then the l_x half of the separable transform,
+// Y(rho_y, l_x) = sum_rho_x X(rho_x, rho_y) exp(+2 pi i rho_x l_x / N), for the
+// epilogue to finish along l_y.
+__global__ void __launch_bounds__(kThreads)
+auto_rho_kernel(const int *__restrict__ autoint, const float2 *__restrict__ gains,
+                const double2 *__restrict__ bauto, const int *__restrict__ chans, const double2 *__restrict__ tw64,
+                int A, int P, int K, int N, double2 *__restrict__ Y)
+{
+    extern __shared__ double2 X[];     // [R][R]
+    const int R = 2 * K - 1, RR = R * R;
+    const int ci = blockIdx.x, pq = blockIdx.y;
+    const int c = chans[ci];
+    for (int rho = threadIdx.x; rho < RR; rho += blockDim.x) {
+        double xr = 0, xi = 0;
+        for (int a = 0; a < A; a++) {
+            const int *ia = autoint + (static_cast<size_t>(c) * A + a) * 4;
+            double ar, ai;
+            double gxr = 1, gxi = 0, gyr = 1, gyi = 0;
+            if (gains) {
+                const float2 gx = gains[(static_cast<size_t>(c) * A + a) * P];
+                gxr = gx.x;
+                gxi = gx.y;
+                if (P == 2) {
+                    const float2 gy = gains[(static_cast<size_t>(c) * A + a) * P + 1];
+                    gyr = gy.x;
+                    gyi = gy.y;
+                }
+            }
+            if (pq == 0) {
+                ar = (gxr * gxr + gxi * gxi) * ia[0];
+                ai = 0;
+            } else if (pq == 1) {
+                ar = (gyr * gyr + gyi * gyi) * ia[1];
+                ai = 0;
+            } else {
+                const double pr = gxr * gyr + gxi * gyi, pi = gxi * gyr - gxr * gyi;
+                ar = pr * ia[2] - pi * ia[3];
+                ai = pr * ia[3] + pi * ia[2];
+            }
+            const double2 b = bauto[static_cast<size_t>(a) * RR + rho];
+            xr += ar * b.x - ai * b.y;
+            xi += ar * b.y + ai * b.x;
+        }
+        X[rho] = make_double2(xr, xi);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * N; e += blockDim.x) {
+        const int ry = e / N, j = e % N;
+        const int lx = j - N / 2;
+        double yr = 0, yi = 0;
+        for (int rx = 0; rx < R; rx++) {
+            const int m = (((rx - (K - 1)) * lx) % N + N) % N;
+            const double2 tw = tw64[m], x = X[ry * R + rx];
+            yr += x.x * tw.x - x.y * tw.y;
+            yi += x.x * tw.y + x.y * tw.x;
+        }
+        Y[(static_cast<size_t>(ci) * 3 * R + static_cast<size_t>(pq) * R + ry) * N + j] = make_double2(yr, yi);
+    }
+}
+
 template <int M, int P>
 int launch_epi(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T, int n_tau, float2 *out,
                cudaStream_t stream)
@@ -177,7 +270,8 @@ int launch_epi(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T,
     epilogue_kernel<M, P><<<grid, kThreads, 0, stream>>>(g.d_partial, n_tau, g.n_items, g.N, g.Q1, g.R1, g.R2,
                                                          g.d_chans,
                                                          g.d_out_off, g.d_wpow, plan->d_autoint, gains, plan->A, T,
-                                                         plan->flags, out, 0, 0);
+                                                         plan->flags, out, 0, 0,
+                                                         plan->nker > 1 ? g.d_Y : nullptr, g.d_tw64, plan->K);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -190,7 +284,7 @@ int launch_epi_raw(const RawImage &r, const float2 *gains, float2 *out, cudaStre
     epilogue_kernel<M, P><<<grid, kThreads, 0, stream>>>(r.partial, r.n_tau, r.n_items, r.N, r.Q1, 8, M / 8,
                                                          r.chans,
                                                          r.out_off, r.wpow, r.autoint, gains, r.A, r.T, r.flags,
-                                                         out, 0, 0);
+                                                         out, 0, 0, nullptr, nullptr, 0);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -231,7 +325,8 @@ int launch_epi_series(epic_plan_s *plan, const GroupCfg &g, const float2 *gains,
                                                          g.d_out_off, g.d_wpow, plan->d_autoint, gains, plan->A, spi,
                                                          plan->flags, out,
                                                          static_cast<size_t>(plan->C) * plan->A * 4,
-                                                         static_cast<long long>(plan->out_floats / 2));
+                                                         static_cast<long long>(plan->out_floats / 2), nullptr,
+                                                         nullptr, 0);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -257,6 +352,15 @@ int launch_epilogue_series(epic_plan_s *plan, const GroupCfg &g, const float2 *g
     case 64 * 4 + 2: return launch_epi_series<64, 2>(plan, g, gains, spi, n_img, out, stream);
     default: return EPIC_ERR_UNSUPPORTED;
     }
+}
+
+int launch_auto_rho(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, cudaStream_t stream)
+{
+    const int R = 2 * plan->K - 1;
+    const dim3 grid(static_cast<unsigned>(g.n_chan), static_cast<unsigned>(plan->P == 2 ? 3 : 1));
+    auto_rho_kernel<<<grid, kThreads, sizeof(double2) * R * R, stream>>>(
+        plan->d_autoint, gains, plan->d_bauto, g.d_chans, g.d_tw64, plan->A, plan->P, plan->K, g.N, g.d_Y);
+    return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
 int launch_autopower(epic_plan_s *plan, const uint8_t *v, int T, cudaStream_t stream)

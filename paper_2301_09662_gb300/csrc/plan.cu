@@ -62,6 +62,7 @@ void free_plan(epic_plan_s *p)
     cudaFree(p->d_cells);
     cudaFree(p->d_kernel);
     cudaFree(p->d_dft);
+    cudaFree(p->d_bauto);
     cudaFree(p->d_autoint);
     cudaFree(p->d_status);
     cudaFree(p->d_stage_v);
@@ -76,6 +77,8 @@ void free_plan(epic_plan_s *p)
         cudaFree(g.d_sched);
         cudaFree(g.d_nrounds);
         cudaFree(g.d_rowmask);
+        cudaFree(g.d_tw64);
+        cudaFree(g.d_Y);
     }
     delete p;
 }
@@ -309,8 +312,12 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     if (n_ant < 1 || (n_pol != 1 && n_pol != 2) || K < 1 || (K % 2) == 0 || K > epic::kMaxK ||
         n_chan < 1 || !(du > 0.0) || du > 0.5 || max_spectra < 0)
         return EPIC_ERR_ARG;
-    if (flags & ~(EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER | EPIC_STOKES)) return EPIC_ERR_ARG;
+    if (flags & ~(EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER | EPIC_STOKES | EPIC_ANTENNA_KERNELS))
+        return EPIC_ERR_ARG;
     if ((flags & EPIC_STOKES) && n_pol != 2) return EPIC_ERR_ARG;
+    const bool ant_kernels = (flags & EPIC_ANTENNA_KERNELS) != 0;
+    if (ant_kernels && (flags & EPIC_KERNEL_TAPER)) return EPIC_ERR_ARG;
+    if (ant_kernels && precision != EPIC_FP32) return EPIC_ERR_UNSUPPORTED;
     if (precision < EPIC_FP32 || precision > EPIC_TC_SPLIT_BF16) return EPIC_ERR_ARG;
     const bool tensor = precision != EPIC_FP32;
     if (tensor) {
@@ -362,6 +369,7 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     // as an image-domain taper
     const bool taper = (flags & EPIC_KERNEL_TAPER) != 0;
     p->K = taper ? 1 : K;
+    p->nker = ant_kernels ? n_ant : 1;
     const float unit_tap[2] = {1.f, 0.f};
     p->max_spectra = max_spectra;
     p->precision = precision;
@@ -383,7 +391,31 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     int rc = dev_upload(&p->d_cells, cells.data(), cells.size());
     if (rc == EPIC_OK)
         rc = taper ? dev_upload(&p->d_kernel, reinterpret_cast<const float2 *>(unit_tap), 1)
-                   : dev_upload(&p->d_kernel, reinterpret_cast<const float2 *>(kernel_c64), static_cast<size_t>(K) * K);
+                   : dev_upload(&p->d_kernel, reinterpret_cast<const float2 *>(kernel_c64),
+                                static_cast<size_t>(p->nker) * K * K);
+    if (rc == EPIC_OK && ant_kernels) {
+        // B_aa(rho) = sum_d W_a(d) W_a^*(d - rho), rho in [-(K-1), K-1]^2, FP64
+        const int R = 2 * K - 1, hh = (K - 1) / 2;
+        std::vector<double2> bauto(static_cast<size_t>(n_ant) * R * R);
+        for (int a = 0; a < n_ant; a++) {
+            const float *Wa = kernel_c64 + static_cast<size_t>(a) * K * K * 2;
+            for (int ry = -(K - 1); ry <= K - 1; ry++)
+                for (int rx = -(K - 1); rx <= K - 1; rx++) {
+                    std::complex<double> acc = 0;
+                    for (int dy = -hh; dy <= hh; dy++)
+                        for (int dx = -hh; dx <= hh; dx++) {
+                            const int ey = dy - ry, ex = dx - rx;
+                            if (ey < -hh || ey > hh || ex < -hh || ex > hh) continue;
+                            const int i0 = (dy + hh) * K + (dx + hh), i1 = (ey + hh) * K + (ex + hh);
+                            acc += std::complex<double>(Wa[2 * i0], Wa[2 * i0 + 1]) *
+                                   std::conj(std::complex<double>(Wa[2 * i1], Wa[2 * i1 + 1]));
+                        }
+                    bauto[(static_cast<size_t>(a) * R + (ry + K - 1)) * R + (rx + K - 1)] =
+                        make_double2(acc.real(), acc.imag());
+                }
+        }
+        rc = dev_upload(&p->d_bauto, bauto.data(), bauto.size());
+    }
 
     if (rc == EPIC_OK) rc = dev_upload(&p->d_status, static_cast<const int *>(nullptr), 1);
     if (rc == EPIC_OK && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) rc = EPIC_ERR_CUDA;
@@ -423,7 +455,7 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
             g.ts = 1;
         } else if (g.M == 64 && (ap % 4) == 0) {
             for (int ts = 2; ts >= 1 && !g.reg64; ts--) {
-                if (epic::reg64_smem_bytes(n_pol, ts, n_ant, p->K) <= static_cast<size_t>(smem_optin)) {
+                if (epic::reg64_smem_bytes(n_pol, ts, n_ant, p->K, p->nker) <= static_cast<size_t>(smem_optin)) {
                     g.reg64 = true;
                     g.ts = ts;
                 }
@@ -444,6 +476,17 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         if (rc == EPIC_OK) rc = dev_upload(&g.d_out_off, offs.data(), offs.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_wpow, wpow.data(), wpow.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_twN, tw.data(), tw.size());
+        if (rc == EPIC_OK && ant_kernels) {
+            std::vector<double2> tw64(g.N);
+            for (int k = 0; k < g.N; k++) {
+                const double ang = 2.0 * M_PI * k / g.N;
+                tw64[k] = make_double2(std::cos(ang), std::sin(ang));
+            }
+            rc = dev_upload(&g.d_tw64, tw64.data(), tw64.size());
+            if (rc == EPIC_OK)
+                rc = dev_upload(&g.d_Y, static_cast<const double2 *>(nullptr),
+                                static_cast<size_t>(g.n_chan) * 3 * (2 * K - 1) * g.N);
+        }
         if (rc == EPIC_OK)
             rc = dev_upload(&g.d_partial, static_cast<const float *>(nullptr),
                             static_cast<size_t>(g.tau_cap) * g.n_items * g.M * g.M * npf);
@@ -517,6 +560,7 @@ int epic_image_series(epic_plan_t plan, const uint8_t *ci4, const float *gains, 
     if (!plan || !out || spi < 1) return EPIC_ERR_ARG;
     if (n_spectra < 0 || n_spectra > plan->max_spectra || n_spectra % spi != 0) return EPIC_ERR_ARG;
     if (n_spectra > 0 && !ci4) return EPIC_ERR_ARG;
+    if (plan->nker > 1) return EPIC_ERR_UNSUPPORTED;
     auto s = static_cast<cudaStream_t>(stream);
     const int n_img = n_spectra / spi;
     const size_t img_floats = plan->out_floats;

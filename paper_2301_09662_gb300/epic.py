@@ -33,6 +33,7 @@ EPIC_MEAN = 1
 EPIC_NO_AUTOSUB = 2
 EPIC_KERNEL_TAPER = 4
 EPIC_STOKES = 8
+EPIC_ANTENNA_KERNELS = 16
 STOKES = ("I", "Q", "U", "V")
 
 PRODUCTS = ("XX", "YY", "XY", "YX")
@@ -108,7 +109,12 @@ class Plan:
         self._freq = np.ascontiguousarray(freq_hz, np.float64)
         if self._ant.ndim != 2 or self._ant.shape[1] != 2:
             raise ValueError("ant_xy must be [A][2]")
-        if self._kern.ndim != 2 or self._kern.shape[0] != self._kern.shape[1]:
+        per_antenna = bool(int(flags) & EPIC_ANTENNA_KERNELS)
+        if per_antenna:
+            if self._kern.ndim != 3 or self._kern.shape[0] != self._ant.shape[0] \
+                    or self._kern.shape[1] != self._kern.shape[2]:
+                raise ValueError("with EPIC_ANTENNA_KERNELS the kernel must be [A][K][K]")
+        elif self._kern.ndim != 2 or self._kern.shape[0] != self._kern.shape[1]:
             raise ValueError("kernel must be [K][K]")
         if self.grid_n.shape != self._freq.shape:
             raise ValueError("grid_n and freq_hz must have one entry per channel")
@@ -116,7 +122,7 @@ class Plan:
         self.P = int(n_pol)
         self.NP = 4 if self.P == 2 else 1
         self.C = len(self._freq)
-        self.K = self._kern.shape[0]
+        self.K = self._kern.shape[-1]
         self.max_spectra = int(max_spectra)
         self.precision = int(precision)
         self.flags = int(flags)

@@ -89,3 +89,14 @@ def test_null_handles_are_rejected(lib):
 def test_tensor_form_rejects_unsupported_shapes_on_host(lib, bad):
     rc, h = epic.make_plan_raw(**_geom(precision=epic.EPIC_TC_SPLIT_FP16, **bad))
     assert rc == epic.EPIC_ERR_UNSUPPORTED and not h.value
+
+
+def test_antenna_kernel_flag_combinations_rejected_on_host(lib):
+    wl = synth.random_small(A=8, P=2, C=2, T=4, N=32, K=3, seed=1)
+    Wa = synth.antenna_kernels(8, 3, np.random.default_rng(0))
+    rc, h = epic.make_plan_raw(**_geom(kernel=Wa.reshape(8 * 3, 3)[:3],
+                                       flags=epic.EPIC_ANTENNA_KERNELS | epic.EPIC_KERNEL_TAPER))
+    assert rc == epic.EPIC_ERR_ARG and not h.value
+    rc, h = epic.make_plan_raw(**_geom(flags=epic.EPIC_ANTENNA_KERNELS, precision=epic.EPIC_TC_SPLIT_FP16,
+                                       grid_n=np.array([64, 64], np.int32)))
+    assert rc == epic.EPIC_ERR_UNSUPPORTED and not h.value
