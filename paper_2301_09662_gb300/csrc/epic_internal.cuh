@@ -62,12 +62,16 @@ struct epic_plan_s {
     std::vector<long long> out_off;    // complex-element offset of each channel's image
     size_t out_floats = 0;
     uint8_t *d_dft = nullptr;          // tensor form: column-DFT operand (hi, lo parts)
+    uint16_t *d_dft_rows = nullptr;    // pipelined tensor form: the same operand as plain rows
+    bool tc_pipe = false;              // use the pipelined tensor kernel
     short2 *d_cells = nullptr;         // [C][A]
     float2 *d_kernel = nullptr;        // [K*K]
     int *d_autoint = nullptr;          // [C][A][4] exact integer auto sums
     int *d_status = nullptr;           // sticky device status word
     std::vector<epic::GroupCfg> groups;
     int force_tau = 0;                 // > 0: time chunks of the next launches (image series)
+    long long wait_budget = 4000000000LL;  // clock cycles a device-side wait may take (~2 s)
+    int test_withhold_mma = 0;         // fault-injection hook: tensor kernel withholds its MMA
     int series_cap = 1;                // images one series batch can hold (partials, auto sums)
     // stage timing (epic_set_profiling)
     bool profiling = false;
@@ -126,6 +130,11 @@ int prepare_tc(const epic_plan_s *plan);
 int launch_tc(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
               cudaStream_t stream);
 void build_dft_operand(bool bf16, std::vector<uint16_t> &words);
+size_t tc_pipe_smem_bytes(int A, int K);
+int prepare_tc_pipe(const epic_plan_s *plan);
+int launch_tc_pipe(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
+                   cudaStream_t stream);
+void build_dft_rows(bool bf16, std::vector<uint16_t> &words);
 
 // M = 64 register-transform kernel (fp32_reg64.cu)
 size_t reg64_smem_bytes(int P, int TS, int A, int K, int nker);

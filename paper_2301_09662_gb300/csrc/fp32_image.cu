@@ -386,7 +386,8 @@ int prepare_fp32(const epic_plan_s *plan, const GroupCfg &g)
 int launch_imaging(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                    cudaStream_t s)
 {
-    if (plan->precision != EPIC_FP32) return launch_tc(plan, g, v, gains, T, n_tau, s);
+    if (plan->precision != EPIC_FP32)
+        return plan->tc_pipe ? launch_tc_pipe(plan, g, v, gains, T, n_tau, s) : launch_tc(plan, g, v, gains, T, n_tau, s);
     if (g.reg64) return launch_reg64(plan, g, v, gains, T, n_tau, s);
     switch (g.M * 4 + plan->P) {
     case 32 * 4 + 2: return launch_group<32, 2>(plan, g, v, gains, T, n_tau, s);

@@ -62,6 +62,7 @@ void free_plan(epic_plan_s *p)
     cudaFree(p->d_cells);
     cudaFree(p->d_kernel);
     cudaFree(p->d_dft);
+    cudaFree(p->d_dft_rows);
     cudaFree(p->d_bauto);
     cudaFree(p->d_autoint);
     cudaFree(p->d_status);
@@ -450,7 +451,9 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         const int ap = n_ant * n_pol;
         if (tensor) {
             // + static shared memory of the kernel (barriers, TMEM slot, alignment)
-            if (epic::tc_smem_bytes(n_ant, p->K) + 2048 > static_cast<size_t>(smem_optin)) rc = EPIC_ERR_UNSUPPORTED;
+            if (std::max(epic::tc_smem_bytes(n_ant, p->K), epic::tc_pipe_smem_bytes(n_ant, p->K)) + 2048 >
+                static_cast<size_t>(smem_optin))
+                rc = EPIC_ERR_UNSUPPORTED;
             g.reg64 = true;   // same gridding schedule and natural pixel order
             g.ts = 1;
         } else if (g.M == 64 && (ap % 4) == 0) {
@@ -500,10 +503,19 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         rc = dev_upload(&p->d_autoint, static_cast<const int *>(nullptr),
                         static_cast<size_t>(p->series_cap) * n_chan * n_ant * 4);
     if (rc == EPIC_OK && tensor) {
+        // the pipelined kernel unless EPIC_TC_SERIAL=1 asks for the one-sample-at-a-time kernel
+        const char *ser = std::getenv("EPIC_TC_SERIAL");
+        p->tc_pipe = !(ser && ser[0] == '1');
         std::vector<uint16_t> ops;
-        epic::build_dft_operand(precision == EPIC_TC_SPLIT_BF16, ops);
-        rc = dev_upload(&p->d_dft, reinterpret_cast<const uint8_t *>(ops.data()), ops.size() * 2);
-        if (rc == EPIC_OK) rc = epic::prepare_tc(p);
+        if (p->tc_pipe) {
+            epic::build_dft_rows(precision == EPIC_TC_SPLIT_BF16, ops);
+            rc = dev_upload(&p->d_dft_rows, ops.data(), ops.size());
+            if (rc == EPIC_OK) rc = epic::prepare_tc_pipe(p);
+        } else {
+            epic::build_dft_operand(precision == EPIC_TC_SPLIT_BF16, ops);
+            rc = dev_upload(&p->d_dft, reinterpret_cast<const uint8_t *>(ops.data()), ops.size() * 2);
+            if (rc == EPIC_OK) rc = epic::prepare_tc(p);
+        }
     }
     for (const auto &g : p->groups) {
         if (rc != EPIC_OK || tensor) break;
@@ -512,6 +524,14 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     if (rc == EPIC_OK) {
         const char *env = std::getenv("EPIC_NO_GRAPH");
         p->use_graph = !(env && env[0] == '1');
+        // Fault injection for the failure-detection test: the tensor kernel
+        // issues no MMA, so its completion wait runs out after a short budget
+        // and the plan's status word reports EPIC_ERR_TIMEOUT.
+        const char *inj = std::getenv("EPIC_TEST_WITHHOLD_MMA");
+        if (inj && inj[0] == '1') {
+            p->test_withhold_mma = 1;
+            p->wait_budget = 2000000;   // ~1 ms
+        }
         if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&p->ev_auto, cudaEventDisableTiming) != cudaSuccess)

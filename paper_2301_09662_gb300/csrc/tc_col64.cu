@@ -38,7 +38,6 @@ constexpr int KT = 128;                          // K of one operand part
 constexpr uint32_t kPartBytes = 128u * KT * 2u;   // one 128 x 128 16-bit operand part
 constexpr uint32_t kLBO = 128;                   // K-adjacent core matrices
 constexpr uint32_t kSBO = KT * 16;               // M/N-adjacent core matrices (2048 B)
-constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
 
 __host__ __device__ constexpr uint32_t op_off(int row, int k)
 {
@@ -81,7 +80,7 @@ tc_col64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
                 const int *__restrict__ chans, const float2 *__restrict__ twN,
                 const uint32_t *__restrict__ sched, const int *__restrict__ nrounds, int rmax,
                 const uint8_t *__restrict__ dft_ops, int A, int C, int T, int N, int Q1, int n_items, int n_tau,
-                float *__restrict__ partial, int *__restrict__ status)
+                float *__restrict__ partial, int *__restrict__ status, long long wait_budget, int withhold_mma)
 {
     constexpr int P = 2;
     constexpr bool kBF16 = VAR == 2;
@@ -279,10 +278,12 @@ tc_col64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
             tc::fence_after_sync();
             bool ok = true;
             if (!ops_ready) {
-                ok = tc::mbar_wait(&bar_ops, 0, kWaitBudget);
+                ok = tc::mbar_wait(&bar_ops, 0, wait_budget);
                 ops_ready = ok;
             }
-            if (ok) {
+            // withhold_mma (fault-injection test hook): issue nothing and arrive
+            // nowhere, so every thread's bounded wait below runs out
+            if (ok && !withhold_mma) {
 #pragma unroll
                 for (int kb = 0; kb < 8; kb++) {
                     const uint32_t koff = static_cast<uint32_t>(kb) * 2u * 128u;
@@ -297,14 +298,14 @@ tc_col64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
                     }
                 }
                 tc::mma_commit(&bar_mma);
-            } else {
+            } else if (!ok) {
                 atomicOr(status, kStatusTimeout);
                 abort_flag = 1;
             }
         }
         __syncthreads();
         if (abort_flag) break;
-        if (!tc::mbar_wait(&bar_mma, phase, kWaitBudget)) {
+        if (!tc::mbar_wait(&bar_mma, phase, wait_budget)) {
             atomicOr(status, kStatusTimeout);
             abort_flag = 1;
         }
@@ -360,8 +361,8 @@ tc_col64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
     }
     // an aborted CTA may still have a copy or an MMA in flight: give them a bounded chance to land
     if (tid == 0 && abort_flag) {
-        if (!ops_ready) tc::mbar_wait(&bar_ops, 0, kWaitBudget);
-        tc::mbar_wait(&bar_mma, phase ^ 1u, kWaitBudget);
+        if (!ops_ready) tc::mbar_wait(&bar_ops, 0, wait_budget);
+        tc::mbar_wait(&bar_mma, phase ^ 1u, wait_budget);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -397,7 +398,8 @@ int launch_tc_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const fl
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));
     tc_col64_kernel<VAR><<<grid, kThreads, tc_smem(plan->A, plan->K), stream>>>(
         v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN, g.d_sched, g.d_nrounds, g.rmax,
-        plan->d_dft, plan->A, plan->C, T, g.N, g.Q1, g.n_items, n_tau, g.d_partial, plan->d_status);
+        plan->d_dft, plan->A, plan->C, T, g.N, g.Q1, g.n_items, n_tau, g.d_partial, plan->d_status,
+        plan->wait_budget, plan->test_withhold_mma);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 

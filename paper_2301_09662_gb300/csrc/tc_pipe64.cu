@@ -1,0 +1,539 @@
+// Pipelined tensor-core form (folded side M = 64, dual polarisation).
+//
+// Same arithmetic as tc_col64.cu -- the column transform of each sample is the
+// real GEMM D[128 x 128] = A[128 x 128] B^T with FP16 (or BF16) hi + lo
+// operands, 3 MMAs per 16-deep k-block -- but laid out so that the tensor
+// cores work while the CUDA cores do the rest:
+//
+//  * A (the 64-point DFT in real 2 x 2 block form, hi and lo) lives in tensor
+//    memory for the whole CTA (loaded once with tcgen05.st), which frees the
+//    shared memory for two B buffers;
+//  * B is MN-major with columns n = 8 (mx mod 8) + mx / 8 (+ 64 for pol Y):
+//    the last radix-8 block of the thread that row-transforms grid row jy
+//    yields 8 consecutive columns, stored as one 16-byte word per part
+//    straight from registers, so H never goes back through the grid;
+//  * two B buffers and two TMEM accumulators: the MMA of sample t runs while
+//    sample t+1 is unpacked, gridded and row-transformed, and warps 4-7 drain
+//    sample t-1's accumulator (products summed over time) while warps 0-3 do
+//    the row transforms.
+//
+// TMEM columns: D0 [0,128), D1 [128,256), A_hi [256,320), A_lo [320,384)
+// (A packs two 16-bit K values per 32-bit column, lower K in the low half),
+// and the time sums [384,512): lane r = (my, part) keeps XX, YY, Re XY, Im XY
+// of its 32 pixels, so the per-pixel accumulators cost no registers in the
+// row-transform warps.
+// Every wait is bounded; a timeout is recorded in the plan's status word.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "epic_internal.cuh"
+#include "fft64.cuh"
+#include "tc_ptx.cuh"
+
+#include <type_traits>
+#include <vector>
+
+namespace epic {
+namespace {
+
+constexpr int M64 = 64;
+constexpr int S64 = 65;
+constexpr uint32_t kPart = 128u * 128u * 2u;     // one 128 x 128 16-bit B part (32 KB)
+constexpr uint32_t kLBO = 128;                  // K-adjacent core matrices
+constexpr uint32_t kSBO = 2048;                 // N-adjacent core matrices (16 along K x 128 B)
+constexpr uint32_t kColA = 256;                 // first TMEM column of A
+constexpr uint32_t kColAcc = 384;               // first TMEM column of the time sums
+
+// byte offset of B element (n, k) in the MN-major canonical layout
+__host__ __device__ constexpr uint32_t b_off(int n, int k)
+{
+    return static_cast<uint32_t>((n >> 3) * kSBO + (k >> 3) * kLBO + (k & 7) * 16 + (n & 7) * 2);
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint16_t to16(float x, float &back)
+{
+    if constexpr (BF16) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        back = __bfloat162float(h);
+        return __bfloat16_as_ushort(h);
+    } else {
+        const __half h = __float2half_rn(x);
+        back = __half2float(h);
+        return __half_as_ushort(h);
+    }
+}
+
+__device__ __forceinline__ float2 ci4_val(uint32_t b)
+{
+    const int re = static_cast<int>(static_cast<int8_t>(b & 0xF0u)) >> 4;
+    const int im = static_cast<int>(static_cast<int8_t>((b << 4) & 0xF0u)) >> 4;
+    return make_float2(static_cast<float>(re), static_cast<float>(im));
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]),
+        "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]),
+        "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+// D(tmem) (+)= A(tmem) x B(smem)^T
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// instruction descriptor: FP32 accumulate, A K-major, B MN-major, M x N
+__host__ __device__ constexpr uint32_t idesc_mn(int M, int N, bool bf16)
+{
+    return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | (1u << 16) |
+           (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+template <int VAR, int KC>
+__global__ void __launch_bounds__(kThreads, 1)
+tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
+                 const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K_rt,
+                 const int *__restrict__ chans, const float2 *__restrict__ twN,
+                 const uint32_t *__restrict__ sched, const int *__restrict__ nrounds, int rmax,
+                 const unsigned long long *__restrict__ rowmask, const uint16_t *__restrict__ dft_rows,
+                 int A, int C, int T, int N, int Q1, int n_items, int n_tau,
+                 float *__restrict__ partial, int *__restrict__ status, long long wait_budget, int withhold_mma)
+{
+    constexpr int P = 2;
+    constexpr bool kBF16 = VAR == 2;
+    constexpr bool kSplit = VAR != 1;
+    constexpr int BUF = M64 * S64;
+    const int K = KC > 0 ? KC : K_rt;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *opB = smem;                                              // [2 buffers][2 parts][32 KB]
+    float2 *G = reinterpret_cast<float2 *>(smem + 4 * kPart);         // [P][64][65]
+    const int AP = A * P, KK = K * K, hk = (K - 1) / 2;
+    const int APW = (AP + 3) >> 2;
+    float2 *es = G + P * BUF;
+    float2 *gp = es + AP;
+    float2 *tapw = gp + AP;
+    uint32_t *stage = reinterpret_cast<uint32_t *>(tapw + KK);
+    __shared__ __align__(8) uint64_t bar_mma[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ float red[kThreads / 32];
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int item = blockIdx.x % n_items;
+    const int tau = blockIdx.x / n_items;
+    const int Q = Q1 * Q1;
+    const int ci = item / Q, h = item % Q, hx = h % Q1, hy = h / Q1;
+    const int c = chans[ci];
+    const int t0 = static_cast<int>(static_cast<long long>(T) * tau / n_tau);
+    const int t1 = static_cast<int>(static_cast<long long>(T) * (tau + 1) / n_tau);
+    const uint32_t *my_sched = sched + (static_cast<size_t>(ci) * 8 + warp) * rmax * 32;
+    const int my_rounds = nrounds[ci * 8 + warp];
+    const unsigned long long rows_used = rowmask[ci];
+
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
+    if (tid == 0) {
+        abort_flag = 0;
+        tc::mbar_init(&bar_mma[0], 1);
+        tc::mbar_init(&bar_mma[1], 1);
+        tc::fence_mbar_init();
+    }
+
+    // ---- set-up: phase-folded gains and taps, the largest gain for the FP16 scale
+    float gmax = 0.f;
+    for (int a = tid; a < A; a += kThreads) {
+        const short2 k = cells[static_cast<size_t>(c) * A + a];
+        if (k.x < hk || k.x >= N - hk || k.y < hk || k.y >= N - hk) atomicOr(status, kStatusDevice);
+        const float2 ph = twN[((k.x * hx + k.y * hy) % N + N) % N];
+        for (int p = 0; p < P; p++) {
+            const float2 g = gains ? gains[(static_cast<size_t>(c) * A + a) * P + p] : make_float2(1.f, 0.f);
+            const float2 gg = cmul(g, ph);
+            gp[a * P + p] = gg;
+            gmax = fmaxf(gmax, sqrtf(gg.x * gg.x + gg.y * gg.y));
+        }
+    }
+    for (int i = tid; i < KK; i += kThreads) {
+        const int dy = i / K - hk, dx = i % K - hk;
+        tapw[i] = cmul(kern[i], twN[((dx * hx + dy * hy) % N + N) % N]);
+    }
+    for (int i = tid; i < P * BUF; i += kThreads) G[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < static_cast<int>(4 * kPart / 16); i += kThreads)
+        reinterpret_cast<uint4 *>(opB)[i] = make_uint4(0u, 0u, 0u, 0u);   // rows never written stay zero
+    if (t0 < t1) {
+        const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(t0) * C + c) * AP);
+        for (int w = tid; w < APW; w += kThreads) stage[w] = row[w];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    if (lane == 0) red[warp] = gmax;
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = tmem_slot;
+    float scale = 1.f;
+    if constexpr (!kBF16) {
+        float gm = 0.f;
+        for (int w = 0; w < kThreads / 32; w++) gm = fmaxf(gm, red[w]);
+        float wsum = 0.f;
+        for (int i = 0; i < KK; i++) wsum += sqrtf(tapw[i].x * tapw[i].x + tapw[i].y * tapw[i].y);
+        const float bound = 2.f * static_cast<float>(A) * 11.3137085f * gm * wsum;
+        int e2 = 0;
+        if (bound > 0.f) e2 = static_cast<int>(floorf(log2f(16384.f / bound)));
+        scale = ldexpf(1.f, max(-40, min(40, e2)));
+    }
+    for (int i = tid; i < AP; i += kThreads) gp[i] = cscale(gp[i], scale);
+    // A (hi, lo) into TMEM: warp w < 4 writes rows 32w .. 32w+31
+    if (warp < 4) {
+        const int r = 32 * warp + lane;
+        for (int part = 0; part < 2; part++)
+            for (int half = 0; half < 2; half++) {
+                uint32_t w[32];
+                const uint16_t *src = dft_rows + (static_cast<size_t>(part) * 128 + r) * 128 + half * 64;
+#pragma unroll
+                for (int j = 0; j < 32; j++) w[j] = static_cast<uint32_t>(src[2 * j]) | (static_cast<uint32_t>(src[2 * j + 1]) << 16);
+                tmem_st32(taddr + (static_cast<uint32_t>(32 * warp) << 16) + kColA + part * 64 + half * 32, w);
+            }
+    }
+    if (warp >= 4) {
+        // zero the time sums of this warp's lanes
+        uint32_t z[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) z[j] = 0u;
+        const uint32_t row_addr = taddr + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + kColAcc;
+        for (int cc = 0; cc < 128; cc += 32) tmem_st32(row_addr + cc, z);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+
+    constexpr uint32_t idesc = idesc_mn(128, 128, kBF16);
+    const uint32_t b_base = tc::smem_u32(opB);
+    uint32_t phase[2] = {0u, 0u};
+    constexpr int kPreW = kMaxAP / 4 / kThreads;
+    for (int t = t0; t <= t1; t++) {
+        const bool work = t < t1;
+        const int buf = (t - t0) & 1;
+        // ---- a1, a2 (sample t) and prefetch of t+1
+        if (work) {
+            for (int i = tid; i < AP; i += kThreads) {
+                const uint32_t b = reinterpret_cast<const uint8_t *>(stage)[i];
+                es[i] = cmul(gp[i], ci4_val(b));
+            }
+        }
+        const bool has_next = t + 1 < t1;
+        uint32_t pre[kPreW];
+        {
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(t + 1) * C + c) * AP);
+#pragma unroll
+            for (int r = 0; r < kPreW; r++) {
+                const int w = tid + r * kThreads;
+                pre[r] = (has_next && w < APW) ? __ldg(row + w) : 0u;
+            }
+        }
+        __syncthreads();
+
+        // ---- a3: scheduled gridding of sample t (the MMA of t-1 is running)
+        if (work) {
+            for (int r = 0; r < my_rounds; r++) {
+                const uint32_t d = __ldg(my_sched + r * 32 + lane);
+                if (d >> 31) {
+                    const int a = static_cast<int>(d & 0xFFFu);
+                    const int dyi = static_cast<int>((d >> 12) & 0xFu);
+                    const int y = static_cast<int>((d >> 16) & 0x3Fu);
+                    const int x0 = static_cast<int>((d >> 22) & 0x3Fu);
+                    const float2 e0 = es[a * P], e1 = es[a * P + 1];
+                    const float2 *wrow = tapw + dyi * K;
+#pragma unroll
+                    for (int dx = 0; dx < (KC > 0 ? KC : K); dx++) {
+                        const float2 w = wrow[dx];
+                        const int x = (x0 + dx) & (M64 - 1);
+                        float2 *c0 = G + y * S64 + x;
+                        float2 *c1 = c0 + BUF;
+                        const float2 v0 = cmul(w, e0), v1 = cmul(w, e1);
+                        float2 o0 = *c0, o1 = *c1;
+                        o0.x += v0.x;
+                        o0.y += v0.y;
+                        o1.x += v1.x;
+                        o1.y += v1.y;
+                        *c0 = o0;
+                        *c1 = o1;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+
+        if (warp < 4) {
+            // ---- a4 (rows) of sample t into B[buf], MN-major, hi/lo
+            const int q = tid;                        // 128 tasks: (pol, row)
+            const int jy = q & 63, p = q >> 6;
+            if (work && ((rows_used >> jy) & 1ull)) {
+                float2 *line = G + p * BUF + jy * S64;
+                float2 x[64];
+#pragma unroll
+                for (int i = 0; i < 64; i++) {
+                    x[i] = line[i];
+                    line[i] = make_float2(0.f, 0.f);
+                }
+                fft64_stage1(x);
+                // stage 2: block k1 yields X[k1 + 8 k2], k2 = 0..7, which sit at the
+                // 8 consecutive B columns n = 8 k1 + k2 (+ 64 p): one 16-byte store per part
+                uint8_t *bb = opB + buf * 2 * kPart;
+                auto pack = [](const uint16_t *s8) {
+                    return make_uint4(s8[0] | (static_cast<uint32_t>(s8[1]) << 16),
+                                      s8[2] | (static_cast<uint32_t>(s8[3]) << 16),
+                                      s8[4] | (static_cast<uint32_t>(s8[5]) << 16),
+                                      s8[6] | (static_cast<uint32_t>(s8[7]) << 16));
+                };
+#pragma unroll
+                for (int k1 = 0; k1 < 8; k1++) {
+                    float2 tt[8];
+#pragma unroll
+                    for (int n2 = 0; n2 < 8; n2++) tt[n2] = x[n2 + 8 * k1];
+                    dft8(tt);
+                    uint16_t rh[8], ih[8], rl[8], il[8];
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        float br, bi, dummy;
+                        rh[j] = to16<kBF16>(tt[j].x, br);
+                        ih[j] = to16<kBF16>(tt[j].y, bi);
+                        if constexpr (kSplit) {
+                            rl[j] = to16<kBF16>(tt[j].x - br, dummy);
+                            il[j] = to16<kBF16>(tt[j].y - bi, dummy);
+                        }
+                    }
+                    const int n0 = 8 * k1 + 64 * p;
+                    *reinterpret_cast<uint4 *>(bb + b_off(n0, jy)) = pack(rh);
+                    *reinterpret_cast<uint4 *>(bb + b_off(n0, 64 + jy)) = pack(ih);
+                    if constexpr (kSplit) {
+                        *reinterpret_cast<uint4 *>(bb + kPart + b_off(n0, jy)) = pack(rl);
+                        *reinterpret_cast<uint4 *>(bb + kPart + b_off(n0, 64 + jy)) = pack(il);
+                    }
+                }
+            }
+            tc::fence_proxy_async();
+        } else if (t > t0 && !abort_flag) {
+            // ---- a5, a6: drain sample t-1 from D[buf ^ 1]
+            const int pb = buf ^ 1;
+            if (!tc::mbar_wait(&bar_mma[pb], phase[pb], wait_budget)) {
+                atomicOr(status, kStatusTimeout);
+                abort_flag = 1;
+            } else {
+                tc::fence_after_sync();
+                const int part = lane >> 4;
+                const uint32_t lane_addr = taddr + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+#pragma unroll
+                for (int hh = 0; hh < 2; hh++) {
+                    float vx[32], vy[32];
+                    tc::tmem_ld32(lane_addr + pb * 128 + 32 * hh, vx);        // pol X, columns 32 hh + j
+                    tc::tmem_ld32(lane_addr + pb * 128 + 64 + 32 * hh, vy);   // pol Y
+#pragma unroll
+                    for (int q8 = 0; q8 < 2; q8++) {
+                        float sm[32];                                          // sums of 8 pixels
+                        const uint32_t acc_addr = lane_addr + kColAcc + 64 * hh + 32 * q8;
+                        tc::tmem_ld32(acc_addr, sm);
+#pragma unroll
+                        for (int jj = 0; jj < 8; jj++) {
+                            const int j = 8 * q8 + jj;
+                            const float ox = part ? vx[16 + j] : vx[j], oy = part ? vy[16 + j] : vy[j];
+                            const float sx = part ? vx[j] : vx[16 + j], sy = part ? vy[j] : vy[16 + j];
+                            const float gx = __shfl_xor_sync(0xffffffffu, sx, 16);
+                            const float gy = __shfl_xor_sync(0xffffffffu, sy, 16);
+                            const float xr = part ? gx : ox, xi = part ? ox : gx;
+                            const float yr = part ? gy : oy, yi = part ? oy : gy;
+                            float *a4 = sm + 4 * jj;
+                            a4[0] = fmaf(xr, xr, fmaf(xi, xi, a4[0]));
+                            a4[1] = fmaf(yr, yr, fmaf(yi, yi, a4[1]));
+                            a4[2] = fmaf(xr, yr, fmaf(xi, yi, a4[2]));
+                            a4[3] = fmaf(xi, yr, fmaf(-xr, yi, a4[3]));
+                        }
+                        uint32_t w[32];
+#pragma unroll
+                        for (int i = 0; i < 32; i++) w[i] = __float_as_uint(sm[i]);
+                        tmem_st32(acc_addr, w);
+                    }
+                }
+            }
+            phase[pb] ^= 1u;
+        }
+        if (has_next) {
+#pragma unroll
+            for (int r = 0; r < kPreW; r++) {
+                const int w = tid + r * kThreads;
+                if (w < APW) stage[w] = pre[r];
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        if (abort_flag) break;
+
+        // ---- a4 (columns) of sample t: D[buf] = A B[buf]^T, one thread issues
+        if (work && tid == 0 && !withhold_mma) {
+            tc::fence_after_sync();
+            const uint32_t d_tmem = taddr + buf * 128;
+            const uint32_t bb = b_base + buf * 2 * kPart;
+#pragma unroll
+            for (int kb = 0; kb < 8; kb++) {
+                const uint64_t b_hi = tc::smem_desc(bb + kb * 256, kLBO, kSBO);
+                const uint32_t a_hi = taddr + kColA + kb * 8;
+                mma_ts(d_tmem, a_hi, b_hi, idesc, kb > 0 ? 1u : 0u);
+                if constexpr (kSplit) {
+                    const uint64_t b_lo = tc::smem_desc(bb + kPart + kb * 256, kLBO, kSBO);
+                    mma_ts(d_tmem, a_hi, b_lo, idesc, 1u);
+                    mma_ts(d_tmem, a_hi + 64, b_hi, idesc, 1u);
+                }
+            }
+            tc::mma_commit(&bar_mma[buf]);
+        }
+    }
+
+    // ---- partial sums from the drain warps' TMEM lanes (undo the FP16 scale exactly)
+    if (warp >= 4) {
+        tc::fence_after_sync();
+        const float inv = 1.f / (scale * scale);
+        const int qd = warp & 3, part = lane >> 4;
+        const int my = 16 * qd + (lane & 15);
+        const uint32_t lane_addr = taddr + (static_cast<uint32_t>(32 * qd) << 16);
+        float4 *dst = reinterpret_cast<float4 *>(partial) + (static_cast<size_t>(tau) * n_items + item) * (M64 * M64);
+#pragma unroll
+        for (int hh = 0; hh < 2; hh++) {
+            float s0[32], s1[32];
+            tc::tmem_ld32(lane_addr + kColAcc + 64 * hh, s0);
+            tc::tmem_ld32(lane_addr + kColAcc + 64 * hh + 32, s1);
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int n = 32 * hh + 16 * part + j;          // B column -> mx = n / 8 + 8 (n mod 8)
+                const int mx = (n >> 3) + 8 * (n & 7);
+                const float *a4 = j < 8 ? s0 + 4 * j : s1 + 4 * (j - 8);
+                dst[my * M64 + mx] = make_float4(a4[0] * inv, a4[1] * inv, a4[2] * inv, a4[3] * inv);
+            }
+        }
+    }
+    // an aborted CTA may still have an MMA in flight: give it a bounded chance to land
+    if (tid == 0 && abort_flag) {
+        tc::mbar_wait(&bar_mma[0], phase[0], wait_budget);
+        tc::mbar_wait(&bar_mma[1], phase[1], wait_budget);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(taddr, 512);
+}
+
+size_t pipe_smem(int A, int K)
+{
+    const int AP = A * 2;
+    size_t b = 4 * static_cast<size_t>(kPart);
+    b += sizeof(float2) * (static_cast<size_t>(2) * M64 * S64 + 2 * AP + K * K);
+    b += sizeof(uint32_t) * ((AP + 3) / 4);
+    return (b + 15) & ~static_cast<size_t>(15);
+}
+
+template <int VAR, int KC>
+int prepare_pipe_t(const epic_plan_s *plan)
+{
+    return cudaFuncSetAttribute(tc_pipe64_kernel<VAR, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(pipe_smem(plan->A, plan->K))) == cudaSuccess
+               ? EPIC_OK
+               : EPIC_ERR_UNSUPPORTED;
+}
+
+template <int VAR, int KC>
+int launch_pipe_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau_out,
+                  cudaStream_t stream)
+{
+    int n_tau = plan->force_tau > 0 ? plan->force_tau : fp32_pick_tau(g.n_items, T, plan->sm_count);
+    if (n_tau > g.tau_cap) n_tau = g.tau_cap;
+    *n_tau_out = n_tau;
+    const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));
+    tc_pipe64_kernel<VAR, KC><<<grid, kThreads, pipe_smem(plan->A, plan->K), stream>>>(
+        v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN, g.d_sched, g.d_nrounds, g.rmax,
+        g.d_rowmask, plan->d_dft_rows, plan->A, plan->C, T, g.N, g.Q1, g.n_items, n_tau, g.d_partial,
+        plan->d_status, plan->wait_budget, plan->test_withhold_mma);
+    return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
+template <class F>
+int pipe_dispatch(int precision, int K, F &&f)
+{
+    const int var = precision == EPIC_TC_SPLIT_FP16 ? 0 : precision == EPIC_TC_FP16 ? 1 : 2;
+    auto with_k = [&](auto vv) {
+        switch (K) {
+        case 1: return f(vv, std::integral_constant<int, 1>{});
+        case 5: return f(vv, std::integral_constant<int, 5>{});
+        default: return f(vv, std::integral_constant<int, 0>{});
+        }
+    };
+    switch (var) {
+    case 0: return with_k(std::integral_constant<int, 0>{});
+    case 1: return with_k(std::integral_constant<int, 1>{});
+    default: return with_k(std::integral_constant<int, 2>{});
+    }
+}
+
+}  // namespace
+
+size_t tc_pipe_smem_bytes(int A, int K) { return pipe_smem(A, K); }
+
+int prepare_tc_pipe(const epic_plan_s *plan)
+{
+    return pipe_dispatch(plan->precision, plan->K, [&](auto vv, auto kc) {
+        return prepare_pipe_t<decltype(vv)::value, decltype(kc)::value>(plan);
+    });
+}
+
+int launch_tc_pipe(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
+                   cudaStream_t stream)
+{
+    return pipe_dispatch(plan->precision, plan->K, [&](auto vv, auto kc) {
+        return launch_pipe_t<decltype(vv)::value, decltype(kc)::value>(plan, g, v, gains, T, n_tau, stream);
+    });
+}
+
+// The column-DFT operand as plain rows for tcgen05.st: [part][128 rows][128 K]
+// 16-bit words, hi part then lo part, FP16 or BF16 bit patterns.
+void build_dft_rows(bool bf16, std::vector<uint16_t> &words)
+{
+    words.assign(2 * 128 * 128, 0);
+    auto to16h = [bf16](double x, double &back) -> uint16_t {
+        if (bf16) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(static_cast<float>(x));
+            back = static_cast<double>(__bfloat162float(h));
+            return __bfloat16_as_ushort(h);
+        }
+        const __half h = __float2half_rn(static_cast<float>(x));
+        back = static_cast<double>(__half2float(h));
+        return __half_as_ushort(h);
+    };
+    for (int r = 0; r < 128; r++) {
+        const int q = r / 32, l = r % 32;
+        const int my = 16 * q + (l % 16), part = l / 16;
+        for (int k = 0; k < 128; k++) {
+            const int jy = k % 64;
+            const bool im_in = k >= 64;
+            const long e = (static_cast<long>(jy) * my) % 64;
+            const double th = 2.0 * M_PI * static_cast<double>(e) / 64.0;
+            double a;
+            if (part == 0) a = im_in ? -std::sin(th) : std::cos(th);
+            else a = im_in ? std::cos(th) : std::sin(th);
+            double hb = 0, lb = 0;
+            words[static_cast<size_t>(r) * 128 + k] = to16h(a, hb);
+            words[static_cast<size_t>(128 * 128) + static_cast<size_t>(r) * 128 + k] = to16h(a - hb, lb);
+        }
+    }
+}
+
+}  // namespace epic

@@ -207,3 +207,27 @@ def test_kernel_taper_lwa_full_size_sampled_channels():
     ref = _oracle(wl, channels=chans)
     got = np.concatenate([p.split(gpu)[c].ravel() for c in chans])
     assert peak_rel_err(got, ref, wl.grid_n[chans], 2).max() < FP32_TOL
+
+
+def test_dense_workload_full_size_sampled_channel():
+    """The dense 2048-antenna array (256 channels, 500 spectra, 7x7 kernel, 512
+    grid) at full size in the benchmark's launch configuration; one channel of
+    the literal form and of the kernel-taper form against the oracle."""
+    wl = synth.dense()
+    chans = [129]
+    ref = _oracle(wl, channels=chans)
+    for flags in (0, epic.EPIC_KERNEL_TAPER):
+        gpu, p = run_gpu(wl, flags=flags)
+        got = p.split(gpu)[chans[0]].ravel()
+        assert peak_rel_err(got, ref, wl.grid_n[chans], 2).max() < FP32_TOL
+        p.close()
+
+
+@pytest.mark.parametrize("A,P,N,K", [(2048, 2, 512, 15), (4096, 1, 128, 5), (1500, 2, 256, 9)])
+def test_largest_supported_shapes(A, P, N, K):
+    """The limits the plan accepts: n_ant * n_pol = 4096 and K = 15 (footprints
+    of 15 x 15 cells), on the M = 64 kernel and its runtime-K path."""
+    wl = synth.random_small(A=A, P=P, C=1, T=2, N=N, K=K, seed=A + N + K)
+    gpu, _ = run_gpu(wl)
+    ref = _oracle(wl)
+    assert peak_rel_err(gpu, ref, wl.grid_n, P).max() < FP32_TOL

@@ -58,3 +58,23 @@ def test_tensor_split_fp16_with_taper_and_flags():
 def test_tensor_lwa_full_size_sampled_channels():
     wl = synth.lwa()
     assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16, channels=[3, 60]).max() < SPLIT_TOL
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(monkeypatch):
+    """Failure detection without a fault: the tensor kernel withholds its MMA,
+    so the mbarrier it waits on never completes; the bounded wait gives up,
+    the plan's status word reads EPIC_ERR_TIMEOUT, and the next plan on the
+    same context images correctly."""
+    import torch
+    from gpu_helpers import torch_inputs
+    wl = synth.random_small(A=40, P=2, C=1, T=3, N=64, K=3, seed=320)
+    monkeypatch.setenv("EPIC_TEST_WITHHOLD_MMA", "1")
+    p = epic.Plan.from_workload(wl, precision=epic.EPIC_TC_SPLIT_FP16)
+    v, g = torch_inputs(wl)
+    p.image(v, g)
+    torch.cuda.synchronize()
+    assert p.status() == epic.EPIC_ERR_TIMEOUT
+    assert p.status() == epic.EPIC_OK          # reading clears it
+    p.close()
+    monkeypatch.delenv("EPIC_TEST_WITHHOLD_MMA")
+    assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16).max() < SPLIT_TOL
