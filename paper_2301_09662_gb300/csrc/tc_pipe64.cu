@@ -9,19 +9,21 @@
 //    memory for the whole CTA (loaded once with tcgen05.st), which frees the
 //    shared memory for two B buffers;
 //  * B is MN-major with columns n = 8 (mx mod 8) + mx / 8 (+ 64 for pol Y):
-//    the last radix-8 block of the thread that row-transforms grid row jy
-//    yields 8 consecutive columns, stored as one 16-byte word per part
-//    straight from registers, so H never goes back through the grid;
+//    a stage-2 radix-8 block of the row transform of grid row jy yields 8
+//    consecutive columns, stored as one 16-byte word per part straight from
+//    registers, so H never goes back through the grid;
 //  * two B buffers and two TMEM accumulators: the MMA of sample t runs while
-//    sample t+1 is unpacked, gridded and row-transformed, and warps 4-7 drain
-//    sample t-1's accumulator (products summed over time) while warps 0-3 do
-//    the row transforms.
+//    sample t+1 is unpacked, gridded and row-transformed, and its products are
+//    summed after that row transform;
+//  * all eight warps share every phase: a row (pol, jy) is transformed by warps
+//    w and w + 4 (half of each radix-8 stage, the stage-1 values exchanged in
+//    place through the grid row under a 64-thread named barrier), and warp w
+//    sums the products of TMEM lanes 32 (w mod 4) .. and column half w / 4.
 //
 // TMEM columns: D0 [0,128), D1 [128,256), A_hi [256,320), A_lo [320,384)
 // (A packs two 16-bit K values per 32-bit column, lower K in the low half),
 // and the time sums [384,512): lane r = (my, part) keeps XX, YY, Re XY, Im XY
-// of its 32 pixels, so the per-pixel accumulators cost no registers in the
-// row-transform warps.
+// of its 32 pixels, so the per-pixel accumulators cost no registers.
 // Every wait is bounded; a timeout is recorded in the plan's status word.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -43,6 +45,9 @@ constexpr uint32_t kLBO = 128;                  // K-adjacent core matrices
 constexpr uint32_t kSBO = 2048;                 // N-adjacent core matrices (16 along K x 128 B)
 constexpr uint32_t kColA = 256;                 // first TMEM column of A
 constexpr uint32_t kColAcc = 384;               // first TMEM column of the time sums
+constexpr int kSimt = kThreads;                 // warps 0-7: unpack, gridding, row transforms, products
+constexpr int kPipeThreads = kSimt + 32;        // warp 8: issues the MMAs
+constexpr int kBarSimt = 5;                     // named barrier of the eight SIMT warps
 
 // byte offset of B element (n, k) in the MN-major canonical layout
 __host__ __device__ constexpr uint32_t b_off(int n, int k)
@@ -50,17 +55,27 @@ __host__ __device__ constexpr uint32_t b_off(int n, int k)
     return static_cast<uint32_t>((n >> 3) * kSBO + (k >> 3) * kLBO + (k & 7) * 16 + (n & 7) * 2);
 }
 
-template <bool BF16>
-__device__ __forceinline__ uint16_t to16(float x, float &back)
+// Two FP32 values as one packed 16-bit pair (a in the low half) and, for the
+// split forms, the pair of their rounding residuals (exact in FP32).
+template <bool BF16, bool SPLIT>
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint32_t &lo)
 {
     if constexpr (BF16) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        back = __bfloat162float(h);
-        return __bfloat16_as_ushort(h);
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        if constexpr (SPLIT) {
+            const float2 back = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(a - back.x, b - back.y);
+            lo = *reinterpret_cast<const uint32_t *>(&l);
+        }
     } else {
-        const __half h = __float2half_rn(x);
-        back = __half2float(h);
-        return __half_as_ushort(h);
+        const __half2 h = __floats2half2_rn(a, b);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        if constexpr (SPLIT) {
+            const float2 back = __half22float2(h);
+            const __half2 l = __floats2half2_rn(a - back.x, b - back.y);
+            lo = *reinterpret_cast<const uint32_t *>(&l);
+        }
     }
 }
 
@@ -102,8 +117,97 @@ __host__ __device__ constexpr uint32_t idesc_mn(int M, int N, bool bf16)
            (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
 }
 
+// Half H of stage 1 of the 8 x 8 row transform (fft64.cuh): for n2 = 4 H .. 4 H + 3,
+// DFT8 over line[n2 + 8 n1], twiddled by w64^(n2 k1), back in place.
+template <int H>
+__device__ __forceinline__ void row_stage1(float2 *line)
+{
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int n2 = 4 * H + i;
+        float2 t[8];
+#pragma unroll
+        for (int n1 = 0; n1 < 8; n1++) t[n1] = line[n2 + 8 * n1];
+        dft8(t);
+        line[n2] = t[0];
+#pragma unroll
+        for (int k1 = 1; k1 < 8; k1++) line[n2 + 8 * k1] = n2 == 0 ? t[k1] : cmul(t[k1], c_tw64.w[n2 * k1]);
+    }
+}
+
+// Half H of stage 2: for k1 = 4 H .. 4 H + 3, DFT8 over line[n2 + 8 k1] (zeroed
+// for the next sample's gridding), which yields X[k1 + 8 k2] for the 8
+// consecutive B columns n = 8 k1 + k2 (+ 64 p): one 16-byte store per part.
+template <int H, bool BF16, bool SPLIT>
+__device__ __forceinline__ void row_stage2(float2 *line, uint8_t *bb, int p, int jy)
+{
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int k1 = 4 * H + j;
+        float2 t[8];
+#pragma unroll
+        for (int n2 = 0; n2 < 8; n2++) {
+            t[n2] = line[n2 + 8 * k1];
+            line[n2 + 8 * k1] = make_float2(0.f, 0.f);
+        }
+        dft8(t);
+        uint32_t rh[4], ih[4], rl[4], il[4];
+#pragma unroll
+        for (int w = 0; w < 4; w++) {
+            split_pair<BF16, SPLIT>(t[2 * w].x, t[2 * w + 1].x, rh[w], rl[w]);
+            split_pair<BF16, SPLIT>(t[2 * w].y, t[2 * w + 1].y, ih[w], il[w]);
+        }
+        const int n0 = 8 * k1 + 64 * p;
+        *reinterpret_cast<uint4 *>(bb + b_off(n0, jy)) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+        *reinterpret_cast<uint4 *>(bb + b_off(n0, 64 + jy)) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+        if constexpr (SPLIT) {
+            *reinterpret_cast<uint4 *>(bb + kPart + b_off(n0, jy)) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+            *reinterpret_cast<uint4 *>(bb + kPart + b_off(n0, 64 + jy)) = make_uint4(il[0], il[1], il[2], il[3]);
+        }
+    }
+}
+
+// XX, YY, XY of one sample added to this warp's time sums.  The warp reads TMEM
+// lanes 32 (w mod 4) + l = (my, part) and B columns 32 hh .. 32 hh + 31 of each
+// polarisation; lane l keeps the 16 pixels j = 16 part .. of that half, at sum
+// columns kColAcc + 64 hh + 4 (j mod 16); Re and Im of a pixel sit in lanes l
+// and l ^ 16 and are exchanged by one shuffle.
+__device__ __forceinline__ void drain_sample(uint32_t lane_addr, uint32_t dcol, int hh, int part)
+{
+    uint32_t rx[32], ry[32], s0[32], s1[32];
+    const uint32_t acc = lane_addr + kColAcc + 64 * hh;
+    tc::tmem_ld32_issue(lane_addr + dcol + 32 * hh, rx);
+    tc::tmem_ld32_issue(lane_addr + dcol + 64 + 32 * hh, ry);
+    tc::tmem_ld32_issue(acc, s0);
+    tc::tmem_ld32_issue(acc + 32, s1);
+    tc::tmem_wait_ld();
+    tc::reg_fence32(rx);
+    tc::reg_fence32(ry);
+    tc::reg_fence32(s0);
+    tc::reg_fence32(s1);
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        const float ox = __uint_as_float(part ? rx[16 + j] : rx[j]);
+        const float oy = __uint_as_float(part ? ry[16 + j] : ry[j]);
+        const float sx = __uint_as_float(part ? rx[j] : rx[16 + j]);
+        const float sy = __uint_as_float(part ? ry[j] : ry[16 + j]);
+        const float gx = __shfl_xor_sync(0xffffffffu, sx, 16);
+        const float gy = __shfl_xor_sync(0xffffffffu, sy, 16);
+        const float xr = part ? gx : ox, xi = part ? ox : gx;
+        const float yr = part ? gy : oy, yi = part ? oy : gy;
+        uint32_t *a4 = j < 8 ? s0 + 4 * j : s1 + 4 * (j - 8);
+        a4[0] = __float_as_uint(fmaf(xr, xr, fmaf(xi, xi, __uint_as_float(a4[0]))));
+        a4[1] = __float_as_uint(fmaf(yr, yr, fmaf(yi, yi, __uint_as_float(a4[1]))));
+        a4[2] = __float_as_uint(fmaf(xr, yr, fmaf(xi, yi, __uint_as_float(a4[2]))));
+        a4[3] = __float_as_uint(fmaf(xi, yr, fmaf(-xr, yi, __uint_as_float(a4[3]))));
+    }
+    tc::tmem_st32_issue(acc, s0);
+    tc::tmem_st32_issue(acc + 32, s1);
+    tc::tmem_wait_st();
+}
+
 template <int VAR, int KC>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kPipeThreads, 1)
 tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
                  const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K_rt,
                  const int *__restrict__ chans, const float2 *__restrict__ twN,
@@ -140,7 +244,7 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
     const int t0 = static_cast<int>(static_cast<long long>(T) * tau / n_tau);
     const int t1 = static_cast<int>(static_cast<long long>(T) * (tau + 1) / n_tau);
     const uint32_t *my_sched = sched + (static_cast<size_t>(ci) * 8 + warp) * rmax * 32;
-    const int my_rounds = nrounds[ci * 8 + warp];
+    const int my_rounds = warp < 8 ? nrounds[ci * 8 + warp] : 0;
     const unsigned long long rows_used = rowmask[ci];
 
     if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
@@ -153,7 +257,8 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
 
     // ---- set-up: phase-folded gains and taps, the largest gain for the FP16 scale
     float gmax = 0.f;
-    for (int a = tid; a < A; a += kThreads) {
+    const bool simt = warp < 8;
+    for (int a = simt ? tid : A; a < A; a += kThreads) {
         const short2 k = cells[static_cast<size_t>(c) * A + a];
         if (k.x < hk || k.x >= N - hk || k.y < hk || k.y >= N - hk) atomicOr(status, kStatusDevice);
         const float2 ph = twN[((k.x * hx + k.y * hy) % N + N) % N];
@@ -164,24 +269,25 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
             gmax = fmaxf(gmax, sqrtf(gg.x * gg.x + gg.y * gg.y));
         }
     }
-    for (int i = tid; i < KK; i += kThreads) {
+    for (int i = simt ? tid : KK; i < KK; i += kThreads) {
         const int dy = i / K - hk, dx = i % K - hk;
         tapw[i] = cmul(kern[i], twN[((dx * hx + dy * hy) % N + N) % N]);
     }
-    for (int i = tid; i < P * BUF; i += kThreads) G[i] = make_float2(0.f, 0.f);
-    for (int i = tid; i < static_cast<int>(4 * kPart / 16); i += kThreads)
+    for (int i = simt ? tid : P * BUF; i < P * BUF; i += kThreads) G[i] = make_float2(0.f, 0.f);
+    for (int i = simt ? tid : static_cast<int>(4 * kPart / 16); i < static_cast<int>(4 * kPart / 16); i += kThreads)
         reinterpret_cast<uint4 *>(opB)[i] = make_uint4(0u, 0u, 0u, 0u);   // rows never written stay zero
-    if (t0 < t1) {
+    if (simt && t0 < t1) {
         const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(t0) * C + c) * AP);
         for (int w = tid; w < APW; w += kThreads) stage[w] = row[w];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-    if (lane == 0) red[warp] = gmax;
+    if (simt && lane == 0) red[warp] = gmax;
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = tmem_slot;
+    const uint32_t lane_addr = taddr + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
     float scale = 1.f;
     if constexpr (!kBF16) {
         float gm = 0.f;
@@ -193,7 +299,7 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
         if (bound > 0.f) e2 = static_cast<int>(floorf(log2f(16384.f / bound)));
         scale = ldexpf(1.f, max(-40, min(40, e2)));
     }
-    for (int i = tid; i < AP; i += kThreads) gp[i] = cscale(gp[i], scale);
+    for (int i = simt ? tid : AP; i < AP; i += kThreads) gp[i] = cscale(gp[i], scale);
     // A (hi, lo) into TMEM: warp w < 4 writes rows 32w .. 32w+31
     if (warp < 4) {
         const int r = 32 * warp + lane;
@@ -206,13 +312,15 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
                 tmem_st32(taddr + (static_cast<uint32_t>(32 * warp) << 16) + kColA + part * 64 + half * 32, w);
             }
     }
-    if (warp >= 4) {
-        // zero the time sums of this warp's lanes
+    if (simt) {
+        // zero this warp's time sums: TMEM lanes 32 (w mod 4) .., columns kColAcc + 64 (w / 4) ..
         uint32_t z[32];
 #pragma unroll
         for (int j = 0; j < 32; j++) z[j] = 0u;
-        const uint32_t row_addr = taddr + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + kColAcc;
-        for (int cc = 0; cc < 128; cc += 32) tmem_st32(row_addr + cc, z);
+        const uint32_t acc = lane_addr + kColAcc + 64 * (warp >> 2);
+        tc::tmem_st32_issue(acc, z);
+        tc::tmem_st32_issue(acc + 32, z);
+        tc::tmem_wait_st();
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -222,7 +330,34 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
     const uint32_t b_base = tc::smem_u32(opB);
     uint32_t phase[2] = {0u, 0u};
     constexpr int kPreW = kMaxAP / 4 / kThreads;
-    for (int t = t0; t <= t1; t++) {
+    if (!simt) {
+        // ---- a4 (columns): D[buf] = A B[buf]^T for each sample, issued by one
+        // thread once the eight SIMT warps have written B[buf] (block barrier)
+        for (int t = t0; t <= t1; t++) {
+            tc::fence_before_sync();
+            __syncthreads();
+            if (abort_flag) break;
+            if (t < t1 && lane == 0 && !withhold_mma) {
+                tc::fence_after_sync();
+                const int buf = (t - t0) & 1;
+                const uint32_t d_tmem = taddr + buf * 128;
+                const uint32_t bb = b_base + buf * 2 * kPart;
+#pragma unroll
+                for (int kb = 0; kb < 8; kb++) {
+                    const uint64_t b_hi = tc::smem_desc(bb + kb * 256, kLBO, kSBO);
+                    const uint32_t a_hi = taddr + kColA + kb * 8;
+                    mma_ts(d_tmem, a_hi, b_hi, idesc, kb > 0 ? 1u : 0u);
+                    if constexpr (kSplit) {
+                        const uint64_t b_lo = tc::smem_desc(bb + kPart + kb * 256, kLBO, kSBO);
+                        mma_ts(d_tmem, a_hi, b_lo, idesc, 1u);
+                        mma_ts(d_tmem, a_hi + 64, b_hi, idesc, 1u);
+                    }
+                }
+                tc::mma_commit(&bar_mma[buf]);
+            }
+            __syncwarp();
+        }
+    } else for (int t = t0; t <= t1; t++) {
         const bool work = t < t1;
         const int buf = (t - t0) & 1;
         // ---- a1, a2 (sample t) and prefetch of t+1
@@ -242,7 +377,7 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
                 pre[r] = (has_next && w < APW) ? __ldg(row + w) : 0u;
             }
         }
-        __syncthreads();
+        tc::named_bar_sync(kBarSimt, kSimt);
 
         // ---- a3: scheduled gridding of sample t (the MMA of t-1 is running)
         if (work) {
@@ -255,120 +390,72 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
                     const int x0 = static_cast<int>((d >> 22) & 0x3Fu);
                     const float2 e0 = es[a * P], e1 = es[a * P + 1];
                     const float2 *wrow = tapw + dyi * K;
+                    float2 *gy = G + y * S64;
+                    if constexpr (KC > 0) {
+                        // the KC cells of one lane are distinct, so every load of the
+                        // round can be issued before its first store
+                        float2 o0[KC], o1[KC];
 #pragma unroll
-                    for (int dx = 0; dx < (KC > 0 ? KC : K); dx++) {
-                        const float2 w = wrow[dx];
-                        const int x = (x0 + dx) & (M64 - 1);
-                        float2 *c0 = G + y * S64 + x;
-                        float2 *c1 = c0 + BUF;
-                        const float2 v0 = cmul(w, e0), v1 = cmul(w, e1);
-                        float2 o0 = *c0, o1 = *c1;
-                        o0.x += v0.x;
-                        o0.y += v0.y;
-                        o1.x += v1.x;
-                        o1.y += v1.y;
-                        *c0 = o0;
-                        *c1 = o1;
+                        for (int dx = 0; dx < KC; dx++) {
+                            const int x = (x0 + dx) & (M64 - 1);
+                            o0[dx] = gy[x];
+                            o1[dx] = gy[BUF + x];
+                        }
+#pragma unroll
+                        for (int dx = 0; dx < KC; dx++) {
+                            const float2 w = wrow[dx];
+                            const float2 v0 = cmul(w, e0), v1 = cmul(w, e1);
+                            const int x = (x0 + dx) & (M64 - 1);
+                            gy[x] = make_float2(o0[dx].x + v0.x, o0[dx].y + v0.y);
+                            gy[BUF + x] = make_float2(o1[dx].x + v1.x, o1[dx].y + v1.y);
+                        }
+                    } else {
+                        for (int dx = 0; dx < K; dx++) {
+                            const float2 w = wrow[dx];
+                            const int x = (x0 + dx) & (M64 - 1);
+                            const float2 v0 = cmul(w, e0), v1 = cmul(w, e1);
+                            const float2 o0 = gy[x], o1 = gy[BUF + x];
+                            gy[x] = make_float2(o0.x + v0.x, o0.y + v0.y);
+                            gy[BUF + x] = make_float2(o1.x + v1.x, o1.y + v1.y);
+                        }
                     }
                 }
                 __syncwarp();
             }
         }
-        __syncthreads();
+        tc::named_bar_sync(kBarSimt, kSimt);
 
-        if (warp < 4) {
-            // ---- a4 (rows) of sample t into B[buf], MN-major, hi/lo
-            const int q = tid;                        // 128 tasks: (pol, row)
-            const int jy = q & 63, p = q >> 6;
-            if (work && ((rows_used >> jy) & 1ull)) {
-                float2 *line = G + p * BUF + jy * S64;
-                float2 x[64];
-#pragma unroll
-                for (int i = 0; i < 64; i++) {
-                    x[i] = line[i];
-                    line[i] = make_float2(0.f, 0.f);
-                }
-                fft64_stage1(x);
-                // stage 2: block k1 yields X[k1 + 8 k2], k2 = 0..7, which sit at the
-                // 8 consecutive B columns n = 8 k1 + k2 (+ 64 p): one 16-byte store per part
-                uint8_t *bb = opB + buf * 2 * kPart;
-                auto pack = [](const uint16_t *s8) {
-                    return make_uint4(s8[0] | (static_cast<uint32_t>(s8[1]) << 16),
-                                      s8[2] | (static_cast<uint32_t>(s8[3]) << 16),
-                                      s8[4] | (static_cast<uint32_t>(s8[5]) << 16),
-                                      s8[6] | (static_cast<uint32_t>(s8[7]) << 16));
-                };
-#pragma unroll
-                for (int k1 = 0; k1 < 8; k1++) {
-                    float2 tt[8];
-#pragma unroll
-                    for (int n2 = 0; n2 < 8; n2++) tt[n2] = x[n2 + 8 * k1];
-                    dft8(tt);
-                    uint16_t rh[8], ih[8], rl[8], il[8];
-#pragma unroll
-                    for (int j = 0; j < 8; j++) {
-                        float br, bi, dummy;
-                        rh[j] = to16<kBF16>(tt[j].x, br);
-                        ih[j] = to16<kBF16>(tt[j].y, bi);
-                        if constexpr (kSplit) {
-                            rl[j] = to16<kBF16>(tt[j].x - br, dummy);
-                            il[j] = to16<kBF16>(tt[j].y - bi, dummy);
-                        }
-                    }
-                    const int n0 = 8 * k1 + 64 * p;
-                    *reinterpret_cast<uint4 *>(bb + b_off(n0, jy)) = pack(rh);
-                    *reinterpret_cast<uint4 *>(bb + b_off(n0, 64 + jy)) = pack(ih);
-                    if constexpr (kSplit) {
-                        *reinterpret_cast<uint4 *>(bb + kPart + b_off(n0, jy)) = pack(rl);
-                        *reinterpret_cast<uint4 *>(bb + kPart + b_off(n0, 64 + jy)) = pack(il);
-                    }
-                }
+        // ---- a4 (rows) of sample t into B[buf]: row (pol, jy) = tid mod 128 is
+        // shared by warps w and w + 4, each taking half of both radix-8 stages;
+        // the twiddled stage-1 values go back through the grid row between them
+        {
+            const int q = tid & 127, jy = q & 63, p = q >> 6;
+            const bool row_on = work && ((rows_used >> jy) & 1ull);
+            float2 *line = G + p * BUF + jy * S64;
+            if (row_on) {
+                if (warp < 4) row_stage1<0>(line);
+                else row_stage1<1>(line);
             }
-            tc::fence_proxy_async();
-        } else if (t > t0 && !abort_flag) {
-            // ---- a5, a6: drain sample t-1 from D[buf ^ 1]
+            tc::named_bar_sync(1 + (warp & 3), 64);
+            if (row_on) {
+                uint8_t *bb = opB + buf * 2 * kPart;
+                if (warp < 4) row_stage2<0, kBF16, kSplit>(line, bb, p, jy);
+                else row_stage2<1, kBF16, kSplit>(line, bb, p, jy);
+            }
+        }
+        // ---- a5, a6: products of sample t-1 from D[buf ^ 1] into the time sums
+        if (t > t0 && !abort_flag) {
             const int pb = buf ^ 1;
             if (!tc::mbar_wait(&bar_mma[pb], phase[pb], wait_budget)) {
                 atomicOr(status, kStatusTimeout);
                 abort_flag = 1;
             } else {
                 tc::fence_after_sync();
-                const int part = lane >> 4;
-                const uint32_t lane_addr = taddr + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
-#pragma unroll
-                for (int hh = 0; hh < 2; hh++) {
-                    float vx[32], vy[32];
-                    tc::tmem_ld32(lane_addr + pb * 128 + 32 * hh, vx);        // pol X, columns 32 hh + j
-                    tc::tmem_ld32(lane_addr + pb * 128 + 64 + 32 * hh, vy);   // pol Y
-#pragma unroll
-                    for (int q8 = 0; q8 < 2; q8++) {
-                        float sm[32];                                          // sums of 8 pixels
-                        const uint32_t acc_addr = lane_addr + kColAcc + 64 * hh + 32 * q8;
-                        tc::tmem_ld32(acc_addr, sm);
-#pragma unroll
-                        for (int jj = 0; jj < 8; jj++) {
-                            const int j = 8 * q8 + jj;
-                            const float ox = part ? vx[16 + j] : vx[j], oy = part ? vy[16 + j] : vy[j];
-                            const float sx = part ? vx[j] : vx[16 + j], sy = part ? vy[j] : vy[16 + j];
-                            const float gx = __shfl_xor_sync(0xffffffffu, sx, 16);
-                            const float gy = __shfl_xor_sync(0xffffffffu, sy, 16);
-                            const float xr = part ? gx : ox, xi = part ? ox : gx;
-                            const float yr = part ? gy : oy, yi = part ? oy : gy;
-                            float *a4 = sm + 4 * jj;
-                            a4[0] = fmaf(xr, xr, fmaf(xi, xi, a4[0]));
-                            a4[1] = fmaf(yr, yr, fmaf(yi, yi, a4[1]));
-                            a4[2] = fmaf(xr, yr, fmaf(xi, yi, a4[2]));
-                            a4[3] = fmaf(xi, yr, fmaf(-xr, yi, a4[3]));
-                        }
-                        uint32_t w[32];
-#pragma unroll
-                        for (int i = 0; i < 32; i++) w[i] = __float_as_uint(sm[i]);
-                        tmem_st32(acc_addr, w);
-                    }
-                }
+                drain_sample(lane_addr, static_cast<uint32_t>(pb * 128), warp >> 2, lane >> 4);
             }
             phase[pb] ^= 1u;
         }
+        tc::fence_proxy_async();
         if (has_next) {
 #pragma unroll
             for (int r = 0; r < kPreW; r++) {
@@ -379,47 +466,29 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
         tc::fence_before_sync();
         __syncthreads();
         if (abort_flag) break;
-
-        // ---- a4 (columns) of sample t: D[buf] = A B[buf]^T, one thread issues
-        if (work && tid == 0 && !withhold_mma) {
-            tc::fence_after_sync();
-            const uint32_t d_tmem = taddr + buf * 128;
-            const uint32_t bb = b_base + buf * 2 * kPart;
-#pragma unroll
-            for (int kb = 0; kb < 8; kb++) {
-                const uint64_t b_hi = tc::smem_desc(bb + kb * 256, kLBO, kSBO);
-                const uint32_t a_hi = taddr + kColA + kb * 8;
-                mma_ts(d_tmem, a_hi, b_hi, idesc, kb > 0 ? 1u : 0u);
-                if constexpr (kSplit) {
-                    const uint64_t b_lo = tc::smem_desc(bb + kPart + kb * 256, kLBO, kSBO);
-                    mma_ts(d_tmem, a_hi, b_lo, idesc, 1u);
-                    mma_ts(d_tmem, a_hi + 64, b_hi, idesc, 1u);
-                }
-            }
-            tc::mma_commit(&bar_mma[buf]);
-        }
     }
 
-    // ---- partial sums from the drain warps' TMEM lanes (undo the FP16 scale exactly)
-    if (warp >= 4) {
+    // ---- partial sums from each warp's TMEM lanes and column half (undo the FP16 scale exactly)
+    if (simt) {
         tc::fence_after_sync();
         const float inv = 1.f / (scale * scale);
-        const int qd = warp & 3, part = lane >> 4;
-        const int my = 16 * qd + (lane & 15);
-        const uint32_t lane_addr = taddr + (static_cast<uint32_t>(32 * qd) << 16);
+        const int hh = warp >> 2, part = lane >> 4;
+        const int my = 16 * (warp & 3) + (lane & 15);
         float4 *dst = reinterpret_cast<float4 *>(partial) + (static_cast<size_t>(tau) * n_items + item) * (M64 * M64);
+        uint32_t s0[32], s1[32];
+        const uint32_t acc = lane_addr + kColAcc + 64 * hh;
+        tc::tmem_ld32_issue(acc, s0);
+        tc::tmem_ld32_issue(acc + 32, s1);
+        tc::tmem_wait_ld();
+        tc::reg_fence32(s0);
+        tc::reg_fence32(s1);
 #pragma unroll
-        for (int hh = 0; hh < 2; hh++) {
-            float s0[32], s1[32];
-            tc::tmem_ld32(lane_addr + kColAcc + 64 * hh, s0);
-            tc::tmem_ld32(lane_addr + kColAcc + 64 * hh + 32, s1);
-#pragma unroll
-            for (int j = 0; j < 16; j++) {
-                const int n = 32 * hh + 16 * part + j;          // B column -> mx = n / 8 + 8 (n mod 8)
-                const int mx = (n >> 3) + 8 * (n & 7);
-                const float *a4 = j < 8 ? s0 + 4 * j : s1 + 4 * (j - 8);
-                dst[my * M64 + mx] = make_float4(a4[0] * inv, a4[1] * inv, a4[2] * inv, a4[3] * inv);
-            }
+        for (int j = 0; j < 16; j++) {
+            const int n = 32 * hh + 16 * part + j;              // B column -> mx = n / 8 + 8 (n mod 8)
+            const int mx = (n >> 3) + 8 * (n & 7);
+            const uint32_t *a4 = j < 8 ? s0 + 4 * j : s1 + 4 * (j - 8);
+            dst[my * M64 + mx] = make_float4(__uint_as_float(a4[0]) * inv, __uint_as_float(a4[1]) * inv,
+                                             __uint_as_float(a4[2]) * inv, __uint_as_float(a4[3]) * inv);
         }
     }
     // an aborted CTA may still have an MMA in flight: give it a bounded chance to land
@@ -459,7 +528,7 @@ int launch_pipe_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const 
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));
-    tc_pipe64_kernel<VAR, KC><<<grid, kThreads, pipe_smem(plan->A, plan->K), stream>>>(
+    tc_pipe64_kernel<VAR, KC><<<grid, kPipeThreads, pipe_smem(plan->A, plan->K), stream>>>(
         v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN, g.d_sched, g.d_nrounds, g.rmax,
         g.d_rowmask, plan->d_dft_rows, plan->A, plan->C, T, g.N, g.Q1, g.n_items, n_tau, g.d_partial,
         plan->d_status, plan->wait_budget, plan->test_withhold_mma);
