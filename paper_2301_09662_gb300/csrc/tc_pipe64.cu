@@ -12,18 +12,23 @@
 //    a stage-2 radix-8 block of the row transform of grid row jy yields 8
 //    consecutive columns, stored as one 16-byte word per part straight from
 //    registers, so H never goes back through the grid;
-//  * two B buffers and two TMEM accumulators: the MMA of sample t runs while
-//    sample t+1 is unpacked, gridded and row-transformed, and its products are
-//    summed after that row transform;
-//  * all eight warps share every phase: a row (pol, jy) is transformed by warps
-//    w and w + 4 (half of each radix-8 stage, the stage-1 values exchanged in
-//    place through the grid row under a 64-thread named barrier), and warp w
-//    sums the products of TMEM lanes 32 (w mod 4) .. and column half w / 4.
+//  * two B buffers: the MMA of sample t runs while sample t+1 is unpacked,
+//    gridded and row-transformed; its products are summed after that row
+//    transform, before the MMA of t+1 is issued, so one accumulator suffices;
+//  * all eight SIMT warps share every phase: a row (pol, jy) is transformed by
+//    warps w and w + 4 (half of each radix-8 stage, the stage-1 values
+//    exchanged in place through the grid row under a 64-thread named barrier),
+//    and warp w sums the products of TMEM lanes 32 (w mod 4) .. and column
+//    half w / 4; a ninth warp only issues the MMAs.
 //
-// TMEM columns: D0 [0,128), D1 [128,256), A_hi [256,320), A_lo [320,384)
-// (A packs two 16-bit K values per 32-bit column, lower K in the low half),
-// and the time sums [384,512): lane r = (my, part) keeps XX, YY, Re XY, Im XY
-// of its 32 pixels, so the per-pixel accumulators cost no registers.
+// TMEM columns: D [0,128), A_hi [128,192), A_lo [192,256) (A packs two 16-bit
+// K values per 32-bit column, lower K in the low half), and the time sums
+// [256,512).  Lane r = (my, part) holds the Re (part 0) or Im (part 1) row of
+// D, and accumulates, for each of its 64 pixels, the partial sums that need no
+// other lane: own_X^2, own_Y^2, own_X own_Y, and other_X own_Y with other_X the
+// partner lane's (l ^ 16) value -- one shuffle per pixel.  The two lanes'
+// partials combine into XX, YY, Re XY, Im XY once, when the partial image is
+// written.
 // Every wait is bounded; a timeout is recorded in the plan's status word.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -43,8 +48,8 @@ constexpr int S64 = 65;
 constexpr uint32_t kPart = 128u * 128u * 2u;     // one 128 x 128 16-bit B part (32 KB)
 constexpr uint32_t kLBO = 128;                  // K-adjacent core matrices
 constexpr uint32_t kSBO = 2048;                 // N-adjacent core matrices (16 along K x 128 B)
-constexpr uint32_t kColA = 256;                 // first TMEM column of A
-constexpr uint32_t kColAcc = 384;               // first TMEM column of the time sums
+constexpr uint32_t kColA = 128;                 // first TMEM column of A (D is [0, 128))
+constexpr uint32_t kColAcc = 256;               // first TMEM column of the time sums
 constexpr int kSimt = kThreads;                 // warps 0-7: unpack, gridding, row transforms, products
 constexpr int kPipeThreads = kSimt + 32;        // warp 8: issues the MMAs
 constexpr int kBarSimt = 5;                     // named barrier of the eight SIMT warps
@@ -118,9 +123,9 @@ __host__ __device__ constexpr uint32_t idesc_mn(int M, int N, bool bf16)
 }
 
 // Half H of stage 1 of the 8 x 8 row transform (fft64.cuh): for n2 = 4 H .. 4 H + 3,
-// DFT8 over line[n2 + 8 n1], twiddled by w64^(n2 k1), back in place.
-template <int H>
-__device__ __forceinline__ void row_stage1(float2 *line)
+// DFT8 over line[n2 + 8 n1], twiddled by w64^(n2 k1), back in place.  H is
+// warp-uniform, so both halves run one copy of the code.
+__device__ __forceinline__ void row_stage1(float2 *line, int H)
 {
 #pragma unroll
     for (int i = 0; i < 4; i++) {
@@ -131,15 +136,15 @@ __device__ __forceinline__ void row_stage1(float2 *line)
         dft8(t);
         line[n2] = t[0];
 #pragma unroll
-        for (int k1 = 1; k1 < 8; k1++) line[n2 + 8 * k1] = n2 == 0 ? t[k1] : cmul(t[k1], c_tw64.w[n2 * k1]);
+        for (int k1 = 1; k1 < 8; k1++) line[n2 + 8 * k1] = cmul(t[k1], c_tw64.w[n2 * k1]);
     }
 }
 
 // Half H of stage 2: for k1 = 4 H .. 4 H + 3, DFT8 over line[n2 + 8 k1] (zeroed
 // for the next sample's gridding), which yields X[k1 + 8 k2] for the 8
 // consecutive B columns n = 8 k1 + k2 (+ 64 p): one 16-byte store per part.
-template <int H, bool BF16, bool SPLIT>
-__device__ __forceinline__ void row_stage2(float2 *line, uint8_t *bb, int p, int jy)
+template <bool BF16, bool SPLIT>
+__device__ __forceinline__ void row_stage2(float2 *line, uint8_t *bb, int p, int jy, int H)
 {
 #pragma unroll
     for (int j = 0; j < 4; j++) {
@@ -167,43 +172,40 @@ __device__ __forceinline__ void row_stage2(float2 *line, uint8_t *bb, int p, int
     }
 }
 
-// XX, YY, XY of one sample added to this warp's time sums.  The warp reads TMEM
-// lanes 32 (w mod 4) + l = (my, part) and B columns 32 hh .. 32 hh + 31 of each
-// polarisation; lane l keeps the 16 pixels j = 16 part .. of that half, at sum
-// columns kColAcc + 64 hh + 4 (j mod 16); Re and Im of a pixel sit in lanes l
-// and l ^ 16 and are exchanged by one shuffle.
-__device__ __forceinline__ void drain_sample(uint32_t lane_addr, uint32_t dcol, int hh, int part)
+// Partial products of one sample added to this warp's time sums.  The warp
+// reads TMEM lanes 32 (w mod 4) + l = (my, part) and B columns 32 hh .. 32 hh + 31
+// of each polarisation (pixels j = 0 .. 31 of the half); pixel j's four partial
+// sums sit at columns kColAcc + 128 hh + 4 j.  Two passes of 16 pixels keep the
+// registers at 96.
+__device__ __forceinline__ void drain_sample(uint32_t lane_addr, int hh)
 {
-    uint32_t rx[32], ry[32], s0[32], s1[32];
-    const uint32_t acc = lane_addr + kColAcc + 64 * hh;
-    tc::tmem_ld32_issue(lane_addr + dcol + 32 * hh, rx);
-    tc::tmem_ld32_issue(lane_addr + dcol + 64 + 32 * hh, ry);
-    tc::tmem_ld32_issue(acc, s0);
-    tc::tmem_ld32_issue(acc + 32, s1);
-    tc::tmem_wait_ld();
-    tc::reg_fence32(rx);
-    tc::reg_fence32(ry);
-    tc::reg_fence32(s0);
-    tc::reg_fence32(s1);
+#pragma unroll 1
+    for (int q = 0; q < 2; q++) {
+        uint32_t rx[16], ry[16], s0[32], s1[32];
+        const uint32_t acc = lane_addr + kColAcc + 128 * hh + 64 * q;
+        tc::tmem_ld16_issue(lane_addr + 32 * hh + 16 * q, rx);
+        tc::tmem_ld16_issue(lane_addr + 64 + 32 * hh + 16 * q, ry);
+        tc::tmem_ld32_issue(acc, s0);
+        tc::tmem_ld32_issue(acc + 32, s1);
+        tc::tmem_wait_ld();
+        tc::reg_fence16(rx);
+        tc::reg_fence16(ry);
+        tc::reg_fence32(s0);
+        tc::reg_fence32(s1);
 #pragma unroll
-    for (int j = 0; j < 16; j++) {
-        const float ox = __uint_as_float(part ? rx[16 + j] : rx[j]);
-        const float oy = __uint_as_float(part ? ry[16 + j] : ry[j]);
-        const float sx = __uint_as_float(part ? rx[j] : rx[16 + j]);
-        const float sy = __uint_as_float(part ? ry[j] : ry[16 + j]);
-        const float gx = __shfl_xor_sync(0xffffffffu, sx, 16);
-        const float gy = __shfl_xor_sync(0xffffffffu, sy, 16);
-        const float xr = part ? gx : ox, xi = part ? ox : gx;
-        const float yr = part ? gy : oy, yi = part ? oy : gy;
-        uint32_t *a4 = j < 8 ? s0 + 4 * j : s1 + 4 * (j - 8);
-        a4[0] = __float_as_uint(fmaf(xr, xr, fmaf(xi, xi, __uint_as_float(a4[0]))));
-        a4[1] = __float_as_uint(fmaf(yr, yr, fmaf(yi, yi, __uint_as_float(a4[1]))));
-        a4[2] = __float_as_uint(fmaf(xr, yr, fmaf(xi, yi, __uint_as_float(a4[2]))));
-        a4[3] = __float_as_uint(fmaf(xi, yr, fmaf(-xr, yi, __uint_as_float(a4[3]))));
+        for (int j = 0; j < 16; j++) {
+            const float x = __uint_as_float(rx[j]), y = __uint_as_float(ry[j]);
+            const float xo = __shfl_xor_sync(0xffffffffu, x, 16);
+            uint32_t *a4 = j < 8 ? s0 + 4 * j : s1 + 4 * (j - 8);
+            a4[0] = __float_as_uint(fmaf(x, x, __uint_as_float(a4[0])));
+            a4[1] = __float_as_uint(fmaf(y, y, __uint_as_float(a4[1])));
+            a4[2] = __float_as_uint(fmaf(x, y, __uint_as_float(a4[2])));
+            a4[3] = __float_as_uint(fmaf(xo, y, __uint_as_float(a4[3])));
+        }
+        tc::tmem_st32_issue(acc, s0);
+        tc::tmem_st32_issue(acc + 32, s1);
+        tc::tmem_wait_st();
     }
-    tc::tmem_st32_issue(acc, s0);
-    tc::tmem_st32_issue(acc + 32, s1);
-    tc::tmem_wait_st();
 }
 
 template <int VAR, int KC>
@@ -313,13 +315,12 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
             }
     }
     if (simt) {
-        // zero this warp's time sums: TMEM lanes 32 (w mod 4) .., columns kColAcc + 64 (w / 4) ..
+        // zero this warp's time sums: TMEM lanes 32 (w mod 4) .., columns kColAcc + 128 (w / 4) ..
         uint32_t z[32];
 #pragma unroll
         for (int j = 0; j < 32; j++) z[j] = 0u;
-        const uint32_t acc = lane_addr + kColAcc + 64 * (warp >> 2);
-        tc::tmem_st32_issue(acc, z);
-        tc::tmem_st32_issue(acc + 32, z);
+        const uint32_t acc = lane_addr + kColAcc + 128 * (warp >> 2);
+        for (int cc = 0; cc < 128; cc += 32) tc::tmem_st32_issue(acc + cc, z);
         tc::tmem_wait_st();
     }
     tc::fence_before_sync();
@@ -328,11 +329,11 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
 
     constexpr uint32_t idesc = idesc_mn(128, 128, kBF16);
     const uint32_t b_base = tc::smem_u32(opB);
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phase = 0u;                          // bit b: parity of bar_mma[b]
     constexpr int kPreW = kMaxAP / 4 / kThreads;
     if (!simt) {
-        // ---- a4 (columns): D[buf] = A B[buf]^T for each sample, issued by one
-        // thread once the eight SIMT warps have written B[buf] (block barrier)
+        // ---- a4 (columns): D = A B[buf]^T for each sample, issued by one thread
+        // once the eight SIMT warps have written B[buf] and drained D (block barrier)
         for (int t = t0; t <= t1; t++) {
             tc::fence_before_sync();
             __syncthreads();
@@ -340,7 +341,7 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
             if (t < t1 && lane == 0 && !withhold_mma) {
                 tc::fence_after_sync();
                 const int buf = (t - t0) & 1;
-                const uint32_t d_tmem = taddr + buf * 128;
+                const uint32_t d_tmem = taddr;
                 const uint32_t bb = b_base + buf * 2 * kPart;
 #pragma unroll
                 for (int kb = 0; kb < 8; kb++) {
@@ -432,28 +433,24 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
             const int q = tid & 127, jy = q & 63, p = q >> 6;
             const bool row_on = work && ((rows_used >> jy) & 1ull);
             float2 *line = G + p * BUF + jy * S64;
-            if (row_on) {
-                if (warp < 4) row_stage1<0>(line);
-                else row_stage1<1>(line);
-            }
+            if (row_on) row_stage1(line, warp >> 2);
             tc::named_bar_sync(1 + (warp & 3), 64);
             if (row_on) {
                 uint8_t *bb = opB + buf * 2 * kPart;
-                if (warp < 4) row_stage2<0, kBF16, kSplit>(line, bb, p, jy);
-                else row_stage2<1, kBF16, kSplit>(line, bb, p, jy);
+                row_stage2<kBF16, kSplit>(line, bb, p, jy, warp >> 2);
             }
         }
-        // ---- a5, a6: products of sample t-1 from D[buf ^ 1] into the time sums
+        // ---- a5, a6: products of sample t-1 (D, written from B[buf ^ 1]) into the time sums
         if (t > t0 && !abort_flag) {
             const int pb = buf ^ 1;
-            if (!tc::mbar_wait(&bar_mma[pb], phase[pb], wait_budget)) {
+            if (!tc::mbar_wait(&bar_mma[pb], (phase >> pb) & 1u, wait_budget)) {
                 atomicOr(status, kStatusTimeout);
                 abort_flag = 1;
             } else {
                 tc::fence_after_sync();
-                drain_sample(lane_addr, static_cast<uint32_t>(pb * 128), warp >> 2, lane >> 4);
+                drain_sample(lane_addr, warp >> 2);
             }
-            phase[pb] ^= 1u;
+            phase ^= 1u << pb;
         }
         tc::fence_proxy_async();
         if (has_next) {
@@ -468,33 +465,47 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
         if (abort_flag) break;
     }
 
-    // ---- partial sums from each warp's TMEM lanes and column half (undo the FP16 scale exactly)
+    // ---- partial image from each warp's TMEM lanes and column half: the Re and
+    // Im lanes' partials combine into XX, YY, Re XY, Im XY (FP16 scale undone exactly)
     if (simt) {
         tc::fence_after_sync();
         const float inv = 1.f / (scale * scale);
         const int hh = warp >> 2, part = lane >> 4;
         const int my = 16 * (warp & 3) + (lane & 15);
         float4 *dst = reinterpret_cast<float4 *>(partial) + (static_cast<size_t>(tau) * n_items + item) * (M64 * M64);
-        uint32_t s0[32], s1[32];
-        const uint32_t acc = lane_addr + kColAcc + 64 * hh;
-        tc::tmem_ld32_issue(acc, s0);
-        tc::tmem_ld32_issue(acc + 32, s1);
-        tc::tmem_wait_ld();
-        tc::reg_fence32(s0);
-        tc::reg_fence32(s1);
+#pragma unroll 1
+        for (int q = 0; q < 2; q++) {
+            uint32_t s0[32], s1[32];
+            const uint32_t acc = lane_addr + kColAcc + 128 * hh + 64 * q;
+            tc::tmem_ld32_issue(acc, s0);
+            tc::tmem_ld32_issue(acc + 32, s1);
+            tc::tmem_wait_ld();
+            tc::reg_fence32(s0);
+            tc::reg_fence32(s1);
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
-            const int n = 32 * hh + 16 * part + j;              // B column -> mx = n / 8 + 8 (n mod 8)
-            const int mx = (n >> 3) + 8 * (n & 7);
-            const uint32_t *a4 = j < 8 ? s0 + 4 * j : s1 + 4 * (j - 8);
-            dst[my * M64 + mx] = make_float4(__uint_as_float(a4[0]) * inv, __uint_as_float(a4[1]) * inv,
-                                             __uint_as_float(a4[2]) * inv, __uint_as_float(a4[3]) * inv);
+            for (int j = 0; j < 16; j++) {
+                const uint32_t *a4 = j < 8 ? s0 + 4 * j : s1 + 4 * (j - 8);
+                float v[4], o[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    v[i] = __uint_as_float(a4[i]);
+                    o[i] = __shfl_xor_sync(0xffffffffu, v[i], 16);
+                }
+                // lane part 0 holds sum xi yr in v[3], part 1 holds sum xr yi
+                const float im = part ? o[3] - v[3] : v[3] - o[3];
+                if ((j >> 3) == part) {
+                    const int n = 32 * hh + 16 * q + j;         // B column -> mx = n / 8 + 8 (n mod 8)
+                    const int mx = (n >> 3) + 8 * (n & 7);
+                    dst[my * M64 + mx] = make_float4((v[0] + o[0]) * inv, (v[1] + o[1]) * inv,
+                                                     (v[2] + o[2]) * inv, im * inv);
+                }
+            }
         }
     }
     // an aborted CTA may still have an MMA in flight: give it a bounded chance to land
     if (tid == 0 && abort_flag) {
-        tc::mbar_wait(&bar_mma[0], phase[0], wait_budget);
-        tc::mbar_wait(&bar_mma[1], phase[1], wait_budget);
+        tc::mbar_wait(&bar_mma[0], phase & 1u, wait_budget);
+        tc::mbar_wait(&bar_mma[1], (phase >> 1) & 1u, wait_budget);
     }
     tc::fence_before_sync();
     __syncthreads();
