@@ -271,12 +271,17 @@ def time_variants(wl, v, g, out, flush, args, stream):
              "tc_split_fp16": dict(precision=epic.EPIC_TC_SPLIT_FP16),
              "tc_fp16": dict(precision=epic.EPIC_TC_FP16),
              "tc_split_bf16": dict(precision=epic.EPIC_TC_SPLIT_BF16),
-             "tc_split_fp16_taper": dict(precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_KERNEL_TAPER)}
+             "tc_split_fp16_taper": dict(precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_KERNEL_TAPER),
+             "fp32_delays": dict()}
     notes = {"kernel_taper": "FP32; image-domain |W^|^2 taper with point gridding (exact for one shared kernel)",
              "tc_split_fp16": "column DFT on tcgen05, FP16 hi+lo operands (3 MMAs), FP32 accumulate in TMEM",
              "tc_fp16": "column DFT on tcgen05, single FP16 operands",
              "tc_split_bf16": "column DFT on tcgen05, BF16 hi+lo operands (3 MMAs)",
-             "tc_split_fp16_taper": "tc_split_fp16 with the image-domain kernel taper"}
+             "tc_split_fp16_taper": "tc_split_fp16 with the image-domain kernel taper",
+             "fp32_delays": "FP32 literal form with per-(t, antenna) geometric-delay phases (epic_image_ex; "
+                            "[T][A] FP64 delays resident in HBM, phases formed in the kernel)"}
+    from paper_2301_09662_gb300 import synth
+    delays = torch.from_numpy(synth.geometric_delays(wl.ant_xy, wl.T)).to(v.device)
     peaks = measured_peaks()
     for name, kw in forms.items():
         try:
@@ -286,8 +291,9 @@ def time_variants(wl, v, g, out, flush, args, stream):
             continue
         p.set_profiling(True)
         o = torch.empty_like(out)
+        dl = delays if name == "fp32_delays" else None
         for _ in range(max(args.warmup, 1)):
-            p.image(v, g, out=o)
+            p.image(v, g, out=o, delays=dl)
         torch.cuda.synchronize()
         ms = []
         for k in range(args.steps):
@@ -295,7 +301,7 @@ def time_variants(wl, v, g, out, flush, args, stream):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            p.image(v, g, out=o)
+            p.image(v, g, out=o, delays=dl)
             b.record(stream)
             b.synchronize()
             ms.append(a.elapsed_time(b))

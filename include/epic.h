@@ -154,6 +154,36 @@ int epic_image(epic_plan_t plan, const uint8_t *ci4, const float *gains_c64,
                int n_spectra, float *out_c64, void *cuda_stream);
 
 /*
+ * epic_image_ex -- epic_image with the geometric-delay correction of Sec. 2.2
+ * (the delay-correction block that compensates each antenna's geometric delay
+ * at every time step, for every channel, before gridding).  Each calibrated
+ * voltage is multiplied by exp(+2 pi i f_c tau_a(t)):
+ *
+ *   e~_{a,p}(t, c) = g_{c,a,p} * exp(+2 pi i f_c tau_a(t)) * e_{a,p}(t, c)
+ *
+ * tau_a(t) is the delay of antenna a's signal relative to the phase centre
+ * (positive = the wavefront reaches it later), so the product re-phases the
+ * array towards the direction the delays were computed for.
+ *
+ *   delays_s    device double [n_spectra][n_ant], seconds; NULL = no correction
+ *               (identical to epic_image)
+ *   (the other arguments as for epic_image)
+ *
+ * A small kernel forms, once per (t, antenna), the FP64 turns at a mid-band
+ * reference frequency (reduced to a fraction) and tau as two floats; the
+ * imaging kernels add the per-channel remainder (f_c - f_ref) tau in FP32 with
+ * an exact two-product and take a single-precision sincospi.  The plan holds
+ * that [max_spectra][n_ant] table, so this call allocates nothing either.  The
+ * correction has unit modulus and is common to both
+ * polarisations of an antenna, so the autocorrelation term is unchanged.
+ * Same errors, ordering and allocation behaviour as epic_image.  The delays
+ * pointer is part of the captured graph's key: a new pointer re-captures.
+ */
+int epic_image_ex(epic_plan_t plan, const uint8_t *ci4, const float *gains_c64,
+                  const double *delays_s, int n_spectra, float *out_c64,
+                  void *cuda_stream);
+
+/*
  * epic_image_host -- the same integration with HOST buffers: copies ci4 and
  * gains to plan-owned device staging (allocated on the first call, reused
  * after), runs epic_image on the given stream, copies the image back into

@@ -10,7 +10,8 @@ readings of points the paper leaves open):
   cell_map        Sec. 3.1, nearest-neighbour antenna -> grid-cell map
   kernel_power    |W^(l)|^2, the image of one antenna's footprint (Eq. 4)
   fft1d / ifft2   the oracle's own mixed-radix FFT (Eq. 4's FT^-1)
-  epic_direct     O1, Eq. 4 with the block chain of Sec. 2.2
+  epic_direct     O1, Eq. 4 with the block chain of Sec. 2.2 (optionally with
+                  the delay-correction block's per-(t, a) phases)
   epic_fx         O2, Eq. 1-3 (FX correlator + gridding with W (x) W^*)
                   (both take one [K][K] kernel or per-antenna [A][K][K] kernels, Eq. 3)
   grid_energy     sum_t sum_k |G_p(k, t)|^2 with O1's gridding (Parseval pin)
@@ -60,7 +61,7 @@ def lib():
             L.oracle_ifft2.argtypes = [P, i]
             for name in ("oracle_epic_direct", "oracle_epic_fx"):
                 f = getattr(L, name)
-                f.argtypes = [P, P, i, i, i, i, P, P, P, i, i, ctypes.c_uint, P]
+                f.argtypes = [P, P, i, i, i, i, P, P, P, i, i, P, P, ctypes.c_uint, P]
                 f.restype = i
             L.oracle_grid_energy.argtypes = [P, P, i, i, i, i, P, P, P, i, i, P]
             L.oracle_grid_energy.restype = i
@@ -142,24 +143,33 @@ def split_channels(flat, grid_n, P):
     return out
 
 
-def _run(name, v, gains, cells, grid_n, W, flags):
+def _run(name, v, gains, cells, grid_n, W, flags, freq=None, delays=None):
     v, g, cells, n, w, T, C, A, P = _common(v, gains, cells, grid_n, W)
+    f = d = None
+    if delays is not None:
+        if freq is None:
+            raise ValueError("delays need the channel frequencies")
+        f = np.ascontiguousarray(freq, np.float64)
+        d = np.ascontiguousarray(delays, np.float64)
+        if f.shape != (C,) or d.shape != (T, A):
+            raise ValueError("freq must be [C] and delays [T][A]")
     out = np.zeros(out_size(n, P), np.complex128)
     rc = getattr(lib(), name)(_ptr(v), _ptr(g), T, C, A, P, _ptr(cells), _ptr(n), _ptr(w),
-                              w.shape[-1], int(w.ndim == 3), int(flags), _ptr(out))
+                              w.shape[-1], int(w.ndim == 3), _ptr(f), _ptr(d), int(flags), _ptr(out))
     if rc:
         raise ValueError(f"{name}: bad arguments")
     return out
 
 
-def epic_direct(v, gains, cells, grid_n, W, flags: int = 0) -> np.ndarray:
-    """O1: packed complex128 output, per channel [NP][N][N] (XX, YY, XY, YX)."""
-    return _run("oracle_epic_direct", v, gains, cells, grid_n, W, flags)
+def epic_direct(v, gains, cells, grid_n, W, flags: int = 0, freq=None, delays=None) -> np.ndarray:
+    """O1: packed complex128 output, per channel [NP][N][N] (XX, YY, XY, YX).
+    delays ([T][A] seconds, with freq [C] Hz) apply the Sec. 2.2 delay correction."""
+    return _run("oracle_epic_direct", v, gains, cells, grid_n, W, flags, freq, delays)
 
 
-def epic_fx(v, gains, cells, grid_n, W, flags: int = 0) -> np.ndarray:
+def epic_fx(v, gains, cells, grid_n, W, flags: int = 0, freq=None, delays=None) -> np.ndarray:
     """O2: same output as epic_direct, by the FX-correlator route."""
-    return _run("oracle_epic_fx", v, gains, cells, grid_n, W, flags)
+    return _run("oracle_epic_fx", v, gains, cells, grid_n, W, flags, freq, delays)
 
 
 def grid_energy(v, gains, cells, grid_n, W) -> np.ndarray:
@@ -172,17 +182,19 @@ def grid_energy(v, gains, cells, grid_n, W) -> np.ndarray:
     return out
 
 
-def workload_image(wl, flags: int = 0, channels=None, form: str = "direct") -> np.ndarray:
-    """Run O1 (or O2) on a synth.Workload, optionally on a subset of channels.
+def workload_image(wl, flags: int = 0, channels=None, form: str = "direct", delays=None) -> np.ndarray:
+    """Run O1 (or O2) on a synth.Workload, optionally on a subset of channels
+    and with [T][A] geometric delays.
 
     Returns the packed output for the selected channels in channel order."""
     cells = cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
-    v, g, grid_n = wl.v, wl.gains, wl.grid_n
+    v, g, grid_n, freq = wl.v, wl.gains, wl.grid_n, wl.freq_hz
     if channels is not None:
         ch = np.asarray(channels)
         v = v[:, ch]
         g = None if g is None else g[ch]
         cells = cells[ch]
         grid_n = grid_n[ch]
+        freq = freq[ch]
     fn = epic_direct if form == "direct" else epic_fx
-    return fn(v, g, cells, grid_n, wl.kernel, flags)
+    return fn(v, g, cells, grid_n, wl.kernel, flags, freq=freq, delays=delays)

@@ -41,6 +41,12 @@
  *   - antenna -> cell map (Sec. 3.1, nearest neighbour on a grid of spacing
  *     du wavelengths): k = llround(((x - x_c) f) / (c0 du)) + N/2 per axis,
  *     x_c the centroid of the layout.
+ *   - geometric-delay correction (Sec. 2.2, the delay-correction block ahead
+ *     of gridding): with delays != NULL ([T][A] seconds, and the channel
+ *     frequencies f_c), e~_ap(t) = g_ap exp(+2 pi i f_c tau_a(t)) e_ap(t);
+ *     tau_a(t) > 0 means the wavefront reaches antenna a later than the phase
+ *     centre.  The factor has unit modulus and is shared by both
+ *     polarisations, so the autocorrelation term does not change.
  *   - per-antenna kernels (Eq. 3 writes W_a; Sec. 3.1 A-projection): with
  *     kernels_per_antenna != 0 the kernel array is [A][K][K] and antenna a
  *     grids through W_a; the auto term becomes sum_a A_a,pq |W^_a(l)|^2 and
@@ -298,6 +304,13 @@ static void auto_image(const uint8_t *v, const cplx *g, int T, int C, int A, int
     free(Wp);
 }
 
+/* exp(+2 pi i f tau), the delay correction of one antenna, straight from the definition */
+static inline cplx delay_factor(const double *freq_hz, const double *delays, int A, int t, int c, int a)
+{
+    double ang = 2.0 * M_PI * freq_hz[c] * delays[(size_t)t * A + a];
+    return cos(ang) + I * sin(ang);
+}
+
 /* product index -> (p, q): XX, YY, XY, YX */
 static const int PQ_P[4] = {0, 1, 0, 1};
 static const int PQ_Q[4] = {0, 1, 1, 0};
@@ -306,9 +319,11 @@ static const int PQ_Q[4] = {0, 1, 1, 0};
 
 int oracle_epic_direct(const uint8_t *v, const double *gains_il, int T, int C, int A, int P,
                        const int *cells, const int *grid_n, const double *W_il, int K,
-                       int per_antenna, unsigned flags, double *out_il)
+                       int per_antenna, const double *freq_hz, const double *delays,
+                       unsigned flags, double *out_il)
 {
     if (check_args(T, C, A, P, K, grid_n)) return -1;
+    if (delays && !freq_hz) return -1;
     const cplx *g = (const cplx *)gains_il;
     const cplx *W = (const cplx *)W_il;
     cplx *out = (cplx *)out_il;
@@ -333,6 +348,7 @@ int oracle_epic_direct(const uint8_t *v, const double *gains_il, int T, int C, i
                 for (int a = 0; a < A; a++) {
                     cplx e = ci4_value(v[(((size_t)t * C + c) * A + a) * P + p]);
                     if (g) e *= g[((size_t)c * A + a) * P + p];
+                    if (delays) e *= delay_factor(freq_hz, delays, A, t, c, a);
                     int kx = cells[((size_t)c * A + a) * 2 + 0];
                     int ky = cells[((size_t)c * A + a) * 2 + 1];
                     for (int dy = -h; dy <= h; dy++)
@@ -410,9 +426,11 @@ int oracle_grid_energy(const uint8_t *v, const double *gains_il, int T, int C, i
 
 int oracle_epic_fx(const uint8_t *v, const double *gains_il, int T, int C, int A, int P,
                    const int *cells, const int *grid_n, const double *W_il, int K,
-                   int per_antenna, unsigned flags, double *out_il)
+                   int per_antenna, const double *freq_hz, const double *delays,
+                   unsigned flags, double *out_il)
 {
     if (check_args(T, C, A, P, K, grid_n)) return -1;
+    if (delays && !freq_hz) return -1;
     const cplx *g = (const cplx *)gains_il;
     const cplx *W = (const cplx *)W_il;
     cplx *out = (cplx *)out_il;
@@ -441,14 +459,20 @@ int oracle_epic_fx(const uint8_t *v, const double *gains_il, int T, int C, int A
     for (int c = 0; c < C; c++) {
         int N = grid_n[c];
         size_t NN = (size_t)N * N;
-        /* Eq. 1: exact integer visibilities V[a][b][p][q] = sum_t e_ap e_bq^* */
+        /* Eq. 1: exact integer visibilities V[a][b][p][q] = sum_t e_ap e_bq^*; with
+         * delay corrections the per-sample phases d_a(t) d_b(t)^* enter the sum, which
+         * is then taken in complex FP64 (Vd) */
         long long *Vre = calloc((size_t)A * A * P * P, sizeof(long long));
         long long *Vim = calloc((size_t)A * A * P * P, sizeof(long long));
+        cplx *Vd = delays ? calloc((size_t)A * A * P * P, sizeof(cplx)) : NULL;
+        cplx *dph = delays ? malloc(sizeof(cplx) * (size_t)A) : NULL;
         int *er = malloc(sizeof(int) * (size_t)A * P), *ei = malloc(sizeof(int) * (size_t)A * P);
         for (int t = 0; t < T; t++) {
             for (int a = 0; a < A; a++)
                 for (int p = 0; p < P; p++)
                     oracle_ci4_unpack(v[(((size_t)t * C + c) * A + a) * P + p], &er[a * P + p], &ei[a * P + p]);
+            if (delays)
+                for (int a = 0; a < A; a++) dph[a] = delay_factor(freq_hz, delays, A, t, c, a);
             for (int a = 0; a < A; a++)
                 for (int b = 0; b < A; b++)
                     for (int p = 0; p < P; p++)
@@ -456,8 +480,13 @@ int oracle_epic_fx(const uint8_t *v, const double *gains_il, int T, int C, int A
                             size_t ix = (((size_t)a * A + b) * P + p) * P + q;
                             int ra = er[a * P + p], ia = ei[a * P + p];
                             int rb = er[b * P + q], ib = ei[b * P + q];
-                            Vre[ix] += (long long)ra * rb + (long long)ia * ib;
-                            Vim[ix] += (long long)ia * rb - (long long)ra * ib;
+                            long long vr = (long long)ra * rb + (long long)ia * ib;
+                            long long vi = (long long)ia * rb - (long long)ra * ib;
+                            if (delays) Vd[ix] += dph[a] * conj(dph[b]) * ((double)vr + I * (double)vi);
+                            else {
+                                Vre[ix] += vr;
+                                Vim[ix] += vi;
+                            }
                         }
         }
         /* Eq. 2-3: grid calibrated cross visibilities with B at offset k_a - k_b */
@@ -470,7 +499,7 @@ int oracle_epic_fx(const uint8_t *v, const double *gains_il, int T, int C, int A
                 for (int pq = 0; pq < NP; pq++) {
                     int p = PQ_P[pq], q = PQ_Q[pq];
                     size_t ix = (((size_t)a * A + b) * P + p) * P + q;
-                    cplx Vab = (double)Vre[ix] + I * (double)Vim[ix];
+                    cplx Vab = delays ? Vd[ix] : (double)Vre[ix] + I * (double)Vim[ix];
                     cplx ga = g ? g[((size_t)c * A + a) * P + p] : 1.0;
                     cplx gb = g ? g[((size_t)c * A + b) * P + q] : 1.0;
                     cplx Vc = ga * conj(gb) * Vab;
@@ -519,7 +548,7 @@ int oracle_epic_fx(const uint8_t *v, const double *gains_il, int T, int C, int A
             }
         }
         free(autos);
-        free(Vre); free(Vim); free(er); free(ei); free(Vg); free(tw); free(tmp);
+        free(Vre); free(Vim); free(Vd); free(dph); free(er); free(ei); free(Vg); free(tw); free(tmp);
     }
     free(B);
     return 0;

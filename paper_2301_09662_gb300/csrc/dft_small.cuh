@@ -14,6 +14,21 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 }
 // a * i
 __device__ __forceinline__ float2 cmul_i(float2 a) { return make_float2(-a.y, a.x); }
+
+// exp(+2 pi i f_c tau): the geometric-delay correction of one antenna at one
+// channel (Sec. 2.2, delay-correction block).  d = (frac(f_ref tau), tau_hi,
+// tau_lo) from the per-integration delay table (FP64 work done once per
+// (t, antenna)); df = f_c - f_ref.  The turns are b + df tau with df tau_hi
+// split exactly (two-product) so that whole turns drop out before rounding.
+__device__ __forceinline__ float2 delay_phase(float4 d, float df)
+{
+    const float p = df * d.y;
+    const float e = fmaf(df, d.y, -p);
+    const float turns = (d.x + (p - rintf(p))) + fmaf(df, d.z, e);
+    float s, c;
+    sincospif(2.0f * turns, &s, &c);
+    return make_float2(c, s);
+}
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
 constexpr float kSqrtHalf = 0.70710678118654752440f;

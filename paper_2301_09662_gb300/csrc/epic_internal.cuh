@@ -68,6 +68,10 @@ struct epic_plan_s {
     float2 *d_kernel = nullptr;        // [K*K]
     int *d_autoint = nullptr;          // [C][A][4] exact integer auto sums
     int *d_status = nullptr;           // sticky device status word
+    double f_ref = 0;                  // delay phases: reference frequency (mid-band, Hz)
+    float *d_dfreq = nullptr;          // [C] f_c - f_ref (Hz)
+    float4 *d_dtab = nullptr;          // [max_spectra][A] (frac(f_ref tau), tau_hi, tau_lo, 0) of the current call
+    const double *delays = nullptr;    // device [T][A] geometric delays (s) of the current call, or null
     std::vector<epic::GroupCfg> groups;
     int force_tau = 0;                 // > 0: time chunks of the next launches (image series)
     long long wait_budget = 4000000000LL;  // clock cycles a device-side wait may take (~2 s)
@@ -84,7 +88,7 @@ struct epic_plan_s {
     cudaEvent_t ev_fork = nullptr, ev_auto = nullptr;
     std::vector<cudaEvent_t> ev_join;
     cudaGraphExec_t gexec = nullptr;
-    const void *g_v = nullptr, *g_gains = nullptr;
+    const void *g_v = nullptr, *g_gains = nullptr, *g_delays = nullptr;
     void *g_out = nullptr;
     int g_T = -1;
     bool g_prof = false;
@@ -116,6 +120,8 @@ int launch_epilogue(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, i
                     float2 *out, cudaStream_t stream);
 // per-antenna kernels: auto-correlation grid X(rho) -> Y(rho_y, l_x) per channel and product
 int launch_auto_rho(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, cudaStream_t stream);
+// delay table of the current call (plan->delays, [T][A] seconds) into plan->d_dtab
+int launch_delay_prep(epic_plan_s *plan, int T, cudaStream_t stream);
 // image series: per-image auto sums and one epilogue image per time chunk
 int launch_autopower_series(epic_plan_s *plan, const uint8_t *v, int spi, int n_img, cudaStream_t stream);
 int launch_epilogue_series(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int spi, int n_img,

@@ -96,7 +96,8 @@ fp32_image_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                   const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K,
                   const int *__restrict__ chans, const float2 *__restrict__ twN,
                   int A, int C, int T, int N, int Q1, int n_items, int n_tau,
-                  float *__restrict__ partial, int *__restrict__ status, int nker)
+                  float *__restrict__ partial, int *__restrict__ status, int nker,
+                  const float *__restrict__ dfreq, const float4 *__restrict__ dtab)
 {
     constexpr int S = M + 1;
     constexpr int NPOS = (M * M + kThreads - 1) / kThreads;
@@ -169,7 +170,9 @@ fp32_image_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         // ---- a1, a2: unpack and calibrate this time sample
         for (int i = tid; i < AP; i += kThreads) {
             const uint32_t b = reinterpret_cast<const uint8_t *>(stage)[i];
-            es[i] = cmul(gp[i], ci4_to_float2(b));
+            float2 e = cmul(gp[i], ci4_to_float2(b));
+            if (dtab) e = cmul(e, delay_phase(dtab[static_cast<size_t>(t) * A + i / P], dfreq[c]));
+            es[i] = e;
         }
         // prefetch the next sample's bytes while this one is gridded and transformed
         const bool has_next = t + 1 < t1;
@@ -309,7 +312,8 @@ int launch_group(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));
     kfn<<<grid, kThreads, smem, stream>>>(v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN,
                                           plan->A, plan->C, T, g.N, g.Q1, g.n_items, n_tau, g.d_partial,
-                                          plan->d_status, plan->nker);
+                                          plan->d_status, plan->nker, plan->d_dfreq,
+                                          plan->delays ? plan->d_dtab : nullptr);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -335,7 +339,7 @@ int launch_raw(const RawImage &r, const uint8_t *v, const float2 *gains, cudaStr
         return EPIC_ERR_UNSUPPORTED;
     const dim3 grid(static_cast<unsigned>(r.n_items * r.n_tau));
     kfn<<<grid, kThreads, smem, stream>>>(v, gains, r.cells, r.kernel, r.K, r.chans, r.twN, r.A, r.C, r.T, r.N, r.Q1,
-                                          r.n_items, r.n_tau, r.partial, r.status, 1);
+                                          r.n_items, r.n_tau, r.partial, r.status, 1, nullptr, nullptr);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -417,6 +421,7 @@ int image_fp32(epic_plan_s *plan, const uint8_t *v, const float2 *gains, int T, 
     int rc = EPIC_OK;
     int stage = 0;
     prof_begin(plan);
+    if (plan->delays && (rc = launch_delay_prep(plan, T, stream)) != EPIC_OK) return rc;
     if (fork && cudaEventRecord(plan->ev_fork, stream) != cudaSuccess) return EPIC_ERR_CUDA;
     if (autosub) {
         prof_mark(plan, stream, stage, true);

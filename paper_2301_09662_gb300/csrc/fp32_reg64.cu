@@ -38,9 +38,10 @@ template <> struct Acc64<2> { using T = float4; };
 
 // Grid buffers: G[ts][p][y][x] with x < 64 at stride S64.  KC > 0 fixes the
 // kernel side at compile time (the gridding loop then unrolls fully); KC = 0
-// takes it from K.  rowmask[ci] marks the folded rows any footprint touches:
+// takes it from K.  DL: voltages take the geometric-delay phase of the
+// per-integration table dtab (Sec. 2.2 delay correction), once per antenna.  rowmask[ci] marks the folded rows any footprint touches:
 // the others stay zero and their row transforms are skipped.
-template <int P, int TS, int KC>
+template <int P, int TS, int KC, bool DL>
 __global__ void __launch_bounds__(kThreads, 1)
 fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
                   const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K_rt,
@@ -48,7 +49,8 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                   const uint32_t *__restrict__ sched, const int *__restrict__ nrounds, int rmax,
                   const unsigned long long *__restrict__ rowmask,
                   int A, int C, int T, int N, int Q1, int n_items, int n_tau,
-                  float *__restrict__ partial, int *__restrict__ status, int nker)
+                  float *__restrict__ partial, int *__restrict__ status, int nker,
+                  const float *__restrict__ dfreq, const float4 *__restrict__ dtab)
 {
     const int K = KC > 0 ? KC : K_rt;
     constexpr int NPOS = M64 * M64 / kThreads;   // 16 pixels per thread
@@ -111,9 +113,23 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
 #pragma unroll
         for (int ts = 0; ts < TS; ts++) {
             const bool ok = t + ts < t1;
-            for (int i = tid; i < AP; i += kThreads) {
-                const uint32_t b = reinterpret_cast<const uint8_t *>(stage + ts * APW)[i];
-                es[ts * AP + i] = ok ? cmul(gp[i], ci4_f2(b)) : make_float2(0.f, 0.f);
+            if constexpr (DL) {
+                // delay phase once per antenna, shared by its polarisations
+                for (int a = tid; a < A; a += kThreads) {
+                    const float2 ph = ok ? delay_phase(dtab[static_cast<size_t>(t + ts) * A + a], dfreq[c])
+                                         : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int p = 0; p < P; p++) {
+                        const int i = a * P + p;
+                        const uint32_t b = reinterpret_cast<const uint8_t *>(stage + ts * APW)[i];
+                        es[ts * AP + i] = cmul(cmul(gp[i], ci4_f2(b)), ph);
+                    }
+                }
+            } else {
+                for (int i = tid; i < AP; i += kThreads) {
+                    const uint32_t b = reinterpret_cast<const uint8_t *>(stage + ts * APW)[i];
+                    es[ts * AP + i] = ok ? cmul(gp[i], ci4_f2(b)) : make_float2(0.f, 0.f);
+                }
             }
         }
         // prefetch the next TS samples while this group is gridded and transformed
@@ -236,11 +252,11 @@ size_t reg64_smem(int A, int K, int nker)
     return (b + 15) & ~static_cast<size_t>(15);
 }
 
-template <int P, int TS, int KC>
+template <int P, int TS, int KC, bool DL>
 int launch_reg64_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau_out,
                    cudaStream_t stream)
 {
-    auto kfn = fp32_reg64_kernel<P, TS, KC>;
+    auto kfn = fp32_reg64_kernel<P, TS, KC, DL>;
     const size_t smem = reg64_smem<P, TS>(plan->A, plan->K, plan->nker);
     int n_tau = plan->force_tau > 0 ? plan->force_tau : fp32_pick_tau(g.n_items, T, plan->sm_count);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
@@ -248,19 +264,21 @@ int launch_reg64_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));
     kfn<<<grid, kThreads, smem, stream>>>(v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN,
                                           g.d_sched, g.d_nrounds, g.rmax, g.d_rowmask, plan->A, plan->C, T, g.N, g.Q1,
-                                          g.n_items, n_tau, g.d_partial, plan->d_status, plan->nker);
+                                          g.n_items, n_tau, g.d_partial, plan->d_status, plan->nker, plan->d_dfreq,
+                                          DL ? plan->d_dtab : nullptr);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
 template <int P, int TS, int KC>
 int prepare_reg64_t(const epic_plan_s *plan)
 {
-    auto kfn = fp32_reg64_kernel<P, TS, KC>;
-    const size_t smem = reg64_smem<P, TS>(plan->A, plan->K, plan->nker);
-    return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) ==
-                   cudaSuccess
-               ? EPIC_OK
-               : EPIC_ERR_UNSUPPORTED;
+    const int smem = static_cast<int>(reg64_smem<P, TS>(plan->A, plan->K, plan->nker));
+    const bool ok =
+        cudaFuncSetAttribute(fp32_reg64_kernel<P, TS, KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(fp32_reg64_kernel<P, TS, KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+            cudaSuccess;
+    return ok ? EPIC_OK : EPIC_ERR_UNSUPPORTED;
 }
 
 // Which instantiation serves a plan: dual polarisation gets kernels specialised
@@ -320,8 +338,10 @@ int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
                  cudaStream_t stream)
 {
     return reg64_dispatch(reg64_key(plan, g), [&](auto p_, auto ts_, auto kc_) {
-        return launch_reg64_t<decltype(p_)::value, decltype(ts_)::value, decltype(kc_)::value>(plan, g, v, gains, T,
-                                                                                                 n_tau, stream);
+        constexpr int P = decltype(p_)::value, TS = decltype(ts_)::value, KC = decltype(kc_)::value;
+        // the delay-corrected form is a separate instantiation, so the plain one carries no trace of it
+        return plan->delays ? launch_reg64_t<P, TS, KC, true>(plan, g, v, gains, T, n_tau, stream)
+                            : launch_reg64_t<P, TS, KC, false>(plan, g, v, gains, T, n_tau, stream);
     });
 }
 

@@ -8,6 +8,8 @@
 // time sum is exact in int32 (|e e^*| components <= 128, T <= 10^5); the
 // antenna sum and the subtraction run in FP64 because the auto term can be
 // much larger than what is left after it is removed.
+#include <algorithm>
+
 #include "epic_internal.cuh"
 
 namespace epic {
@@ -288,6 +290,20 @@ int launch_epi_raw(const RawImage &r, const float2 *gains, float2 *out, cudaStre
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
+// Per (t, antenna): the FP64 part of the delay phase, once per integration,
+// so the imaging kernels need only FP32 (Sec. 2.2 delay correction).
+__global__ void delay_prep_kernel(const double *__restrict__ delays, int n, double f_ref, float4 *__restrict__ tab)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double tau = delays[i];
+        double b = f_ref * tau;
+        b -= rint(b);
+        const float hi = static_cast<float>(tau);
+        const float lo = static_cast<float>(tau - static_cast<double>(hi));
+        tab[i] = make_float4(static_cast<float>(b), hi, lo, 0.f);
+    }
+}
+
 }  // namespace
 
 int launch_autopower_raw(const RawImage &r, const uint8_t *v, int sm_count, cudaStream_t stream)
@@ -352,6 +368,15 @@ int launch_epilogue_series(epic_plan_s *plan, const GroupCfg &g, const float2 *g
     case 64 * 4 + 2: return launch_epi_series<64, 2>(plan, g, gains, spi, n_img, out, stream);
     default: return EPIC_ERR_UNSUPPORTED;
     }
+}
+
+int launch_delay_prep(epic_plan_s *plan, int T, cudaStream_t stream)
+{
+    const int n = T * plan->A;
+    if (n <= 0) return EPIC_OK;
+    const int blocks = std::min((n + kThreads - 1) / kThreads, 4 * plan->sm_count);
+    delay_prep_kernel<<<blocks, kThreads, 0, stream>>>(plan->delays, n, plan->f_ref, plan->d_dtab);
+    return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
 int launch_auto_rho(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, cudaStream_t stream)

@@ -66,6 +66,8 @@ void free_plan(epic_plan_s *p)
     cudaFree(p->d_bauto);
     cudaFree(p->d_autoint);
     cudaFree(p->d_status);
+    cudaFree(p->d_dfreq);
+    cudaFree(p->d_dtab);
     cudaFree(p->d_stage_v);
     cudaFree(p->d_stage_g);
     cudaFree(p->d_stage_out);
@@ -247,8 +249,8 @@ void prof_mark(epic_plan_s *plan, cudaStream_t stream, int stage, bool start)
 int run_image(epic_plan_s *p, const uint8_t *v, const float2 *gains, int T, float2 *out, cudaStream_t stream)
 {
     if (!p->use_graph) return image_fp32(p, v, gains, T, out, stream, false);
-    if (!p->gexec || p->g_v != v || p->g_gains != gains || p->g_out != out || p->g_T != T ||
-        p->g_prof != p->profiling) {
+    if (!p->gexec || p->g_v != v || p->g_gains != gains || p->g_delays != p->delays || p->g_out != out ||
+        p->g_T != T || p->g_prof != p->profiling) {
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return EPIC_ERR_CUDA;
         const int rc = image_fp32(p, v, gains, T, out, p->cap, true);
@@ -276,6 +278,7 @@ int run_image(epic_plan_s *p, const uint8_t *v, const float2 *gains, int T, floa
         cudaGraphDestroy(graph);
         p->g_v = v;
         p->g_gains = gains;
+        p->g_delays = p->delays;
         p->g_out = out;
         p->g_T = T;
         p->g_prof = p->profiling;
@@ -419,6 +422,22 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     }
 
     if (rc == EPIC_OK) rc = dev_upload(&p->d_status, static_cast<const int *>(nullptr), 1);
+    if (rc == EPIC_OK) {
+        // delay phases: FP64 turns at a mid-band reference once per (t, antenna),
+        // the per-channel remainder (f_c - f_ref) tau in FP32 inside the kernels
+        double fmin = freq_hz[0], fmax = freq_hz[0];
+        for (int c = 1; c < n_chan; c++) {
+            fmin = std::min(fmin, freq_hz[c]);
+            fmax = std::max(fmax, freq_hz[c]);
+        }
+        p->f_ref = 0.5 * (fmin + fmax);
+        std::vector<float> dfreq(n_chan);
+        for (int c = 0; c < n_chan; c++) dfreq[c] = static_cast<float>(freq_hz[c] - p->f_ref);
+        rc = dev_upload(&p->d_dfreq, dfreq.data(), dfreq.size());
+        if (rc == EPIC_OK)
+            rc = dev_upload(&p->d_dtab, static_cast<const float4 *>(nullptr),
+                            static_cast<size_t>(max_spectra) * static_cast<size_t>(n_ant));
+    }
     if (rc == EPIC_OK && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) rc = EPIC_ERR_CUDA;
 
     // channel groups by grid side
@@ -570,8 +589,23 @@ int epic_image(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_s
     if (n_spectra < 0 || n_spectra > plan->max_spectra) return EPIC_ERR_ARG;
     if (n_spectra > 0 && !ci4) return EPIC_ERR_ARG;
     auto s = static_cast<cudaStream_t>(stream);
+    plan->delays = nullptr;
     return epic::run_image(plan, ci4, reinterpret_cast<const float2 *>(gains), n_spectra,
                            reinterpret_cast<float2 *>(out), s);
+}
+
+int epic_image_ex(epic_plan_t plan, const uint8_t *ci4, const float *gains, const double *delays_s, int n_spectra,
+                  float *out, void *stream)
+{
+    if (!plan || !out) return EPIC_ERR_ARG;
+    if (n_spectra < 0 || n_spectra > plan->max_spectra) return EPIC_ERR_ARG;
+    if (n_spectra > 0 && !ci4) return EPIC_ERR_ARG;
+    auto s = static_cast<cudaStream_t>(stream);
+    plan->delays = delays_s;
+    const int rc = epic::run_image(plan, ci4, reinterpret_cast<const float2 *>(gains), n_spectra,
+                                   reinterpret_cast<float2 *>(out), s);
+    plan->delays = nullptr;
+    return rc;
 }
 
 int epic_image_series(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra, int spi, float *out,

@@ -80,7 +80,8 @@ tc_col64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
                 const int *__restrict__ chans, const float2 *__restrict__ twN,
                 const uint32_t *__restrict__ sched, const int *__restrict__ nrounds, int rmax,
                 const uint8_t *__restrict__ dft_ops, int A, int C, int T, int N, int Q1, int n_items, int n_tau,
-                float *__restrict__ partial, int *__restrict__ status, long long wait_budget, int withhold_mma)
+                float *__restrict__ partial, int *__restrict__ status, long long wait_budget, int withhold_mma,
+                const float *__restrict__ dfreq, const float4 *__restrict__ dtab)
 {
     constexpr int P = 2;
     constexpr bool kBF16 = VAR == 2;
@@ -181,7 +182,9 @@ tc_col64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
         // ---- a1, a2
         for (int i = tid; i < AP; i += kThreads) {
             const uint32_t b = reinterpret_cast<const uint8_t *>(stage)[i];
-            es[i] = cmul(gp[i], ci4_value(b));
+            float2 e = cmul(gp[i], ci4_value(b));
+            if (dtab) e = cmul(e, delay_phase(dtab[static_cast<size_t>(t) * A + i / P], dfreq[c]));
+            es[i] = e;
         }
         const bool has_next = t + 1 < t1;
         uint32_t pre[kPreW];
@@ -399,7 +402,7 @@ int launch_tc_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const fl
     tc_col64_kernel<VAR><<<grid, kThreads, tc_smem(plan->A, plan->K), stream>>>(
         v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN, g.d_sched, g.d_nrounds, g.rmax,
         plan->d_dft, plan->A, plan->C, T, g.N, g.Q1, g.n_items, n_tau, g.d_partial, plan->d_status,
-        plan->wait_budget, plan->test_withhold_mma);
+        plan->wait_budget, plan->test_withhold_mma, plan->d_dfreq, plan->delays ? plan->d_dtab : nullptr);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 

@@ -39,7 +39,7 @@ STOKES = ("I", "Q", "U", "V")
 PRODUCTS = ("XX", "YY", "XY", "YX")
 
 #: every symbol include/epic.h declares
-EXPORTS = ("epic_plan", "epic_image", "epic_image_host", "epic_out_floats", "epic_status",
+EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_image_host", "epic_out_floats", "epic_status",
            "epic_set_profiling", "epic_stage_times", "epic_image_static", "epic_image_series", "epic_destroy",
            "epic_strerror")
 
@@ -70,6 +70,8 @@ def load():
     L.epic_image_series.argtypes = [vp, vp, vp, i, i, vp, vp]
     L.epic_image_series.restype = i
     L.epic_image_host.restype = i
+    L.epic_image_ex.argtypes = [vp, vp, vp, vp, i, vp, vp]
+    L.epic_image_ex.restype = i
     L.epic_out_floats.argtypes = [vp]
     L.epic_out_floats.restype = ctypes.c_size_t
     L.epic_status.argtypes = [vp]
@@ -165,18 +167,29 @@ class Plan:
             if not gains.is_contiguous() or gains.is_cuda != device:
                 raise ValueError("gains must be contiguous and on the same device as v")
 
-    def image(self, v, gains=None, out=None, stream=None):
+    def image(self, v, gains=None, out=None, stream=None, delays=None):
         """Image one integration of device-resident voltages; returns (or fills)
-        a flat complex64 device tensor of epic_out_floats/2 elements."""
+        a flat complex64 device tensor of epic_out_floats/2 elements.  delays:
+        optional float64 device tensor [T][A] of geometric delays in seconds
+        (epic_image_ex, the delay-correction block of Sec. 2.2)."""
         import torch
         self._check_inputs(v, gains, device=True)
+        if delays is not None:
+            if (not isinstance(delays, torch.Tensor) or delays.dtype != torch.float64 or not delays.is_cuda
+                    or tuple(delays.shape) != (v.shape[0], self.A) or not delays.is_contiguous()):
+                raise ValueError(f"delays must be a contiguous float64 CUDA tensor [{v.shape[0]}][{self.A}]")
         if out is None:
             out = torch.empty(self.out_floats // 2, dtype=torch.complex64, device=v.device)
         elif out.dtype != torch.complex64 or out.numel() * 2 != self.out_floats or not out.is_contiguous():
             raise ValueError("out must be a contiguous complex64 tensor of the plan's output size")
-        rc = load().epic_image(self._h, v.data_ptr(), gains.data_ptr() if gains is not None else None,
-                               int(v.shape[0]), out.data_ptr(), self._stream(stream))
-        _check(rc, "epic_image")
+        g = gains.data_ptr() if gains is not None else None
+        if delays is None:
+            rc = load().epic_image(self._h, v.data_ptr(), g, int(v.shape[0]), out.data_ptr(), self._stream(stream))
+            _check(rc, "epic_image")
+        else:
+            rc = load().epic_image_ex(self._h, v.data_ptr(), g, delays.data_ptr(), int(v.shape[0]), out.data_ptr(),
+                                      self._stream(stream))
+            _check(rc, "epic_image_ex")
         return out
 
     def image_series(self, v, spectra_per_image, gains=None, out=None, stream=None):

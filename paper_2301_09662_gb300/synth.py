@@ -165,6 +165,20 @@ def sky_voltages(ant_xy: np.ndarray, freq_hz: np.ndarray, T: int, P: int,
     return out
 
 
+def geometric_delays(ant_xy: np.ndarray, T: int, l0: float = 0.3, m0: float = -0.2,
+                     dl: float = 1e-4, dm: float = 5e-5) -> np.ndarray:
+    """[T][A] float64 geometric delays (s) towards a phase centre that drifts
+    as the sky turns: (l, m)(t) = (l0 + t dl, m0 + t dm).  Positions are taken
+    relative to the layout centroid; an antenna further along the direction
+    sees the wavefront earlier, tau_a(t) = -(x_a l(t) + y_a m(t)) / c0."""
+    xy = np.asarray(ant_xy, np.float64)
+    xy = xy - xy.mean(axis=0)
+    t = np.arange(T, dtype=np.float64)
+    l = l0 + dl * t
+    m = m0 + dm * t
+    return -(np.outer(l, xy[:, 0]) + np.outer(m, xy[:, 1])) / C0
+
+
 def random_ci4(shape, rng: np.random.Generator, lo: int = -7, hi: int = 7) -> np.ndarray:
     """Uniform random packed ci4 bytes with parts in [lo, hi]."""
     re = rng.integers(lo, hi + 1, size=shape)

@@ -352,3 +352,90 @@ def test_antenna_kernels_single_antenna_is_zero():
     o = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, Wa)
     raw = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, Wa, oracle.NO_AUTOSUB)
     assert np.max(np.abs(o)) <= 1e-12 * np.max(np.abs(raw))
+
+
+# ------------------------------------------------------------------ delay correction
+# Sec. 2.2: a per-(t, antenna) geometric-delay phase exp(+2 pi i f_c tau_a(t))
+# multiplies each voltage before gridding.
+
+def _steered_case(time_varying):
+    """Quarter-field source whose phase pattern (-i)^{(kx+ky) m_t} is undone by
+    delays with f tau_a(t) = ((kx+ky) m_t mod 4) / 4: the corrected voltages are
+    all s_t, so the image is the zenith closed form of P4."""
+    N, K, A, T = 32, 3, 12, 6
+    wl = synth.random_small(A=A, P=1, C=1, T=T, N=N, K=K, seed=44, gains=False)
+    wl.kernel = synth.gaussian_kernel(K)
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    rng = np.random.default_rng(6)
+    s = rng.integers(-7, 8, T) + 1j * rng.integers(-7, 8, T)
+    m = rng.integers(0, 4, T) if time_varying else np.ones(T, int)
+    n = cells[0, :, 0] + cells[0, :, 1]
+    e = s[:, None] * (-1j) ** (np.outer(m, n) % 4)
+    v = synth.pack_ci4(np.rint(e.real).astype(int), np.rint(e.imag).astype(int)).reshape(T, 1, A, 1)
+    f = wl.freq_hz[0]
+    tau = (np.outer(m, n) % 4) / (4.0 * f)
+    return wl, cells, v, tau, s, N, A
+
+
+@pytest.mark.parametrize("time_varying", [False, True])
+def test_delays_steer_source_to_phase_centre(time_varying):
+    wl, cells, v, tau, s, N, A = _steered_case(time_varying)
+    img = oracle.epic_direct(v, None, cells, wl.grid_n, wl.kernel, freq=wl.freq_hz, delays=tau).reshape(N, N)
+    expect = abs(np.sum(wl.kernel.astype(np.complex128))) ** 2 * (A * A - A) * np.sum(np.abs(s) ** 2)
+    assert abs(img[N // 2, N // 2] - expect) < 1e-12 * expect
+    assert np.unravel_index(np.argmax(img.real), img.shape) == (N // 2, N // 2)
+    # without the correction the source stays off centre
+    raw = oracle.epic_direct(v, None, cells, wl.grid_n, wl.kernel).reshape(N, N)
+    assert raw[N // 2, N // 2].real < 0.5 * expect
+
+
+def test_delays_integer_turns_are_identity():
+    wl = synth.random_small(A=7, P=2, C=1, T=5, N=16, K=3, seed=950)
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    n = np.random.default_rng(3).integers(-5, 6, (wl.T, wl.A))
+    tau = n / wl.freq_hz[0]
+    o = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, wl.kernel, freq=wl.freq_hz, delays=tau)
+    ref = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, wl.kernel)
+    assert rel_err(o, ref) < 1e-12
+
+
+def test_delays_constant_in_time_equal_gains():
+    wl = synth.random_small(A=6, P=2, C=3, T=4, N=16, K=3, seed=960)
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    tau_a = np.random.default_rng(4).uniform(-80e-9, 80e-9, wl.A)
+    tau = np.repeat(tau_a[None], wl.T, axis=0)
+    o = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, wl.kernel, freq=wl.freq_hz, delays=tau)
+    g2 = wl.gains * np.exp(2j * np.pi * np.outer(wl.freq_hz, tau_a))[:, :, None]
+    ref = oracle.epic_direct(wl.v, g2, cells, wl.grid_n, wl.kernel)
+    assert rel_err(o, ref) < 1e-11
+
+
+@pytest.mark.parametrize("A,N,K,P", [(5, 16, 3, 2), (8, 16, 1, 1)])
+def test_delays_direct_equals_fx(A, N, K, P):
+    wl = synth.random_small(A=A, P=P, C=2, T=5, N=N, K=K, seed=970 + A)
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    tau = synth.geometric_delays(wl.ant_xy, wl.T, dl=3e-3, dm=-2e-3)
+    o1 = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, wl.kernel, freq=wl.freq_hz, delays=tau)
+    o2 = oracle.epic_fx(wl.v, wl.gains, cells, wl.grid_n, wl.kernel, freq=wl.freq_hz, delays=tau)
+    assert rel_err(o1, o2) < 1e-12
+
+
+def test_delays_leave_the_auto_term_unchanged():
+    wl = synth.random_small(A=6, P=2, C=2, T=5, N=16, K=3, seed=980)
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    tau = synth.geometric_delays(wl.ant_xy, wl.T, dl=2e-3)
+    kw = dict(freq=wl.freq_hz, delays=tau)
+    auto_d = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, wl.kernel, oracle.NO_AUTOSUB, **kw) - \
+        oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, wl.kernel, **kw)
+    auto = oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, wl.kernel, oracle.NO_AUTOSUB) - \
+        oracle.epic_direct(wl.v, wl.gains, cells, wl.grid_n, wl.kernel)
+    assert rel_err(auto_d, auto) < 1e-11
+
+
+def test_geometric_delays_recipe():
+    ant = np.array([[10.0, 0.0], [-10.0, 0.0], [0.0, 5.0], [0.0, -5.0]])
+    tau = synth.geometric_delays(ant, 3, l0=0.5, m0=0.0, dl=0.0, dm=0.0)
+    # the antenna at +x along l = 0.5 sees the wavefront 10 m * 0.5 / c0 earlier
+    assert np.allclose(tau[:, 0], -5.0 / synth.C0, rtol=0, atol=1e-20)
+    assert np.allclose(tau[:, 1], 5.0 / synth.C0, rtol=0, atol=1e-20)
+    assert np.all(tau[:, 2:] == 0)
