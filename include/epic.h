@@ -273,6 +273,69 @@ int epic_image_static(const double *ant_xy_m, int n_ant, int n_pol,
                       const uint8_t *ci4, const float *gains_c64, int n_spectra,
                       unsigned flags, float *out_c64, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Transient search on the image cube (Sec. 4: per-channel light curves from
+ * the images, the dispersive delay corrected across the band, a single-pulse
+ * search of the de-dispersed light curves; Sec. 5: real-time de-dispersion
+ * and transient detection).  Works on any float intensity cube
+ * I[t][c][p] reached through strides -- a plain [T][C][P] array, or the
+ * Stokes-I slot of an epic_image_series output made with EPIC_STOKES.
+ * ------------------------------------------------------------------------ */
+typedef struct epic_search_s *epic_search_t;
+
+/*
+ * epic_search_plan -- delay table of a de-dispersion search.
+ *
+ *   freq_hz     host double [n_chan] channel centre frequencies
+ *   dt_s        sampling interval of the cube (s)
+ *   dm          host double [n_dm] trial dispersion measures (pc cm^-3, >= 0)
+ *   n_pix       pixels per channel image; n_time samples per channel
+ *   width_mask  boxcar widths of the single-pulse search: bit k = width 2^k,
+ *               k < 6 (1 .. 32 samples); at least one bit
+ *
+ * Channel c at trial d is delayed by s = floor(k_DM DM (f_c^-2 - f_max^-2) / dt
+ * + 1/2) samples (f in MHz, k_DM = 4.148808e3 s MHz^2 pc^-1 cm^3, FP64 on the
+ * host); t_out = n_time - max s output samples remain.  EPIC_ERR_ARG for bad
+ * arguments, EPIC_ERR_TOO_LARGE when the largest delay leaves fewer output
+ * samples than the smallest width.  The plan owns the device delay table.
+ */
+int epic_search_plan(epic_search_t *out, const double *freq_hz, int n_chan, double dt_s,
+                     const double *dm, int n_dm, int n_pix, int n_time, unsigned width_mask);
+
+/* Output samples per trial (t_out) and the largest delay (samples); either pointer may be NULL. */
+int epic_search_info(epic_search_t s, int *t_out, int *max_shift);
+
+/*
+ * epic_dedisperse -- D[d][t][p] = sum_c I[t + s[d][c]][c][p] for t < t_out.
+ *
+ *   cube       device float; I[t][c][p] = cube[t * t_stride + c * c_stride + p * pix_stride]
+ *              (strides in floats, >= 1)
+ *   dd         device float [n_dm][t_out][n_pix], overwritten
+ *
+ * FP32 sums in channel order.  Asynchronous on the stream; allocates nothing.
+ */
+int epic_dedisperse(epic_search_t s, const float *cube, long long t_stride, long long c_stride,
+                    long long pix_stride, float *dd, void *cuda_stream);
+
+/*
+ * epic_single_pulse -- boxcar search of every de-dispersed light curve.
+ *
+ * Per (d, p): mu and sigma are the mean and population standard deviation of
+ * D[d][:][p]; S/N(t, w) = (sum_{k<w} D[d][t+k][p] - w mu) / (sigma sqrt(w))
+ * for the plan's widths w and t <= t_out - w.  Written per (d, p), device
+ * [n_dm][n_pix]: best_snr, best_t and best_w of the largest S/N (ties: the
+ * smaller width, then the earlier start; sigma = 0 gives S/N 0 at t = 0 and
+ * the smallest width).  Then cand (device int pairs (d, p), capacity
+ * cand_cap, may be NULL when cand_cap = 0) receives, in increasing d * n_pix + p
+ * order, every pair whose best S/N >= threshold, and *n_cand (device int) their
+ * number (which can exceed cand_cap; only the first cand_cap are stored).
+ * Asynchronous on the stream; allocates nothing.
+ */
+int epic_single_pulse(epic_search_t s, const float *dd, float threshold, float *best_snr, int *best_t,
+                      int *best_w, int *cand, int cand_cap, int *n_cand, void *cuda_stream);
+
+void epic_search_destroy(epic_search_t s);
+
 /* Static, human-readable text for an EPIC_* code. */
 const char *epic_strerror(int code);
 

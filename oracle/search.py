@@ -74,9 +74,11 @@ def single_pulse(dd, widths):
     x = np.asarray(dd, np.float64)
     n_dm, T_out, P = x.shape
     ws = sorted(int(w) for w in widths if int(w) <= T_out)
+    if not ws:
+        raise ValueError("no boxcar width fits the light curve")
     snr = np.zeros((n_dm, P))
     bt = np.zeros((n_dm, P), np.int64)
-    bw = np.full((n_dm, P), ws[0] if ws else 0, np.int64)
+    bw = np.full((n_dm, P), ws[0], np.int64)
     for d in range(n_dm):
         for p in range(P):
             best, arg = -np.inf, (0, ws[0])

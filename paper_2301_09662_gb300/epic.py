@@ -41,7 +41,8 @@ PRODUCTS = ("XX", "YY", "XY", "YX")
 #: every symbol include/epic.h declares
 EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_image_host", "epic_out_floats", "epic_status",
            "epic_set_profiling", "epic_stage_times", "epic_image_static", "epic_image_series", "epic_destroy",
-           "epic_strerror")
+           "epic_strerror", "epic_search_plan", "epic_search_info", "epic_dedisperse", "epic_single_pulse",
+           "epic_search_destroy")
 
 _lib = None
 
@@ -86,6 +87,17 @@ def load():
     L.epic_destroy.restype = None
     L.epic_strerror.argtypes = [i]
     L.epic_strerror.restype = ctypes.c_char_p
+    ll = ctypes.c_longlong
+    L.epic_search_plan.argtypes = [ctypes.POINTER(vp), vp, i, ctypes.c_double, vp, i, i, i, u]
+    L.epic_search_plan.restype = i
+    L.epic_search_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.epic_search_info.restype = i
+    L.epic_dedisperse.argtypes = [vp, vp, ll, ll, ll, vp, vp]
+    L.epic_dedisperse.restype = i
+    L.epic_single_pulse.argtypes = [vp, vp, ctypes.c_float, vp, vp, vp, vp, i, vp, vp]
+    L.epic_single_pulse.restype = i
+    L.epic_search_destroy.argtypes = [vp]
+    L.epic_search_destroy.restype = None
     _lib = L
     return L
 
@@ -301,3 +313,76 @@ def make_plan_raw(ant_xy, n_pol, kernel, grid_n, freq_hz, du=0.5, max_spectra=16
     rc = L.epic_plan(ctypes.byref(h), ant.ctypes.data, ant.shape[0], int(n_pol), kern.ctypes.data, kern.shape[0],
                      gn.ctypes.data, fr.ctypes.data, len(fr), float(du), int(max_spectra), int(precision), int(flags))
     return rc, h
+
+
+class Search:
+    """De-dispersion and single-pulse search of an intensity cube (epic_search_*).
+
+    freq_hz [C], dt_s, dms [n_dm] (pc cm^-3), n_pix, n_time; widths: boxcar
+    widths, powers of two up to 32."""
+
+    def __init__(self, freq_hz, dt_s, dms, n_pix, n_time, widths=(1, 2, 4, 8, 16, 32)):
+        L = load()
+        self._f = np.ascontiguousarray(freq_hz, np.float64)
+        self._dm = np.ascontiguousarray(dms, np.float64)
+        mask = 0
+        for w in widths:
+            k = int(w).bit_length() - 1
+            if int(w) != 1 << k or k > 5:
+                raise ValueError("widths must be powers of two up to 32")
+            mask |= 1 << k
+        self.C, self.n_dm, self.n_pix, self.n_time = len(self._f), len(self._dm), int(n_pix), int(n_time)
+        self._h = ctypes.c_void_p()
+        rc = L.epic_search_plan(ctypes.byref(self._h), self._f.ctypes.data, self.C, float(dt_s), self._dm.ctypes.data,
+                                self.n_dm, self.n_pix, self.n_time, mask)
+        _check(rc, "epic_search_plan")
+        t_out, smax = ctypes.c_int(), ctypes.c_int()
+        _check(L.epic_search_info(self._h, ctypes.byref(t_out), ctypes.byref(smax)), "epic_search_info")
+        self.t_out, self.max_shift = t_out.value, smax.value
+
+    def dedisperse(self, cube, strides=None, out=None, stream=None):
+        """cube: float32 CUDA tensor; strides (t, c, p) in elements, default the
+        contiguous [n_time][C][n_pix] layout.  Returns dd [n_dm][t_out][n_pix]."""
+        import torch
+        if not isinstance(cube, torch.Tensor) or cube.dtype != torch.float32 or not cube.is_cuda:
+            raise TypeError("cube must be a float32 CUDA tensor")
+        ts, cs, ps = strides if strides is not None else (self.C * self.n_pix, self.n_pix, 1)
+        last = (self.n_time - 1) * ts + (self.C - 1) * cs + (self.n_pix - 1) * ps
+        if min(ts, cs, ps) < 1 or last >= cube.numel() or not cube.is_contiguous():
+            raise ValueError("cube is too small for the plan's shape and these strides")
+        if out is None:
+            out = torch.empty((self.n_dm, self.t_out, self.n_pix), dtype=torch.float32, device=cube.device)
+        rc = load().epic_dedisperse(self._h, cube.data_ptr(), int(ts), int(cs), int(ps), out.data_ptr(),
+                                    Plan._stream(None, stream))
+        _check(rc, "epic_dedisperse")
+        return out
+
+    def single_pulse(self, dd, threshold, cand_cap=4096, stream=None):
+        """Returns (best_snr, best_t, best_w [n_dm][n_pix], cand [cap][2] int32, n_cand) on the device."""
+        import torch
+        if (dd.dtype != torch.float32 or not dd.is_cuda or not dd.is_contiguous()
+                or tuple(dd.shape) != (self.n_dm, self.t_out, self.n_pix)):
+            raise ValueError(f"dd must be float32 CUDA [{self.n_dm}][{self.t_out}][{self.n_pix}]")
+        dev = dd.device
+        snr = torch.empty((self.n_dm, self.n_pix), dtype=torch.float32, device=dev)
+        bt = torch.empty((self.n_dm, self.n_pix), dtype=torch.int32, device=dev)
+        bw = torch.empty_like(bt)
+        cand = torch.empty((max(int(cand_cap), 1), 2), dtype=torch.int32, device=dev)
+        n = torch.empty(1, dtype=torch.int32, device=dev)
+        rc = load().epic_single_pulse(self._h, dd.data_ptr(), float(threshold), snr.data_ptr(), bt.data_ptr(),
+                                      bw.data_ptr(), cand.data_ptr(), int(cand_cap), n.data_ptr(),
+                                      Plan._stream(None, stream))
+        _check(rc, "epic_single_pulse")
+        return snr, bt, bw, cand, n
+
+    def close(self):
+        if self._h:
+            load().epic_search_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

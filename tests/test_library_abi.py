@@ -101,3 +101,25 @@ def test_antenna_kernel_flag_combinations_rejected_on_host(lib):
     rc, h = epic.make_plan_raw(**_geom(flags=epic.EPIC_ANTENNA_KERNELS, precision=epic.EPIC_TC_SPLIT_FP16,
                                        grid_n=np.array([64, 64], np.int32)))
     assert rc == epic.EPIC_ERR_UNSUPPORTED and not h.value
+
+
+def test_search_plan_rejects_bad_arguments_on_host(lib):
+    f = np.array([42.1e6, 42.125e6, 42.15e6])
+    dm = np.array([0.0, 5.0])
+    h = ctypes.c_void_p()
+    P = lambda a: a.ctypes.data if a is not None else None
+    assert lib.epic_search_plan(ctypes.byref(h), P(f), 3, 0.04, P(dm), 2, 64, 100, 0) == epic.EPIC_ERR_ARG
+    assert lib.epic_search_plan(ctypes.byref(h), P(f), 3, 0.04, P(dm), 2, 64, 100, 64) == epic.EPIC_ERR_ARG
+    assert lib.epic_search_plan(ctypes.byref(h), P(f), 3, -1.0, P(dm), 2, 64, 100, 1) == epic.EPIC_ERR_ARG
+    assert lib.epic_search_plan(ctypes.byref(h), None, 3, 0.04, P(dm), 2, 64, 100, 1) == epic.EPIC_ERR_ARG
+    neg = np.array([-1.0])
+    assert lib.epic_search_plan(ctypes.byref(h), P(f), 3, 0.04, P(neg), 1, 64, 100, 1) == epic.EPIC_ERR_ARG
+    # DM 5000 delays the lowest channel by far more than 100 samples of 40 ms
+    big = np.array([5000.0])
+    assert lib.epic_search_plan(ctypes.byref(h), P(f), 3, 0.04, P(big), 1, 64, 100, 1) == epic.EPIC_ERR_TOO_LARGE
+    assert lib.epic_search_plan(ctypes.byref(h), P(f), 3, 0.04, P(dm), 2, 64, 20, 32) == epic.EPIC_ERR_TOO_LARGE
+    assert h.value is None
+    assert lib.epic_search_info(None, None, None) == epic.EPIC_ERR_ARG
+    assert lib.epic_dedisperse(None, None, 1, 1, 1, None, None) == epic.EPIC_ERR_ARG
+    assert lib.epic_single_pulse(None, None, 0.0, None, None, None, None, 0, None, None) == epic.EPIC_ERR_ARG
+    lib.epic_search_destroy(None)
