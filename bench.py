@@ -249,16 +249,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def tensor_stages():
+    """DFT stages the tensor form runs as GEMMs: both (default), or the column
+    stage alone when EPIC_TC_PIPE=1 or EPIC_TC_SERIAL=1 selects an earlier form."""
+    return 1 if os.environ.get("EPIC_TC_PIPE") == "1" or os.environ.get("EPIC_TC_SERIAL") == "1" else 2
+
+
 def tensor_roofline(wl, form, img_ms, peaks):
     """Executed tensor FLOPs of the tensor-core imaging launch over its time:
-    per CTA (pixel class) and sample, 8 k-blocks x terms MMAs of 128 x 128 x 16."""
+    per CTA (pixel class), sample and DFT stage, 8 k-blocks x terms MMAs of
+    128 x 128 x 16."""
     terms = 1 if form == "tc_fp16" else 3
     n_items = sum((int(n) // 64) ** 2 for n in wl.grid_n)
-    flops = n_items * wl.T * 8 * terms * 2.0 * 128 * 128 * 16
+    flops = n_items * wl.T * tensor_stages() * 8 * terms * 2.0 * 128 * 128 * 16
     ach = flops / (img_ms / 1e3) / 1e12
     peak = float(peaks.get("bf16_tflops", 1892.1))
     return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": None, "executed_flops_per_launch": flops, "ms_per_launch": img_ms,
+            "dft_stages_on_tensor_cores": tensor_stages(),
             "peak_source": "MEASURED_PEAKS bf16_tflops burst (dense FP16 rate equals BF16)"}
 
 
@@ -276,9 +284,10 @@ def time_variants(wl, v, g, out, flush, args, stream):
              "tc_split_fp16_taper": dict(precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_KERNEL_TAPER),
              "fp32_delays": dict()}
     notes = {"kernel_taper": "FP32; image-domain |W^|^2 taper with point gridding (exact for one shared kernel)",
-             "tc_split_fp16": "column DFT on tcgen05, FP16 hi+lo operands (3 MMAs), FP32 accumulate in TMEM",
-             "tc_fp16": "column DFT on tcgen05, single FP16 operands",
-             "tc_split_bf16": "column DFT on tcgen05, BF16 hi+lo operands (3 MMAs)",
+             "tc_split_fp16": "row and column DFTs on tcgen05, FP16 hi+lo operands (3 MMAs per k-block), "
+                              "FP32 accumulate in TMEM",
+             "tc_fp16": "row and column DFTs on tcgen05, single FP16 operands",
+             "tc_split_bf16": "row and column DFTs on tcgen05, BF16 hi+lo operands (3 MMAs per k-block)",
              "tc_split_fp16_taper": "tc_split_fp16 with the image-domain kernel taper",
              "fp32_delays": "FP32 literal form with per-(t, antenna) geometric-delay phases (epic_image_ex; "
                             "[T][A] FP64 delays resident in HBM, phases formed in the kernel)"}

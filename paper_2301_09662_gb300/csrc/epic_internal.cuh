@@ -63,7 +63,7 @@ struct epic_plan_s {
     size_t out_floats = 0;
     uint8_t *d_dft = nullptr;          // tensor form: column-DFT operand (hi, lo parts)
     uint16_t *d_dft_rows = nullptr;    // pipelined tensor form: the same operand as plain rows
-    bool tc_pipe = false;              // use the pipelined tensor kernel
+    int tc_form = 2;                   // tensor kernel: 0 serial column DFT, 1 pipelined column DFT, 2 both DFTs
     short2 *d_cells = nullptr;         // [C][A]
     float2 *d_kernel = nullptr;        // [K*K]
     int *d_autoint = nullptr;          // [C][A][4] exact integer auto sums
@@ -137,6 +137,10 @@ int launch_tc(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const floa
               cudaStream_t stream);
 void build_dft_operand(bool bf16, std::vector<uint16_t> &words);
 size_t tc_pipe_smem_bytes(int A, int K);
+size_t tc_dual_smem_bytes(int A, int K);
+int prepare_tc_dual(const epic_plan_s *plan);
+int launch_tc_dual(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
+                   cudaStream_t stream);
 int prepare_tc_pipe(const epic_plan_s *plan);
 int launch_tc_pipe(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                    cudaStream_t stream);

@@ -470,7 +470,7 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         const int ap = n_ant * n_pol;
         if (tensor) {
             // + static shared memory of the kernel (barriers, TMEM slot, alignment)
-            if (std::max(epic::tc_smem_bytes(n_ant, p->K), epic::tc_pipe_smem_bytes(n_ant, p->K)) + 2048 >
+            if (std::max({epic::tc_smem_bytes(n_ant, p->K), epic::tc_pipe_smem_bytes(n_ant, p->K), epic::tc_dual_smem_bytes(n_ant, p->K)}) + 2048 >
                 static_cast<size_t>(smem_optin))
                 rc = EPIC_ERR_UNSUPPORTED;
             g.reg64 = true;   // same gridding schedule and natural pixel order
@@ -522,18 +522,20 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         rc = dev_upload(&p->d_autoint, static_cast<const int *>(nullptr),
                         static_cast<size_t>(p->series_cap) * n_chan * n_ant * 4);
     if (rc == EPIC_OK && tensor) {
-        // the pipelined kernel unless EPIC_TC_SERIAL=1 asks for the one-sample-at-a-time kernel
+        // both DFT stages on the tensor cores unless EPIC_TC_PIPE=1 (column stage only,
+        // pipelined) or EPIC_TC_SERIAL=1 (column stage only, one sample at a time) asks otherwise
         const char *ser = std::getenv("EPIC_TC_SERIAL");
-        p->tc_pipe = !(ser && ser[0] == '1');
+        const char *pip = std::getenv("EPIC_TC_PIPE");
+        p->tc_form = (ser && ser[0] == '1') ? 0 : (pip && pip[0] == '1') ? 1 : 2;
         std::vector<uint16_t> ops;
-        if (p->tc_pipe) {
+        if (p->tc_form == 1) {
             epic::build_dft_rows(precision == EPIC_TC_SPLIT_BF16, ops);
             rc = dev_upload(&p->d_dft_rows, ops.data(), ops.size());
             if (rc == EPIC_OK) rc = epic::prepare_tc_pipe(p);
         } else {
             epic::build_dft_operand(precision == EPIC_TC_SPLIT_BF16, ops);
             rc = dev_upload(&p->d_dft, reinterpret_cast<const uint8_t *>(ops.data()), ops.size() * 2);
-            if (rc == EPIC_OK) rc = epic::prepare_tc(p);
+            if (rc == EPIC_OK) rc = p->tc_form == 2 ? epic::prepare_tc_dual(p) : epic::prepare_tc(p);
         }
     }
     for (const auto &g : p->groups) {

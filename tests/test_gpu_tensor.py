@@ -1,5 +1,6 @@
-"""Parity of the tensor-core form (tcgen05 column DFT-as-GEMM) with the FP64
-oracle, per operand precision: split FP16 within 1e-5 of the channel peak,
+"""Parity of the tensor-core forms (tcgen05 DFT-as-GEMM: both transform stages by
+default, the column stage alone with EPIC_TC_PIPE=1 or EPIC_TC_SERIAL=1) with the
+FP64 oracle, per operand precision: split FP16 within 1e-5 of the channel peak,
 single FP16 within 2e-3; the BF16 two-part split is reported and bounded."""
 import numpy as np
 import pytest
@@ -77,4 +78,21 @@ def test_bounded_wait_reports_timeout_and_context_survives(monkeypatch):
     assert p.status() == epic.EPIC_OK          # reading clears it
     p.close()
     monkeypatch.delenv("EPIC_TEST_WITHHOLD_MMA")
+    assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16).max() < SPLIT_TOL
+
+
+@pytest.mark.parametrize("form", ["EPIC_TC_PIPE", "EPIC_TC_SERIAL"])
+@pytest.mark.parametrize("precision,tol", [(epic.EPIC_TC_SPLIT_FP16, SPLIT_TOL), (epic.EPIC_TC_SPLIT_BF16, BF16_TOL)])
+def test_column_stage_only_forms(monkeypatch, form, precision, tol):
+    """The earlier forms (column DFT on the tensor cores, row FFT in FP32) stay correct."""
+    wl = synth.random_small(A=48, P=2, C=2, T=21, N=128, K=5, seed=330)
+    monkeypatch.setenv(form, "1")
+    assert _cmp(wl, precision).max() < tol
+
+
+@pytest.mark.parametrize("T", [1, 2, 65])
+def test_two_stage_form_sample_counts(T):
+    """One sample (no overlap), two (one hand-off each way) and an odd count over
+    several time chunks: the row/column stage pipeline drains every sample."""
+    wl = synth.random_small(A=40, P=2, C=1, T=T, N=64, K=3, seed=340 + T)
     assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16).max() < SPLIT_TOL
