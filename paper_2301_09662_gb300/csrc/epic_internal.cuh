@@ -36,6 +36,7 @@ struct GroupCfg {
     int R1 = 1, R2 = 1;
     // M = 64 register-transform kernel: gridding schedule and samples per iteration
     bool reg64 = false;
+    bool tensor = false;               // a tensor plan's group that folds to 64 runs the tensor kernel
     int ts = 1;
     int rmax = 0;
     uint32_t *d_sched = nullptr;       // device: [n_chan][8 warps][rmax][32] segment descriptors

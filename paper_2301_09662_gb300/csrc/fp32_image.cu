@@ -390,7 +390,7 @@ int prepare_fp32(const epic_plan_s *plan, const GroupCfg &g)
 int launch_imaging(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                    cudaStream_t s)
 {
-    if (plan->precision != EPIC_FP32)
+    if (g.tensor)
         return plan->tc_form == 2   ? launch_tc_dual(plan, g, v, gains, T, n_tau, s)
                : plan->tc_form == 1 ? launch_tc_pipe(plan, g, v, gains, T, n_tau, s)
                                     : launch_tc(plan, g, v, gains, T, n_tau, s);

@@ -325,10 +325,12 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     if (precision < EPIC_FP32 || precision > EPIC_TC_SPLIT_BF16) return EPIC_ERR_ARG;
     const bool tensor = precision != EPIC_FP32;
     if (tensor) {
-        // the tensor form exists for dual polarisation on folded side 64
+        // the tensor form exists for dual polarisation on folded side 64; channel groups of
+        // other sides (32, 96) in the same plan run the FP32 kernel, but at least one must fold
         if (n_pol != 2 || (n_ant * n_pol) % 4 != 0) return EPIC_ERR_UNSUPPORTED;
-        for (int c = 0; c < n_chan; c++)
-            if (grid_n[c] == 32 || grid_n[c] == 96) return EPIC_ERR_UNSUPPORTED;
+        bool any = false;
+        for (int c = 0; c < n_chan; c++) any = any || (grid_n[c] != 32 && grid_n[c] != 96);
+        if (!any) return EPIC_ERR_UNSUPPORTED;
     }
     if (static_cast<long long>(n_ant) * n_pol > epic::kMaxAP) return EPIC_ERR_UNSUPPORTED;
     for (int c = 0; c < n_chan; c++) {
@@ -468,7 +470,8 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         g.R1 = 8;
         g.R2 = g.M / 8;
         const int ap = n_ant * n_pol;
-        if (tensor) {
+        g.tensor = tensor && g.M == 64;
+        if (g.tensor) {
             // + static shared memory of the kernel (barriers, TMEM slot, alignment)
             if (std::max({epic::tc_smem_bytes(n_ant, p->K), epic::tc_pipe_smem_bytes(n_ant, p->K), epic::tc_dual_smem_bytes(n_ant, p->K)}) + 2048 >
                 static_cast<size_t>(smem_optin))
@@ -539,8 +542,8 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         }
     }
     for (const auto &g : p->groups) {
-        if (rc != EPIC_OK || tensor) break;
-        rc = epic::prepare_fp32(p, g);
+        if (rc != EPIC_OK) break;
+        if (!g.tensor) rc = epic::prepare_fp32(p, g);
     }
     if (rc == EPIC_OK) {
         const char *env = std::getenv("EPIC_NO_GRAPH");

@@ -96,3 +96,12 @@ def test_two_stage_form_sample_counts(T):
     several time chunks: the row/column stage pipeline drains every sample."""
     wl = synth.random_small(A=40, P=2, C=1, T=T, N=64, K=3, seed=340 + T)
     assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16).max() < SPLIT_TOL
+
+
+@pytest.mark.parametrize("precision,tol", [(epic.EPIC_TC_SPLIT_FP16, SPLIT_TOL), (epic.EPIC_TC_SPLIT_BF16, BF16_TOL)])
+def test_mixed_grid_sides_in_a_tensor_plan(precision, tol):
+    """Channel groups of sides 64, 96 and 128 in one tensor plan: 64 and 128 fold to the
+    tensor kernel, 96 runs the FP32 kernel; every channel meets the form's bound."""
+    wl = synth.random_small(A=40, P=2, C=3, T=17, N=64, K=5, seed=350)
+    wl.grid_n = np.array([64, 96, 128], np.int32)
+    assert _cmp(wl, precision).max() < tol

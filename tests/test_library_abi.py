@@ -86,7 +86,7 @@ def test_null_handles_are_rejected(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(n_pol=1), dict(grid_n=np.array([32, 32], np.int32)),
-                                 dict(grid_n=np.array([96, 128], np.int32))])
+                                 dict(grid_n=np.array([96, 32], np.int32))])
 def test_tensor_form_rejects_unsupported_shapes_on_host(lib, bad):
     rc, h = epic.make_plan_raw(**_geom(precision=epic.EPIC_TC_SPLIT_FP16, **bad))
     assert rc == epic.EPIC_ERR_UNSUPPORTED and not h.value
