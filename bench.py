@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--channels", type=int, default=None,
                     help="shrink the workload to this many channels (profiling captures only)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the cost model's launch shapes instead of epic_autotune's measured ones")
     ap.add_argument("--search-only", action="store_true",
                     help="time only the transient search of a synthetic image cube and print its JSON")
     return ap.parse_args()
@@ -297,6 +299,8 @@ def time_variants(wl, v, g, out, flush, args, stream):
     for name, kw in forms.items():
         try:
             p = epic.Plan.from_workload(wl, **kw)
+            if not args.no_autotune:
+                p.autotune(wl.T)
         except epic.EpicError as e:
             res[name] = {"unavailable": str(e)}
             continue
@@ -434,6 +438,8 @@ def run_ours(args):
     precision = {"fp32": epic.EPIC_FP32, "tc_split_fp16": epic.EPIC_TC_SPLIT_FP16, "tc_fp16": epic.EPIC_TC_FP16,
                  "tc_split_bf16": epic.EPIC_TC_SPLIT_BF16}[args.precision]
     plan = epic.Plan.from_workload(wl, precision=precision, flags=epic.EPIC_KERNEL_TAPER if args.taper else 0)
+    if not args.no_autotune:
+        plan.autotune(wl.T)      # plan-time launch-shape measurement, outside the timed region
     v = torch.from_numpy(wl.v).cuda()
     g = None if wl.gains is None else torch.from_numpy(wl.gains).cuda()
     out = torch.empty(plan.out_floats // 2, dtype=torch.complex64, device="cuda")
@@ -497,6 +503,7 @@ def run_ours(args):
         traffic = rec[0]
 
     config = describe(wl, args.workload)
+    config["launch_shapes"] = "cost model" if args.no_autotune else "measured per channel group (epic_autotune)"
     config["form"] = args.precision + (" + image-domain kernel taper" if args.taper else " (literal gridding)")
     roofline = {"bound": "alu", "kernel": f"FP32 imaging kernel {image_stage}", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,

@@ -154,6 +154,23 @@ int epic_image(epic_plan_t plan, const uint8_t *ci4, const float *gains_c64,
                int n_spectra, float *out_c64, void *cuda_stream);
 
 /*
+ * epic_autotune -- pick each channel group's launch shape by measurement.
+ *
+ * For every channel group the imaging and epilogue launches of an n_spectra
+ * integration are timed (CUDA events on the stream, zero voltages, unit
+ * gains, scratch buffers the call allocates and frees) at a handful of
+ * time-chunk counts -- the cost model's choice, its neighbours, and the counts
+ * that fill whole waves of SMs -- and the fastest is kept for later epic_image /
+ * epic_image_ex calls with the same n_spectra (other counts fall back to the
+ * cost model; epic_image_series keeps one chunk per image).  The next call
+ * re-captures its CUDA graph.  Blocks the host until the timing runs finish.
+ * Results are unchanged up to the FP32 summation order of the time chunks.
+ * EPIC_ERR_ARG for a null plan or n_spectra outside [1, max_spectra];
+ * EPIC_ERR_NOMEM / EPIC_ERR_CUDA if the scratch buffers or launches fail.
+ */
+int epic_autotune(epic_plan_t plan, int n_spectra, void *cuda_stream);
+
+/*
  * epic_image_ex -- epic_image with the geometric-delay correction of Sec. 2.2
  * (the delay-correction block that compensates each antenna's geometric delay
  * at every time step, for every channel, before gridding).  Each calibrated

@@ -37,6 +37,7 @@ struct GroupCfg {
     // M = 64 register-transform kernel: gridding schedule and samples per iteration
     bool reg64 = false;
     bool tensor = false;               // a tensor plan's group that folds to 64 runs the tensor kernel
+    int tuned_tau = 0, tuned_T = -1;   // time chunks epic_autotune measured fastest for T = tuned_T
     int ts = 1;
     int rmax = 0;
     uint32_t *d_sched = nullptr;       // device: [n_chan][8 warps][rmax][32] segment descriptors
@@ -172,6 +173,8 @@ struct RawImage {
     int *status = nullptr;
 };
 int fp32_pick_tau(int n_items, int T, int sms);
+// time chunks of one launch: forced (image series), else autotuned for this T, else the cost model
+int choose_tau(const epic_plan_s *plan, const GroupCfg &g, int T);
 size_t fp32_smem_bytes(int M, int P, int A, int K);
 int launch_fp32_raw(const RawImage &r, const uint8_t *v, const float2 *gains, cudaStream_t stream);
 int launch_autopower_raw(const RawImage &r, const uint8_t *v, int sm_count, cudaStream_t stream);

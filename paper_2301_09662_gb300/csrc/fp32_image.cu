@@ -20,6 +20,8 @@
 #include <cstdio>
 
 #include "dft_small.cuh"
+#include <algorithm>
+
 #include "epic_internal.cuh"
 
 namespace epic {
@@ -306,7 +308,7 @@ int launch_group(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
 {
     auto kfn = fp32_image_kernel<M, P>;
     const size_t smem = smem_bytes<M, P>(plan->A, plan->K, plan->nker);
-    int n_tau = plan->force_tau > 0 ? plan->force_tau : pick_tau(g.n_items, T, plan->sm_count);
+    int n_tau = choose_tau(plan, g, T);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));
@@ -346,6 +348,14 @@ int launch_raw(const RawImage &r, const uint8_t *v, const float2 *gains, cudaStr
 }  // namespace
 
 int fp32_pick_tau(int n_items, int T, int sms) { return pick_tau(n_items, T, sms); }
+
+int choose_tau(const epic_plan_s *plan, const GroupCfg &g, int T)
+{
+    int n = plan->force_tau > 0                       ? plan->force_tau
+            : (g.tuned_tau > 0 && g.tuned_T == T) ? g.tuned_tau
+                                                  : pick_tau(g.n_items, T, plan->sm_count);
+    return std::max(1, std::min(n, g.tau_cap));
+}
 
 size_t fp32_smem_bytes(int M, int P, int A, int K)
 {

@@ -258,7 +258,7 @@ int launch_reg64_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
 {
     auto kfn = fp32_reg64_kernel<P, TS, KC, DL>;
     const size_t smem = reg64_smem<P, TS>(plan->A, plan->K, plan->nker);
-    int n_tau = plan->force_tau > 0 ? plan->force_tau : fp32_pick_tau(g.n_items, T, plan->sm_count);
+    int n_tau = choose_tau(plan, g, T);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));

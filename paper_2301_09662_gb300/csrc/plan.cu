@@ -613,6 +613,75 @@ int epic_image_ex(epic_plan_t plan, const uint8_t *ci4, const float *gains, cons
     return rc;
 }
 
+// Autotuner: for each channel group, time the imaging and epilogue launches of
+// an n_spectra integration (zero voltages, unit gains, scratch buffers) at a few
+// time-chunk counts -- the cost model's choice, its neighbours, and the counts
+// that fill whole waves of SMs -- and keep the fastest (min of three timed runs).
+int epic_autotune(epic_plan_t plan, int n_spectra, void *stream)
+{
+    if (!plan || n_spectra < 1 || n_spectra > plan->max_spectra) return EPIC_ERR_ARG;
+    auto s = static_cast<cudaStream_t>(stream);
+    const size_t vbytes = static_cast<size_t>(n_spectra) * plan->C * plan->A * plan->P;
+    uint8_t *v = nullptr;
+    float2 *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = EPIC_OK;
+    if (cudaMalloc(&v, vbytes) != cudaSuccess || cudaMalloc(&out, plan->out_floats * sizeof(float)) != cudaSuccess)
+        rc = EPIC_ERR_NOMEM;
+    if (rc == EPIC_OK && (cudaMemsetAsync(v, 0, vbytes, s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+                          cudaEventCreate(&e1) != cudaSuccess))
+        rc = EPIC_ERR_CUDA;
+    const double *saved_delays = plan->delays;
+    plan->delays = nullptr;
+    const bool autosub = !(plan->flags & EPIC_NO_AUTOSUB);
+    if (rc == EPIC_OK && autosub) rc = epic::launch_autopower(plan, v, n_spectra, s);
+    for (auto &g : plan->groups) {
+        if (rc != EPIC_OK) break;
+        const int cap = std::max(1, std::min(g.tau_cap, n_spectra));
+        std::vector<int> cand;
+        auto add = [&](int n) {
+            if (n >= 1 && n <= cap && std::find(cand.begin(), cand.end(), n) == cand.end()) cand.push_back(n);
+        };
+        const int c0 = epic::fp32_pick_tau(g.n_items, n_spectra, plan->sm_count);
+        for (int d = -2; d <= 2; d++) add(c0 + d);
+        for (int waves = 1; waves <= 4; waves++)
+            add(static_cast<int>((static_cast<long long>(waves) * plan->sm_count) / std::max(1, g.n_items)));
+        float best = 1e30f;
+        int best_n = c0;
+        for (int n : cand) {
+            g.tuned_tau = n;
+            g.tuned_T = n_spectra;
+            float t_min = 1e30f;
+            for (int rep = 0; rep < 4 && rc == EPIC_OK; rep++) {
+                int nt = 0;
+                if (cudaEventRecord(e0, s) != cudaSuccess) rc = EPIC_ERR_CUDA;
+                if (rc == EPIC_OK) rc = epic::launch_imaging(plan, g, v, nullptr, n_spectra, &nt, s);
+                if (rc == EPIC_OK) rc = epic::launch_epilogue(plan, g, nullptr, n_spectra, nt, out, s);
+                if (rc == EPIC_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+                    rc = EPIC_ERR_CUDA;
+                float ms = 0;
+                if (rc == EPIC_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = EPIC_ERR_CUDA;
+                if (rc == EPIC_OK && rep > 0) t_min = std::min(t_min, ms);   // the first run warms up
+            }
+            if (rc != EPIC_OK) break;
+            if (t_min < best) {
+                best = t_min;
+                best_n = n;
+            }
+        }
+        g.tuned_tau = best_n;
+        g.tuned_T = n_spectra;
+    }
+    plan->delays = saved_delays;
+    plan->g_T = -1;                      // the next epic_image re-captures its graph
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(v);
+    cudaFree(out);
+    if (rc == EPIC_OK && cudaGetLastError() != cudaSuccess) rc = EPIC_ERR_CUDA;
+    return rc;
+}
+
 int epic_image_series(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra, int spi, float *out,
                       void *stream)
 {

@@ -395,7 +395,7 @@ template <int VAR>
 int launch_tc_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau_out,
                 cudaStream_t stream)
 {
-    int n_tau = plan->force_tau > 0 ? plan->force_tau : fp32_pick_tau(g.n_items, T, plan->sm_count);
+    int n_tau = choose_tau(plan, g, T);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));

@@ -39,7 +39,7 @@ STOKES = ("I", "Q", "U", "V")
 PRODUCTS = ("XX", "YY", "XY", "YX")
 
 #: every symbol include/epic.h declares
-EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_image_host", "epic_out_floats", "epic_status",
+EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_autotune", "epic_image_host", "epic_out_floats", "epic_status",
            "epic_set_profiling", "epic_stage_times", "epic_image_static", "epic_image_series", "epic_destroy",
            "epic_strerror", "epic_search_plan", "epic_search_info", "epic_dedisperse", "epic_single_pulse",
            "epic_search_destroy")
@@ -73,6 +73,8 @@ def load():
     L.epic_image_host.restype = i
     L.epic_image_ex.argtypes = [vp, vp, vp, vp, i, vp, vp]
     L.epic_image_ex.restype = i
+    L.epic_autotune.argtypes = [vp, i, vp]
+    L.epic_autotune.restype = i
     L.epic_out_floats.argtypes = [vp]
     L.epic_out_floats.restype = ctypes.c_size_t
     L.epic_status.argtypes = [vp]
@@ -203,6 +205,11 @@ class Plan:
                                       self._stream(stream))
             _check(rc, "epic_image_ex")
         return out
+
+    def autotune(self, n_spectra, stream=None):
+        """Time a few launch shapes per channel group for n_spectra and keep the
+        fastest (epic_autotune); blocks until done."""
+        _check(load().epic_autotune(self._h, int(n_spectra), self._stream(stream)), "epic_autotune")
 
     def image_series(self, v, spectra_per_image, gains=None, out=None, stream=None):
         """Time-resolved images: one image per block of spectra_per_image spectra

@@ -231,3 +231,22 @@ def test_largest_supported_shapes(A, P, N, K):
     gpu, _ = run_gpu(wl)
     ref = _oracle(wl)
     assert peak_rel_err(gpu, ref, wl.grid_n, P).max() < FP32_TOL
+
+
+def test_autotuned_plan_keeps_parity():
+    """epic_autotune picks each group's time-chunk count by measurement; the
+    images stay within the FP32 bound (only the chunk summation order moves),
+    and n_spectra outside the plan is rejected."""
+    import torch
+    wl = synth.random_small(A=40, P=2, C=3, T=50, N=64, K=5, seed=1200)
+    wl.grid_n = np.array([64, 96, 128], np.int32)
+    p = epic.Plan.from_workload(wl)
+    p.autotune(wl.T)
+    v, g = torch_inputs(wl)
+    out = p.image(v, g)
+    torch.cuda.synchronize()
+    assert p.status() == epic.EPIC_OK
+    ref = oracle.workload_image(wl)
+    assert np.max(peak_rel_err(out.cpu().numpy().astype(np.complex128), ref, wl.grid_n, 2)) < 1e-5
+    with pytest.raises(epic.EpicError):
+        p.autotune(wl.T + 1)
