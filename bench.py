@@ -179,20 +179,24 @@ class ClockSampler:
 
 
 def cpu_baseline(wl, budget_s):
-    """Time the FP64 oracle (O1, OpenMP over channels) on a bounded sample:
-    one channel per thread, as many time samples as fit the budget."""
+    """Time the FP64 oracle (O1, OpenMP over channels) on a bounded sample of
+    about budget_s seconds: whole channels, one per thread per round, all
+    spectra when they fit, more channels (in multiples of the thread count)
+    while the budget allows."""
     import oracle
     threads = oracle.threads()
     C_s = max(1, min(wl.C, threads))
-    chans = list(range(C_s))
-    # calibrate the per-spectrum cost on a short run
+    # calibrate the per-spectrum cost on a short run over one round of channels
     T_probe = max(1, min(wl.T, 8))
-    sub = _sub_workload(wl, chans, T_probe)
+    sub = _sub_workload(wl, list(range(C_s)), T_probe)
     t0 = time.perf_counter()
     oracle.workload_image(sub)
-    dt = time.perf_counter() - t0
-    per_t = dt / T_probe
+    per_t = (time.perf_counter() - t0) / T_probe          # one spectrum of every channel in the round
     T_s = int(max(1, min(wl.T, budget_s / max(per_t, 1e-9))))
+    if T_s == wl.T:                                       # whole integrations fit: add channel rounds
+        rounds = int(max(1, min(wl.C // C_s, budget_s / max(per_t * wl.T, 1e-9))))
+        C_s = min(wl.C, C_s * rounds)
+    chans = list(range(C_s))
     sub = _sub_workload(wl, chans, T_s)
     t0 = time.perf_counter()
     oracle.workload_image(sub)
