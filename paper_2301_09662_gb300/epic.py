@@ -104,6 +104,14 @@ def load():
     return L
 
 
+def _stream_handle(stream):
+    """cudaStream_t of a torch stream, a raw handle, or torch's current stream (None)."""
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
 def strerror(code: int) -> str:
     return load().epic_strerror(code).decode()
 
@@ -160,10 +168,7 @@ class Plan:
         return self._h.value
 
     def _stream(self, stream):
-        import torch
-        if stream is None:
-            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-        return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        return _stream_handle(stream)
 
     def _check_inputs(self, v, gains, device: bool):
         import torch
@@ -360,7 +365,7 @@ class Search:
         if out is None:
             out = torch.empty((self.n_dm, self.t_out, self.n_pix), dtype=torch.float32, device=cube.device)
         rc = load().epic_dedisperse(self._h, cube.data_ptr(), int(ts), int(cs), int(ps), out.data_ptr(),
-                                    Plan._stream(None, stream))
+                                    _stream_handle(stream))
         _check(rc, "epic_dedisperse")
         return out
 
@@ -378,7 +383,7 @@ class Search:
         n = torch.empty(1, dtype=torch.int32, device=dev)
         rc = load().epic_single_pulse(self._h, dd.data_ptr(), float(threshold), snr.data_ptr(), bt.data_ptr(),
                                       bw.data_ptr(), cand.data_ptr(), int(cand_cap), n.data_ptr(),
-                                      Plan._stream(None, stream))
+                                      _stream_handle(stream))
         _check(rc, "epic_single_pulse")
         return snr, bt, bw, cand, n
 
