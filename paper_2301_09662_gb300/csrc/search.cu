@@ -14,10 +14,11 @@
 //    serves DM grids too coarse for the staging buffer.  The cube is read
 //    through (time, channel, pixel) strides, so the Stokes-I slot of an image
 //    series (complex64 layout) is searched in place;
-//  * single_pulse_kernel: one thread per (DM, pixel) light curve: mean and
-//    standard deviation (one blocked FP32 pass), then the prefix sums of x - mu in
-//    registers, 32 samples at a time, give every boxcar of width 2^k <= 32 by
-//    one difference; the best S/N, its start and width are kept;
+//  * curve_stats_kernel + single_pulse_kernel: one thread per (DM, pixel) light
+//    curve: mean and standard deviation in one blocked FP32 pass (a low-register
+//    kernel of its own), then running window sums of x - mu for every boxcar
+//    width 2^k <= 32 (the previous 32 samples in registers); the best S/N, its
+//    start and width are kept;
 //  * candidates_kernel: one block compacts the (DM, pixel) pairs whose best S/N
 //    reaches the threshold, in index order (deterministic).
 #include <algorithm>
@@ -31,6 +32,7 @@ struct epic_search_s {
     int C = 0, n_dm = 0, npix = 0, T = 0, T_out = 0, smax = 0;
     unsigned widths = 0;          // bit k: boxcar width 2^k (k < 6)
     int *d_shift = nullptr;       // [n_dm][C]
+    float2 *d_stats = nullptr;    // [n_dm][npix] mean, standard deviation of each light curve
     bool staged = true;           // every block's sweep spread fits the staging buffer
 };
 
@@ -165,23 +167,22 @@ __device__ __forceinline__ void keep_best(float s, int t, int w, float &bs, int 
     }
 }
 
-__global__ void __launch_bounds__(128)
-single_pulse_kernel(const float *__restrict__ dd, int T_out, int npix, int n_dm, unsigned widths,
-                    float *__restrict__ best_snr, int *__restrict__ best_t, int *__restrict__ best_w)
+// Mean and population standard deviation of every (DM, pixel) light curve, one
+// shifted pass (x - x_0, x_0 the first sample, keeps the two sums small),
+// summed in blocks of 16.  Few registers, so many warps hide the loads.
+__global__ void __launch_bounds__(256)
+curve_stats_kernel(const float *__restrict__ dd, int T_out, int npix, int n_dm, float2 *__restrict__ stats)
 {
     const int pix = blockIdx.x * blockDim.x + threadIdx.x, d = blockIdx.y;
     if (pix >= npix || d >= n_dm) return;
     const float *x = dd + static_cast<size_t>(d) * T_out * npix + pix;
-    auto at = [&](int t) { return __ldg(x + static_cast<size_t>(t) * npix); };
-    // mean and population standard deviation in one pass over x - x_0 (x_0 the
-    // first sample keeps the two sums small), summed in blocks of 16
-    const float x0 = at(0);
+    const float x0 = __ldg(x);
     float s1 = 0.f, s2 = 0.f;
     for (int t0 = 0; t0 < T_out; t0 += 16) {
         float b1 = 0.f, b2 = 0.f;
 #pragma unroll
         for (int k = 0; k < 16; k++) {
-            const float y = t0 + k < T_out ? at(t0 + k) - x0 : 0.f;
+            const float y = t0 + k < T_out ? __ldg(x + static_cast<size_t>(t0 + k) * npix) - x0 : 0.f;
             b1 += y;
             b2 = fmaf(y, y, b2);
         }
@@ -189,8 +190,23 @@ single_pulse_kernel(const float *__restrict__ dd, int T_out, int npix, int n_dm,
         s2 += b2;
     }
     const float m1 = s1 / static_cast<float>(T_out);
-    const float mu = x0 + m1;
-    const float sigma = sqrtf(fmaxf(s2 / static_cast<float>(T_out) - m1 * m1, 0.f));
+    stats[static_cast<size_t>(d) * npix + pix] =
+        make_float2(x0 + m1, sqrtf(fmaxf(s2 / static_cast<float>(T_out) - m1 * m1, 0.f)));
+}
+
+// Boxcar search of every light curve: y = x - mu streamed 32 samples at a time;
+// for each width w = 2^k the running window sum S_w gains y_e and drops y_{e-w}
+// (the previous 32 samples stay in registers), and S_w / (sigma sqrt(w)) is the
+// S/N of the window starting at e - w + 1.
+__global__ void __launch_bounds__(128)
+single_pulse_kernel(const float *__restrict__ dd, const float2 *__restrict__ stats, int T_out, int npix, int n_dm,
+                    unsigned widths, float *__restrict__ best_snr, int *__restrict__ best_t, int *__restrict__ best_w)
+{
+    const int pix = blockIdx.x * blockDim.x + threadIdx.x, d = blockIdx.y;
+    if (pix >= npix || d >= n_dm) return;
+    const float *x = dd + static_cast<size_t>(d) * T_out * npix + pix;
+    const float2 ms = stats[static_cast<size_t>(d) * npix + pix];
+    const float mu = ms.x, sigma = ms.y;
     int wmin = 0;
     while (wmin < 6 && !((widths >> wmin) & 1u)) wmin++;
     float bs = -INFINITY;
@@ -198,39 +214,33 @@ single_pulse_kernel(const float *__restrict__ dd, int T_out, int npix, int n_dm,
     if (!(sigma > 0.f)) {
         bs = 0.f;
     } else {
-        float inv[6];
+        float inv[6], S[6];
 #pragma unroll
-        for (int k = 0; k < 6; k++) inv[k] = 1.f / (sigma * sqrtf(static_cast<float>(1 << k)));
-        // P[i] = sum_{t < i} (x_t - mu).  Chunk q: cur[j] = P[32 q + j] (j <= 32),
-        // nxt[j] = P[32 q + 33 + j] (j < 32); a window (t, w) is P[t + w] - P[t].
-        float cur[33], nxt[32];
-        cur[0] = 0.f;
+        for (int k = 0; k < 6; k++) {
+            inv[k] = 1.f / (sigma * sqrtf(static_cast<float>(1 << k)));
+            S[k] = 0.f;
+        }
+        float prev[32], cur[32];
 #pragma unroll
-        for (int j = 0; j < 32; j++) cur[j + 1] = cur[j] + (j < T_out ? at(j) - mu : 0.f);
-        for (int q = 0; 32 * q < T_out; q++) {
-            const int base = 32 * q;
-            float run = cur[32];
+        for (int j = 0; j < 32; j++) prev[j] = 0.f;
+        for (int base = 0; base < T_out; base += 32) {
 #pragma unroll
-            for (int j = 0; j < 32; j++) {
-                const int t = base + 32 + j;
-                run += (t < T_out) ? at(t) - mu : 0.f;
-                nxt[j] = run;
-            }
+            for (int j = 0; j < 32; j++)
+                cur[j] = base + j < T_out ? __ldg(x + static_cast<size_t>(base + j) * npix) - mu : 0.f;
 #pragma unroll
             for (int j = 0; j < 32; j++) {
-                const int t = base + j;
+                const int e = base + j;
 #pragma unroll
                 for (int k = 0; k < 6; k++) {
                     const int w = 1 << k;
-                    if (!((widths >> k) & 1u) || t + w > T_out) continue;
-                    const float pe = (j + w <= 32) ? cur[j + w] : nxt[j + w - 33];
-                    keep_best((pe - cur[j]) * inv[k], t, w, bs, bt, bw);
+                    const float old = j - w >= 0 ? cur[j - w] : prev[32 + j - w];
+                    S[k] += cur[j] - old;
+                    if (((widths >> k) & 1u) && e >= w - 1 && e < T_out)
+                        keep_best(S[k] * inv[k], e - w + 1, w, bs, bt, bw);
                 }
             }
-            const float c32 = cur[32];
 #pragma unroll
-            for (int j = 0; j < 32; j++) cur[j + 1] = nxt[j];
-            cur[0] = c32;
+            for (int j = 0; j < 32; j++) prev[j] = cur[j];
         }
     }
     const size_t o = static_cast<size_t>(d) * npix + pix;
@@ -332,6 +342,11 @@ int epic_search_plan(epic_search_t *out, const double *freq_hz, int n_chan, doub
         delete s;
         return EPIC_ERR_CUDA;
     }
+    if (cudaMalloc(&s->d_stats, sizeof(float2) * static_cast<size_t>(n_dm) * n_pix) != cudaSuccess) {
+        cudaFree(s->d_shift);
+        delete s;
+        return EPIC_ERR_NOMEM;
+    }
     *out = s;
     return EPIC_OK;
 }
@@ -375,9 +390,12 @@ int epic_single_pulse(epic_search_t s, const float *dd, float threshold, float *
     if (!s || !dd || !best_snr || !best_t || !best_w || cand_cap < 0 || (cand_cap > 0 && !cand) || !n_cand)
         return EPIC_ERR_ARG;
     auto st = static_cast<cudaStream_t>(stream);
+    epic::curve_stats_kernel<<<dim3(static_cast<unsigned>((s->npix + 255) / 256), static_cast<unsigned>(s->n_dm)),
+                                256, 0, st>>>(dd, s->T_out, s->npix, s->n_dm, s->d_stats);
+    if (cudaGetLastError() != cudaSuccess) return EPIC_ERR_CUDA;
     const dim3 grid(static_cast<unsigned>((s->npix + 127) / 128), static_cast<unsigned>(s->n_dm));
-    epic::single_pulse_kernel<<<grid, 128, 0, st>>>(dd, s->T_out, s->npix, s->n_dm, s->widths, best_snr, best_t,
-                                                     best_w);
+    epic::single_pulse_kernel<<<grid, 128, 0, st>>>(dd, s->d_stats, s->T_out, s->npix, s->n_dm, s->widths, best_snr,
+                                                     best_t, best_w);
     if (cudaGetLastError() != cudaSuccess) return EPIC_ERR_CUDA;
     epic::candidates_kernel<<<1, 1024, 0, st>>>(best_snr, s->n_dm * s->npix, threshold,
                                                 reinterpret_cast<int2 *>(cand), cand_cap, s->npix, n_cand);
@@ -388,6 +406,7 @@ void epic_search_destroy(epic_search_t s)
 {
     if (!s) return;
     cudaFree(s->d_shift);
+    cudaFree(s->d_stats);
     delete s;
 }
 
