@@ -337,6 +337,27 @@ def time_variants(wl, v, g, out, flush, args, stream):
     return res
 
 
+def time_calibration(plan, wl, v, flush, args, stream):
+    """epic_solve_gains on the same integration (2 iterations, one calibrator
+    direction), timed per call on the device like the imaging step."""
+    import torch
+    for _ in range(max(args.warmup, 1)):
+        plan.solve_gains(v, 0.3, -0.2, 2)
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.solve_gains(v, 0.3, -0.2, 2)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = sum(ms) / len(ms)
+    return {"what": "epic_solve_gains, 2 iterations, all channels and polarisations of the integration",
+            "ms": t, "value": wl.spectra / (t / 1e3), "unit": UNIT}
+
+
 def time_search(flush, args, stream):
     """De-dispersion + single-pulse search of an image cube shaped like the
     deployed system's output (64 x 64 pixels, 72 channels of 25 kHz at 42 MHz,
@@ -531,6 +552,7 @@ def run_ours(args):
     if not args.no_variants:
         line["variants"] = time_variants(wl, v, g, out, flush, args, stream)
         line["search"] = time_search(flush, args, stream)
+        line["calibration"] = time_calibration(plan, wl, v, flush, args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     if rank == 0:

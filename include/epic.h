@@ -290,6 +290,38 @@ int epic_image_static(const double *ant_xy_m, int n_ant, int n_pol,
                       const uint8_t *ci4, const float *gains_c64, int n_spectra,
                       unsigned flags, float *out_c64, void *cuda_stream);
 
+/*
+ * epic_solve_gains -- per-antenna complex gains from one calibrator, in the
+ * E-field domain (the feedback calibration Sec. 1 cites for EPIC; Sec. 5 lists
+ * real-time calibration as future work; the paper gives no algorithm, this is
+ * a single-calibrator solver in that spirit).
+ *
+ * For each channel c and polarisation p, from unit gains, n_iter times:
+ *   E(t) = (1/A) sum_a g_a e_a(t) conj(phi_a)           beamformed calibrator field
+ *   g_a  = phi_a sum_t E(t) conj(e_a(t)) / sum_t |e_a(t)|^2   (0 if e_a is all zero)
+ *   antenna 0's phase set to 0, the RMS of |g_a| set to 1
+ * with phi_a = exp(-2 pi i (kx_a lx + ky_a ly) / N_c), (lx, ly) = (l N_c du,
+ * m N_c du): the phase the calibrator at direction cosines (l, m) puts on the
+ * antenna's cell (it then appears at +(lx, ly) in epic_image's output).  The
+ * result is what epic_image's gains_c64 expects (g multiplies e) up to one
+ * complex factor per (channel, polarisation), which a single calibrator of
+ * unknown flux cannot fix.  The start needs the unit-gain beam to see the
+ * calibrator: if the instrumental gains sum to zero, E vanishes and the gains
+ * come out zero.
+ *
+ *   ci4         device uint8 [n_spectra][n_chan][n_ant][n_pol], 1 <= n_spectra <= max_spectra
+ *   l, m        calibrator direction cosines
+ *   n_iter      1 .. 64 (one iteration suffices when one source dominates)
+ *   gains_out   device complex64 [n_chan][n_ant][n_pol], overwritten
+ *
+ * FP32 sums, exact integer |e|^2 sums; one CTA per (channel, polarisation).
+ * Asynchronous on the stream; allocates nothing.  EPIC_ERR_ARG for null
+ * pointers or out-of-range arguments, EPIC_ERR_TOO_LARGE when the per-CTA
+ * shared memory (8 n_spectra + 20 n_ant bytes) exceeds 200 KB.
+ */
+int epic_solve_gains(epic_plan_t plan, const uint8_t *ci4, int n_spectra, double l, double m,
+                     int n_iter, float *gains_out, void *cuda_stream);
+
 /* ------------------------------------------------------------------------
  * Transient search on the image cube (Sec. 4: per-channel light curves from
  * the images, the dispersive delay corrected across the band, a single-pulse

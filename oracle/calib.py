@@ -18,6 +18,11 @@ spirit (the readings are in the design notes):
   g_a        <- sum_t E(t) phi_a conj(e_a(t)) / sum_t |e_a(t)|^2
                 (least squares g_a e_a(t) ~ E(t) phi_a; 0 when e_a is all zero)
   normalise   antenna 0's phase to 0 (when g_0 != 0), then the RMS |g| to 1
+
+The iteration needs the unit-gain beam to see the calibrator: when the
+instrumental gains sum to zero, E vanishes and the exact update is g = 0 (in
+floating point the phases' rounding leaves a residue that the normalisation
+would blow up, so callers avoid that degenerate case).
 """
 from __future__ import annotations
 

@@ -71,6 +71,7 @@ struct epic_plan_s {
     int *d_autoint = nullptr;          // [C][A][4] exact integer auto sums
     int *d_status = nullptr;           // sticky device status word
     double f_ref = 0;                  // delay phases: reference frequency (mid-band, Hz)
+    double du = 0.5;                   // grid cell size in wavelengths
     float *d_dfreq = nullptr;          // [C] f_c - f_ref (Hz)
     float4 *d_dtab = nullptr;          // [max_spectra][A] (frac(f_ref tau), tau_hi, tau_lo, 0) of the current call
     const double *delays = nullptr;    // device [T][A] geometric delays (s) of the current call, or null

@@ -379,6 +379,7 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     const float unit_tap[2] = {1.f, 0.f};
     p->max_spectra = max_spectra;
     p->precision = precision;
+    p->du = du;
     p->flags = flags;
     p->grid_n.assign(grid_n, grid_n + n_chan);
     p->out_off.resize(n_chan);

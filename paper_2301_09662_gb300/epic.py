@@ -39,7 +39,7 @@ STOKES = ("I", "Q", "U", "V")
 PRODUCTS = ("XX", "YY", "XY", "YX")
 
 #: every symbol include/epic.h declares
-EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_autotune", "epic_image_host", "epic_out_floats", "epic_status",
+EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_autotune", "epic_solve_gains", "epic_image_host", "epic_out_floats", "epic_status",
            "epic_set_profiling", "epic_stage_times", "epic_image_static", "epic_image_series", "epic_destroy",
            "epic_strerror", "epic_search_plan", "epic_search_info", "epic_dedisperse", "epic_single_pulse",
            "epic_search_destroy")
@@ -75,6 +75,8 @@ def load():
     L.epic_image_ex.restype = i
     L.epic_autotune.argtypes = [vp, i, vp]
     L.epic_autotune.restype = i
+    L.epic_solve_gains.argtypes = [vp, vp, i, ctypes.c_double, ctypes.c_double, i, vp, vp]
+    L.epic_solve_gains.restype = i
     L.epic_out_floats.argtypes = [vp]
     L.epic_out_floats.restype = ctypes.c_size_t
     L.epic_status.argtypes = [vp]
@@ -215,6 +217,18 @@ class Plan:
         """Time a few launch shapes per channel group for n_spectra and keep the
         fastest (epic_autotune); blocks until done."""
         _check(load().epic_autotune(self._h, int(n_spectra), self._stream(stream)), "epic_autotune")
+
+    def solve_gains(self, v, l, m, n_iter=2, out=None, stream=None):
+        """Per-antenna gains from one calibrator at direction cosines (l, m)
+        (epic_solve_gains); returns a complex64 device tensor [C][A][P]."""
+        import torch
+        self._check_inputs(v, None, device=True)
+        if out is None:
+            out = torch.empty((self.C, self.A, self.P), dtype=torch.complex64, device=v.device)
+        rc = load().epic_solve_gains(self._h, v.data_ptr(), int(v.shape[0]), float(l), float(m), int(n_iter),
+                                     out.data_ptr(), self._stream(stream))
+        _check(rc, "epic_solve_gains")
+        return out
 
     def image_series(self, v, spectra_per_image, gains=None, out=None, stream=None):
         """Time-resolved images: one image per block of spectra_per_image spectra

