@@ -171,6 +171,16 @@ int epic_image(epic_plan_t plan, const uint8_t *ci4, const float *gains_c64,
 int epic_autotune(epic_plan_t plan, int n_spectra, void *cuda_stream);
 
 /*
+ * epic_image_series_ex -- epic_image_series with the geometric-delay correction
+ * of epic_image_ex: delays_s is device double [n_spectra][n_ant] (seconds),
+ * indexed like the voltages; NULL = no correction (identical to
+ * epic_image_series).  Same errors and behaviour as epic_image_series.
+ */
+int epic_image_series_ex(epic_plan_t plan, const uint8_t *ci4, const float *gains_c64,
+                         const double *delays_s, int n_spectra, int spectra_per_image,
+                         float *out_c64, void *cuda_stream);
+
+/*
  * epic_image_ex -- epic_image with the geometric-delay correction of Sec. 2.2
  * (the delay-correction block that compensates each antenna's geometric delay
  * at every time step, for every channel, before gridding).  Each calibrated

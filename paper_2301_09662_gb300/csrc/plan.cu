@@ -683,8 +683,8 @@ int epic_autotune(epic_plan_t plan, int n_spectra, void *stream)
     return rc;
 }
 
-int epic_image_series(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra, int spi, float *out,
-                      void *stream)
+int epic_image_series_ex(epic_plan_t plan, const uint8_t *ci4, const float *gains, const double *delays_s,
+                         int n_spectra, int spi, float *out, void *stream)
 {
     if (!plan || !out || spi < 1) return EPIC_ERR_ARG;
     if (n_spectra < 0 || n_spectra > plan->max_spectra || n_spectra % spi != 0) return EPIC_ERR_ARG;
@@ -702,6 +702,9 @@ int epic_image_series(epic_plan_t plan, const uint8_t *ci4, const float *gains, 
         const uint8_t *vb = ci4 + static_cast<size_t>(i0) * spi * row_bytes;
         float2 *ob = out2 + static_cast<size_t>(i0) * (img_floats / 2);
         if (!(plan->flags & EPIC_NO_AUTOSUB)) rc = epic::launch_autopower_series(plan, vb, spi, b, s);
+        // the batch's delays, time-indexed from the batch's first spectrum like its voltages
+        plan->delays = delays_s ? delays_s + static_cast<size_t>(i0) * spi * plan->A : nullptr;
+        if (rc == EPIC_OK && plan->delays) rc = epic::launch_delay_prep(plan, spi * b, s);
         plan->force_tau = b;   // one time chunk per image
         for (const auto &g : plan->groups) {
             if (rc != EPIC_OK) break;
@@ -710,8 +713,15 @@ int epic_image_series(epic_plan_t plan, const uint8_t *ci4, const float *gains, 
             if (rc == EPIC_OK) rc = epic::launch_epilogue_series(plan, g, g2, spi, b, ob, s);
         }
         plan->force_tau = 0;
+        plan->delays = nullptr;
     }
     return rc;
+}
+
+int epic_image_series(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra, int spi, float *out,
+                      void *stream)
+{
+    return epic_image_series_ex(plan, ci4, gains, nullptr, n_spectra, spi, out, stream);
 }
 
 int epic_image_host(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra,

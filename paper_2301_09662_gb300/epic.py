@@ -39,7 +39,7 @@ STOKES = ("I", "Q", "U", "V")
 PRODUCTS = ("XX", "YY", "XY", "YX")
 
 #: every symbol include/epic.h declares
-EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_autotune", "epic_solve_gains", "epic_image_host", "epic_out_floats", "epic_status",
+EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_autotune", "epic_solve_gains", "epic_image_series_ex", "epic_image_host", "epic_out_floats", "epic_status",
            "epic_set_profiling", "epic_stage_times", "epic_image_static", "epic_image_series", "epic_destroy",
            "epic_strerror", "epic_search_plan", "epic_search_info", "epic_dedisperse", "epic_single_pulse",
            "epic_search_destroy")
@@ -77,6 +77,8 @@ def load():
     L.epic_autotune.restype = i
     L.epic_solve_gains.argtypes = [vp, vp, i, ctypes.c_double, ctypes.c_double, i, vp, vp]
     L.epic_solve_gains.restype = i
+    L.epic_image_series_ex.argtypes = [vp, vp, vp, vp, i, i, vp, vp]
+    L.epic_image_series_ex.restype = i
     L.epic_out_floats.argtypes = [vp]
     L.epic_out_floats.restype = ctypes.c_size_t
     L.epic_status.argtypes = [vp]
@@ -230,20 +232,26 @@ class Plan:
         _check(rc, "epic_solve_gains")
         return out
 
-    def image_series(self, v, spectra_per_image, gains=None, out=None, stream=None):
+    def image_series(self, v, spectra_per_image, gains=None, out=None, stream=None, delays=None):
         """Time-resolved images: one image per block of spectra_per_image spectra
-        (epic_image_series); returns a [n_img, out_floats/2] complex64 tensor."""
+        (epic_image_series, or epic_image_series_ex with [T][A] float64 device
+        delays); returns a [n_img, out_floats/2] complex64 tensor."""
         import torch
         self._check_inputs(v, gains, device=True)
         T = int(v.shape[0])
         if spectra_per_image < 1 or T % spectra_per_image:
             raise ValueError("n_spectra must be a positive multiple of spectra_per_image")
+        if delays is not None and (not isinstance(delays, torch.Tensor) or delays.dtype != torch.float64
+                                   or not delays.is_cuda or tuple(delays.shape) != (T, self.A)
+                                   or not delays.is_contiguous()):
+            raise ValueError(f"delays must be a contiguous float64 CUDA tensor [{T}][{self.A}]")
         n_img = T // spectra_per_image
         if out is None:
             out = torch.empty((n_img, self.out_floats // 2), dtype=torch.complex64, device=v.device)
-        rc = load().epic_image_series(self._h, v.data_ptr(), gains.data_ptr() if gains is not None else None, T,
-                                      int(spectra_per_image), out.data_ptr(), self._stream(stream))
-        _check(rc, "epic_image_series")
+        rc = load().epic_image_series_ex(self._h, v.data_ptr(), gains.data_ptr() if gains is not None else None,
+                                         delays.data_ptr() if delays is not None else None, T,
+                                         int(spectra_per_image), out.data_ptr(), self._stream(stream))
+        _check(rc, "epic_image_series_ex")
         return out
 
     def image_host(self, v, gains=None, out=None, stream=None):

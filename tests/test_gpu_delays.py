@@ -106,3 +106,22 @@ def test_delays_shape_checked_on_host():
         p.image(v, g, delays=torch.zeros(4, 7, dtype=torch.float64, device="cuda"))
     with pytest.raises(ValueError):
         p.image(v, g, delays=torch.zeros(4, 8, dtype=torch.float32, device="cuda"))
+
+
+def test_series_with_delays_equals_blockwise_delay_images():
+    """epic_image_series_ex: each image equals epic_image_ex of its own block of
+    spectra with that block's delays (delays indexed like the voltages, across
+    series batches)."""
+    import torch
+    wl = synth.random_small(A=32, P=2, C=2, T=4 * 70, N=128, K=5, seed=1190)
+    tau = synth.geometric_delays(wl.ant_xy, wl.T, dl=2e-3, dm=-1e-3)
+    p = epic.Plan.from_workload(wl)
+    v, g = torch_inputs(wl)
+    d = torch.from_numpy(tau).cuda()
+    series = p.image_series(v, 4, g, delays=d).cpu().numpy()
+    torch.cuda.synchronize()
+    assert p.status() == epic.EPIC_OK
+    for k in (0, 33, 69):
+        blk = p.image(v[4 * k:4 * k + 4].contiguous(), g, delays=d[4 * k:4 * k + 4].contiguous()).cpu().numpy()
+        ref = np.max(np.abs(blk))
+        assert np.max(np.abs(series[k] - blk)) < 1e-5 * ref

@@ -79,6 +79,7 @@ def test_null_handles_are_rejected(lib):
     assert lib.epic_image_host(None, None, None, 0, None, None) == epic.EPIC_ERR_ARG
     assert lib.epic_image_ex(None, None, None, None, 0, None, None) == epic.EPIC_ERR_ARG
     assert lib.epic_autotune(None, 1, None) == epic.EPIC_ERR_ARG
+    assert lib.epic_image_series_ex(None, None, None, None, 0, 1, None, None) == epic.EPIC_ERR_ARG
     assert lib.epic_solve_gains(None, None, 1, 0.0, 0.0, 1, None, None) == epic.EPIC_ERR_ARG
     assert lib.epic_status(None) == epic.EPIC_ERR_ARG
     assert lib.epic_out_floats(None) == 0
