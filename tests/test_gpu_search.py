@@ -42,6 +42,60 @@ def test_dedisperse_parity_ragged():
     assert np.max(np.abs(dd - ref)) <= 1e-5 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("grid", ["fine", "coarse", "unsorted"])
+def test_dedisperse_forms_agree_bitwise(grid, monkeypatch):
+    """The 32- and 16-trial staged blocks and the direct form sum every sweep in
+    channel order, so they agree bit for bit; all match the oracle.  'fine'
+    trials differ by 0 or 1 sample per step (the register-shared second
+    window), 'coarse' by 1 to 3 (its own window), 'unsorted' by either sign."""
+    import torch
+    T, C, P = 300, 20, 70                           # 70 pixels: two lane blocks and a ragged third
+    f = 42.1e6 + 25e3 * np.arange(C)
+    dt = 0.04
+    dms = {"fine": np.arange(45) * 0.25, "coarse": np.arange(37) * 1.7,
+           "unsorted": np.random.default_rng(2).permutation(np.arange(45) * 0.25)}[grid]
+    sh = osearch.dm_shifts(f, dt, dms)
+    cube = _cube(T, C, P, 9)
+    ref = osearch.dedisperse(cube, sh)
+    x = torch.from_numpy(cube).cuda()
+    outs = []
+    for cap in ("32", "16", "0"):
+        monkeypatch.setenv("EPIC_SEARCH_DM_BLOCK", cap)
+        s = epic.Search(f, dt, dms, P, T)
+        outs.append(s.dedisperse(x).cpu().numpy())
+        s.close()
+    assert np.max(np.abs(outs[0] - ref)) <= 1e-5 * np.max(np.abs(ref))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("T,widths", [(20, (1, 2, 4, 8, 16, 32)), (64, (2, 8)), (97, (1, 32)), (33, (32,))])
+def test_single_pulse_lengths_and_width_sets(T, widths):
+    """Light curves shorter than one 32-sample chunk, an exact number of chunks,
+    a ragged tail, widths longer than the curve (never scored) and width subsets."""
+    import torch
+    n_dm, P = 3, 45
+    f = 42.1e6 + 25e3 * np.arange(4)
+    s = epic.Search(f, 0.04, [0.0] * n_dm, P, T, widths=widths)
+    rng = np.random.default_rng(T)
+    dd = rng.normal(50.0, 3.0, (n_dm, T, P)).astype(np.float32)
+    dd[1, T // 3:T // 3 + 3, 7] += 25.0
+    snr, bt, bw, cand, n = s.single_pulse(torch.from_numpy(dd).cuda(), threshold=4.0)
+    snr, bt, bw = snr.cpu().numpy(), bt.cpu().numpy(), bw.cpu().numpy()
+    rs, rt, rw = osearch.single_pulse(dd, widths)
+    assert np.max(np.abs(snr - rs)) < 1e-3
+    for d, p in zip(*np.nonzero((bt != rt) | (bw != rw))):
+        assert int(bw[d, p]) in widths and int(bt[d, p]) + int(bw[d, p]) <= T
+        alt = osearch.boxcar_snr(dd[d, :, p], int(bw[d, p]))[int(bt[d, p])]
+        assert abs(alt - rs[d, p]) < 1e-3
+    nc = int(n.item())
+    got = [tuple(x) for x in cand[:nc].cpu().numpy().tolist()]
+    assert got == sorted(got)
+    sure = {(int(d), int(p)) for d, p in zip(*np.nonzero(rs >= 4.0 + 1e-3))}
+    maybe = {(int(d), int(p)) for d, p in zip(*np.nonzero(rs >= 4.0 - 1e-3))}
+    assert sure <= set(got) <= maybe
+    s.close()
+
+
 def test_dedisperse_strided_stokes_series_layout():
     """I in the real part of slot 0 of a complex64 [T][C][4][P] series is searched in place."""
     import torch
