@@ -372,6 +372,9 @@ int epic_search_info(epic_search_t s, int *t_out, int *max_shift);
  *   dd         device float [n_dm][t_out][n_pix], overwritten
  *
  * FP32 sums in channel order.  Asynchronous on the stream; allocates nothing.
+ * With unit pixel stride and row pitches that are multiples of 4 floats (a
+ * 16-byte aligned cube) the rows are fetched by tensor-memory-access copies
+ * whose waits are bounded; see epic_search_status.
  */
 int epic_dedisperse(epic_search_t s, const float *cube, long long t_stride, long long c_stride,
                     long long pix_stride, float *dd, void *cuda_stream);
@@ -392,6 +395,15 @@ int epic_dedisperse(epic_search_t s, const float *cube, long long t_stride, long
  */
 int epic_single_pulse(epic_search_t s, const float *dd, float threshold, float *best_snr, int *best_t,
                       int *best_w, int *cand, int cand_cap, int *n_cand, void *cuda_stream);
+
+/*
+ * epic_search_status -- synchronise the device and return the sticky
+ * device-side status of the search plan: EPIC_OK, or EPIC_ERR_TIMEOUT when a
+ * bounded wait inside epic_dedisperse ran out (that call's output is then
+ * undefined); EPIC_ERR_CUDA if the synchronisation itself failed.  Reading the
+ * status clears it.
+ */
+int epic_search_status(epic_search_t s);
 
 void epic_search_destroy(epic_search_t s);
 

@@ -1,5 +1,6 @@
 // Inline-PTX helpers for the sm_100-family tensor path: shared-memory
-// descriptors, tcgen05 MMA / TMEM, mbarriers and 1-D bulk (TMA) copies.
+// descriptors, tcgen05 MMA / TMEM, mbarriers, 1-D bulk and 3-D tiled (TMA)
+// copies.
 // Every wait is bounded by a clock budget so a lost arrival turns into an
 // error flag instead of a hang.
 #pragma once
@@ -77,6 +78,19 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+}
+
+// 3-D tiled bulk tensor copy global -> shared: the tensor map's box at
+// coordinates (x, y, z), elements outside the tensor filled with zeros;
+// completion counted on `bar`.  `map` is the generic address of a
+// __grid_constant__ CUtensorMap parameter.
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

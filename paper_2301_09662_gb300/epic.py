@@ -42,7 +42,7 @@ PRODUCTS = ("XX", "YY", "XY", "YX")
 EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_autotune", "epic_solve_gains", "epic_image_series_ex", "epic_image_host", "epic_out_floats", "epic_status",
            "epic_set_profiling", "epic_stage_times", "epic_image_static", "epic_image_series", "epic_destroy",
            "epic_strerror", "epic_search_plan", "epic_search_info", "epic_dedisperse", "epic_single_pulse",
-           "epic_search_destroy")
+           "epic_search_status", "epic_search_destroy")
 
 _lib = None
 
@@ -102,6 +102,8 @@ def load():
     L.epic_dedisperse.restype = i
     L.epic_single_pulse.argtypes = [vp, vp, ctypes.c_float, vp, vp, vp, vp, i, vp, vp]
     L.epic_single_pulse.restype = i
+    L.epic_search_status.argtypes = [vp]
+    L.epic_search_status.restype = i
     L.epic_search_destroy.argtypes = [vp]
     L.epic_search_destroy.restype = None
     _lib = L
@@ -408,6 +410,10 @@ class Search:
                                       _stream_handle(stream))
         _check(rc, "epic_single_pulse")
         return snr, bt, bw, cand, n
+
+    def status(self) -> int:
+        """Sticky device status (EPIC_OK or EPIC_ERR_TIMEOUT); reading clears it."""
+        return load().epic_search_status(self._h)
 
     def close(self):
         if self._h:

@@ -44,12 +44,14 @@ def test_dedisperse_parity_ragged():
 
 @pytest.mark.parametrize("grid", ["fine", "coarse", "unsorted"])
 def test_dedisperse_forms_agree_bitwise(grid, monkeypatch):
-    """The 32- and 16-trial staged blocks and the direct form sum every sweep in
-    channel order, so they agree bit for bit; all match the oracle.  'fine'
+    """The 32- and 16-trial staged blocks (TMA producer warp or cp.async
+    staging; two pixels per lane with packed adds, or one) and the direct form
+    sum every sweep in channel order, so they agree bit for bit; all match the
+    oracle.  'fine'
     trials differ by 0 or 1 sample per step (the register-shared second
     window), 'coarse' by 1 to 3 (its own window), 'unsorted' by either sign."""
     import torch
-    T, C, P = 300, 20, 70                           # 70 pixels: two lane blocks and a ragged third
+    T, C, P = 300, 20, 71                           # 71 pixels: ragged pixel blocks, an odd last pixel
     f = 42.1e6 + 25e3 * np.arange(C)
     dt = 0.04
     dms = {"fine": np.arange(45) * 0.25, "coarse": np.arange(37) * 1.7,
@@ -57,15 +59,48 @@ def test_dedisperse_forms_agree_bitwise(grid, monkeypatch):
     sh = osearch.dm_shifts(f, dt, dms)
     cube = _cube(T, C, P, 9)
     ref = osearch.dedisperse(cube, sh)
-    x = torch.from_numpy(cube).cuda()
+    x = torch.from_numpy(cube).cuda()                  # odd pitch: one pixel per lane
+    pad4 = np.full((T, C, P + 1), np.nan, np.float32)  # 72-float pitch: the TMA form applies
+    pad4[:, :, :P] = cube
+    x_pad4 = torch.from_numpy(pad4.reshape(-1)).cuda()
     outs = []
-    for cap in ("32", "16", "0"):
+    for cap, pix2, tma in (("32", "1", "1"), ("16", "1", "1"), ("32", "1", "0"), ("16", "1", "0"),
+                           ("32", "0", "1"), ("16", "0", "1"), ("0", "1", "1")):
         monkeypatch.setenv("EPIC_SEARCH_DM_BLOCK", cap)
+        monkeypatch.setenv("EPIC_SEARCH_PIX2", pix2)
+        monkeypatch.setenv("EPIC_SEARCH_TMA", tma)
         s = epic.Search(f, dt, dms, P, T)
+        outs.append(s.dedisperse(x_pad4, strides=(C * (P + 1), P + 1, 1)).cpu().numpy())
         outs.append(s.dedisperse(x).cpu().numpy())
+        assert s.status() == epic.EPIC_OK
         s.close()
     assert np.max(np.abs(outs[0] - ref)) <= 1e-5 * np.max(np.abs(ref))
-    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+
+
+def test_dedisperse_wait_timeout_sets_status(monkeypatch):
+    """Failure detection without a fault: the TMA form's producer withholds
+    channel 0, the consumers' bounded wait runs out, the plan's status word
+    reads EPIC_ERR_TIMEOUT, and a fresh plan on the same context is correct."""
+    import torch
+    T, C, P = 120, 12, 128
+    f, dms, dt, sh = _setup(T, C, P, n_dm=8)
+    cube = _cube(T, C, P, 12)
+    x = torch.from_numpy(cube).cuda()
+    monkeypatch.setenv("EPIC_TEST_WITHHOLD_TMA", "1")
+    s = epic.Search(f, dt, dms, P, T)
+    s.dedisperse(x)
+    assert s.status() == epic.EPIC_ERR_TIMEOUT
+    assert s.status() == epic.EPIC_OK               # reading clears it
+    s.close()
+    monkeypatch.delenv("EPIC_TEST_WITHHOLD_TMA")
+    s = epic.Search(f, dt, dms, P, T)
+    dd = s.dedisperse(x).cpu().numpy()
+    assert s.status() == epic.EPIC_OK
+    ref = osearch.dedisperse(cube, sh)
+    assert np.max(np.abs(dd - ref)) <= 1e-5 * np.max(np.abs(ref))
+    s.close()
 
 
 @pytest.mark.parametrize("T,widths", [(20, (1, 2, 4, 8, 16, 32)), (64, (2, 8)), (97, (1, 32)), (33, (32,))])

@@ -123,6 +123,7 @@ def test_search_plan_rejects_bad_arguments_on_host(lib):
     assert lib.epic_search_plan(ctypes.byref(h), P(f), 3, 0.04, P(dm), 2, 64, 20, 32) == epic.EPIC_ERR_TOO_LARGE
     assert h.value is None
     assert lib.epic_search_info(None, None, None) == epic.EPIC_ERR_ARG
+    assert lib.epic_search_status(None) == epic.EPIC_ERR_ARG
     assert lib.epic_dedisperse(None, None, 1, 1, 1, None, None) == epic.EPIC_ERR_ARG
     assert lib.epic_single_pulse(None, None, 0.0, None, None, None, None, 0, None, None) == epic.EPIC_ERR_ARG
     lib.epic_search_destroy(None)
