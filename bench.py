@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 256 << 20
 # lwa: one full 64-channel launch captured: 34 701 824 B read (the 32.8 MB ci4
 # input plus tables) + 108 019 968 B written (time-chunk partial sums that spill
 # out of L2 before the epilogue reads them).
-NCU_TRAFFIC = {"lwa": (142_721_792, "c553ae1039c2988c")}
+NCU_TRAFFIC = {"lwa": (108_820_480, "23f8b65041a4140c")}
 
 
 def parse():

@@ -31,6 +31,49 @@ __device__ __forceinline__ float2 delay_phase(float4 d, float df)
 }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
+// Packed FP32 pairs: one instruction performs the operation on both lanes of a
+// float2 (each an IEEE round-to-nearest operation, the same result as the
+// scalar one).  The float2 halves already sit in a register pair, so packing
+// costs no moves; pswap (a lane exchange) does.
+__device__ __forceinline__ unsigned long long p_pack(float2 a)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 p_unpack(unsigned long long r)
+{
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ float2 padd(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(p_pack(a)), "l"(p_pack(b)));
+    return p_unpack(r);
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(p_pack(a)), "l"(p_pack(b)));
+    return p_unpack(r);
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(p_pack(a)), "l"(p_pack(b)));
+    return p_unpack(r);
+}
+// lane-wise a * b + c, one rounding per lane
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(p_pack(a)), "l"(p_pack(b)), "l"(p_pack(c)));
+    return p_unpack(r);
+}
+__device__ __forceinline__ float2 pswap(float2 a) { return make_float2(a.y, a.x); }
+
 constexpr float kSqrtHalf = 0.70710678118654752440f;
 constexpr float kSin60 = 0.86602540378443864676f;
 
@@ -69,6 +112,42 @@ __device__ __forceinline__ void dft8(float2 *x)
     x[6] = csub(e[2], o2);
     x[3] = cadd(e[3], o3);
     x[7] = csub(e[3], o3);
+}
+
+// dft4 and dft8 in packed pairs.  Multiplying by +-i is a lane exchange and an
+// FMA with a (-1, +1) or (+1, -1) pair, exact like the scalar add it replaces;
+// the w8 twiddles fold sqrt(1/2) into the final FMA (one rounding fewer than
+// the scalar form).
+__device__ __forceinline__ void dft4p(float2 *x)
+{
+    const float2 NP = make_float2(-1.f, 1.f), PN = make_float2(1.f, -1.f);
+    const float2 s02 = padd(x[0], x[2]), d02 = psub(x[0], x[2]);
+    const float2 s13 = padd(x[1], x[3]), u = pswap(psub(x[1], x[3]));
+    x[0] = padd(s02, s13);
+    x[2] = psub(s02, s13);
+    x[1] = pfma(u, NP, d02);          // d02 + i (x1 - x3)
+    x[3] = pfma(u, PN, d02);          // d02 - i (x1 - x3)
+}
+
+__device__ __forceinline__ void dft8p(float2 *x)
+{
+    const float2 NP = make_float2(-1.f, 1.f), PN = make_float2(1.f, -1.f);
+    const float2 H = make_float2(kSqrtHalf, kSqrtHalf), NH = make_float2(-kSqrtHalf, -kSqrtHalf);
+    float2 e[4] = {x[0], x[2], x[4], x[6]};
+    float2 o[4] = {x[1], x[3], x[5], x[7]};
+    dft4p(e);
+    dft4p(o);
+    const float2 v1 = pfma(pswap(o[1]), NP, o[1]);   // (o.x - o.y, o.y + o.x) = w8 o / sqrt(1/2)
+    const float2 u2 = pswap(o[2]);                   // i o = (-o.y, o.x) via NP
+    const float2 v3 = pfma(pswap(o[3]), PN, o[3]);   // (o.x + o.y, o.y - o.x) = -w8^3 o / sqrt(1/2)
+    x[0] = padd(e[0], o[0]);
+    x[4] = psub(e[0], o[0]);
+    x[1] = pfma(v1, H, e[1]);
+    x[5] = pfma(v1, NH, e[1]);
+    x[2] = pfma(u2, NP, e[2]);
+    x[6] = pfma(u2, PN, e[2]);
+    x[3] = pfma(v3, NH, e[3]);
+    x[7] = pfma(v3, H, e[3]);
 }
 
 __device__ __forceinline__ void dft3(float2 *x)

@@ -64,6 +64,22 @@ constexpr Twiddle64 make_twiddle64()
 
 __constant__ const Twiddle64 c_tw64 = make_twiddle64();
 
+// The same twiddles as lane pairs for the packed form: (re, re) and (-im, im).
+struct Twiddle64p {
+    float2 rr[64], ni[64];
+};
+constexpr Twiddle64p make_twiddle64p()
+{
+    Twiddle64p t{};
+    for (int j = 0; j < 64; j++) {
+        const float2 w = ce_w64(j);
+        t.rr[j] = float2{w.x, w.x};
+        t.ni[j] = float2{-w.y, w.y};
+    }
+    return t;
+}
+__constant__ const Twiddle64p c_tw64p = make_twiddle64p();
+
 // Stage 1 in place: for each n2, DFT8 over x[n2 + 8 n1] and twiddle by w64^{n2 k1}.
 __device__ __forceinline__ void fft64_stage1(float2 (&x)[64])
 {
@@ -89,6 +105,38 @@ __device__ __forceinline__ void fft64_stage2(float2 (&x)[64], Sink &&sink)
 #pragma unroll
         for (int n2 = 0; n2 < 8; n2++) t[n2] = x[n2 + 8 * k1];
         dft8(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 8; k2++) sink(k1 + 8 * k2, t[k2]);
+    }
+}
+
+// The two stages in packed pairs (dft8p; twiddle a w = a.x (w.x, w.x) +
+// (a.y, a.x) (-w.y, w.y), one multiply and one FMA per pair).
+__device__ __forceinline__ void fft64p_stage1(float2 (&x)[64])
+{
+#pragma unroll
+    for (int n2 = 0; n2 < 8; n2++) {
+        float2 t[8];
+#pragma unroll
+        for (int n1 = 0; n1 < 8; n1++) t[n1] = x[n2 + 8 * n1];
+        dft8p(t);
+        x[n2] = t[0];
+#pragma unroll
+        for (int k1 = 1; k1 < 8; k1++)
+            x[n2 + 8 * k1] = n2 == 0 ? t[k1]
+                                     : pfma(pswap(t[k1]), c_tw64p.ni[n2 * k1], pmul(t[k1], c_tw64p.rr[n2 * k1]));
+    }
+}
+
+template <class Sink>
+__device__ __forceinline__ void fft64p_stage2(float2 (&x)[64], Sink &&sink)
+{
+#pragma unroll
+    for (int k1 = 0; k1 < 8; k1++) {
+        float2 t[8];
+#pragma unroll
+        for (int n2 = 0; n2 < 8; n2++) t[n2] = x[n2 + 8 * k1];
+        dft8p(t);
 #pragma unroll
         for (int k2 = 0; k2 < 8; k2++) sink(k1 + 8 * k2, t[k2]);
     }

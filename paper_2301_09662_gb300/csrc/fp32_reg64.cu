@@ -12,7 +12,9 @@
 //  * the 64-point transforms run in registers (one row or column per thread),
 //    so each axis costs one shared-memory read and one write;
 //  * two time samples per iteration share the schedule, the twiddles and the
-//    synchronisation.
+//    synchronisation;
+//  * the transforms and the gridding multiply-adds run on packed FP32 pairs
+//    (add/sub/mul/fma .f32x2: one instruction for both lanes of a float2).
 #include <type_traits>
 
 #include "epic_internal.cuh"
@@ -154,26 +156,27 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 const int dyi = static_cast<int>((d >> 12) & 0xFu);
                 const int y = static_cast<int>((d >> 16) & 0x3Fu);
                 const int x0 = static_cast<int>((d >> 22) & 0x3Fu);
-                float2 e[TS][P];
+                float2 e[TS][P], eswap[TS][P];
 #pragma unroll
                 for (int ts = 0; ts < TS; ts++)
 #pragma unroll
-                    for (int p = 0; p < P; p++) e[ts][p] = es[ts * AP + a * P + p];
+                    for (int p = 0; p < P; p++) {
+                        e[ts][p] = es[ts * AP + a * P + p];
+                        eswap[ts][p] = pswap(e[ts][p]);
+                    }
                 const float2 *wrow = tapw + (nker > 1 ? a * KK : 0) + dyi * K;
 #pragma unroll
                 for (int dx = 0; dx < (KC > 0 ? KC : K); dx++) {
+                    // cell += w e as two packed FMAs: w.x (e.x, e.y) + (-w.y, w.y) (e.y, e.x)
                     const float2 w = wrow[dx];
+                    const float2 wr = make_float2(w.x, w.x), wi = make_float2(-w.y, w.y);
                     const int x = (x0 + dx) & (M64 - 1);
 #pragma unroll
                     for (int ts = 0; ts < TS; ts++)
 #pragma unroll
                         for (int p = 0; p < P; p++) {
                             float2 *cell = G + (ts * P + p) * BUF + y * S64 + x;
-                            const float2 cv = cmul(w, e[ts][p]);
-                            float2 old = *cell;
-                            old.x += cv.x;
-                            old.y += cv.y;
-                            *cell = old;
+                            *cell = pfma(wi, eswap[ts][p], pfma(wr, e[ts][p], *cell));
                         }
                 }
             }
@@ -188,8 +191,8 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             float2 x[64];
 #pragma unroll
             for (int i = 0; i < 64; i++) x[i] = line[i];
-            fft64_stage1(x);
-            fft64_stage2(x, [&](int k, float2 val) { line[k] = val; });
+            fft64p_stage1(x);
+            fft64p_stage2(x, [&](int k, float2 val) { line[k] = val; });
         }
         __syncthreads();
         for (int q = tid; q < TS * P * M64; q += kThreads) {
@@ -197,8 +200,8 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             float2 x[64];
 #pragma unroll
             for (int i = 0; i < 64; i++) x[i] = col[i * S64];
-            fft64_stage1(x);
-            fft64_stage2(x, [&](int k, float2 val) { col[k * S64] = val; });
+            fft64p_stage1(x);
+            fft64p_stage2(x, [&](int k, float2 val) { col[k * S64] = val; });
         }
         __syncthreads();
 

@@ -336,16 +336,17 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
                     const int y = static_cast<int>((d >> 16) & 0x3Fu);
                     const int x0 = static_cast<int>((d >> 22) & 0x3Fu);
                     const float2 e0 = es[a * P], e1 = es[a * P + 1];
+                    const float2 e0s = pswap(e0), e1s = pswap(e1);
                     const float2 *wrow = tapw + dyi * K;
                     float2 *gy = G + y * S64;
 #pragma unroll
                     for (int dx = 0; dx < (KC > 0 ? KC : K); dx++) {
+                        // cell += w e as two packed FMAs: w.x (e.x, e.y) + (-w.y, w.y) (e.y, e.x)
                         const float2 w = wrow[dx];
+                        const float2 wr = make_float2(w.x, w.x), wi = make_float2(-w.y, w.y);
                         const int x = (x0 + dx) & (M64 - 1);
-                        const float2 v0 = cmul(w, e0), v1 = cmul(w, e1);
-                        const float2 o0 = gy[x], o1 = gy[BUF + x];
-                        gy[x] = make_float2(o0.x + v0.x, o0.y + v0.y);
-                        gy[BUF + x] = make_float2(o1.x + v1.x, o1.y + v1.y);
+                        gy[x] = pfma(wi, e0s, pfma(wr, e0, gy[x]));
+                        gy[BUF + x] = pfma(wi, e1s, pfma(wr, e1, gy[BUF + x]));
                     }
                 }
                 __syncwarp();
