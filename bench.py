@@ -44,6 +44,12 @@ L2_FLUSH_BYTES = 256 << 20
 # input plus tables) + 108 019 968 B written (time-chunk partial sums that spill
 # out of L2 before the epilogue reads them).
 NCU_TRAFFIC = {"lwa": (108_820_480, "23f8b65041a4140c")}
+# What the same ncu capture shows binds the kernel (full set, one LWA launch): shared-memory
+# wavefronts per SM cycle at the capture's clock, against 1 per cycle (128 B/clk).
+NCU_LIMITER = {"lwa": ({"unit": "shared-memory wavefronts per SM cycle", "achieved": 0.80, "peak": 1.0,
+                        "wavefronts_per_launch": 1_762_534_810, "issue_active_pct": 39.6,
+                        "fma_pipe_pct": 35.6},
+                       "23f8b65041a4140c")}
 
 
 def parse():
@@ -540,8 +546,12 @@ def run_ours(args):
     traffic = None
     rec = NCU_TRAFFIC.get(args.workload) if (args.precision == "fp32" and not args.taper
                                               and args.channels is None) else None
+    limiter = None
     if rec and rec[1] == kernel_source_hash():
         traffic = rec[0]
+        lim = NCU_LIMITER.get(args.workload)
+        if lim and lim[1] == rec[1]:
+            limiter = lim[0]
 
     config = describe(wl, args.workload)
     config["launch_shapes"] = "cost model" if args.no_autotune else "measured per channel group (epic_autotune)"
@@ -550,7 +560,7 @@ def run_ours(args):
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                 "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS)",
-                "flops_per_launch": flops, "ms_per_launch": img_ms}
+                "flops_per_launch": flops, "ms_per_launch": img_ms, "measured_limiter": limiter}
     if args.precision != "fp32":
         roofline = tensor_roofline(wl, args.precision, img_ms, peaks)
         roofline["kernel"] = f"tensor-core imaging kernel {image_stage}"

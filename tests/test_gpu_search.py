@@ -79,6 +79,39 @@ def test_dedisperse_forms_agree_bitwise(grid, monkeypatch):
         assert np.array_equal(outs[0], o)
 
 
+@pytest.mark.parametrize("T,C,P,n_dm,layout", [
+    (40, 1, 8, 1, "tcp"),        # one channel, one trial, eight pixels: the 64-pixel box overhangs
+    (12, 6, 4, 3, "tcp"),        # t_out below one 16-sample tile
+    (90, 9, 132, 37, "tcp"),     # ragged in every axis (TMA form: pitch a multiple of 4)
+    (90, 9, 130, 37, "tcp"),     # the same with an even pitch (two-pixel cp.async form)
+    (80, 7, 64, 20, "ctp"),      # channel-major cube: the time stride is the smaller one
+])
+def test_dedisperse_edge_shapes_all_forms(T, C, P, n_dm, layout, monkeypatch):
+    import torch
+    f = 42.1e6 + 25e3 * np.arange(C)
+    dms = np.linspace(0, 3, n_dm)
+    sh = osearch.dm_shifts(f, 0.04, dms)
+    cube = _cube(T, C, P, T + C + P)
+    ref = osearch.dedisperse(cube, sh)
+    if layout == "tcp":
+        x, strides = torch.from_numpy(cube).cuda(), None
+    else:
+        x = torch.from_numpy(np.ascontiguousarray(cube.transpose(1, 0, 2))).cuda()
+        strides = (P, T * P, 1)
+    outs = []
+    for cap, pix2, tma in (("16", "1", "1"), ("16", "1", "0"), ("16", "0", "1"), ("32", "1", "1"), ("0", "1", "1")):
+        monkeypatch.setenv("EPIC_SEARCH_DM_BLOCK", cap)
+        monkeypatch.setenv("EPIC_SEARCH_PIX2", pix2)
+        monkeypatch.setenv("EPIC_SEARCH_TMA", tma)
+        s = epic.Search(f, 0.04, dms, P, T, widths=(1,))
+        outs.append(s.dedisperse(x, strides=strides).cpu().numpy())
+        assert s.status() == epic.EPIC_OK
+        s.close()
+    assert np.max(np.abs(outs[0] - ref)) <= 1e-5 * np.max(np.abs(ref))
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+
+
 def test_dedisperse_wait_timeout_sets_status(monkeypatch):
     """Failure detection without a fault: the TMA form's producer withholds
     channel 0, the consumers' bounded wait runs out, the plan's status word
