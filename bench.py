@@ -35,6 +35,7 @@ if ROOT not in sys.path:
 METRIC = "imaged spectra/s (chan x time x pol)"
 UNIT = "spectra/s"
 FP32_LANES_PER_SM = 128
+SERIES_SPI = 40                      # spectra per image of the time-resolved variant (1.6 ms at 25 k spectra/s)
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM traffic of one launch of the dominant kernel from an ncu capture
@@ -284,7 +285,10 @@ def tensor_roofline(wl, form, img_ms, peaks):
 
 def time_variants(wl, v, g, out, flush, args, stream):
     """Other forms of the same integration, timed the same way (device events
-    per step, L2 flushed between steps); same output up to rounding."""
+    per step, L2 flushed between steps): the taper and tensor forms (same output
+    up to rounding), delay correction, per-antenna kernels and time-resolved
+    Stokes images."""
+    import numpy as np
     import torch
 
     from paper_2301_09662_gb300 import epic
@@ -294,7 +298,9 @@ def time_variants(wl, v, g, out, flush, args, stream):
              "tc_fp16": dict(precision=epic.EPIC_TC_FP16),
              "tc_split_bf16": dict(precision=epic.EPIC_TC_SPLIT_BF16),
              "tc_split_fp16_taper": dict(precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_KERNEL_TAPER),
-             "fp32_delays": dict()}
+             "fp32_delays": dict(),
+             "fp32_antenna_kernels": dict(flags=epic.EPIC_ANTENNA_KERNELS),
+             "fp32_series_stokes": dict(flags=epic.EPIC_STOKES)}
     notes = {"kernel_taper": "FP32; image-domain |W^|^2 taper with point gridding (exact for one shared kernel)",
              "tc_split_fp16": "row and column DFTs on tcgen05, FP16 hi+lo operands (3 MMAs per k-block), "
                               "FP32 accumulate in TMEM",
@@ -302,23 +308,44 @@ def time_variants(wl, v, g, out, flush, args, stream):
              "tc_split_bf16": "row and column DFTs on tcgen05, BF16 hi+lo operands (3 MMAs per k-block)",
              "tc_split_fp16_taper": "tc_split_fp16 with the image-domain kernel taper",
              "fp32_delays": "FP32 literal form with per-(t, antenna) geometric-delay phases (epic_image_ex; "
-                            "[T][A] FP64 delays resident in HBM, phases formed in the kernel)"}
+                            "[T][A] FP64 delays resident in HBM, phases formed in the kernel)",
+             "fp32_antenna_kernels": "FP32 literal form with a kernel per antenna (seeded Gaussians of +-20 % "
+                                     "width and a small phase gradient); auto term sum_a A_a |W_a^|^2",
+             "fp32_series_stokes": f"FP32 literal form, epic_image_series: one Stokes (I, Q, U, V) image per "
+                                   f"{SERIES_SPI} spectra ({wl.T // SERIES_SPI if wl.T % SERIES_SPI == 0 else 0} "
+                                   f"images per integration)"}
+    import copy
+
     from paper_2301_09662_gb300 import synth
     delays = torch.from_numpy(synth.geometric_delays(wl.ant_xy, wl.T)).to(v.device)
+    wl_ak = copy.copy(wl)
+    wl_ak.kernel = synth.antenna_kernels(wl.A, wl.K, np.random.default_rng(20230120))
     peaks = measured_peaks()
     for name, kw in forms.items():
+        series = name == "fp32_series_stokes"
+        if series and wl.T % SERIES_SPI:
+            res[name] = {"unavailable": f"{wl.T} spectra are not a multiple of {SERIES_SPI}"}
+            continue
         try:
-            p = epic.Plan.from_workload(wl, **kw)
-            if not args.no_autotune:
+            p = epic.Plan.from_workload(wl_ak if name == "fp32_antenna_kernels" else wl, **kw)
+            if not args.no_autotune and not series:
                 p.autotune(wl.T)
         except epic.EpicError as e:
             res[name] = {"unavailable": str(e)}
             continue
         p.set_profiling(True)
-        o = torch.empty_like(out)
+        o = torch.empty((wl.T // SERIES_SPI, out.numel()), dtype=out.dtype, device=out.device) if series \
+            else torch.empty_like(out)
         dl = delays if name == "fp32_delays" else None
+
+        def call():
+            if series:
+                p.image_series(v, SERIES_SPI, g, out=o)
+            else:
+                p.image(v, g, out=o, delays=dl)
+
         for _ in range(max(args.warmup, 1)):
-            p.image(v, g, out=o, delays=dl)
+            call()
         torch.cuda.synchronize()
         ms = []
         for k in range(args.steps):
@@ -326,15 +353,15 @@ def time_variants(wl, v, g, out, flush, args, stream):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            p.image(v, g, out=o, delays=dl)
+            call()
             b.record(stream)
             b.synchronize()
             ms.append(a.elapsed_time(b))
-        stages = p.stage_times()
+        stages = None if series else p.stage_times()   # epic_image_series runs unprofiled
         step = sum(ms) / len(ms)
         entry = {"value": wl.spectra / (step / 1e3), "unit": UNIT, "ms_per_step": step, "note": notes[name],
                  "stages_ms_last": stages}
-        if name.startswith("tc_"):
+        if name.startswith("tc_") and stages:
             img = max((v for k, v in stages.items() if k.startswith("image[")), default=None)
             if img:
                 entry["roofline"] = tensor_roofline(wl, name.replace("_taper", ""), img, peaks)
