@@ -131,19 +131,33 @@ epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N
         const int item = ci * Q + hy * Q1 + hx;
         const int px = R2 * (mx % R1) + mx / R1, py = R2 * (my % R1) + my / R1;
         const size_t pos = static_cast<size_t>(py) * M + px;
-        double s[4] = {0, 0, 0, 0};
+        // time chunks added in time order as compensated FP32 (hi, lo) pairs: TwoSum keeps
+        // hi + lo equal to the exact running sum up to the roundings of lo, far below FP32;
+        // FP64 only for the pair and the auto-term subtraction (FP64 is ~2 ops/clock/SM here)
+        float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+        auto two_sum = [](float &h, float &l, float x) {
+            const float t = h + x;
+            const float bp = t - h;
+            l += (h - (t - bp)) + (x - bp);
+            h = t;
+        };
+        const float *src0 = partial + (static_cast<size_t>(item) * (M * M) + pos) * NPF;
+        const size_t tau_stride = static_cast<size_t>(n_items) * (M * M) * NPF;
         for (int tau = 0; tau < n_tau; tau++) {
-            const float *src = partial + ((static_cast<size_t>(tau) * n_items + item) * (M * M) + pos) * NPF;
+            const float *src = src0 + tau * tau_stride;
             if constexpr (P == 2) {
-                const float4 f = *reinterpret_cast<const float4 *>(src);
-                s[0] += f.x;
-                s[1] += f.y;
-                s[2] += f.z;
-                s[3] += f.w;
+                const float4 f = __ldg(reinterpret_cast<const float4 *>(src));
+                two_sum(hi[0], lo[0], f.x);
+                two_sum(hi[1], lo[1], f.y);
+                two_sum(hi[2], lo[2], f.z);
+                two_sum(hi[3], lo[3], f.w);
             } else {
-                s[0] += src[0];
+                two_sum(hi[0], lo[0], __ldg(src));
             }
         }
+        double s[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) s[k] = static_cast<double>(hi[k]) + static_cast<double>(lo[k]);
         const double w = wpow[pix];
         if (ant_kernels) {
             if (autosub) {
