@@ -53,7 +53,9 @@ gain_solve_kernel(const uint8_t *__restrict__ v, const short2 *__restrict__ cell
     __shared__ float2 ref;
     const int c = chans[blockIdx.x / P], p = blockIdx.x % P;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    auto byte = [&](int t, int a) { return static_cast<uint32_t>(v[((static_cast<size_t>(t) * C + c) * A + a) * P + p]); };
+    auto byte = [&](int t, int a) {
+        return static_cast<uint32_t>(__ldg(v + ((static_cast<size_t>(t) * C + c) * A + a) * P + p));
+    };
 
     for (int a = tid; a < A; a += kCalThreads) {
         const short2 k = cells[static_cast<size_t>(c) * A + a];
@@ -64,6 +66,7 @@ gain_solve_kernel(const uint8_t *__restrict__ v, const short2 *__restrict__ cell
         phi[a] = make_float2(static_cast<float>(co), static_cast<float>(s));
         g[a] = make_float2(1.f, 0.f);
         int acc = 0;
+#pragma unroll 8
         for (int t = 0; t < T; t++) {
             const float2 e = ci4_cal(byte(t, a));
             acc += static_cast<int>(e.x * e.x + e.y * e.y);
@@ -77,6 +80,7 @@ gain_solve_kernel(const uint8_t *__restrict__ v, const short2 *__restrict__ cell
         // E(t) = (1/A) sum_a g_a conj(phi_a) e_a(t): one warp per sample
         for (int t = warp; t < T; t += kCalThreads / 32) {
             float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 8
             for (int a = lane; a < A; a += 32) {
                 const float2 w = cmul(g[a], make_float2(phi[a].x, -phi[a].y));
                 const float2 e = ci4_cal(byte(t, a));
@@ -94,6 +98,7 @@ gain_solve_kernel(const uint8_t *__restrict__ v, const short2 *__restrict__ cell
         // g_a = phi_a sum_t E(t) conj(e_a(t)) / sum_t |e_a(t)|^2
         for (int a = tid; a < A; a += kCalThreads) {
             float2 num = make_float2(0.f, 0.f);
+#pragma unroll 8
             for (int t = 0; t < T; t++) {
                 const float2 e = ci4_cal(byte(t, a));
                 const float2 x = E[t];
