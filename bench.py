@@ -44,13 +44,13 @@ L2_FLUSH_BYTES = 256 << 20
 # lwa: one full 64-channel launch captured: 34 701 824 B read (the 32.8 MB ci4
 # input plus tables) + 108 019 968 B written (time-chunk partial sums that spill
 # out of L2 before the epilogue reads them).
-NCU_TRAFFIC = {"lwa": (108_820_480, "23f8b65041a4140c")}
+NCU_TRAFFIC = {"lwa": (108_311_296, "e063a5dee4f9da79")}
 # What the same ncu capture shows binds the kernel (full set, one LWA launch): shared-memory
 # wavefronts per SM cycle at the capture's clock, against 1 per cycle (128 B/clk).
 NCU_LIMITER = {"lwa": ({"unit": "shared-memory wavefronts per SM cycle", "achieved": 0.80, "peak": 1.0,
-                        "wavefronts_per_launch": 1_762_534_810, "issue_active_pct": 39.6,
-                        "fma_pipe_pct": 35.6},
-                       "23f8b65041a4140c")}
+                        "wavefronts_per_launch": 1_762_614_382, "issue_active_pct": 39.5,
+                        "fma_pipe_pct": 35.4},
+                       "e063a5dee4f9da79")}
 
 
 def parse():
@@ -106,12 +106,13 @@ def fp32_flops_per_spectrum(A, K, N):
 
 
 def kernel_source_hash():
-    """Hash of the dominant kernel's device code (the fp32_reg64_kernel template
-    and the transform headers it includes)."""
+    """Hash of the dominant kernel's device code (the transform_products
+    function and the fp32_reg64_kernel template, and the transform headers they
+    include)."""
     csrc = os.path.join(ROOT, "paper_2301_09662_gb300", "csrc")
     src = open(os.path.join(csrc, "fp32_reg64.cu")).read()
-    start = src.index("fp32_reg64_kernel(")
-    end = src.index("size_t reg64_smem(", start)
+    start = src.index("template <int P, int TS, bool CLEAR>")
+    end = src.index("// Large grid sides: the folded grids", start)
     h = hashlib.sha256(src[start:end].encode())
     for f in ("fft64.cuh", "dft_small.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:

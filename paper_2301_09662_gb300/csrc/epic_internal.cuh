@@ -43,6 +43,15 @@ struct GroupCfg {
     uint32_t *d_sched = nullptr;       // device: [n_chan][8 warps][rmax][32] segment descriptors
     int *d_nrounds = nullptr;          // device: [n_chan][8] rounds per warp
     unsigned long long *d_rowmask = nullptr;  // device: [n_chan] folded rows touched by any footprint
+    // large grid sides (8 x 8 pixel classes): grid once per (channel, sample) into the occupied
+    // alias blocks, fold all classes with one 8 x 8 DFT per folded cell (alias_fold_kernel), then
+    // transform each class's loaded grid (fp32_fold64_kernel), in time batches of alias_tb samples
+    bool alias = false;
+    int alias_tb = 0;
+    float2 *d_gf = nullptr;            // device: [alias_tb][n_items][P][64][64] folded grids
+    short2 *d_j0 = nullptr;            // device: [n_chan] first occupied alias block (x, y)
+    uint32_t *d_bseg = nullptr;        // device: footprint rows (a << 8 | dyi) per (channel, 8-row band)
+    int *d_boff = nullptr;             // device: [n_chan * 8 + 1] offsets into d_bseg
 };
 
 struct KernelTables {
@@ -176,6 +185,15 @@ struct RawImage {
 int fp32_pick_tau(int n_items, int T, int sms);
 // time chunks of one launch: forced (image series), else autotuned for this T, else the cost model
 int choose_tau(const epic_plan_s *plan, const GroupCfg &g, int T);
+// large grid sides (GroupCfg::alias)
+size_t fold64_smem_bytes(int P);
+int prepare_fold64(int P);
+int launch_fold64(const GroupCfg &g, int P, const float2 *gf, int nb, bool accumulate, cudaStream_t stream);
+int build_alias_tables(const std::vector<short2> &cells, int A, int K, int N, const std::vector<int> &chans,
+                       std::vector<short2> &j0, std::vector<uint32_t> &bseg, std::vector<int> &boff);
+int prepare_alias(const epic_plan_s *plan);
+int launch_alias(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
+                 cudaStream_t stream);
 size_t fp32_smem_bytes(int M, int P, int A, int K);
 int launch_fp32_raw(const RawImage &r, const uint8_t *v, const float2 *gains, cudaStream_t stream);
 int launch_autopower_raw(const RawImage &r, const uint8_t *v, int sm_count, cudaStream_t stream);

@@ -38,6 +38,58 @@ struct Acc64;
 template <> struct Acc64<1> { using T = float; };
 template <> struct Acc64<2> { using T = float4; };
 
+constexpr int NPOS64 = M64 * M64 / kThreads;   // pixels whose time sums a thread keeps
+
+// a4-a6 on the TS x P planes of G ([ts][p][y][x], x < 64 at stride S64): rows
+// then columns, one 64-point transform per thread, then the products of every
+// pixel added to the thread's time sums; CLEAR zeroes the planes for the next
+// gridding.  Rows outside rows_used are empty and stay zero.
+template <int P, int TS, bool CLEAR>
+__device__ __forceinline__ void transform_products(float2 *G, unsigned long long rows_used,
+                                                   typename Acc64<P>::T (&acc)[NPOS64], int tid)
+{
+    constexpr int BUF = M64 * S64;
+    for (int q = tid; q < TS * P * M64; q += kThreads) {
+        if (!((rows_used >> (q % M64)) & 1ull)) continue;   // empty row: stays zero
+        float2 *line = G + (q / M64) * BUF + (q % M64) * S64;
+        float2 x[64];
+#pragma unroll
+        for (int i = 0; i < 64; i++) x[i] = line[i];
+        fft64p_stage1(x);
+        fft64p_stage2(x, [&](int k, float2 val) { line[k] = val; });
+    }
+    __syncthreads();
+    for (int q = tid; q < TS * P * M64; q += kThreads) {
+        float2 *col = G + (q / M64) * BUF + (q % M64);
+        float2 x[64];
+#pragma unroll
+        for (int i = 0; i < 64; i++) x[i] = col[i * S64];
+        fft64p_stage1(x);
+        fft64p_stage2(x, [&](int k, float2 val) { col[k * S64] = val; });
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < NPOS64; r++) {
+        const int pos = tid + r * kThreads;
+        const int idx = (pos >> 6) * S64 + (pos & 63);
+#pragma unroll
+        for (int ts = 0; ts < TS; ts++) {
+            const float2 f0 = G[(ts * P) * BUF + idx];
+            if constexpr (CLEAR) G[(ts * P) * BUF + idx] = make_float2(0.f, 0.f);
+            if constexpr (P == 2) {
+                const float2 f1 = G[(ts * P + 1) * BUF + idx];
+                if constexpr (CLEAR) G[(ts * P + 1) * BUF + idx] = make_float2(0.f, 0.f);
+                acc[r].x = fmaf(f0.x, f0.x, fmaf(f0.y, f0.y, acc[r].x));
+                acc[r].y = fmaf(f1.x, f1.x, fmaf(f1.y, f1.y, acc[r].y));
+                acc[r].z = fmaf(f0.x, f1.x, fmaf(f0.y, f1.y, acc[r].z));
+                acc[r].w = fmaf(f0.y, f1.x, fmaf(-f0.x, f1.y, acc[r].w));
+            } else {
+                acc[r] = fmaf(f0.x, f0.x, fmaf(f0.y, f0.y, acc[r]));
+            }
+        }
+    }
+}
+
 // Grid buffers: G[ts][p][y][x] with x < 64 at stride S64.  KC > 0 fixes the
 // kernel side at compile time (the gridding loop then unrolls fully); KC = 0
 // takes it from K.  DL: voltages take the geometric-delay phase of the
@@ -55,7 +107,7 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                   const float *__restrict__ dfreq, const float4 *__restrict__ dtab)
 {
     const int K = KC > 0 ? KC : K_rt;
-    constexpr int NPOS = M64 * M64 / kThreads;   // 16 pixels per thread
+    constexpr int NPOS = NPOS64;                 // 16 pixels per thread
     constexpr int BUF = M64 * S64;               // one [y][x] plane
     extern __shared__ float4 smem_raw[];
     const int AP = A * P, KK = K * K, hk = (K - 1) / 2;
@@ -184,48 +236,8 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         }
         __syncthreads();
 
-        // ---- a4: rows then columns, one 64-point transform per thread
-        for (int q = tid; q < TS * P * M64; q += kThreads) {
-            if (!((rows_used >> (q % M64)) & 1ull)) continue;   // empty row: stays zero
-            float2 *line = G + (q / M64) * BUF + (q % M64) * S64;
-            float2 x[64];
-#pragma unroll
-            for (int i = 0; i < 64; i++) x[i] = line[i];
-            fft64p_stage1(x);
-            fft64p_stage2(x, [&](int k, float2 val) { line[k] = val; });
-        }
-        __syncthreads();
-        for (int q = tid; q < TS * P * M64; q += kThreads) {
-            float2 *col = G + (q / M64) * BUF + (q % M64);
-            float2 x[64];
-#pragma unroll
-            for (int i = 0; i < 64; i++) x[i] = col[i * S64];
-            fft64p_stage1(x);
-            fft64p_stage2(x, [&](int k, float2 val) { col[k * S64] = val; });
-        }
-        __syncthreads();
-
-        // ---- a5, a6: products summed over time; clear the grids for the next group
-#pragma unroll
-        for (int r = 0; r < NPOS; r++) {
-            const int pos = tid + r * kThreads;
-            const int idx = (pos >> 6) * S64 + (pos & 63);
-#pragma unroll
-            for (int ts = 0; ts < TS; ts++) {
-                const float2 f0 = G[(ts * P) * BUF + idx];
-                G[(ts * P) * BUF + idx] = make_float2(0.f, 0.f);
-                if constexpr (P == 2) {
-                    const float2 f1 = G[(ts * P + 1) * BUF + idx];
-                    G[(ts * P + 1) * BUF + idx] = make_float2(0.f, 0.f);
-                    acc[r].x = fmaf(f0.x, f0.x, fmaf(f0.y, f0.y, acc[r].x));
-                    acc[r].y = fmaf(f1.x, f1.x, fmaf(f1.y, f1.y, acc[r].y));
-                    acc[r].z = fmaf(f0.x, f1.x, fmaf(f0.y, f1.y, acc[r].z));
-                    acc[r].w = fmaf(f0.y, f1.x, fmaf(-f0.x, f1.y, acc[r].w));
-                } else {
-                    acc[r] = fmaf(f0.x, f0.x, fmaf(f0.y, f0.y, acc[r]));
-                }
-            }
-        }
+        // ---- a4, a5, a6: transforms, products summed over time; planes cleared for the next group
+        transform_products<P, TS, true>(G, rows_used, acc, tid);
 #pragma unroll
         for (int ts = 0; ts < TS; ts++)
 #pragma unroll
@@ -239,6 +251,48 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     float *dst = partial + (static_cast<size_t>(tau) * n_items + item) * (M64 * M64) * (P == 2 ? 4 : 1);
 #pragma unroll
     for (int r = 0; r < NPOS; r++) {
+        const int pos = tid + r * kThreads;
+        if constexpr (P == 2) reinterpret_cast<float4 *>(dst)[pos] = acc[r];
+        else dst[pos] = acc[r];
+    }
+}
+
+// Large grid sides: the folded grids of every pixel class were formed once per
+// (channel, sample) by alias_fold_kernel; this kernel loads its class's grid
+// for each sample of a time batch instead of gridding, then transforms and
+// sums products like fp32_reg64_kernel.  gf is [nb][n_items][P][64][64]; the
+// time sums go to partial slot 0, added to what is there when accumulate is set
+// (batches of one integration follow each other on the stream).
+template <int P>
+__global__ void __launch_bounds__(kThreads, 1)
+fp32_fold64_kernel(const float2 *__restrict__ gf, int nb, int accumulate, float *__restrict__ partial)
+{
+    constexpr int BUF = M64 * S64;
+    extern __shared__ float4 smem_raw[];
+    float2 *G = reinterpret_cast<float2 *>(smem_raw);          // [P][64][65]
+    const int item = blockIdx.x, n_items = gridDim.x, tid = threadIdx.x;
+    float *dst = partial + static_cast<size_t>(item) * (M64 * M64) * (P == 2 ? 4 : 1);
+    typename Acc64<P>::T acc[NPOS64];
+#pragma unroll
+    for (int r = 0; r < NPOS64; r++) {
+        const int pos = tid + r * kThreads;
+        if constexpr (P == 2) acc[r] = accumulate ? reinterpret_cast<const float4 *>(dst)[pos] : make_float4(0.f, 0.f, 0.f, 0.f);
+        else acc[r] = accumulate ? dst[pos] : 0.f;
+    }
+    for (int bt = 0; bt < nb; bt++) {
+        const float4 *src = reinterpret_cast<const float4 *>(gf + (static_cast<size_t>(bt) * n_items + item) * P * (M64 * M64));
+        for (int i = tid; i < P * M64 * M64 / 2; i += kThreads) {   // two cells per load
+            const float4 f = __ldg(src + i);
+            const int e = 2 * i, pl = e >> 12, y = (e >> 6) & 63, x = e & 63;
+            G[pl * BUF + y * S64 + x] = make_float2(f.x, f.y);
+            G[pl * BUF + y * S64 + x + 1] = make_float2(f.z, f.w);
+        }
+        __syncthreads();
+        transform_products<P, 1, false>(G, ~0ull, acc, tid);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < NPOS64; r++) {
         const int pos = tid + r * kThreads;
         if constexpr (P == 2) reinterpret_cast<float4 *>(dst)[pos] = acc[r];
         else dst[pos] = acc[r];
@@ -335,6 +389,25 @@ size_t reg64_smem_bytes(int P, int TS, int A, int K, int nker)
 {
     if (P == 2) return TS == 2 ? reg64_smem<2, 2>(A, K, nker) : reg64_smem<2, 1>(A, K, nker);
     return TS == 2 ? reg64_smem<1, 2>(A, K, nker) : reg64_smem<1, 1>(A, K, nker);
+}
+
+size_t fold64_smem_bytes(int P) { return sizeof(float2) * static_cast<size_t>(P) * M64 * S64; }
+
+int prepare_fold64(int P)
+{
+    const int smem = static_cast<int>(fold64_smem_bytes(P));
+    const cudaError_t e = P == 2 ? cudaFuncSetAttribute(fp32_fold64_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                                 : cudaFuncSetAttribute(fp32_fold64_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e == cudaSuccess ? EPIC_OK : EPIC_ERR_UNSUPPORTED;
+}
+
+int launch_fold64(const GroupCfg &g, int P, const float2 *gf, int nb, bool accumulate, cudaStream_t stream)
+{
+    const size_t smem = fold64_smem_bytes(P);
+    const dim3 grid(static_cast<unsigned>(g.n_items));
+    if (P == 2) fp32_fold64_kernel<2><<<grid, kThreads, smem, stream>>>(gf, nb, accumulate ? 1 : 0, g.d_partial);
+    else fp32_fold64_kernel<1><<<grid, kThreads, smem, stream>>>(gf, nb, accumulate ? 1 : 0, g.d_partial);
+    return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
 int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,

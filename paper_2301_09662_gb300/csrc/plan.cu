@@ -79,6 +79,10 @@ void free_plan(epic_plan_s *p)
         cudaFree(g.d_partial);
         cudaFree(g.d_sched);
         cudaFree(g.d_nrounds);
+        cudaFree(g.d_gf);
+        cudaFree(g.d_j0);
+        cudaFree(g.d_bseg);
+        cudaFree(g.d_boff);
         cudaFree(g.d_rowmask);
         cudaFree(g.d_tw64);
         cudaFree(g.d_Y);
@@ -497,6 +501,28 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
             if (rc == EPIC_OK) rc = dev_upload(&g.d_sched, desc.data(), desc.size());
             if (rc == EPIC_OK) rc = dev_upload(&g.d_nrounds, nr.data(), nr.size());
             if (rc == EPIC_OK) rc = dev_upload(&g.d_rowmask, rows.data(), rows.size());
+            // large sides with one shared kernel of more than one tap: grid once per (channel,
+            // sample) and fold all classes (alias_fold.cu).  With one tap (the taper) re-gridding
+            // per class is cheaper than moving the folded grids through HBM (measured at N = 512:
+            // 0.24 s against 0.44 s per dense integration).  EPIC_NO_ALIAS=1 keeps the per-class
+            // gridding.
+            const char *na = std::getenv("EPIC_NO_ALIAS");
+            if (rc == EPIC_OK && !g.tensor && g.Q1 == 8 && p->nker == 1 && p->K > 1 && !(na && na[0] == '1')) {
+                std::vector<short2> j0;
+                std::vector<uint32_t> bseg;
+                std::vector<int> boff;
+                if (epic::build_alias_tables(cells, n_ant, p->K, g.N, g.chans, j0, bseg, boff) == EPIC_OK) {
+                    const size_t per_sample = static_cast<size_t>(g.n_items) * n_pol * 64 * 64 * sizeof(float2);
+                    constexpr size_t kBudget = size_t(4) << 30;   // folded grids of one time batch
+                    g.alias_tb = static_cast<int>(std::max<size_t>(1, std::min<size_t>(max_spectra, kBudget / per_sample)));
+                    rc = dev_upload(&g.d_j0, j0.data(), j0.size());
+                    if (rc == EPIC_OK) rc = dev_upload(&g.d_bseg, bseg.data(), std::max<size_t>(1, bseg.size()));
+                    if (rc == EPIC_OK) rc = dev_upload(&g.d_boff, boff.data(), boff.size());
+                    if (rc == EPIC_OK)
+                        rc = dev_upload(&g.d_gf, static_cast<const float2 *>(nullptr), per_sample / sizeof(float2) * g.alias_tb);
+                    g.alias = rc == EPIC_OK;
+                }
+            }
         }
         if (rc == EPIC_OK) rc = dev_upload(&g.d_chans, g.chans.data(), g.chans.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_out_off, offs.data(), offs.size());
@@ -545,6 +571,7 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     for (const auto &g : p->groups) {
         if (rc != EPIC_OK) break;
         if (!g.tensor) rc = epic::prepare_fp32(p, g);
+        if (rc == EPIC_OK && g.alias) rc = epic::prepare_alias(p);
     }
     if (rc == EPIC_OK) {
         const char *env = std::getenv("EPIC_NO_GRAPH");
@@ -638,6 +665,7 @@ int epic_autotune(epic_plan_t plan, int n_spectra, void *stream)
     if (rc == EPIC_OK && autosub) rc = epic::launch_autopower(plan, v, n_spectra, s);
     for (auto &g : plan->groups) {
         if (rc != EPIC_OK) break;
+        if (g.alias) continue;               // one time chunk, batched by the plan: nothing to tune
         const int cap = std::max(1, std::min(g.tau_cap, n_spectra));
         std::vector<int> cand;
         auto add = [&](int n) {

@@ -158,6 +158,22 @@ def test_folded64_path_is_bitwise_deterministic():
     assert np.array_equal(a, b)
 
 
+def test_large_grid_fold_path_matches_per_class_path_and_is_deterministic(monkeypatch):
+    """At N = 512 the plan grids once per (channel, sample) and folds the 64
+    pixel classes with one 8 x 8 DFT per folded cell; EPIC_NO_ALIAS=1 keeps the
+    per-class gridding.  Both agree to FP32 rounding, the fold path repeats bit
+    for bit (no atomics), and it matches the oracle."""
+    wl = synth.random_small(A=150, P=2, C=2, T=7, N=512, K=5, seed=31)
+    a, p = run_gpu(wl)
+    b, _ = run_gpu(wl, plan=p)
+    assert np.array_equal(a, b)
+    monkeypatch.setenv("EPIC_NO_ALIAS", "1")
+    c, _ = run_gpu(wl)
+    assert peak_rel_err(a, c, wl.grid_n, 2).max() < 1e-6
+    ref = oracle.workload_image(wl)
+    assert peak_rel_err(a, ref, wl.grid_n, 2).max() < FP32_TOL
+
+
 def test_uneven_workload_full_size_sampled_channels():
     """192 channels over 30-80 MHz in three grid-side groups (64/96/128), 1000
     spectra, one graph launch per integration; one channel of each group against
