@@ -18,6 +18,7 @@
 // a << 8 | dyi) are taken 32 at a time, each lane calibrating one, then applied
 // one after another with lane dx adding tap dx.
 #include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "dft_small.cuh"
@@ -40,6 +41,43 @@ __device__ __forceinline__ float2 ci4_alias(uint32_t b)
 // exp(+2 pi i k / 8); indexed with warp-uniform k (alias block x class), a broadcast read
 __constant__ float2 c_w8[8] = {{1.f, 0.f},   {kSqrtHalf, kSqrtHalf},   {0.f, 1.f},  {-kSqrtHalf, kSqrtHalf},
                                {-1.f, 0.f},  {-kSqrtHalf, -kSqrtHalf}, {0.f, -1.f}, {kSqrtHalf, -kSqrtHalf}};
+
+// s += a w8^K with K known at compile time: +-1 and +-i are adds, the odd
+// powers (+-1 +-i) sqrt(1/2) two FMAs per component
+template <int K>
+__device__ __forceinline__ void cmac8(float2 &s, float2 a)
+{
+    constexpr int k = K & 7;
+    if constexpr (k == 0) {
+        s.x += a.x;
+        s.y += a.y;
+    } else if constexpr (k == 2) {
+        s.x -= a.y;
+        s.y += a.x;
+    } else if constexpr (k == 4) {
+        s.x -= a.x;
+        s.y -= a.y;
+    } else if constexpr (k == 6) {
+        s.x += a.y;
+        s.y -= a.x;
+    } else {
+        constexpr float c = (k == 1 || k == 7) ? kSqrtHalf : -kSqrtHalf;
+        constexpr float d = (k == 1 || k == 3) ? kSqrtHalf : -kSqrtHalf;
+        s.x = fmaf(a.x, c, fmaf(-a.y, d, s.x));
+        s.y = fmaf(a.x, d, fmaf(a.y, c, s.y));
+    }
+}
+
+template <class F, int... I>
+__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>)
+{
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
 
 __global__ void __launch_bounds__(kAliasThreads)
 alias_fold_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains, const short2 *__restrict__ cells,
@@ -94,39 +132,38 @@ alias_fold_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     }
     __syncthreads();
 
-    // ---- fold: per folded cell (my, mx), the kNJ x kNJ aliases -> 8 x 8 class values
+    // ---- fold: per folded cell (my, mx), the kNJ x kNJ aliases -> 8 x 8 class values.
+    // w_N^{m.h} w8^{(j0 + i).h} = fx(hx) fy(hy) w8^{i.h}: the alias offset j0 and the class
+    // phase go into per-cell factors fx, fy, the remaining 4-input 8-point DFTs have
+    // compile-time roots
     for (int cl = tid; cl < 8 * 64; cl += kAliasThreads) {
         const int r = cl >> 6, mx = cl & 63, mfy = 8 * band + r;
         const float2 *src = al + cl * kCS;
-        float2 B[kNJ][8];                          // B[iy][hx] = sum_ix A[iy][ix] w8^{(j0x + ix) hx}
+        float2 fx[8], fy[8];
 #pragma unroll
-        for (int iy = 0; iy < kNJ; iy++)
+        for (int hh = 0; hh < 8; hh++) {
+            fx[hh] = cmul(c_w8[(j0.x * hh) & 7], twN[(mx * hh) % N]);
+            fy[hh] = cmul(c_w8[(j0.y * hh) & 7], twN[(mfy * hh) % N]);
+        }
+        float2 B[kNJ][8];                          // B[iy][hx] = fx(hx) sum_ix A[iy][ix] w8^{ix hx}
+        static_for<kNJ>([&](auto iy) {
+            float2 av[kNJ];
 #pragma unroll
-            for (int hx = 0; hx < 8; hx++) {
-                float2 s = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int ix = 0; ix < kNJ; ix++) {
-                    const float2 a = src[iy * kNJ + ix], w = c_w8[((j0.x + ix) * hx) & 7];
-                    s.x = fmaf(a.x, w.x, fmaf(-a.y, w.y, s.x));
-                    s.y = fmaf(a.x, w.y, fmaf(a.y, w.x, s.y));
-                }
-                B[iy][hx] = s;
-            }
-#pragma unroll 1
-        for (int hy = 0; hy < 8; hy++)
-#pragma unroll
-            for (int hx = 0; hx < 8; hx++) {
-                float2 s = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int iy = 0; iy < kNJ; iy++) {
-                    const float2 b = B[iy][hx], w = c_w8[((j0.y + iy) * hy) & 7];
-                    s.x = fmaf(b.x, w.x, fmaf(-b.y, w.y, s.x));
-                    s.y = fmaf(b.x, w.y, fmaf(b.y, w.x, s.y));
-                }
-                const float2 g = cmul(s, twN[(mx * hx + mfy * hy) % N]);   // class phase w_N^{m.h}
-                const int item = ci * 64 + hy * 8 + hx;
-                gf[((static_cast<size_t>(bt) * n_items + item) * P + p) * 4096 + mfy * 64 + mx] = g;
-            }
+            for (int ix = 0; ix < kNJ; ix++) av[ix] = src[iy.value * kNJ + ix];
+            static_for<8>([&](auto hx) {
+                float2 acc2 = make_float2(0.f, 0.f);
+                static_for<kNJ>([&](auto ix) { cmac8<ix.value * hx.value>(acc2, av[ix.value]); });
+                B[iy.value][hx.value] = cmul(acc2, fx[hx.value]);
+            });
+        });
+        float2 *out = gf + (static_cast<size_t>(bt) * n_items + ci * 64) * P * 4096 + p * 4096 + mfy * 64 + mx;
+        static_for<8>([&](auto hy) {
+            static_for<8>([&](auto hx) {
+                float2 acc2 = make_float2(0.f, 0.f);
+                static_for<kNJ>([&](auto iy) { cmac8<iy.value * hy.value>(acc2, B[iy.value][hx.value]); });
+                out[static_cast<size_t>(hy.value * 8 + hx.value) * P * 4096] = cmul(acc2, fy[hy.value]);
+            });
+        });
     }
 }
 

@@ -260,16 +260,24 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
 // Large grid sides: the folded grids of every pixel class were formed once per
 // (channel, sample) by alias_fold_kernel; this kernel loads its class's grid
 // for each sample of a time batch instead of gridding, then transforms and
-// sums products like fp32_reg64_kernel.  gf is [nb][n_items][P][64][64]; the
-// time sums go to partial slot 0, added to what is there when accumulate is set
-// (batches of one integration follow each other on the stream).
+// sums products like fp32_reg64_kernel.  Two grid buffers: the next sample's
+// grid streams in (cp.async) while the current one is transformed.  gf is
+// [nb][n_items][P][64][64]; the time sums go to partial slot 0, added to what
+// is there when accumulate is set (batches of one integration follow each other
+// on the stream).
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 template <int P>
 __global__ void __launch_bounds__(kThreads, 1)
 fp32_fold64_kernel(const float2 *__restrict__ gf, int nb, int accumulate, float *__restrict__ partial)
 {
     constexpr int BUF = M64 * S64;
     extern __shared__ float4 smem_raw[];
-    float2 *G = reinterpret_cast<float2 *>(smem_raw);          // [P][64][65]
+    float2 *Gb = reinterpret_cast<float2 *>(smem_raw);         // two x [P][64][65]
     const int item = blockIdx.x, n_items = gridDim.x, tid = threadIdx.x;
     float *dst = partial + static_cast<size_t>(item) * (M64 * M64) * (P == 2 ? 4 : 1);
     typename Acc64<P>::T acc[NPOS64];
@@ -279,18 +287,24 @@ fp32_fold64_kernel(const float2 *__restrict__ gf, int nb, int accumulate, float 
         if constexpr (P == 2) acc[r] = accumulate ? reinterpret_cast<const float4 *>(dst)[pos] : make_float4(0.f, 0.f, 0.f, 0.f);
         else acc[r] = accumulate ? dst[pos] : 0.f;
     }
-    for (int bt = 0; bt < nb; bt++) {
-        const float4 *src = reinterpret_cast<const float4 *>(gf + (static_cast<size_t>(bt) * n_items + item) * P * (M64 * M64));
-        for (int i = tid; i < P * M64 * M64 / 2; i += kThreads) {   // two cells per load
-            const float4 f = __ldg(src + i);
-            const int e = 2 * i, pl = e >> 12, y = (e >> 6) & 63, x = e & 63;
-            G[pl * BUF + y * S64 + x] = make_float2(f.x, f.y);
-            G[pl * BUF + y * S64 + x + 1] = make_float2(f.z, f.w);
+    auto issue = [&](int bt) {                       // sample bt of the batch into buffer bt mod 2
+        if (bt < nb) {
+            const float2 *src = gf + (static_cast<size_t>(bt) * n_items + item) * P * (M64 * M64);
+            float2 *G = Gb + (bt & 1) * P * BUF;
+            for (int i = tid; i < P * M64 * M64; i += kThreads)
+                cp_async8(G + (i >> 12) * BUF + ((i >> 6) & 63) * S64 + (i & 63), src + i);
         }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    issue(0);
+    for (int bt = 0; bt < nb; bt++) {
+        issue(bt + 1);
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // sample bt has landed (this thread's part)
         __syncthreads();
-        transform_products<P, 1, false>(G, ~0ull, acc, tid);
-        __syncthreads();
+        transform_products<P, 1, false>(Gb + (bt & 1) * P * BUF, ~0ull, acc, tid);
+        __syncthreads();                             // buffer bt mod 2 is refilled two samples on
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 #pragma unroll
     for (int r = 0; r < NPOS64; r++) {
         const int pos = tid + r * kThreads;
@@ -391,7 +405,7 @@ size_t reg64_smem_bytes(int P, int TS, int A, int K, int nker)
     return TS == 2 ? reg64_smem<1, 2>(A, K, nker) : reg64_smem<1, 1>(A, K, nker);
 }
 
-size_t fold64_smem_bytes(int P) { return sizeof(float2) * static_cast<size_t>(P) * M64 * S64; }
+size_t fold64_smem_bytes(int P) { return 2 * sizeof(float2) * static_cast<size_t>(P) * M64 * S64; }
 
 int prepare_fold64(int P)
 {
