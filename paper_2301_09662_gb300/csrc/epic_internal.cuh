@@ -41,6 +41,7 @@ struct GroupCfg {
     int ts = 1;
     int rmax = 0;
     uint32_t *d_sched = nullptr;       // device: [n_chan][8 warps][rmax][32] segment descriptors
+    uint16_t *d_first = nullptr;       // device (tensor plans): per descriptor, taps that write their cell first
     int *d_nrounds = nullptr;          // device: [n_chan][8] rounds per warp
     unsigned long long *d_rowmask = nullptr;  // device: [n_chan] folded rows touched by any footprint
     // large grid sides (8 x 8 pixel classes): grid once per (channel, sample) into the occupied
@@ -165,7 +166,7 @@ int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
 // Gridding schedule of the M = 64 kernel for the channels of one group (plan.cu).
 int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
                          std::vector<uint32_t> &desc, std::vector<int> &nrounds, int &rmax,
-                         std::vector<unsigned long long> &rowmask);
+                         std::vector<unsigned long long> &rowmask, std::vector<uint16_t> &first);
 
 // One single-grid-side FP32 imaging job on caller-provided device tables and
 // workspace (used by the static-scratch entry point).

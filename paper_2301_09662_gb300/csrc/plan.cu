@@ -78,6 +78,7 @@ void free_plan(epic_plan_s *p)
         cudaFree(g.d_twN);
         cudaFree(g.d_partial);
         cudaFree(g.d_sched);
+        cudaFree(g.d_first);
         cudaFree(g.d_nrounds);
         cudaFree(g.d_gf);
         cudaFree(g.d_j0);
@@ -161,7 +162,7 @@ void host_kernel_power(const float *kern, int K, int N, std::vector<double> &out
 // lane of a half-warp on its own pair of banks for each of the K cells.
 int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
                          std::vector<uint32_t> &desc, std::vector<int> &nrounds, int &rmax,
-                         std::vector<unsigned long long> &rowmask)
+                         std::vector<unsigned long long> &rowmask, std::vector<uint16_t> &first)
 {
     constexpr int M = 64, W = 8;
     const int h = (K - 1) / 2;
@@ -213,15 +214,32 @@ int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, const s
     }
     if (rmax == 0) rmax = 1;
     desc.assign(static_cast<size_t>(nc) * W * rmax * 32, 0u);
+    first.assign(desc.size(), 0);
     nrounds.assign(static_cast<size_t>(nc) * W, 0);
-    for (int ci = 0; ci < nc; ci++)
+    for (int ci = 0; ci < nc; ci++) {
+        // first[.] bit dx: tap dx of that segment is the first write of its cell in round order
+        // (each warp owns its rows, so per channel one pass over the warps' rounds decides it)
+        std::vector<uint8_t> touched(M * M, 0);
         for (int w = 0; w < W; w++) {
             const auto &rounds = all[ci][w];
             nrounds[ci * W + w] = static_cast<int>(rounds.size());
             for (size_t r = 0; r < rounds.size(); r++)
-                for (int l = 0; l < 32; l++)
-                    desc[((static_cast<size_t>(ci) * W + w) * rmax + r) * 32 + l] = rounds[r].lane[l];
+                for (int l = 0; l < 32; l++) {
+                    const uint32_t d = rounds[r].lane[l];
+                    const size_t at = ((static_cast<size_t>(ci) * W + w) * rmax + r) * 32 + l;
+                    desc[at] = d;
+                    if (!(d >> 31)) continue;
+                    const int y = static_cast<int>((d >> 16) & 0x3Fu), x0 = static_cast<int>((d >> 22) & 0x3Fu);
+                    uint16_t m = 0;
+                    for (int dx = 0; dx < K; dx++) {
+                        uint8_t &tc = touched[y * M + ((x0 + dx) & (M - 1))];
+                        if (!tc) m |= static_cast<uint16_t>(1u << dx);
+                        tc = 1;
+                    }
+                    first[at] = m;
+                }
         }
+    }
     return EPIC_OK;
 }
 
@@ -497,8 +515,10 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
             std::vector<uint32_t> desc;
             std::vector<int> nr;
             std::vector<unsigned long long> rows;
-            rc = epic::build_reg64_schedule(cells, n_ant, p->K, g.chans, desc, nr, g.rmax, rows);
+            std::vector<uint16_t> first;
+            rc = epic::build_reg64_schedule(cells, n_ant, p->K, g.chans, desc, nr, g.rmax, rows, first);
             if (rc == EPIC_OK) rc = dev_upload(&g.d_sched, desc.data(), desc.size());
+            if (rc == EPIC_OK && g.tensor) rc = dev_upload(&g.d_first, first.data(), first.size());
             if (rc == EPIC_OK) rc = dev_upload(&g.d_nrounds, nr.data(), nr.size());
             if (rc == EPIC_OK) rc = dev_upload(&g.d_rowmask, rows.data(), rows.size());
             // large sides with one shared kernel of more than one tap: grid once per (channel,

@@ -23,8 +23,9 @@
 // half).  Shared memory: X (hi, lo: 64 KB, one bulk copy per CTA), H16 (64 KB),
 // the FP32 grid (66.5 KB).
 //
-// Warps 0-7 (SIMT), iteration t: convert G(t) -> G16 in TMEM (and clear G) and
-// arrive on bar_g; unpack, calibrate and grid sample t+1 while the row stage
+// Warps 0-7 (SIMT), iteration t: convert G(t) -> G16 in TMEM and arrive on
+// bar_g (G is never cleared: each cell's first write in the static gridding
+// schedule stores instead of adding); unpack, calibrate and grid sample t+1 while the row stage
 // of t runs; sum the products of D2(t-1); wait for the row stage of t, convert
 // D1 -> H16 and arrive on bar_h.  Warp 8 issues the row stage of t after bar_g
 // and the column stage after bar_h, each committed to its own mbarrier; the
@@ -152,7 +153,8 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
                  const uint32_t *__restrict__ sched, const int *__restrict__ nrounds, int rmax,
                  const uint8_t *__restrict__ dft_ops, int A, int C, int T, int N, int Q1, int n_items, int n_tau,
                  float *__restrict__ partial, int *__restrict__ status, long long wait_budget, int withhold_mma,
-                 const float *__restrict__ dfreq, const float4 *__restrict__ dtab)
+                 const float *__restrict__ dfreq, const float4 *__restrict__ dtab,
+                 const uint16_t *__restrict__ first)
 {
     constexpr int P = 2;
     constexpr bool kBF16 = VAR == 2;
@@ -184,6 +186,10 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
     const int t0 = static_cast<int>(static_cast<long long>(T) * tau / n_tau);
     const int t1 = static_cast<int>(static_cast<long long>(T) * (tau + 1) / n_tau);
     const uint32_t *my_sched = sched + (static_cast<size_t>(ci) * 8 + min(warp, 7)) * rmax * 32;
+    // first: per descriptor, the taps whose cell no earlier round writes.  Those store instead of
+    // adding, so G (gridded values only: the transforms run in TMEM) needs no clearing between
+    // samples -- cells no footprint touches stay zero from the start
+    const uint16_t *my_first = first + (static_cast<size_t>(ci) * 8 + min(warp, 7)) * rmax * 32;
     const int my_rounds = simt ? nrounds[ci * 8 + warp] : 0;
 
     if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
@@ -331,6 +337,7 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
             for (int r = 0; r < my_rounds; r++) {
                 const uint32_t d = __ldg(my_sched + r * 32 + lane);
                 if (d >> 31) {
+                    const uint32_t fm = __ldg(my_first + r * 32 + lane);
                     const int a = static_cast<int>(d & 0xFFFu);
                     const int dyi = static_cast<int>((d >> 12) & 0xFu);
                     const int y = static_cast<int>((d >> 16) & 0x3Fu);
@@ -341,12 +348,15 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
                     float2 *gy = G + y * S64;
 #pragma unroll
                     for (int dx = 0; dx < (KC > 0 ? KC : K); dx++) {
-                        // cell += w e as two packed FMAs: w.x (e.x, e.y) + (-w.y, w.y) (e.y, e.x)
+                        // cell = (first write ? 0 : cell) + w e as two packed FMAs:
+                        // w.x (e.x, e.y) + (-w.y, w.y) (e.y, e.x)
                         const float2 w = wrow[dx];
                         const float2 wr = make_float2(w.x, w.x), wi = make_float2(-w.y, w.y);
                         const int x = (x0 + dx) & (M64 - 1);
-                        gy[x] = pfma(wi, e0s, pfma(wr, e0, gy[x]));
-                        gy[BUF + x] = pfma(wi, e1s, pfma(wr, e1, gy[BUF + x]));
+                        const bool fresh = (fm >> dx) & 1u;
+                        const float2 z = make_float2(0.f, 0.f);
+                        gy[x] = pfma(wi, e0s, pfma(wr, e0, fresh ? z : gy[x]));
+                        gy[BUF + x] = pfma(wi, e1s, pfma(wr, e1, fresh ? z : gy[BUF + x]));
                     }
                 }
                 __syncwarp();
@@ -383,16 +393,14 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
         uint32_t ph = 0;                                // parity of sample t - t0
         for (int t = t0; t <= t1; t++) {
             const bool work = t < t1, nxt = t + 1 < t1;
-            // ---- G (FP32) -> G16 in TMEM (row stage A operand), grid cleared for t+1.
+            // ---- G (FP32) -> G16 in TMEM (row stage A operand).
             // Thread: lane m = (pol, jy); half hp takes jx = 32 hp .. 32 hp + 31.
             if (work) {
                 float2 *line = G + (m >> 6) * BUF + (m & 63) * S64 + 32 * hp;
                 uint32_t rh[16], ih[16], rl[16], il[16];
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
-                    const float2 a = line[2 * j], b = line[2 * j + 1];
-                    line[2 * j] = make_float2(0.f, 0.f);
-                    line[2 * j + 1] = make_float2(0.f, 0.f);
+                    const float2 a = line[2 * j], b = line[2 * j + 1];   // no clearing: see my_first
                     split_pair<kBF16, kSplit>(a.x, b.x, rh[j], rl[j]);
                     split_pair<kBF16, kSplit>(a.y, b.y, ih[j], il[j]);
                 }
@@ -407,7 +415,7 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
                 tc::fence_before_sync();
                 tc::mbar_arrive(&bar_g);
             }
-            tc::named_bar_sync(kBarSimt, kSimt);        // G is clear, es is free
+            tc::named_bar_sync(kBarSimt, kSimt);        // G has been read, es is free
 
             // ---- sample t+1: unpack and grid while the row stage of t runs
             uint32_t pre[kPreW];
@@ -533,7 +541,8 @@ int launch_dual_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const 
     tc_dual64_kernel<VAR, KC><<<grid, kDualThreads, dual_smem(plan->A, plan->K), stream>>>(
         v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN, g.d_sched, g.d_nrounds, g.rmax,
         plan->d_dft, plan->A, plan->C, T, g.N, g.Q1, g.n_items, n_tau, g.d_partial, plan->d_status,
-        plan->wait_budget, plan->test_withhold_mma, plan->d_dfreq, plan->delays ? plan->d_dtab : nullptr);
+        plan->wait_budget, plan->test_withhold_mma, plan->d_dfreq, plan->delays ? plan->d_dtab : nullptr,
+        g.d_first);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
