@@ -44,13 +44,13 @@ L2_FLUSH_BYTES = 256 << 20
 # lwa: one full 64-channel launch captured: 34 701 824 B read (the 32.8 MB ci4
 # input plus tables) + 108 019 968 B written (time-chunk partial sums that spill
 # out of L2 before the epilogue reads them).
-NCU_TRAFFIC = {"lwa": (108_311_296, "e063a5dee4f9da79")}
+NCU_TRAFFIC = {"lwa": (107_952_896, "05a22060f3c0276e")}
 # What the same ncu capture shows binds the kernel (full set, one LWA launch): shared-memory
 # wavefronts per SM cycle at the capture's clock, against 1 per cycle (128 B/clk).
 NCU_LIMITER = {"lwa": ({"unit": "shared-memory wavefronts per SM cycle", "achieved": 0.80, "peak": 1.0,
-                        "wavefronts_per_launch": 1_762_614_382, "issue_active_pct": 39.5,
+                        "wavefronts_per_launch": 1_762_623_285, "issue_active_pct": 39.5,
                         "fma_pipe_pct": 35.4},
-                       "e063a5dee4f9da79")}
+                       "05a22060f3c0276e")}
 
 
 def parse():

@@ -31,13 +31,6 @@ constexpr int kAliasThreads = 256;   // 8 warps = 8 folded rows of a band
 constexpr int kNJ = 4;               // occupied alias blocks per axis
 constexpr int kCS = kNJ * kNJ + 1;   // float2 per folded cell in shared memory (odd: no bank conflicts)
 
-__device__ __forceinline__ float2 ci4_alias(uint32_t b)
-{
-    const int re = static_cast<int>(static_cast<int8_t>(b & 0xF0u)) >> 4;
-    const int im = static_cast<int>(static_cast<int8_t>((b << 4) & 0xF0u)) >> 4;
-    return make_float2(static_cast<float>(re), static_cast<float>(im));
-}
-
 // exp(+2 pi i k / 8); indexed with warp-uniform k (alias block x class), a broadcast read
 __constant__ float2 c_w8[8] = {{1.f, 0.f},   {kSqrtHalf, kSqrtHalf},   {0.f, 1.f},  {-kSqrtHalf, kSqrtHalf},
                                {-1.f, 0.f},  {-kSqrtHalf, -kSqrtHalf}, {0.f, -1.f}, {kSqrtHalf, -kSqrtHalf}};
@@ -112,7 +105,7 @@ alias_fold_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             const short2 k = cells[static_cast<size_t>(c) * A + a];
             cx = k.x;
             iy = ((k.y + dyi - h) >> 6) - j0.y;
-            e = ci4_alias(v[((static_cast<size_t>(t) * C + c) * A + a) * P + p]);
+            e = ci4_decode(v[((static_cast<size_t>(t) * C + c) * A + a) * P + p]);
             if (gains) e = cmul(gains[(static_cast<size_t>(c) * A + a) * P + p], e);
             if (dtab) e = cmul(e, delay_phase(dtab[static_cast<size_t>(t) * A + a], dfreq[c]));
         }

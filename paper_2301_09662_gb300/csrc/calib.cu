@@ -21,13 +21,6 @@ namespace {
 
 constexpr int kCalThreads = 256;
 
-__device__ __forceinline__ float2 ci4_cal(uint32_t b)
-{
-    const int re = static_cast<int>(static_cast<int8_t>(b & 0xF0u)) >> 4;
-    const int im = static_cast<int>(static_cast<int8_t>((b << 4) & 0xF0u)) >> 4;
-    return make_float2(static_cast<float>(re), static_cast<float>(im));
-}
-
 __device__ __forceinline__ float block_sum(float x, float *red)
 {
 #pragma unroll
@@ -68,7 +61,7 @@ gain_solve_kernel(const uint8_t *__restrict__ v, const short2 *__restrict__ cell
         int acc = 0;
 #pragma unroll 8
         for (int t = 0; t < T; t++) {
-            const float2 e = ci4_cal(byte(t, a));
+            const float2 e = ci4_decode(byte(t, a));
             acc += static_cast<int>(e.x * e.x + e.y * e.y);
         }
         den[a] = acc;
@@ -83,7 +76,7 @@ gain_solve_kernel(const uint8_t *__restrict__ v, const short2 *__restrict__ cell
 #pragma unroll 8
             for (int a = lane; a < A; a += 32) {
                 const float2 w = cmul(g[a], make_float2(phi[a].x, -phi[a].y));
-                const float2 e = ci4_cal(byte(t, a));
+                const float2 e = ci4_decode(byte(t, a));
                 acc.x = fmaf(w.x, e.x, fmaf(-w.y, e.y, acc.x));
                 acc.y = fmaf(w.x, e.y, fmaf(w.y, e.x, acc.y));
             }
@@ -100,7 +93,7 @@ gain_solve_kernel(const uint8_t *__restrict__ v, const short2 *__restrict__ cell
             float2 num = make_float2(0.f, 0.f);
 #pragma unroll 8
             for (int t = 0; t < T; t++) {
-                const float2 e = ci4_cal(byte(t, a));
+                const float2 e = ci4_decode(byte(t, a));
                 const float2 x = E[t];
                 num.x = fmaf(x.x, e.x, fmaf(x.y, e.y, num.x));    // x conj(e)
                 num.y = fmaf(x.y, e.x, fmaf(-x.x, e.y, num.y));

@@ -19,6 +19,15 @@ constexpr int kMaxAP = 4096;           // n_ant * n_pol handled by one CTA's sta
 // How one grid side N is imaged by the FP32 kernel: the sky is split into
 // Q1 x Q1 pixel classes l = (Q1 m + h) and each CTA owns one class, so it grids
 // into an M x M folded aperture (M = N / Q1) and runs an M x M transform.
+// One 4+4-bit complex voltage byte: Re = the high nibble, Im = the low nibble,
+// both two's complement (-8..7; Sec. 3's "4+4 complex integers", reading 1).
+__device__ __forceinline__ float2 ci4_decode(uint32_t b)
+{
+    const int re = static_cast<int>(static_cast<int8_t>(b & 0xF0u)) >> 4;
+    const int im = static_cast<int>(static_cast<int8_t>((b << 4) & 0xF0u)) >> 4;
+    return make_float2(static_cast<float>(re), static_cast<float>(im));
+}
+
 struct GroupCfg {
     int N = 0, M = 0, Q1 = 1, Q = 1;
     int n_chan = 0;

@@ -33,13 +33,6 @@ template <> struct Radix<32> { static constexpr int R1 = 8, R2 = 4; };
 template <> struct Radix<48> { static constexpr int R1 = 8, R2 = 6; };
 template <> struct Radix<64> { static constexpr int R1 = 8, R2 = 8; };
 
-__device__ __forceinline__ float2 ci4_to_float2(uint32_t b)
-{
-    const int re = static_cast<int>(static_cast<int8_t>(b & 0xF0u)) >> 4;
-    const int im = static_cast<int>(static_cast<int8_t>((b << 4) & 0xF0u)) >> 4;
-    return make_float2(static_cast<float>(re), static_cast<float>(im));
-}
-
 // pass 1 of a length-M transform along rows (ROWS) or columns, both pols:
 // element n2 + R2 n1 -> DFT over n1, twiddle w_M^{n2 k1}, back to n2 + R2 k1
 template <int M, int P, bool ROWS>
@@ -172,7 +165,7 @@ fp32_image_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         // ---- a1, a2: unpack and calibrate this time sample
         for (int i = tid; i < AP; i += kThreads) {
             const uint32_t b = reinterpret_cast<const uint8_t *>(stage)[i];
-            float2 e = cmul(gp[i], ci4_to_float2(b));
+            float2 e = cmul(gp[i], ci4_decode(b));
             if (dtab) e = cmul(e, delay_phase(dtab[static_cast<size_t>(t) * A + i / P], dfreq[c]));
             es[i] = e;
         }

@@ -26,13 +26,6 @@ namespace {
 constexpr int M64 = 64;
 constexpr int S64 = 65;                       // padded row stride (float2)
 
-__device__ __forceinline__ float2 ci4_f2(uint32_t b)
-{
-    const int re = static_cast<int>(static_cast<int8_t>(b & 0xF0u)) >> 4;
-    const int im = static_cast<int>(static_cast<int8_t>((b << 4) & 0xF0u)) >> 4;
-    return make_float2(static_cast<float>(re), static_cast<float>(im));
-}
-
 template <int P>
 struct Acc64;
 template <> struct Acc64<1> { using T = float; };
@@ -176,13 +169,13 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                     for (int p = 0; p < P; p++) {
                         const int i = a * P + p;
                         const uint32_t b = reinterpret_cast<const uint8_t *>(stage + ts * APW)[i];
-                        es[ts * AP + i] = cmul(cmul(gp[i], ci4_f2(b)), ph);
+                        es[ts * AP + i] = cmul(cmul(gp[i], ci4_decode(b)), ph);
                     }
                 }
             } else {
                 for (int i = tid; i < AP; i += kThreads) {
                     const uint32_t b = reinterpret_cast<const uint8_t *>(stage + ts * APW)[i];
-                    es[ts * AP + i] = ok ? cmul(gp[i], ci4_f2(b)) : make_float2(0.f, 0.f);
+                    es[ts * AP + i] = ok ? cmul(gp[i], ci4_decode(b)) : make_float2(0.f, 0.f);
                 }
             }
         }

@@ -65,13 +65,6 @@ struct Half16<true> {
     }
 };
 
-__device__ __forceinline__ float2 ci4_value(uint32_t b)
-{
-    const int re = static_cast<int>(static_cast<int8_t>(b & 0xF0u)) >> 4;
-    const int im = static_cast<int>(static_cast<int8_t>((b << 4) & 0xF0u)) >> 4;
-    return make_float2(static_cast<float>(re), static_cast<float>(im));
-}
-
 // VAR: 0 = FP16 two-part split (3 MMAs per k-block), 1 = single FP16, 2 = BF16 two-part split
 template <int VAR>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -182,7 +175,7 @@ tc_col64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
         // ---- a1, a2
         for (int i = tid; i < AP; i += kThreads) {
             const uint32_t b = reinterpret_cast<const uint8_t *>(stage)[i];
-            float2 e = cmul(gp[i], ci4_value(b));
+            float2 e = cmul(gp[i], ci4_decode(b));
             if (dtab) e = cmul(e, delay_phase(dtab[static_cast<size_t>(t) * A + i / P], dfreq[c]));
             es[i] = e;
         }

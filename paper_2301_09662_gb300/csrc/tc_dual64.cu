@@ -88,13 +88,6 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint3
     }
 }
 
-__device__ __forceinline__ float2 ci4_f2(uint32_t b)
-{
-    const int re = static_cast<int>(static_cast<int8_t>(b & 0xF0u)) >> 4;
-    const int im = static_cast<int>(static_cast<int8_t>((b << 4) & 0xF0u)) >> 4;
-    return make_float2(static_cast<float>(re), static_cast<float>(im));
-}
-
 // D(tmem) (+)= A(tmem) x B(smem)^T
 __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
                                        uint32_t accumulate)
@@ -327,7 +320,7 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
         auto unpack = [&](int t) {
             for (int i = tid; i < AP; i += kSimt) {
                 const uint32_t b = reinterpret_cast<const uint8_t *>(stage)[i];
-                float2 e = cmul(gp[i], ci4_f2(b));
+                float2 e = cmul(gp[i], ci4_decode(b));
                 if (dtab) e = cmul(e, delay_phase(dtab[static_cast<size_t>(t) * A + i / P], dfreq[c]));
                 es[i] = e;
             }

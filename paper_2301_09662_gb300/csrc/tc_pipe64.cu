@@ -84,13 +84,6 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t &hi, uint3
     }
 }
 
-__device__ __forceinline__ float2 ci4_val(uint32_t b)
-{
-    const int re = static_cast<int>(static_cast<int8_t>(b & 0xF0u)) >> 4;
-    const int im = static_cast<int>(static_cast<int8_t>((b << 4) & 0xF0u)) >> 4;
-    return make_float2(static_cast<float>(re), static_cast<float>(im));
-}
-
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
 {
     asm volatile(
@@ -366,7 +359,7 @@ tc_pipe64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
         if (work) {
             for (int i = tid; i < AP; i += kThreads) {
                 const uint32_t b = reinterpret_cast<const uint8_t *>(stage)[i];
-                float2 e = cmul(gp[i], ci4_val(b));
+                float2 e = cmul(gp[i], ci4_decode(b));
                 if (dtab) e = cmul(e, delay_phase(dtab[static_cast<size_t>(t) * A + i / P], dfreq[c]));
                 es[i] = e;
             }
