@@ -10,7 +10,8 @@
 // of the 8 x 8 blocks), then forms all 64 folded grids with one 8 x 8 DFT over
 // the alias index per folded cell (factored: 4 rows of 8-point DFTs over jx,
 // then 8 columns over jy) and the class phase w_N^{m.h}.  fp32_fold64_kernel
-// then loads each class's grid and transforms it.
+// (or, for a tensor plan, tc_dual64_kernel in its folded-grid mode) then loads
+// each class's grid and transforms it.
 //
 // Block = (8-row band of the folded grid, channel, sample x polarisation); warp
 // w owns folded row 8 band + w, so the alias buffers are written without
@@ -225,7 +226,8 @@ int launch_alias(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
             plan->A, plan->C, plan->P, g.N, g.n_items, tb0, plan->d_dfreq, plan->delays ? plan->d_dtab : nullptr,
             g.d_gf);
         if (cudaGetLastError() != cudaSuccess) return EPIC_ERR_CUDA;
-        const int rc = launch_fold64(g, plan->P, g.d_gf, nb, tb0 > 0, stream);
+        const int rc = g.tensor ? launch_tc_dual_fold(plan, g, gains, g.d_gf, nb, tb0 > 0, stream)
+                                : launch_fold64(g, plan->P, g.d_gf, nb, tb0 > 0, stream);
         if (rc != EPIC_OK) return rc;
     }
     return EPIC_OK;

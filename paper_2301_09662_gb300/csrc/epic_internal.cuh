@@ -46,6 +46,7 @@ struct GroupCfg {
     // M = 64 register-transform kernel: gridding schedule and samples per iteration
     bool reg64 = false;
     bool tensor = false;               // a tensor plan's group that folds to 64 runs the tensor kernel
+    bool tc_regular = true;            // the tensor kernel's per-antenna buffers fit (else only the fold path)
     int tuned_tau = 0, tuned_T = -1;   // time chunks epic_autotune measured fastest for T = tuned_T
     int ts = 1;
     int rmax = 0;
@@ -160,7 +161,10 @@ int launch_tc(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const floa
 void build_dft_operand(bool bf16, std::vector<uint16_t> &words);
 size_t tc_pipe_smem_bytes(int A, int K);
 size_t tc_dual_smem_bytes(int A, int K);
-int prepare_tc_dual(const epic_plan_s *plan);
+int prepare_tc_dual(const epic_plan_s *plan, size_t smem);
+size_t tc_dual_fold_smem_bytes();
+int launch_tc_dual_fold(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, const float2 *gf, int nb,
+                        bool accumulate, cudaStream_t stream);
 int launch_tc_dual(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                    cudaStream_t stream);
 int prepare_tc_pipe(const epic_plan_s *plan);

@@ -393,11 +393,12 @@ int prepare_fp32(const epic_plan_s *plan, const GroupCfg &g)
 int launch_imaging(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                    cudaStream_t s)
 {
+    if (g.alias && plan->force_tau == 0) return launch_alias(plan, g, v, gains, T, n_tau, s);
+    if (g.tensor && !g.tc_regular) return EPIC_ERR_UNSUPPORTED;   // e.g. an image series: no fold path there
     if (g.tensor)
         return plan->tc_form == 2   ? launch_tc_dual(plan, g, v, gains, T, n_tau, s)
                : plan->tc_form == 1 ? launch_tc_pipe(plan, g, v, gains, T, n_tau, s)
                                     : launch_tc(plan, g, v, gains, T, n_tau, s);
-    if (g.alias && plan->force_tau == 0) return launch_alias(plan, g, v, gains, T, n_tau, s);
     if (g.reg64) return launch_reg64(plan, g, v, gains, T, n_tau, s);
     switch (g.M * 4 + plan->P) {
     case 32 * 4 + 2: return launch_group<32, 2>(plan, g, v, gains, T, n_tau, s);

@@ -494,10 +494,15 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         g.R2 = g.M / 8;
         const int ap = n_ant * n_pol;
         g.tensor = tensor && g.M == 64;
+        const char *na = std::getenv("EPIC_NO_ALIAS");
+        const bool fold_ok = g.Q1 == 8 && p->nker == 1 && p->K > 1 && !(na && na[0] == '1');
         if (g.tensor) {
-            // + static shared memory of the kernel (barriers, TMEM slot, alignment)
-            if (std::max({epic::tc_smem_bytes(n_ant, p->K), epic::tc_pipe_smem_bytes(n_ant, p->K), epic::tc_dual_smem_bytes(n_ant, p->K)}) + 2048 >
-                static_cast<size_t>(smem_optin))
+            // + static shared memory of the kernel (barriers, TMEM slot, alignment); a large side
+            // that can take the fold path needs only the operands and the grid there
+            g.tc_regular = std::max({epic::tc_smem_bytes(n_ant, p->K), epic::tc_pipe_smem_bytes(n_ant, p->K),
+                                     epic::tc_dual_smem_bytes(n_ant, p->K)}) + 2048 <=
+                           static_cast<size_t>(smem_optin);
+            if (!g.tc_regular && !(fold_ok && epic::tc_dual_fold_smem_bytes() + 2048 <= static_cast<size_t>(smem_optin)))
                 rc = EPIC_ERR_UNSUPPORTED;
             g.reg64 = true;   // same gridding schedule and natural pixel order
             g.ts = 1;
@@ -522,12 +527,11 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
             if (rc == EPIC_OK) rc = dev_upload(&g.d_nrounds, nr.data(), nr.size());
             if (rc == EPIC_OK) rc = dev_upload(&g.d_rowmask, rows.data(), rows.size());
             // large sides with one shared kernel of more than one tap: grid once per (channel,
-            // sample) and fold all classes (alias_fold.cu).  With one tap (the taper) re-gridding
-            // per class is cheaper than moving the folded grids through HBM (measured at N = 512:
-            // 0.24 s against 0.44 s per dense integration).  EPIC_NO_ALIAS=1 keeps the per-class
-            // gridding.
-            const char *na = std::getenv("EPIC_NO_ALIAS");
-            if (rc == EPIC_OK && !g.tensor && g.Q1 == 8 && p->nker == 1 && p->K > 1 && !(na && na[0] == '1')) {
+            // sample) and fold all classes (alias_fold.cu), for the FP32 and the two-stage tensor
+            // kernel.  With one tap (the taper) re-gridding per class is cheaper than moving the
+            // folded grids through HBM (measured at N = 512: 0.24 s against 0.44 s per dense
+            // integration).  EPIC_NO_ALIAS=1 keeps the per-class gridding.
+            if (rc == EPIC_OK && fold_ok) {
                 std::vector<short2> j0;
                 std::vector<uint32_t> bseg;
                 std::vector<int> boff;
@@ -543,6 +547,7 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                     g.alias = rc == EPIC_OK;
                 }
             }
+            if (rc == EPIC_OK && g.tensor && !g.tc_regular && !g.alias) rc = EPIC_ERR_UNSUPPORTED;
         }
         if (rc == EPIC_OK) rc = dev_upload(&g.d_chans, g.chans.data(), g.chans.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_out_off, offs.data(), offs.size());
@@ -585,7 +590,16 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         } else {
             epic::build_dft_operand(precision == EPIC_TC_SPLIT_BF16, ops);
             rc = dev_upload(&p->d_dft, reinterpret_cast<const uint8_t *>(ops.data()), ops.size() * 2);
-            if (rc == EPIC_OK) rc = p->tc_form == 2 ? epic::prepare_tc_dual(p) : epic::prepare_tc(p);
+            // the dual kernel's dynamic shared memory: the largest any of its groups needs (a
+            // large side on the fold path needs the operands and the grid only)
+            size_t dual = 0;
+            for (const auto &g : p->groups)
+                if (g.tensor) {
+                    if (g.alias && p->tc_form != 2) rc = EPIC_ERR_UNSUPPORTED;   // only the two-stage form folds
+                    dual = std::max(dual, g.tc_regular ? epic::tc_dual_smem_bytes(n_ant, p->K)
+                                                       : epic::tc_dual_fold_smem_bytes());
+                }
+            if (rc == EPIC_OK) rc = p->tc_form == 2 ? epic::prepare_tc_dual(p, dual) : epic::prepare_tc(p);
         }
     }
     for (const auto &g : p->groups) {

@@ -147,7 +147,7 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
                  const uint8_t *__restrict__ dft_ops, int A, int C, int T, int N, int Q1, int n_items, int n_tau,
                  float *__restrict__ partial, int *__restrict__ status, long long wait_budget, int withhold_mma,
                  const float *__restrict__ dfreq, const float4 *__restrict__ dtab,
-                 const uint16_t *__restrict__ first)
+                 const uint16_t *__restrict__ first, const float2 *__restrict__ gf, int accumulate)
 {
     constexpr int P = 2;
     constexpr bool kBF16 = VAR == 2;
@@ -202,7 +202,10 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
         tc::bulk_g2s(opX + kPart, dft_ops + kPart, kPart, &bar_x);
     }
 
-    // ---- set-up: phase-folded gains and taps, the largest gain for the FP16 scale
+    // ---- set-up: phase-folded gains and taps, the largest gain for the FP16 scale.  With gf
+    // (large grid sides) the class grids arrive folded from alias_fold_kernel: no per-antenna
+    // tables (the launch does not even allocate them), only the largest gain for the scale.
+    const bool lg = gf != nullptr;
     float gmax = 0.f;
     for (int a = simt ? tid : A; a < A; a += kSimt) {
         const short2 k = cells[static_cast<size_t>(c) * A + a];
@@ -211,16 +214,16 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
         for (int p = 0; p < P; p++) {
             const float2 g = gains ? gains[(static_cast<size_t>(c) * A + a) * P + p] : make_float2(1.f, 0.f);
             const float2 gg = cmul(g, ph);
-            gp[a * P + p] = gg;
+            if (!lg) gp[a * P + p] = gg;
             gmax = fmaxf(gmax, sqrtf(gg.x * gg.x + gg.y * gg.y));
         }
     }
-    for (int i = simt ? tid : KK; i < KK; i += kSimt) {
+    for (int i = simt && !lg ? tid : KK; i < KK; i += kSimt) {
         const int dy = i / K - hk, dx = i % K - hk;
         tapw[i] = cmul(kern[i], twN[((dx * hx + dy * hy) % N + N) % N]);
     }
     for (int i = simt ? tid : P * BUF; i < P * BUF; i += kSimt) G[i] = make_float2(0.f, 0.f);
-    if (simt && t0 < t1) {
+    if (simt && t0 < t1 && !lg) {
         const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(t0) * C + c) * AP);
         for (int w = tid; w < APW; w += kSimt) stage[w] = row[w];
     }
@@ -238,13 +241,16 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
         float gm = 0.f;
         for (int w = 0; w < kSimt / 32; w++) gm = fmaxf(gm, red[w]);
         float wsum = 0.f;
-        for (int i = 0; i < KK; i++) wsum += sqrtf(tapw[i].x * tapw[i].x + tapw[i].y * tapw[i].y);
+        for (int i = 0; i < KK; i++) {
+            const float2 w = lg ? kern[i] : tapw[i];       // the class phases have unit modulus
+            wsum += sqrtf(w.x * w.x + w.y * w.y);
+        }
         const float bound = 2.f * static_cast<float>(A) * 11.3137085f * gm * wsum;
         int e2 = 0;
         if (bound > 0.f) e2 = static_cast<int>(floorf(log2f(16384.f / bound)));
         scale = ldexpf(1.f, max(-40, min(40, e2)));
     }
-    for (int i = simt ? tid : AP; i < AP; i += kSimt) gp[i] = cscale(gp[i], scale);
+    for (int i = simt && !lg ? tid : AP; i < AP; i += kSimt) gp[i] = cscale(gp[i], scale);
     if (simt) {
         // zero this warp's time sums: lanes 32 (w mod 4) .., columns kColAcc + 64 (w / 4) ..
         uint32_t z[32];
@@ -371,14 +377,30 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
             }
         };
 
+        // large grid sides: sample t's folded class grid (gf [T][n_items][P][64][64]) into G,
+        // scaled like the gridded voltages
+        auto load_grid = [&](int t) {
+            const float4 *src = reinterpret_cast<const float4 *>(gf + (static_cast<size_t>(t) * n_items + item) * P * 4096);
+            for (int i = tid; i < P * 4096 / 2; i += kSimt) {
+                const float4 f = __ldg(src + i);
+                const int e = 2 * i, pl = e >> 12, y = (e >> 6) & 63, x = e & 63;
+                G[pl * BUF + y * S64 + x] = make_float2(f.x * scale, f.y * scale);
+                G[pl * BUF + y * S64 + x + 1] = make_float2(f.z * scale, f.w * scale);
+            }
+        };
+
         // prologue: sample t0 gridded, the bytes of t0 + 1 staged
         if (t0 < t1) {
-            unpack(t0);
-            tc::named_bar_sync(kBarSimt, kSimt);
-            grid();
-            uint32_t pre[kPreW];
-            load_stage(t0 + 1, pre);
-            put_stage(pre);
+            if (lg) {
+                load_grid(t0);
+            } else {
+                unpack(t0);
+                tc::named_bar_sync(kBarSimt, kSimt);
+                grid();
+                uint32_t pre[kPreW];
+                load_stage(t0 + 1, pre);
+                put_stage(pre);
+            }
             tc::named_bar_sync(kBarSimt, kSimt);
         }
         // Iteration t: G(t) -> G16 (row stage of t starts); unpack and grid t+1 while it
@@ -410,13 +432,17 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
             }
             tc::named_bar_sync(kBarSimt, kSimt);        // G has been read, es is free
 
-            // ---- sample t+1: unpack and grid while the row stage of t runs
+            // ---- sample t+1: unpack and grid (or load its folded grid) while the row stage of t runs
             uint32_t pre[kPreW];
-            load_stage(t + 2, pre);
+            if (!lg) load_stage(t + 2, pre);
             if (nxt) {
-                unpack(t + 1);
-                tc::named_bar_sync(kBarSimt, kSimt);
-                grid();
+                if (lg) {
+                    load_grid(t + 1);
+                } else {
+                    unpack(t + 1);
+                    tc::named_bar_sync(kBarSimt, kSimt);
+                    grid();
+                }
             }
 
             // ---- a5, a6: products of sample t-1 (column stage in D2) into the time sums
@@ -466,7 +492,7 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
                     tc::mbar_arrive(&bar_h);
                 }
             }
-            if (t + 2 < t1) put_stage(pre);             // bytes of t+2 for the next iteration
+            if (!lg && t + 2 < t1) put_stage(pre);      // bytes of t+2 for the next iteration
             tc::named_bar_sync(kBarSimt, kSimt);
             if (abort_flag) break;
             ph ^= 1u;
@@ -488,8 +514,13 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
         for (int j = 0; j < 16; j++) {
             const int mx = 32 * hp + 16 * part + j;
             const uint32_t *a4 = j < 8 ? s0 + 4 * j : s1 + 4 * (j - 8);
-            dst[my * M64 + mx] = make_float4(__uint_as_float(a4[0]) * inv, __uint_as_float(a4[1]) * inv,
-                                             __uint_as_float(a4[2]) * inv, __uint_as_float(a4[3]) * inv);
+            float4 o = make_float4(__uint_as_float(a4[0]) * inv, __uint_as_float(a4[1]) * inv,
+                                   __uint_as_float(a4[2]) * inv, __uint_as_float(a4[3]) * inv);
+            if (accumulate) {                              // a later time batch of a large-side group
+                const float4 q = dst[my * M64 + mx];
+                o = make_float4(q.x + o.x, q.y + o.y, q.z + o.z, q.w + o.w);
+            }
+            dst[my * M64 + mx] = o;
         }
     }
     // an aborted CTA may still have MMAs in flight: give them a bounded chance to land
@@ -515,15 +546,6 @@ size_t dual_smem(int A, int K)
 }
 
 template <int VAR, int KC>
-int prepare_dual_t(const epic_plan_s *plan)
-{
-    return cudaFuncSetAttribute(tc_dual64_kernel<VAR, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(dual_smem(plan->A, plan->K))) == cudaSuccess
-               ? EPIC_OK
-               : EPIC_ERR_UNSUPPORTED;
-}
-
-template <int VAR, int KC>
 int launch_dual_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau_out,
                   cudaStream_t stream)
 {
@@ -535,7 +557,24 @@ int launch_dual_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const 
         v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN, g.d_sched, g.d_nrounds, g.rmax,
         plan->d_dft, plan->A, plan->C, T, g.N, g.Q1, g.n_items, n_tau, g.d_partial, plan->d_status,
         plan->wait_budget, plan->test_withhold_mma, plan->d_dfreq, plan->delays ? plan->d_dtab : nullptr,
-        g.d_first);
+        g.d_first, nullptr, 0);
+    return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
+// Large grid sides: one time batch of folded class grids (gf), time sums into
+// partial slot 0 (added to it when accumulate is set).  Shared memory: the
+// operands and G only.
+size_t dual_fold_smem() { return 4 * static_cast<size_t>(kPart) + sizeof(float2) * 2 * M64 * S64; }
+
+template <int VAR, int KC>
+int launch_dual_fold_t(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, const float2 *gf, int nb,
+                       bool accumulate, cudaStream_t stream)
+{
+    const dim3 grid(static_cast<unsigned>(g.n_items));
+    tc_dual64_kernel<VAR, KC><<<grid, kDualThreads, dual_fold_smem(), stream>>>(
+        nullptr, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN, g.d_sched, g.d_nrounds, g.rmax,
+        plan->d_dft, plan->A, plan->C, nb, g.N, g.Q1, g.n_items, 1, g.d_partial, plan->d_status,
+        plan->wait_budget, plan->test_withhold_mma, plan->d_dfreq, nullptr, g.d_first, gf, accumulate ? 1 : 0);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -561,10 +600,24 @@ int dual_dispatch(int precision, int K, F &&f)
 
 size_t tc_dual_smem_bytes(int A, int K) { return dual_smem(A, K); }
 
-int prepare_tc_dual(const epic_plan_s *plan)
+int prepare_tc_dual(const epic_plan_s *plan, size_t smem)
 {
     return dual_dispatch(plan->precision, plan->K, [&](auto vv, auto kc) {
-        return prepare_dual_t<decltype(vv)::value, decltype(kc)::value>(plan);
+        return cudaFuncSetAttribute(tc_dual64_kernel<decltype(vv)::value, decltype(kc)::value>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) == cudaSuccess
+                   ? EPIC_OK
+                   : EPIC_ERR_UNSUPPORTED;
+    });
+}
+
+size_t tc_dual_fold_smem_bytes() { return dual_fold_smem(); }
+
+int launch_tc_dual_fold(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, const float2 *gf, int nb,
+                        bool accumulate, cudaStream_t stream)
+{
+    return dual_dispatch(plan->precision, plan->K, [&](auto vv, auto kc) {
+        return launch_dual_fold_t<decltype(vv)::value, decltype(kc)::value>(plan, g, gains, gf, nb, accumulate,
+                                                                            stream);
     });
 }
 

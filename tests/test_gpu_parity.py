@@ -228,12 +228,13 @@ def test_kernel_taper_lwa_full_size_sampled_channels():
 def test_dense_workload_full_size_sampled_channel():
     """The dense 2048-antenna array (256 channels, 500 spectra, 7x7 kernel, 512
     grid) at full size in the benchmark's launch configuration; one channel of
-    the literal form and of the kernel-taper form against the oracle."""
+    the literal form (fold path), the kernel-taper form and the split-FP16
+    tensor form (fold path) against the oracle."""
     wl = synth.dense()
     chans = [129]
     ref = _oracle(wl, channels=chans)
-    for flags in (0, epic.EPIC_KERNEL_TAPER):
-        gpu, p = run_gpu(wl, flags=flags)
+    for kw in (dict(flags=0), dict(flags=epic.EPIC_KERNEL_TAPER), dict(precision=epic.EPIC_TC_SPLIT_FP16)):
+        gpu, p = run_gpu(wl, **kw)
         got = p.split(gpu)[chans[0]].ravel()
         assert peak_rel_err(got, ref, wl.grid_n[chans], 2).max() < FP32_TOL
         p.close()

@@ -38,6 +38,15 @@ def test_tensor_split_fp16(A, C, T, N, K):
     assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16).max() < SPLIT_TOL
 
 
+@pytest.mark.parametrize("precision,tol", [(epic.EPIC_TC_SPLIT_FP16, SPLIT_TOL), (epic.EPIC_TC_SPLIT_BF16, BF16_TOL)])
+def test_tensor_large_grid_fold_path(precision, tol):
+    """At N = 512 the tensor plan takes the fold path: every class grid is formed
+    once per (channel, sample) by alias_fold_kernel and the two-stage tensor
+    kernel loads it instead of gridding."""
+    wl = synth.random_small(A=150, P=2, C=2, T=7, N=512, K=5, seed=331)
+    assert _cmp(wl, precision).max() < tol
+
+
 def test_tensor_single_fp16():
     wl = synth.random_small(A=256, P=2, C=2, T=6, N=128, K=5, seed=310)
     err = _cmp(wl, epic.EPIC_TC_FP16).max()
