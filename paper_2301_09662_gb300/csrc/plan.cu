@@ -539,6 +539,9 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                     const size_t per_sample = static_cast<size_t>(g.n_items) * n_pol * 64 * 64 * sizeof(float2);
                     constexpr size_t kBudget = size_t(4) << 30;   // folded grids of one time batch
                     g.alias_tb = static_cast<int>(std::max<size_t>(1, std::min<size_t>(max_spectra, kBudget / per_sample)));
+                    // EPIC_ALIAS_BATCH caps the time batch (tests: several batches on a small case)
+                    const char *ab = std::getenv("EPIC_ALIAS_BATCH");
+                    if (ab && std::atoi(ab) > 0) g.alias_tb = std::min(g.alias_tb, std::atoi(ab));
                     rc = dev_upload(&g.d_j0, j0.data(), j0.size());
                     if (rc == EPIC_OK) rc = dev_upload(&g.d_bseg, bseg.data(), std::max<size_t>(1, bseg.size()));
                     if (rc == EPIC_OK) rc = dev_upload(&g.d_boff, boff.data(), boff.size());

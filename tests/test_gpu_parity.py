@@ -174,6 +174,18 @@ def test_large_grid_fold_path_matches_per_class_path_and_is_deterministic(monkey
     assert peak_rel_err(a, ref, wl.grid_n, 2).max() < FP32_TOL
 
 
+@pytest.mark.parametrize("P,precision", [(1, epic.EPIC_FP32), (2, epic.EPIC_FP32), (2, epic.EPIC_TC_SPLIT_FP16)])
+def test_large_grid_fold_path_in_time_batches(P, precision, monkeypatch):
+    """The fold path sums time batches into one partial slot: 7 spectra in
+    batches of 3 (3 + 3 + 1) give the oracle's image, single and dual
+    polarisation, FP32 and split-FP16 tensor kernels."""
+    monkeypatch.setenv("EPIC_ALIAS_BATCH", "3")
+    wl = synth.random_small(A=92, P=P, C=2, T=7, N=512, K=3, seed=41 + P)   # A*P a multiple of 4: the M = 64 path
+    gpu, _ = run_gpu(wl, precision=precision)
+    ref = oracle.workload_image(wl)
+    assert peak_rel_err(gpu, ref, wl.grid_n, P).max() < FP32_TOL
+
+
 def test_uneven_workload_full_size_sampled_channels():
     """192 channels over 30-80 MHz in three grid-side groups (64/96/128), 1000
     spectra, one graph launch per integration; one channel of each group against
