@@ -39,6 +39,27 @@ def test_series_images_equal_block_integrations(flags, precision):
         assert peak_rel_err(got[i], ref, wl.grid_n, 2).max() < FP32_TOL
 
 
+@pytest.mark.parametrize("precision", [epic.EPIC_FP32, epic.EPIC_TC_SPLIT_FP16])
+def test_series_on_a_large_grid_side(precision):
+    """At N = 512 a plain integration takes the fold path; a series needs one
+    time chunk per image, so it runs the per-class gridding of the same plan."""
+    import torch
+    spi = 3
+    wl = synth.random_small(A=64, P=2, C=1, T=6, N=512, K=3, seed=405)
+    p = epic.Plan.from_workload(wl, precision=precision)
+    v, g = torch_inputs(wl)
+    out = p.image_series(v, spi, g)
+    whole = p.image(v, g)
+    torch.cuda.synchronize()
+    assert p.status() == epic.EPIC_OK
+    got = out.cpu().numpy().astype(np.complex128)
+    for i in range(wl.T // spi):
+        ref = oracle.workload_image(_block(wl, i * spi, (i + 1) * spi))
+        assert peak_rel_err(got[i], ref, wl.grid_n, 2).max() < FP32_TOL
+    ref = oracle.workload_image(wl)
+    assert peak_rel_err(whole.cpu().numpy().astype(np.complex128), ref, wl.grid_n, 2).max() < FP32_TOL
+
+
 def test_series_mixed_grid_sides_and_single_pol():
     import torch
     wl = synth.random_small(A=30, P=1, C=3, T=9, N=64, K=3, seed=402)
