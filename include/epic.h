@@ -119,7 +119,12 @@ enum {
  *                  EPIC_ANTENNA_KERNELS
  *
  * Uses the current CUDA device.  Allocates device memory (tables and
- * workspace) and returns EPIC_ERR_NOMEM if that fails.  Returns
+ * workspace) and returns EPIC_ERR_NOMEM if that fails.  Channels with a
+ * 512 grid side and one shared kernel wider than one tap are imaged by
+ * gridding each (channel, sample) once and folding the 64 pixel classes from
+ * it: their workspace adds the folded class grids of one time batch, up to
+ * 4 GiB (C * 64 * n_pol * 32 KB per spectrum, batched); the environment
+ * variable EPIC_NO_ALIAS=1 keeps the per-class gridding instead.  Returns
  * EPIC_ERR_OUT_OF_GRID when some antenna footprint k_a +- (K-1)/2 leaves
  * [0, N_c) in some channel; EPIC_ERR_UNSUPPORTED for a grid side, precision or
  * size this build does not provide.
@@ -230,8 +235,10 @@ int epic_image_host(epic_plan_t plan, const uint8_t *ci4_host, const float *gain
  * spectra_per_image).  out_c64 holds n_img consecutive outputs of
  * epic_out_floats(plan) floats each.  Other arguments as for epic_image.
  * Returns EPIC_ERR_ARG if n_spectra is not a multiple of spectra_per_image or
- * exceeds max_spectra.  Asynchronous; allocates nothing; runs as direct
- * launches (no graph).
+ * exceeds max_spectra, and EPIC_ERR_UNSUPPORTED for a tensor-form plan whose
+ * 512-side channels only fit the folded path (series need one time chunk per
+ * image, which that path does not provide).  Asynchronous; allocates nothing;
+ * runs as direct launches (no graph).
  */
 int epic_image_series(epic_plan_t plan, const uint8_t *ci4, const float *gains_c64,
                       int n_spectra, int spectra_per_image, float *out_c64, void *cuda_stream);
