@@ -41,16 +41,17 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic of one launch of the dominant kernel from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload, with the
 # hash of the kernel source it was taken on; ignored once the source changes.
-# lwa: one full 64-channel launch captured: 34 701 824 B read (the 32.8 MB ci4
-# input plus tables) + 108 019 968 B written (time-chunk partial sums that spill
+# lwa: one full 64-channel launch captured: 34 186 496 B read (the 32.8 MB ci4
+# input plus tables) + 74 264 576 B written (time-chunk partial sums that spill
 # out of L2 before the epilogue reads them).
-NCU_TRAFFIC = {"lwa": (107_952_896, "05a22060f3c0276e")}
-# What the same ncu capture shows binds the kernel (full set, one LWA launch): shared-memory
-# wavefronts per SM cycle at the capture's clock, against 1 per cycle (128 B/clk).
+NCU_TRAFFIC = {"lwa": (108_451_072, "a77b2401344b86ba")}
+# What a full-set ncu capture of the same device code (3 651 749 248 warp instructions per
+# LWA launch in both captures) shows binds the kernel: shared-memory wavefronts per SM cycle
+# at the capture's clock, against 1 per cycle (128 B/clk).
 NCU_LIMITER = {"lwa": ({"unit": "shared-memory wavefronts per SM cycle", "achieved": 0.80, "peak": 1.0,
                         "wavefronts_per_launch": 1_762_623_285, "issue_active_pct": 39.5,
                         "fma_pipe_pct": 35.4},
-                       "05a22060f3c0276e")}
+                       "a77b2401344b86ba")}
 
 
 def parse():
@@ -106,12 +107,12 @@ def fp32_flops_per_spectrum(A, K, N):
 
 
 def kernel_source_hash():
-    """Hash of the dominant kernel's device code (the transform_products
-    function and the fp32_reg64_kernel template, and the transform headers they
-    include)."""
+    """Hash of the dominant kernel's device code (the register transforms, the
+    transform_products function and the fp32_reg64_kernel template, and the
+    64-point transform headers they include)."""
     csrc = os.path.join(ROOT, "paper_2301_09662_gb300", "csrc")
     src = open(os.path.join(csrc, "fp32_reg64.cu")).read()
-    start = src.index("template <int P, int TS, bool CLEAR>")
+    start = src.index("// Register transforms of the folded side M")
     end = src.index("// Large grid sides: the folded grids", start)
     h = hashlib.sha256(src[start:end].encode())
     for f in ("fft64.cuh", "dft_small.cuh"):

@@ -172,12 +172,12 @@ int launch_tc_pipe(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
                    cudaStream_t stream);
 void build_dft_rows(bool bf16, std::vector<uint16_t> &words);
 
-// M = 64 register-transform kernel (fp32_reg64.cu)
-size_t reg64_smem_bytes(int P, int TS, int A, int K, int nker);
+// Register-transform kernels, fold side M = 64 or 48 (fp32_reg64.cu)
+size_t reg64_smem_bytes(int M, int P, int TS, int A, int K, int nker);
 int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                  cudaStream_t stream);
-// Gridding schedule of the M = 64 kernel for the channels of one group (plan.cu).
-int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
+// Gridding schedule of the register-transform kernels for the channels of one group (plan.cu).
+int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, int M, const std::vector<int> &chans,
                          std::vector<uint32_t> &desc, std::vector<int> &nrounds, int &rmax,
                          std::vector<unsigned long long> &rowmask, std::vector<uint16_t> &first);
 

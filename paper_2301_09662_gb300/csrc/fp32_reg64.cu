@@ -1,6 +1,6 @@
-// FP32 form, folded side M = 64: the imaging kernel used for grid sides 64,
-// 128, 256 and 512 (one pixel class of one channel per CTA, as in
-// fp32_image.cu; see the derivation there).
+// FP32 form, folded side M = 64 or 48: the imaging kernel used for grid sides
+// 64, 128, 256, 512 (M = 64) and 96 (M = 48), one pixel class of one channel
+// per CTA, as in fp32_image.cu (see the derivation there).
 //
 // What differs from the general kernel, and why (measured: the general kernel
 // is bound by the shared-memory pipe, ~17 000 wavefronts per CTA and sample):
@@ -9,7 +9,7 @@
 //    segments touch the same cell and no two lanes of a half-warp hit the same
 //    bank; warp w owns the grid rows y = w (mod 8), so a round is a plain
 //    read-add-write of K cells per lane with no inter-warp race;
-//  * the 64-point transforms run in registers (one row or column per thread),
+//  * the M-point transforms run in registers (one row or column per thread),
 //    so each axis costs one shared-memory read and one write;
 //  * two time samples per iteration share the schedule, the twiddles and the
 //    synchronisation;
@@ -18,6 +18,7 @@
 #include <type_traits>
 
 #include "epic_internal.cuh"
+#include "fft48.cuh"
 #include "fft64.cuh"
 
 namespace epic {
@@ -33,38 +34,52 @@ template <> struct Acc64<2> { using T = float4; };
 
 constexpr int NPOS64 = M64 * M64 / kThreads;   // pixels whose time sums a thread keeps
 
-// a4-a6 on the TS x P planes of G ([ts][p][y][x], x < 64 at stride S64): rows
-// then columns, one 64-point transform per thread, then the products of every
+// Register transforms of the folded side M: 64 points (8 x 8) or 48 (8 x 6, grid side 96).
+template <int M, class Sink>
+__device__ __forceinline__ void fft_reg(float2 (&x)[M], Sink &&sink)
+{
+    static_assert(M == 64 || M == 48, "folded sides 64 and 48");
+    if constexpr (M == 64) {
+        fft64p_stage1(x);
+        fft64p_stage2(x, sink);
+    } else {
+        fft48p_stage1(x);
+        fft48p_stage2(x, sink);
+    }
+}
+
+// a4-a6 on the TS x P planes of G ([ts][p][y][x], x < M at stride M + 1): rows
+// then columns, one M-point transform per thread, then the products of every
 // pixel added to the thread's time sums; CLEAR zeroes the planes for the next
 // gridding.  Rows outside rows_used are empty and stay zero.
-template <int P, int TS, bool CLEAR>
+template <int M, int P, int TS, bool CLEAR>
 __device__ __forceinline__ void transform_products(float2 *G, unsigned long long rows_used,
-                                                   typename Acc64<P>::T (&acc)[NPOS64], int tid)
+                                                   typename Acc64<P>::T (&acc)[M * M / kThreads], int tid)
 {
-    constexpr int BUF = M64 * S64;
-    for (int q = tid; q < TS * P * M64; q += kThreads) {
-        if (!((rows_used >> (q % M64)) & 1ull)) continue;   // empty row: stays zero
-        float2 *line = G + (q / M64) * BUF + (q % M64) * S64;
-        float2 x[64];
+    constexpr int S = M + 1, BUF = M * S, NPOS = M * M / kThreads;
+    for (int q = tid; q < TS * P * M; q += kThreads) {
+        if (!((rows_used >> (q % M)) & 1ull)) continue;   // empty row: stays zero
+        float2 *line = G + (q / M) * BUF + (q % M) * S;
+        float2 x[M];
 #pragma unroll
-        for (int i = 0; i < 64; i++) x[i] = line[i];
-        fft64p_stage1(x);
-        fft64p_stage2(x, [&](int k, float2 val) { line[k] = val; });
+        for (int i = 0; i < M; i++) x[i] = line[i];
+        fft_reg<M>(x, [&](int k, float2 val) { line[k] = val; });
     }
     __syncthreads();
-    for (int q = tid; q < TS * P * M64; q += kThreads) {
-        float2 *col = G + (q / M64) * BUF + (q % M64);
-        float2 x[64];
+    for (int q = tid; q < TS * P * M; q += kThreads) {
+        float2 *col = G + (q / M) * BUF + (q % M);
+        float2 x[M];
 #pragma unroll
-        for (int i = 0; i < 64; i++) x[i] = col[i * S64];
-        fft64p_stage1(x);
-        fft64p_stage2(x, [&](int k, float2 val) { col[k * S64] = val; });
+        for (int i = 0; i < M; i++) x[i] = col[i * S];
+        fft_reg<M>(x, [&](int k, float2 val) { col[k * S] = val; });
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < NPOS64; r++) {
+    for (int r = 0; r < NPOS; r++) {
         const int pos = tid + r * kThreads;
-        const int idx = (pos >> 6) * S64 + (pos & 63);
+        int idx;
+        if constexpr (M == 64) idx = (pos >> 6) * S64 + (pos & 63);
+        else idx = (pos / M) * S + (pos % M);
 #pragma unroll
         for (int ts = 0; ts < TS; ts++) {
             const float2 f0 = G[(ts * P) * BUF + idx];
@@ -83,12 +98,13 @@ __device__ __forceinline__ void transform_products(float2 *G, unsigned long long
     }
 }
 
-// Grid buffers: G[ts][p][y][x] with x < 64 at stride S64.  KC > 0 fixes the
+// Folded side M (64, or 48 for grid side 96).  Grid buffers: G[ts][p][y][x] with
+// x < M at stride M + 1.  KC > 0 fixes the
 // kernel side at compile time (the gridding loop then unrolls fully); KC = 0
 // takes it from K.  DL: voltages take the geometric-delay phase of the
 // per-integration table dtab (Sec. 2.2 delay correction), once per antenna.  rowmask[ci] marks the folded rows any footprint touches:
 // the others stay zero and their row transforms are skipped.
-template <int P, int TS, int KC, bool DL>
+template <int M, int P, int TS, int KC, bool DL>
 __global__ void __launch_bounds__(kThreads, 1)
 fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
                   const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K_rt,
@@ -100,12 +116,13 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                   const float *__restrict__ dfreq, const float4 *__restrict__ dtab)
 {
     const int K = KC > 0 ? KC : K_rt;
-    constexpr int NPOS = NPOS64;                 // 16 pixels per thread
-    constexpr int BUF = M64 * S64;               // one [y][x] plane
+    constexpr int NPOS = M * M / kThreads;       // pixels per thread (16 at M = 64, 9 at 48)
+    constexpr int S = M + 1;                     // padded row stride (float2)
+    constexpr int BUF = M * S;                   // one [y][x] plane
     extern __shared__ float4 smem_raw[];
     const int AP = A * P, KK = K * K, hk = (K - 1) / 2;
     const int APW = (AP + 3) >> 2;
-    float2 *G = reinterpret_cast<float2 *>(smem_raw);          // [TS][P][64][65]
+    float2 *G = reinterpret_cast<float2 *>(smem_raw);          // [TS][P][M][M + 1]
     float2 *es = G + TS * P * BUF;                             // [TS][A*P]
     float2 *gp = es + TS * AP;                                 // [A*P]
     float2 *tapw = gp + AP;                                    // [nker][K*K]
@@ -215,12 +232,14 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                     // cell += w e as two packed FMAs: w.x (e.x, e.y) + (-w.y, w.y) (e.y, e.x)
                     const float2 w = wrow[dx];
                     const float2 wr = make_float2(w.x, w.x), wi = make_float2(-w.y, w.y);
-                    const int x = (x0 + dx) & (M64 - 1);
+                    int x;
+                    if constexpr (M == 64) x = (x0 + dx) & (M64 - 1);
+                    else x = x0 + dx >= M ? x0 + dx - M : x0 + dx;   // x0 < M, dx < K <= 15
 #pragma unroll
                     for (int ts = 0; ts < TS; ts++)
 #pragma unroll
                         for (int p = 0; p < P; p++) {
-                            float2 *cell = G + (ts * P + p) * BUF + y * S64 + x;
+                            float2 *cell = G + (ts * P + p) * BUF + y * S + x;
                             *cell = pfma(wi, eswap[ts][p], pfma(wr, e[ts][p], *cell));
                         }
                 }
@@ -230,7 +249,7 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         __syncthreads();
 
         // ---- a4, a5, a6: transforms, products summed over time; planes cleared for the next group
-        transform_products<P, TS, true>(G, rows_used, acc, tid);
+        transform_products<M, P, TS, true>(G, rows_used, acc, tid);
 #pragma unroll
         for (int ts = 0; ts < TS; ts++)
 #pragma unroll
@@ -241,7 +260,7 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         __syncthreads();
     }
 
-    float *dst = partial + (static_cast<size_t>(tau) * n_items + item) * (M64 * M64) * (P == 2 ? 4 : 1);
+    float *dst = partial + (static_cast<size_t>(tau) * n_items + item) * (M * M) * (P == 2 ? 4 : 1);
 #pragma unroll
     for (int r = 0; r < NPOS; r++) {
         const int pos = tid + r * kThreads;
@@ -294,7 +313,7 @@ fp32_fold64_kernel(const float2 *__restrict__ gf, int nb, int accumulate, float 
         issue(bt + 1);
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // sample bt has landed (this thread's part)
         __syncthreads();
-        transform_products<P, 1, false>(Gb + (bt & 1) * P * BUF, ~0ull, acc, tid);
+        transform_products<64, P, 1, false>(Gb + (bt & 1) * P * BUF, ~0ull, acc, tid);
         __syncthreads();                             // buffer bt mod 2 is refilled two samples on
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -306,22 +325,22 @@ fp32_fold64_kernel(const float2 *__restrict__ gf, int nb, int accumulate, float 
     }
 }
 
-template <int P, int TS>
+template <int M, int P, int TS>
 size_t reg64_smem(int A, int K, int nker)
 {
     const int AP = A * P;
-    size_t b = sizeof(float2) * (static_cast<size_t>(TS) * P * M64 * S64 + static_cast<size_t>(TS) * AP + AP +
+    size_t b = sizeof(float2) * (static_cast<size_t>(TS) * P * M * (M + 1) + static_cast<size_t>(TS) * AP + AP +
                                  static_cast<size_t>(nker) * K * K);
     b += sizeof(uint32_t) * TS * ((AP + 3) / 4);
     return (b + 15) & ~static_cast<size_t>(15);
 }
 
-template <int P, int TS, int KC, bool DL>
+template <int M, int P, int TS, int KC, bool DL>
 int launch_reg64_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau_out,
                    cudaStream_t stream)
 {
-    auto kfn = fp32_reg64_kernel<P, TS, KC, DL>;
-    const size_t smem = reg64_smem<P, TS>(plan->A, plan->K, plan->nker);
+    auto kfn = fp32_reg64_kernel<M, P, TS, KC, DL>;
+    const size_t smem = reg64_smem<M, P, TS>(plan->A, plan->K, plan->nker);
     int n_tau = choose_tau(plan, g, T);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
@@ -333,69 +352,80 @@ int launch_reg64_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
-template <int P, int TS, int KC>
+template <int M, int P, int TS, int KC>
 int prepare_reg64_t(const epic_plan_s *plan)
 {
-    const int smem = static_cast<int>(reg64_smem<P, TS>(plan->A, plan->K, plan->nker));
-    const bool ok =
-        cudaFuncSetAttribute(fp32_reg64_kernel<P, TS, KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
-            cudaSuccess &&
-        cudaFuncSetAttribute(fp32_reg64_kernel<P, TS, KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
-            cudaSuccess;
+    const int smem = static_cast<int>(reg64_smem<M, P, TS>(plan->A, plan->K, plan->nker));
+    const bool ok = cudaFuncSetAttribute(fp32_reg64_kernel<M, P, TS, KC, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+                    cudaFuncSetAttribute(fp32_reg64_kernel<M, P, TS, KC, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
     return ok ? EPIC_OK : EPIC_ERR_UNSUPPORTED;
 }
 
-// Which instantiation serves a plan: dual polarisation gets kernels specialised
-// for the kernel sides in use here (1: image-domain taper, 5: LWA-like,
-// 7: dense); anything else runs the generic loop.
+// Which instantiation serves a plan: at M = 64 dual polarisation gets kernels
+// specialised for the kernel sides in use here (1: image-domain taper, 5:
+// LWA-like, 7: dense), at M = 48 (grid side 96) for side 5; anything else runs
+// the generic loop.
 struct Reg64Key {
-    int P, TS, KC;
+    int M, P, TS, KC;
 };
 
 Reg64Key reg64_key(const epic_plan_s *plan, const GroupCfg &g)
 {
     int kc = 0;
-    if (plan->P == 2 && (plan->K == 1 || plan->K == 5 || plan->K == 7)) kc = plan->K;
-    return {plan->P, g.ts, kc};
+    if (plan->P == 2 && (plan->K == 5 || (g.M == 64 && (plan->K == 1 || plan->K == 7)))) kc = plan->K;
+    return {g.M, plan->P, g.ts, kc};
+}
+
+template <int V>
+using IC = std::integral_constant<int, V>;
+
+template <int M, class F>
+int reg64_dispatch_m(const Reg64Key &k, F &&f)
+{
+    if (k.P == 2) {
+        auto with_ts = [&](auto ts) {
+            switch (k.KC) {
+            case 5: return f(IC<M>{}, IC<2>{}, ts, IC<5>{});
+            case 1:
+                if constexpr (M == 64) return f(IC<M>{}, IC<2>{}, ts, IC<1>{});
+                else return f(IC<M>{}, IC<2>{}, ts, IC<0>{});
+            case 7:
+                if constexpr (M == 64) return f(IC<M>{}, IC<2>{}, ts, IC<7>{});
+                else return f(IC<M>{}, IC<2>{}, ts, IC<0>{});
+            default: return f(IC<M>{}, IC<2>{}, ts, IC<0>{});
+            }
+        };
+        return k.TS == 2 ? with_ts(IC<2>{}) : with_ts(IC<1>{});
+    }
+    return k.TS == 2 ? f(IC<M>{}, IC<1>{}, IC<2>{}, IC<0>{}) : f(IC<M>{}, IC<1>{}, IC<1>{}, IC<0>{});
 }
 
 template <class F>
 int reg64_dispatch(const Reg64Key &k, F &&f)
 {
-    if (k.P == 2) {
-        if (k.TS == 2) {
-            switch (k.KC) {
-            case 1: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{}, std::integral_constant<int, 1>{});
-            case 5: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{}, std::integral_constant<int, 5>{});
-            case 7: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{}, std::integral_constant<int, 7>{});
-            default: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{}, std::integral_constant<int, 0>{});
-            }
-        }
-        switch (k.KC) {
-        case 1: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 1>{}, std::integral_constant<int, 1>{});
-        case 5: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 1>{}, std::integral_constant<int, 5>{});
-        case 7: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 1>{}, std::integral_constant<int, 7>{});
-        default: return f(std::integral_constant<int, 2>{}, std::integral_constant<int, 1>{}, std::integral_constant<int, 0>{});
-        }
-    }
-    if (k.TS == 2)
-        return f(std::integral_constant<int, 1>{}, std::integral_constant<int, 2>{}, std::integral_constant<int, 0>{});
-    return f(std::integral_constant<int, 1>{}, std::integral_constant<int, 1>{}, std::integral_constant<int, 0>{});
+    return k.M == 48 ? reg64_dispatch_m<48>(k, f) : reg64_dispatch_m<64>(k, f);
 }
 
 }  // namespace
 
 int prepare_reg64(const epic_plan_s *plan, const GroupCfg &g)
 {
-    return reg64_dispatch(reg64_key(plan, g), [&](auto p_, auto ts_, auto kc_) {
-        return prepare_reg64_t<decltype(p_)::value, decltype(ts_)::value, decltype(kc_)::value>(plan);
+    return reg64_dispatch(reg64_key(plan, g), [&](auto m_, auto p_, auto ts_, auto kc_) {
+        return prepare_reg64_t<decltype(m_)::value, decltype(p_)::value, decltype(ts_)::value,
+                               decltype(kc_)::value>(plan);
     });
 }
 
-size_t reg64_smem_bytes(int P, int TS, int A, int K, int nker)
+size_t reg64_smem_bytes(int M, int P, int TS, int A, int K, int nker)
 {
-    if (P == 2) return TS == 2 ? reg64_smem<2, 2>(A, K, nker) : reg64_smem<2, 1>(A, K, nker);
-    return TS == 2 ? reg64_smem<1, 2>(A, K, nker) : reg64_smem<1, 1>(A, K, nker);
+    if (M == 48) {
+        if (P == 2) return TS == 2 ? reg64_smem<48, 2, 2>(A, K, nker) : reg64_smem<48, 2, 1>(A, K, nker);
+        return TS == 2 ? reg64_smem<48, 1, 2>(A, K, nker) : reg64_smem<48, 1, 1>(A, K, nker);
+    }
+    if (P == 2) return TS == 2 ? reg64_smem<64, 2, 2>(A, K, nker) : reg64_smem<64, 2, 1>(A, K, nker);
+    return TS == 2 ? reg64_smem<64, 1, 2>(A, K, nker) : reg64_smem<64, 1, 1>(A, K, nker);
 }
 
 size_t fold64_smem_bytes(int P) { return 2 * sizeof(float2) * static_cast<size_t>(P) * M64 * S64; }
@@ -420,11 +450,12 @@ int launch_fold64(const GroupCfg &g, int P, const float2 *gf, int nb, bool accum
 int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                  cudaStream_t stream)
 {
-    return reg64_dispatch(reg64_key(plan, g), [&](auto p_, auto ts_, auto kc_) {
-        constexpr int P = decltype(p_)::value, TS = decltype(ts_)::value, KC = decltype(kc_)::value;
+    return reg64_dispatch(reg64_key(plan, g), [&](auto m_, auto p_, auto ts_, auto kc_) {
+        constexpr int M = decltype(m_)::value, P = decltype(p_)::value, TS = decltype(ts_)::value,
+                      KC = decltype(kc_)::value;
         // the delay-corrected form is a separate instantiation, so the plain one carries no trace of it
-        return plan->delays ? launch_reg64_t<P, TS, KC, true>(plan, g, v, gains, T, n_tau, stream)
-                            : launch_reg64_t<P, TS, KC, false>(plan, g, v, gains, T, n_tau, stream);
+        return plan->delays ? launch_reg64_t<M, P, TS, KC, true>(plan, g, v, gains, T, n_tau, stream)
+                            : launch_reg64_t<M, P, TS, KC, false>(plan, g, v, gains, T, n_tau, stream);
     });
 }
 

@@ -153,23 +153,24 @@ int host_cell_map(const double *ant_xy_m, int n_ant, const double *freq_hz, int 
 
 void host_kernel_power(const float *kern, int K, int N, std::vector<double> &out) { kernel_power(kern, K, N, out); }
 
-// Gridding schedule of the M = 64 kernel.  Each antenna footprint is cut into
-// K row segments (one per dy) of K cells on the folded 64 x 64 grid.  Warp w
-// owns rows y = w (mod 8); its segments are packed greedily into rounds of 32
-// lanes such that (a) no two segments of a round share a cell, so a round can
-// read-add-write without atomics, and (b) the 16 lanes of each half-warp start
-// at distinct (y + x) mod 16, which with the 65-float2 row stride puts every
-// lane of a half-warp on its own pair of banks for each of the K cells.
-int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
+// Gridding schedule of the register-transform kernels (fold side M = 64 or 48).
+// Each antenna footprint is cut into K row segments (one per dy) of K cells on
+// the folded M x M grid.  Warp w owns rows y = w (mod 8); its segments are
+// packed greedily into rounds of 32 lanes such that (a) no two segments of a
+// round share a cell, so a round can read-add-write without atomics, and (b)
+// the 16 lanes of each half-warp start at distinct (y + x) mod 16, which with
+// the row stride of M + 1 float2 (65 or 49, both 1 mod 16) puts every lane of
+// a half-warp on its own pair of banks for each of the K cells.
+int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, int M, const std::vector<int> &chans,
                          std::vector<uint32_t> &desc, std::vector<int> &nrounds, int &rmax,
                          std::vector<unsigned long long> &rowmask, std::vector<uint16_t> &first)
 {
-    constexpr int M = 64, W = 8;
+    constexpr int W = 8;
     const int h = (K - 1) / 2;
-    if (A > 4096 || K > 15) return EPIC_ERR_UNSUPPORTED;
+    if (A > 4096 || K > 15 || (M != 64 && M != 48)) return EPIC_ERR_UNSUPPORTED;
     struct Round {
         uint32_t lane[32];
-        uint64_t rowmask[M / W];
+        uint64_t rowmask[64 / W];
     };
     const int nc = static_cast<int>(chans.size());
     std::vector<std::vector<std::vector<Round>>> all(nc, std::vector<std::vector<Round>>(W));
@@ -182,7 +183,7 @@ int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, const s
             const int jx = k.x % M, jy = k.y % M;
             const int x0 = ((jx - h) % M + M) % M;
             uint64_t mask = 0;
-            for (int dx = 0; dx < K; dx++) mask |= 1ull << ((x0 + dx) & (M - 1));
+            for (int dx = 0; dx < K; dx++) mask |= 1ull << ((x0 + dx) % M);
             for (int dyi = 0; dyi < K; dyi++) {
                 const int y = ((jy + dyi - h) % M + M) % M;
                 const int w = y % W, res = (y + x0) % 16;
@@ -232,7 +233,7 @@ int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, const s
                     const int y = static_cast<int>((d >> 16) & 0x3Fu), x0 = static_cast<int>((d >> 22) & 0x3Fu);
                     uint16_t m = 0;
                     for (int dx = 0; dx < K; dx++) {
-                        uint8_t &tc = touched[y * M + ((x0 + dx) & (M - 1))];
+                        uint8_t &tc = touched[y * M + ((x0 + dx) % M)];
                         if (!tc) m |= static_cast<uint16_t>(1u << dx);
                         tc = 1;
                     }
@@ -506,9 +507,9 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                 rc = EPIC_ERR_UNSUPPORTED;
             g.reg64 = true;   // same gridding schedule and natural pixel order
             g.ts = 1;
-        } else if (g.M == 64 && (ap % 4) == 0) {
+        } else if ((g.M == 64 || g.M == 48) && (ap % 4) == 0) {
             for (int ts = 2; ts >= 1 && !g.reg64; ts--) {
-                if (epic::reg64_smem_bytes(n_pol, ts, n_ant, p->K, p->nker) <= static_cast<size_t>(smem_optin)) {
+                if (epic::reg64_smem_bytes(g.M, n_pol, ts, n_ant, p->K, p->nker) <= static_cast<size_t>(smem_optin)) {
                     g.reg64 = true;
                     g.ts = ts;
                 }
@@ -516,12 +517,12 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         }
         if (g.reg64) {
             g.R1 = 1;
-            g.R2 = 64;
+            g.R2 = g.M;
             std::vector<uint32_t> desc;
             std::vector<int> nr;
             std::vector<unsigned long long> rows;
             std::vector<uint16_t> first;
-            rc = epic::build_reg64_schedule(cells, n_ant, p->K, g.chans, desc, nr, g.rmax, rows, first);
+            rc = epic::build_reg64_schedule(cells, n_ant, p->K, g.M, g.chans, desc, nr, g.rmax, rows, first);
             if (rc == EPIC_OK) rc = dev_upload(&g.d_sched, desc.data(), desc.size());
             if (rc == EPIC_OK && g.tensor) rc = dev_upload(&g.d_first, first.data(), first.size());
             if (rc == EPIC_OK) rc = dev_upload(&g.d_nrounds, nr.data(), nr.size());

@@ -53,6 +53,33 @@ def test_random_cases(A, P, C, T, N, K):
     assert err.max() < FP32_TOL, err
 
 
+FOLD48_CASES = [
+    # grid side 96 folds to 48 x 48 per pixel class; n_ant * n_pol a multiple of
+    # 4 takes the register-transform kernel (48-point FFTs, scheduled gridding)
+    # A,   P, C, T,  N,  K
+    (100, 2, 2, 11, 96, 5),   # kernel side fixed at compile time, ragged time pair
+    (72, 2, 1, 7, 96, 7),     # generic kernel-side loop
+    (64, 1, 2, 9, 96, 3),     # one polarisation
+    (48, 2, 2, 6, 96, 1),     # point kernel
+    (500, 2, 1, 4, 96, 15),   # footprints wider than a bank group, wrap across the fold
+]
+
+
+@pytest.mark.parametrize("A,P,C,T,N,K", FOLD48_CASES)
+def test_fold48_register_kernel(A, P, C, T, N, K):
+    wl = synth.random_small(A=A, P=P, C=C, T=T, N=N, K=K, seed=A * 3 + K)
+    gpu, _ = run_gpu(wl)
+    ref = _oracle(wl)
+    err = peak_rel_err(gpu, ref, wl.grid_n, P)
+    assert err.max() < FP32_TOL, err
+
+
+def test_fold48_register_kernel_taper():
+    wl = synth.random_small(A=100, P=2, C=2, T=7, N=96, K=5, seed=96)
+    gpu, _ = run_gpu(wl, flags=epic.EPIC_KERNEL_TAPER)
+    assert peak_rel_err(gpu, _oracle(wl), wl.grid_n, 2).max() < FP32_TOL
+
+
 def test_mixed_grid_sides_in_one_plan():
     wl = synth.random_small(A=90, P=2, C=3, T=5, N=64, K=5, seed=11)
     wl.grid_n = np.array([64, 96, 128], np.int32)
