@@ -104,7 +104,7 @@ __device__ __forceinline__ void fft48p_stage2(float2 (&x)[48], Sink &&sink)
         float2 u[6];
 #pragma unroll
         for (int n2 = 0; n2 < 6; n2++) u[n2] = x[6 * k1 + n2];
-        dft6(u);
+        dft6p(u);
 #pragma unroll
         for (int k2 = 0; k2 < 6; k2++) sink(k1 + 8 * k2, u[k2]);
     }
