@@ -54,6 +54,11 @@ struct GroupCfg {
     uint16_t *d_first = nullptr;       // device (tensor plans): per descriptor, taps that write their cell first
     int *d_nrounds = nullptr;          // device: [n_chan][8] rounds per warp
     unsigned long long *d_rowmask = nullptr;  // device: [n_chan] folded rows touched by any footprint
+    uint32_t *d_gtab = nullptr;        // device (FP32 register kernel): gather table, build_gather_table
+    int4 *d_gidx = nullptr;            // device: [n_chan][8 warps] (zero offset, zero steps, batch offset, batches)
+    int2 *d_gchan = nullptr;           // device: [n_chan] (block start, block words)
+    int gwords = 0;                    // largest channel block (words)
+    bool gstage = false;               // blocks staged in shared memory
     // large grid sides (8 x 8 pixel classes): grid once per (channel, sample) into the occupied
     // alias blocks, fold all classes with one 8 x 8 DFT per folded cell (alias_fold_kernel), then
     // transform each class's loaded grid (fp32_fold64_kernel), in time batches of alias_tb samples
@@ -172,6 +177,10 @@ int launch_tc_pipe(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
                    cudaStream_t stream);
 void build_dft_rows(bool bf16, std::vector<uint16_t> &words);
 
+// Gather table of the FP32 register-transform kernel for the channels of one group (plan.cu).
+int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, int P, const std::vector<int> &chans,
+                       std::vector<uint32_t> &tab, std::vector<int4> &idx, std::vector<int2> &chan,
+                       std::vector<unsigned long long> &rowmask);
 // Register-transform kernels, fold side M = 64 or 48 (fp32_reg64.cu)
 size_t reg64_smem_bytes(int M, int P, int TS, int A, int K, int nker);
 int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,

@@ -4,11 +4,11 @@
 //
 // What differs from the general kernel, and why (measured: the general kernel
 // is bound by the shared-memory pipe, ~17 000 wavefronts per CTA and sample):
-//  * gridding without atomics: the plan splits every antenna footprint into K
-//    row segments and packs them into rounds of 32 lanes in which no two
-//    segments touch the same cell and no two lanes of a half-warp hit the same
-//    bank; warp w owns the grid rows y = w (mod 8), so a round is a plain
-//    read-add-write of K cells per lane with no inter-warp race;
+//  * gridding as a gather, without atomics and without reading the grid: the
+//    plan lists, per folded cell, the (antenna, tap) pairs that cover it; a
+//    lane sums one cell's list in registers and stores the cell once (cells no
+//    footprint covers get zeros), so the grid is never cleared and each cell
+//    costs one store per plane instead of a read-add-write per tap;
 //  * the M-point transforms run in registers (one row or column per thread),
 //    so each axis costs one shared-memory read and one write;
 //  * two time samples per iteration share the schedule, the twiddles and the
@@ -51,7 +51,9 @@ __device__ __forceinline__ void fft_reg(float2 (&x)[M], Sink &&sink)
 // a4-a6 on the TS x P planes of G ([ts][p][y][x], x < M at stride M + 1): rows
 // then columns, one M-point transform per thread, then the products of every
 // pixel added to the thread's time sums; CLEAR zeroes the planes for the next
-// gridding.  Rows outside rows_used are empty and stay zero.
+// gridding.  Rows outside rows_used are empty: the row pass skips them and the
+// column pass reads them as zeros (their cells hold whatever the last
+// transform left there).
 template <int M, int P, int TS, bool CLEAR>
 __device__ __forceinline__ void transform_products(float2 *G, unsigned long long rows_used,
                                                    typename Acc64<P>::T (&acc)[M * M / kThreads], int tid)
@@ -70,7 +72,7 @@ __device__ __forceinline__ void transform_products(float2 *G, unsigned long long
         float2 *col = G + (q / M) * BUF + (q % M);
         float2 x[M];
 #pragma unroll
-        for (int i = 0; i < M; i++) x[i] = col[i * S];
+        for (int i = 0; i < M; i++) x[i] = ((rows_used >> i) & 1ull) ? col[i * S] : make_float2(0.f, 0.f);
         fft_reg<M>(x, [&](int k, float2 val) { col[k * S] = val; });
     }
     __syncthreads();
@@ -99,23 +101,25 @@ __device__ __forceinline__ void transform_products(float2 *G, unsigned long long
 }
 
 // Folded side M (64, or 48 for grid side 96).  Grid buffers: G[ts][p][y][x] with
-// x < M at stride M + 1.  KC > 0 fixes the
-// kernel side at compile time (the gridding loop then unrolls fully); KC = 0
-// takes it from K.  DL: voltages take the geometric-delay phase of the
-// per-integration table dtab (Sec. 2.2 delay correction), once per antenna.  rowmask[ci] marks the folded rows any footprint touches:
-// the others stay zero and their row transforms are skipped.
-template <int M, int P, int TS, int KC, bool DL>
+// x < M at stride M + 1.  DL: voltages take the geometric-delay phase of the
+// per-integration table dtab (Sec. 2.2 delay correction), once per antenna.
+// gtab/gidx/gchan: the gather table (per channel a block of per-warp zero lists
+// and batches of 32 cells with their (antenna, tap) lists; layout in the plan's
+// builder); GS: the channel's block is copied to shared memory first (when it
+// fits beside the grids), else it is read through the L1 cache.  rowmask[ci]
+// marks the folded rows any footprint touches: the others are never written
+// and their transforms are skipped.
+template <int M, int P, int TS, bool DL, bool GS>
 __global__ void __launch_bounds__(kThreads, 1)
 fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
-                  const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K_rt,
+                  const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K,
                   const int *__restrict__ chans, const float2 *__restrict__ twN,
-                  const uint32_t *__restrict__ sched, const int *__restrict__ nrounds, int rmax,
+                  const uint32_t *__restrict__ gtab, const int4 *__restrict__ gidx, const int2 *__restrict__ gchan,
                   const unsigned long long *__restrict__ rowmask,
                   int A, int C, int T, int N, int Q1, int n_items, int n_tau,
                   float *__restrict__ partial, int *__restrict__ status, int nker,
                   const float *__restrict__ dfreq, const float4 *__restrict__ dtab)
 {
-    const int K = KC > 0 ? KC : K_rt;
     constexpr int NPOS = M * M / kThreads;       // pixels per thread (16 at M = 64, 9 at 48)
     constexpr int S = M + 1;                     // padded row stride (float2)
     constexpr int BUF = M * S;                   // one [y][x] plane
@@ -127,6 +131,7 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     float2 *gp = es + TS * AP;                                 // [A*P]
     float2 *tapw = gp + AP;                                    // [nker][K*K]
     uint32_t *stage = reinterpret_cast<uint32_t *>(tapw + nker * KK); // [TS][APW]
+    uint32_t *stab = stage + TS * APW;                         // [block words] (GS)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int item = blockIdx.x % n_items;
@@ -136,8 +141,8 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     const int c = chans[ci];
     const int t0 = static_cast<int>(static_cast<long long>(T) * tau / n_tau);
     const int t1 = static_cast<int>(static_cast<long long>(T) * (tau + 1) / n_tau);
-    const uint32_t *my_sched = sched + (static_cast<size_t>(ci) * 8 + warp) * rmax * 32;
-    const int my_rounds = nrounds[ci * 8 + warp];
+    const int4 my_idx = gidx[ci * 8 + warp];
+    const int2 my_chan = gchan[ci];
     const unsigned long long rows_used = rowmask[ci];
 
     // ---- set-up: phase-folded gains and taps (class phase w_N^{k.h})
@@ -156,6 +161,8 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         tapw[i] = cmul(kern[i], twN[((dx * hx + dy * hy) % N + N) % N]);
     }
     for (int i = tid; i < TS * P * BUF; i += kThreads) G[i] = make_float2(0.f, 0.f);
+    if constexpr (GS)
+        for (int i = tid; i < my_chan.y; i += kThreads) stab[i] = __ldg(gtab + my_chan.x + i);
     for (int ts = 0; ts < TS; ts++) {
         if (t0 + ts < t1) {
             const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(t0 + ts) * C + c) * AP);
@@ -210,46 +217,75 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         }
         __syncthreads();
 
-        // ---- a3: scheduled gridding, warp w owns rows y = w (mod 8)
-        for (int r = 0; r < my_rounds; r++) {
-            const uint32_t d = __ldg(my_sched + r * 32 + lane);
-            if (d >> 31) {
-                const int a = static_cast<int>(d & 0xFFFu);
-                const int dyi = static_cast<int>((d >> 12) & 0xFu);
-                const int y = static_cast<int>((d >> 16) & 0x3Fu);
-                const int x0 = static_cast<int>((d >> 22) & 0x3Fu);
-                float2 e[TS][P], eswap[TS][P];
+        // ---- a3: gridding as a gather: zeros for the uncovered cells of touched rows, then
+        // each lane sums its cell's (antenna, tap) list in registers and stores the cell once
+        {
+            const uint32_t *tb;
+            if constexpr (GS) tb = stab;
+            else tb = gtab + my_chan.x;
+            auto ld = [&](const uint32_t *q) -> uint32_t {
+                if constexpr (GS) return *q;
+                else return __ldg(q);
+            };
+            const uint32_t *zl = tb + my_idx.x + lane;
+#pragma unroll 4
+            for (int r = 0; r < my_idx.y; r++) {
+                const uint32_t cell = ld(zl + r * 32);
+                if (cell != ~0u) {
+#pragma unroll
+                    for (int q = 0; q < TS * P; q++) G[q * BUF + cell] = make_float2(0.f, 0.f);
+                }
+            }
+            const uint32_t *bt = tb + my_idx.z;
+            uint32_t hdr = my_idx.w > 0 ? ld(bt) : 0u;
+            for (int b = 0; b < my_idx.w; b++) {
+                const int d = static_cast<int>(hdr);
+                const uint32_t cell = ld(bt + 1 + lane);
+                const uint32_t *ent = bt + 33 + lane;
+                const uint32_t *next = bt + 33 + d * 32;
+                if (b + 1 < my_idx.w) hdr = ld(next);                 // next batch's length in flight
+                float2 acc_g[TS][P];
 #pragma unroll
                 for (int ts = 0; ts < TS; ts++)
 #pragma unroll
-                    for (int p = 0; p < P; p++) {
-                        e[ts][p] = es[ts * AP + a * P + p];
-                        eswap[ts][p] = pswap(e[ts][p]);
-                    }
-                const float2 *wrow = tapw + (nker > 1 ? a * KK : 0) + dyi * K;
+                    for (int p = 0; p < P; p++) acc_g[ts][p] = make_float2(0.f, 0.f);
+                uint32_t en = d > 0 ? ld(ent) : ~0u;
+                for (int j = 0; j < d; j++) {
+                    const uint32_t cur = en;
+                    if (j + 1 < d) en = ld(ent + (j + 1) * 32);        // next step's entry in flight
+                    if (cur != ~0u) {
+                        const int a = static_cast<int>(cur >> 8), tap = static_cast<int>(cur & 0xFFu);
+                        // cell += w e as two packed FMAs: w.x (e.x, e.y) + (-w.y, w.y) (e.y, e.x)
+                        const float2 w = tapw[(nker > 1 ? a * KK : 0) + tap];
+                        const float2 wr = make_float2(w.x, w.x), wi = make_float2(-w.y, w.y);
 #pragma unroll
-                for (int dx = 0; dx < (KC > 0 ? KC : K); dx++) {
-                    // cell += w e as two packed FMAs: w.x (e.x, e.y) + (-w.y, w.y) (e.y, e.x)
-                    const float2 w = wrow[dx];
-                    const float2 wr = make_float2(w.x, w.x), wi = make_float2(-w.y, w.y);
-                    int x;
-                    if constexpr (M == 64) x = (x0 + dx) & (M64 - 1);
-                    else x = x0 + dx >= M ? x0 + dx - M : x0 + dx;   // x0 < M, dx < K <= 15
+                        for (int ts = 0; ts < TS; ts++) {
+                            if constexpr (P == 2) {
+                                const float4 e2 = reinterpret_cast<const float4 *>(es + ts * AP)[a];
+                                const float2 e0 = make_float2(e2.x, e2.y), e1 = make_float2(e2.z, e2.w);
+                                acc_g[ts][0] = pfma(wi, pswap(e0), pfma(wr, e0, acc_g[ts][0]));
+                                acc_g[ts][1] = pfma(wi, pswap(e1), pfma(wr, e1, acc_g[ts][1]));
+                            } else {
+                                const float2 e0 = es[ts * AP + a];
+                                acc_g[ts][0] = pfma(wi, pswap(e0), pfma(wr, e0, acc_g[ts][0]));
+                            }
+                        }
+                    }
+                }
+                if (cell != ~0u) {
 #pragma unroll
                     for (int ts = 0; ts < TS; ts++)
 #pragma unroll
-                        for (int p = 0; p < P; p++) {
-                            float2 *cell = G + (ts * P + p) * BUF + y * S + x;
-                            *cell = pfma(wi, eswap[ts][p], pfma(wr, e[ts][p], *cell));
-                        }
+                        for (int p = 0; p < P; p++) G[(ts * P + p) * BUF + cell] = acc_g[ts][p];
                 }
+                bt = next;
             }
-            __syncwarp();
         }
         __syncthreads();
 
-        // ---- a4, a5, a6: transforms, products summed over time; planes cleared for the next group
-        transform_products<M, P, TS, true>(G, rows_used, acc, tid);
+        // ---- a4, a5, a6: transforms, products summed over time (the next gather overwrites
+        // every cell of the touched rows, so nothing is cleared)
+        transform_products<M, P, TS, false>(G, rows_used, acc, tid);
 #pragma unroll
         for (int ts = 0; ts < TS; ts++)
 #pragma unroll
@@ -335,86 +371,72 @@ size_t reg64_smem(int A, int K, int nker)
     return (b + 15) & ~static_cast<size_t>(15);
 }
 
-template <int M, int P, int TS, int KC, bool DL>
+template <int M, int P, int TS, bool DL, bool GS>
 int launch_reg64_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau_out,
                    cudaStream_t stream)
 {
-    auto kfn = fp32_reg64_kernel<M, P, TS, KC, DL>;
-    const size_t smem = reg64_smem<M, P, TS>(plan->A, plan->K, plan->nker);
+    auto kfn = fp32_reg64_kernel<M, P, TS, DL, GS>;
+    const size_t smem = reg64_smem<M, P, TS>(plan->A, plan->K, plan->nker) +
+                        (GS ? sizeof(uint32_t) * static_cast<size_t>(g.gwords) : 0);
     int n_tau = choose_tau(plan, g, T);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
     const dim3 grid(static_cast<unsigned>(g.n_items * n_tau));
     kfn<<<grid, kThreads, smem, stream>>>(v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN,
-                                          g.d_sched, g.d_nrounds, g.rmax, g.d_rowmask, plan->A, plan->C, T, g.N, g.Q1,
-                                          g.n_items, n_tau, g.d_partial, plan->d_status, plan->nker, plan->d_dfreq,
-                                          DL ? plan->d_dtab : nullptr);
+                                          g.d_gtab, g.d_gidx, g.d_gchan, g.d_rowmask, plan->A, plan->C, T, g.N,
+                                          g.Q1, g.n_items, n_tau, g.d_partial, plan->d_status, plan->nker,
+                                          plan->d_dfreq, DL ? plan->d_dtab : nullptr);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
-template <int M, int P, int TS, int KC>
-int prepare_reg64_t(const epic_plan_s *plan)
+// The dynamic shared-memory cap is set to the device's opt-in limit, not to this
+// group's size: the cap is per kernel and process, and another group or plan with
+// a smaller table must not lower it under this one.
+template <int M, int P, int TS, bool GS>
+int prepare_reg64_t(const epic_plan_s *plan, const GroupCfg &g)
 {
-    const int smem = static_cast<int>(reg64_smem<M, P, TS>(plan->A, plan->K, plan->nker));
-    const bool ok = cudaFuncSetAttribute(fp32_reg64_kernel<M, P, TS, KC, false>,
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return EPIC_ERR_CUDA;
+    const size_t need = reg64_smem<M, P, TS>(plan->A, plan->K, plan->nker) +
+                        (GS ? sizeof(uint32_t) * static_cast<size_t>(g.gwords) : 0);
+    if (need > static_cast<size_t>(optin)) return EPIC_ERR_UNSUPPORTED;
+    const int smem = optin;
+    const bool ok = cudaFuncSetAttribute(fp32_reg64_kernel<M, P, TS, false, GS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
-                    cudaFuncSetAttribute(fp32_reg64_kernel<M, P, TS, KC, true>,
+                    cudaFuncSetAttribute(fp32_reg64_kernel<M, P, TS, true, GS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
     return ok ? EPIC_OK : EPIC_ERR_UNSUPPORTED;
-}
-
-// Which instantiation serves a plan: at M = 64 dual polarisation gets kernels
-// specialised for the kernel sides in use here (1: image-domain taper, 5:
-// LWA-like, 7: dense), at M = 48 (grid side 96) for side 5; anything else runs
-// the generic loop.
-struct Reg64Key {
-    int M, P, TS, KC;
-};
-
-Reg64Key reg64_key(const epic_plan_s *plan, const GroupCfg &g)
-{
-    int kc = 0;
-    if (plan->P == 2 && (plan->K == 5 || (g.M == 64 && (plan->K == 1 || plan->K == 7)))) kc = plan->K;
-    return {g.M, plan->P, g.ts, kc};
 }
 
 template <int V>
 using IC = std::integral_constant<int, V>;
 
-template <int M, class F>
-int reg64_dispatch_m(const Reg64Key &k, F &&f)
-{
-    if (k.P == 2) {
-        auto with_ts = [&](auto ts) {
-            switch (k.KC) {
-            case 5: return f(IC<M>{}, IC<2>{}, ts, IC<5>{});
-            case 1:
-                if constexpr (M == 64) return f(IC<M>{}, IC<2>{}, ts, IC<1>{});
-                else return f(IC<M>{}, IC<2>{}, ts, IC<0>{});
-            case 7:
-                if constexpr (M == 64) return f(IC<M>{}, IC<2>{}, ts, IC<7>{});
-                else return f(IC<M>{}, IC<2>{}, ts, IC<0>{});
-            default: return f(IC<M>{}, IC<2>{}, ts, IC<0>{});
-            }
-        };
-        return k.TS == 2 ? with_ts(IC<2>{}) : with_ts(IC<1>{});
-    }
-    return k.TS == 2 ? f(IC<M>{}, IC<1>{}, IC<2>{}, IC<0>{}) : f(IC<M>{}, IC<1>{}, IC<1>{}, IC<0>{});
-}
-
+// The instantiation that serves a group: fold side, polarisations, samples per
+// iteration, and whether the gather table is staged in shared memory.
 template <class F>
-int reg64_dispatch(const Reg64Key &k, F &&f)
+int reg64_dispatch(const epic_plan_s *plan, const GroupCfg &g, F &&f)
 {
-    return k.M == 48 ? reg64_dispatch_m<48>(k, f) : reg64_dispatch_m<64>(k, f);
+    auto with_m = [&](auto m_) {
+        auto with_p = [&](auto p_) {
+            auto with_ts = [&](auto ts_) {
+                return g.gstage ? f(m_, p_, ts_, IC<1>{}) : f(m_, p_, ts_, IC<0>{});
+            };
+            return g.ts == 2 ? with_ts(IC<2>{}) : with_ts(IC<1>{});
+        };
+        return plan->P == 2 ? with_p(IC<2>{}) : with_p(IC<1>{});
+    };
+    return g.M == 48 ? with_m(IC<48>{}) : with_m(IC<64>{});
 }
 
 }  // namespace
 
 int prepare_reg64(const epic_plan_s *plan, const GroupCfg &g)
 {
-    return reg64_dispatch(reg64_key(plan, g), [&](auto m_, auto p_, auto ts_, auto kc_) {
+    return reg64_dispatch(plan, g, [&](auto m_, auto p_, auto ts_, auto gs_) {
         return prepare_reg64_t<decltype(m_)::value, decltype(p_)::value, decltype(ts_)::value,
-                               decltype(kc_)::value>(plan);
+                               decltype(gs_)::value != 0>(plan, g);
     });
 }
 
@@ -450,12 +472,12 @@ int launch_fold64(const GroupCfg &g, int P, const float2 *gf, int nb, bool accum
 int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                  cudaStream_t stream)
 {
-    return reg64_dispatch(reg64_key(plan, g), [&](auto m_, auto p_, auto ts_, auto kc_) {
-        constexpr int M = decltype(m_)::value, P = decltype(p_)::value, TS = decltype(ts_)::value,
-                      KC = decltype(kc_)::value;
+    return reg64_dispatch(plan, g, [&](auto m_, auto p_, auto ts_, auto gs_) {
+        constexpr int M = decltype(m_)::value, P = decltype(p_)::value, TS = decltype(ts_)::value;
+        constexpr bool GS = decltype(gs_)::value != 0;
         // the delay-corrected form is a separate instantiation, so the plain one carries no trace of it
-        return plan->delays ? launch_reg64_t<M, P, TS, KC, true>(plan, g, v, gains, T, n_tau, stream)
-                            : launch_reg64_t<M, P, TS, KC, false>(plan, g, v, gains, T, n_tau, stream);
+        return plan->delays ? launch_reg64_t<M, P, TS, true, GS>(plan, g, v, gains, T, n_tau, stream)
+                            : launch_reg64_t<M, P, TS, false, GS>(plan, g, v, gains, T, n_tau, stream);
     });
 }
 

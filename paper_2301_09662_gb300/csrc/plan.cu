@@ -85,6 +85,9 @@ void free_plan(epic_plan_s *p)
         cudaFree(g.d_bseg);
         cudaFree(g.d_boff);
         cudaFree(g.d_rowmask);
+        cudaFree(g.d_gtab);
+        cudaFree(g.d_gidx);
+        cudaFree(g.d_gchan);
         cudaFree(g.d_tw64);
         cudaFree(g.d_Y);
     }
@@ -241,6 +244,135 @@ int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, int M, 
                 }
         }
     }
+    return EPIC_OK;
+}
+
+// Gather table of the FP32 register-transform kernel (fold side M = 64 or 48).
+// Per channel every folded cell lists the (antenna, tap) pairs whose footprints
+// cover it; a lane owns one cell, sums its list in registers and stores the
+// cell once, so the gridding reads no grid cell and needs no cleared grid.
+// Cells are sorted by list length and dealt in batches of 32 lanes (one list
+// step per warp iteration; a batch runs as long as its longest list).  Within
+// each group of lanes that one shared-memory request serves (8 for the 16-byte
+// dual-polarisation voltage loads, 16 for the 8-byte single-polarisation ones)
+// the list order is chosen greedily so that one step reads distinct banks.
+// Cells no footprint covers in rows that some footprint touches get zeros,
+// from per-warp lists of 32 cells per step; rows nobody touches are skipped by
+// the transform and need nothing.  Batches go to the warps longest first, each
+// to the warp with the least work so far, then the zero steps.
+//   channel block: [zero lists of warps 0..7][gather batches of warps 0..7]
+//   gather batch:  [length d][32 cell offsets y (M + 1) + x, or ~0][d x 32 entries a << 8 | tap, or ~0]
+//   idx[ci * 8 + w] = (zero list offset, zero steps, first batch offset, batches), offsets from the
+//   channel block's start; chan[ci] = (block start, block words)
+int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, int P, const std::vector<int> &chans,
+                       std::vector<uint32_t> &tab, std::vector<int4> &idx, std::vector<int2> &chan,
+                       std::vector<unsigned long long> &rowmask)
+{
+    constexpr int W = 8;
+    const int h = (K - 1) / 2, S = M + 1;
+    if (A > 4096 || K > 15 || (M != 64 && M != 48)) return EPIC_ERR_UNSUPPORTED;
+    const int nc = static_cast<int>(chans.size());
+    const int grp = P == 2 ? 8 : 16;    // lanes per request; bank slot = a mod grp
+    tab.clear();
+    idx.assign(static_cast<size_t>(nc) * W, make_int4(0, 0, 0, 0));
+    chan.assign(nc, make_int2(0, 0));
+    rowmask.assign(nc, 0ull);
+    for (int ci = 0; ci < nc; ci++) {
+        const int c = chans[ci];
+        std::vector<std::vector<uint32_t>> list(M * M);   // per cell: a << 8 | tap
+        for (int a = 0; a < A; a++) {
+            const short2 k = cells[static_cast<size_t>(c) * A + a];
+            const int jx = k.x % M, jy = k.y % M;
+            for (int dyi = 0; dyi < K; dyi++) {
+                const int y = ((jy + dyi - h) % M + M) % M;
+                rowmask[ci] |= 1ull << y;
+                for (int dx = 0; dx < K; dx++) {
+                    const int x = ((jx + dx - h) % M + M) % M;
+                    list[y * M + x].push_back((static_cast<uint32_t>(a) << 8) | static_cast<uint32_t>(dyi * K + dx));
+                }
+            }
+        }
+        std::vector<int> touched, zero;
+        for (int i = 0; i < M * M; i++) {
+            if (!list[i].empty()) touched.push_back(i);
+            else if ((rowmask[ci] >> (i / M)) & 1ull) zero.push_back(i);
+        }
+        std::stable_sort(touched.begin(), touched.end(),
+                         [&](int u, int v) { return list[u].size() > list[v].size(); });
+        auto cell_word = [&](int i) { return static_cast<uint32_t>((i / M) * S + i % M); };
+        std::vector<std::vector<uint32_t>> batches;
+        for (size_t b0 = 0; b0 < touched.size(); b0 += 32) {
+            const int nl = static_cast<int>(std::min<size_t>(32, touched.size() - b0));
+            int d = 0;
+            for (int l = 0; l < nl; l++) d = std::max(d, static_cast<int>(list[touched[b0 + l]].size()));
+            std::vector<uint32_t> words(1 + 32 + static_cast<size_t>(d) * 32, ~0u);
+            words[0] = static_cast<uint32_t>(d);
+            for (int l = 0; l < nl; l++) words[1 + l] = cell_word(touched[b0 + l]);
+            for (int g0 = 0; g0 < 32; g0 += grp) {
+                std::vector<std::vector<uint32_t>> rem(grp);
+                for (int l = 0; l < grp; l++)
+                    if (g0 + l < nl) rem[l] = list[touched[b0 + g0 + l]];
+                for (int j = 0; j < d; j++) {
+                    std::vector<int> order(grp);
+                    for (int l = 0; l < grp; l++) order[l] = l;
+                    std::stable_sort(order.begin(), order.end(),
+                                     [&](int u, int v) { return rem[u].size() > rem[v].size(); });
+                    std::vector<int> slot(grp, -1);   // antenna already reading that bank slot this step
+                    for (int l : order) {
+                        auto &r = rem[l];
+                        if (r.empty()) continue;
+                        const bool must = static_cast<int>(r.size()) >= d - j;
+                        int pick = -1;
+                        for (size_t q = 0; q < r.size() && pick < 0; q++) {
+                            const int a = static_cast<int>(r[q] >> 8), sl = a % grp;
+                            if (slot[sl] < 0 || slot[sl] == a) pick = static_cast<int>(q);
+                        }
+                        if (pick < 0 && must) pick = 0;
+                        if (pick < 0) continue;
+                        const uint32_t e = r[pick];
+                        r.erase(r.begin() + pick);
+                        slot[static_cast<int>(e >> 8) % grp] = static_cast<int>(e >> 8);
+                        words[1 + 32 + static_cast<size_t>(j) * 32 + g0 + l] = e;
+                    }
+                }
+            }
+            batches.push_back(std::move(words));
+        }
+        // longest first, each to the least-loaded warp (cost ~ list steps; a store step ~ 1/4)
+        std::vector<int> ord(batches.size());
+        for (size_t i = 0; i < ord.size(); i++) ord[i] = static_cast<int>(i);
+        std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) { return batches[u][0] > batches[v][0]; });
+        std::vector<std::vector<int>> per_warp(W);
+        std::vector<long long> load(W, 0);
+        for (int b : ord) {
+            const int w = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+            per_warp[w].push_back(b);
+            load[w] += 4 * static_cast<long long>(batches[b][0]) + 2;
+        }
+        std::vector<int> zsteps(W, 0);
+        for (size_t z0 = 0; z0 < zero.size(); z0 += 32) {
+            const int w = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+            zsteps[w]++;
+            load[w] += 1;
+        }
+        const size_t start = tab.size();
+        if (start > 0x7FFFFFFFull) return EPIC_ERR_UNSUPPORTED;
+        size_t zi = 0;   // zero cells dealt in natural order: consecutive cells, distinct banks
+        for (int w = 0; w < W; w++) {
+            idx[static_cast<size_t>(ci) * W + w].x = static_cast<int>(tab.size() - start);
+            idx[static_cast<size_t>(ci) * W + w].y = zsteps[w];
+            for (int st = 0; st < zsteps[w]; st++)
+                for (int l = 0; l < 32; l++, zi++) tab.push_back(zi < zero.size() ? cell_word(zero[zi]) : ~0u);
+        }
+        for (int w = 0; w < W; w++) {
+            idx[static_cast<size_t>(ci) * W + w].z = static_cast<int>(tab.size() - start);
+            idx[static_cast<size_t>(ci) * W + w].w = static_cast<int>(per_warp[w].size());
+            for (int b : per_warp[w]) tab.insert(tab.end(), batches[b].begin(), batches[b].end());
+        }
+        if (tab.size() - start > 0x7FFFFFFFull) return EPIC_ERR_UNSUPPORTED;
+        chan[ci] = make_int2(static_cast<int>(start), static_cast<int>(tab.size() - start));
+    }
+    if (tab.empty()) tab.push_back(0);
     return EPIC_OK;
 }
 
@@ -522,10 +654,29 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
             std::vector<int> nr;
             std::vector<unsigned long long> rows;
             std::vector<uint16_t> first;
-            rc = epic::build_reg64_schedule(cells, n_ant, p->K, g.M, g.chans, desc, nr, g.rmax, rows, first);
-            if (rc == EPIC_OK) rc = dev_upload(&g.d_sched, desc.data(), desc.size());
-            if (rc == EPIC_OK && g.tensor) rc = dev_upload(&g.d_first, first.data(), first.size());
-            if (rc == EPIC_OK) rc = dev_upload(&g.d_nrounds, nr.data(), nr.size());
+            if (g.tensor) {
+                // the tensor kernels grid by scheduled rounds into a cleared-once grid
+                rc = epic::build_reg64_schedule(cells, n_ant, p->K, g.M, g.chans, desc, nr, g.rmax, rows, first);
+                if (rc == EPIC_OK) rc = dev_upload(&g.d_sched, desc.data(), desc.size());
+                if (rc == EPIC_OK) rc = dev_upload(&g.d_first, first.data(), first.size());
+                if (rc == EPIC_OK) rc = dev_upload(&g.d_nrounds, nr.data(), nr.size());
+            } else {
+                std::vector<uint32_t> tab;
+                std::vector<int4> gidx;
+                std::vector<int2> gchan;
+                rc = epic::build_gather_table(cells, n_ant, p->K, g.M, n_pol, g.chans, tab, gidx, gchan, rows);
+                if (rc == EPIC_OK) rc = dev_upload(&g.d_gtab, tab.data(), tab.size());
+                if (rc == EPIC_OK) rc = dev_upload(&g.d_gidx, gidx.data(), gidx.size());
+                if (rc == EPIC_OK) rc = dev_upload(&g.d_gchan, gchan.data(), gchan.size());
+                // a channel's whole table in shared memory when it fits beside the grids
+                g.gwords = 0;
+                for (const int2 &ch : gchan) g.gwords = std::max(g.gwords, ch.y);
+                g.gstage = epic::reg64_smem_bytes(g.M, n_pol, g.ts, n_ant, p->K, p->nker) +
+                               sizeof(uint32_t) * static_cast<size_t>(g.gwords) <=
+                           static_cast<size_t>(smem_optin);
+                const char *ng = std::getenv("EPIC_GATHER_GLOBAL");   // test hook: the unstaged form
+                if (ng && ng[0] == '1') g.gstage = false;
+            }
             if (rc == EPIC_OK) rc = dev_upload(&g.d_rowmask, rows.data(), rows.size());
             // large sides with one shared kernel of more than one tap: grid once per (channel,
             // sample) and fold all classes (alias_fold.cu), for the FP32 and the two-stage tensor

@@ -80,6 +80,19 @@ def test_fold48_register_kernel_taper():
     assert peak_rel_err(gpu, _oracle(wl), wl.grid_n, 2).max() < FP32_TOL
 
 
+@pytest.mark.parametrize("A,P,N,K", [(100, 2, 128, 5), (64, 1, 96, 3)])
+def test_gather_table_staged_and_global_forms_agree(monkeypatch, A, P, N, K):
+    """The gather table read from shared memory (staged per channel) and through
+    the L1 cache give bitwise the same image (same lists, same order), and both
+    match the oracle."""
+    wl = synth.random_small(A=A, P=P, C=2, T=9, N=N, K=K, seed=A + N)
+    staged, _ = run_gpu(wl)
+    monkeypatch.setenv("EPIC_GATHER_GLOBAL", "1")
+    unstaged, _ = run_gpu(wl)
+    assert np.array_equal(staged, unstaged)
+    assert peak_rel_err(staged, _oracle(wl), wl.grid_n, P).max() < FP32_TOL
+
+
 def test_mixed_grid_sides_in_one_plan():
     wl = synth.random_small(A=90, P=2, C=3, T=5, N=64, K=5, seed=11)
     wl.grid_n = np.array([64, 96, 128], np.int32)
