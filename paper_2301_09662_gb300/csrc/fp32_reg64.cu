@@ -5,10 +5,12 @@
 // What differs from the general kernel, and why (measured: the general kernel
 // is bound by the shared-memory pipe, ~17 000 wavefronts per CTA and sample):
 //  * gridding as a gather, without atomics and without reading the grid: the
-//    plan lists, per folded cell, the (antenna, tap) pairs that cover it; a
-//    lane sums one cell's list in registers and stores the cell once (cells no
-//    footprint covers get zeros), so the grid is never cleared and each cell
-//    costs one store per plane instead of a read-add-write per tap;
+//    plan lists, per pair of adjacent folded cells, the antennas whose
+//    footprints cover them with the matching pair of taps; a lane sums one
+//    pair's list in registers and stores both cells once (cells no footprint
+//    covers get zeros), so the grid is never cleared, each cell costs one store
+//    per plane instead of a read-add-write per tap, and one voltage load serves
+//    two cells;
 //  * the M-point transforms run in registers (one row or column per thread),
 //    so each axis costs one shared-memory read and one write;
 //  * two time samples per iteration share the schedule, the twiddles and the
@@ -127,7 +129,8 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     const int AP = A * P, KK = K * K, hk = (K - 1) / 2;
     const int APW = (AP + 3) >> 2;
     float2 *G = reinterpret_cast<float2 *>(smem_raw);          // [TS][P][M][M + 1]
-    float2 *es = G + TS * P * BUF;                             // [TS][A*P]
+    float4 *tw2 = reinterpret_cast<float4 *>(G + TS * P * BUF);  // [K][K + 1] tap pairs (one kernel)
+    float2 *es = reinterpret_cast<float2 *>(tw2 + K * (K + 1)); // [TS][A*P]
     float2 *gp = es + TS * AP;                                 // [A*P]
     float2 *tapw = gp + AP;                                    // [nker][K*K]
     uint32_t *stage = reinterpret_cast<uint32_t *>(tapw + nker * KK); // [TS][APW]
@@ -159,6 +162,18 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         const int tap = i % KK;
         const int dy = tap / K - hk, dx = tap % K - hk;
         tapw[i] = cmul(kern[i], twN[((dx * hx + dy * hy) % N + N) % N]);
+    }
+    // tap pairs of the gather: (w(dy, dxl), w(dy, dxl + 1)) with zero outside the footprint row
+    for (int i = tid; i < K * (K + 1); i += kThreads) {
+        const int dyi = i / (K + 1), j = i % (K + 1);
+        float2 w[2];
+        for (int u = 0; u < 2; u++) {
+            const int dx = j - 1 + u;
+            w[u] = (dx >= 0 && dx < K)
+                       ? cmul(kern[dyi * K + dx], twN[(((dx - hk) * hx + (dyi - hk) * hy) % N + N) % N])
+                       : make_float2(0.f, 0.f);
+        }
+        tw2[i] = make_float4(w[0].x, w[0].y, w[1].x, w[1].y);
     }
     for (int i = tid; i < TS * P * BUF; i += kThreads) G[i] = make_float2(0.f, 0.f);
     if constexpr (GS)
@@ -218,7 +233,8 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         __syncthreads();
 
         // ---- a3: gridding as a gather: zeros for the uncovered cells of touched rows, then
-        // each lane sums its cell's (antenna, tap) list in registers and stores the cell once
+        // each lane sums its cell pair's (antenna, tap pair) list in registers and stores the
+        // two cells once
         {
             const uint32_t *tb;
             if constexpr (GS) tb = stab;
@@ -240,34 +256,55 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             uint32_t hdr = my_idx.w > 0 ? ld(bt) : 0u;
             for (int b = 0; b < my_idx.w; b++) {
                 const int d = static_cast<int>(hdr);
-                const uint32_t cell = ld(bt + 1 + lane);
+                const uint32_t cell = ld(bt + 1 + lane);              // left cell of the lane's pair
                 const uint32_t *ent = bt + 33 + lane;
                 const uint32_t *next = bt + 33 + d * 32;
                 if (b + 1 < my_idx.w) hdr = ld(next);                 // next batch's length in flight
-                float2 acc_g[TS][P];
+                float2 acc_g[TS][P][2];
 #pragma unroll
                 for (int ts = 0; ts < TS; ts++)
 #pragma unroll
-                    for (int p = 0; p < P; p++) acc_g[ts][p] = make_float2(0.f, 0.f);
+                    for (int p = 0; p < P; p++) acc_g[ts][p][0] = acc_g[ts][p][1] = make_float2(0.f, 0.f);
                 uint32_t en = d > 0 ? ld(ent) : ~0u;
                 for (int j = 0; j < d; j++) {
                     const uint32_t cur = en;
                     if (j + 1 < d) en = ld(ent + (j + 1) * 32);        // next step's entry in flight
                     if (cur != ~0u) {
-                        const int a = static_cast<int>(cur >> 8), tap = static_cast<int>(cur & 0xFFu);
+                        const int a = static_cast<int>(cur >> 8), tp = static_cast<int>(cur & 0xFFu);
+                        float2 w[2];
+                        if (nker > 1) {   // per-antenna kernels: the pair from the antenna's taps
+                            const int dyi = tp / (K + 1), dxl = tp - dyi * (K + 1) - 1;
+                            const float2 *wrow = tapw + a * KK + dyi * K;
+                            w[0] = dxl >= 0 ? wrow[dxl] : make_float2(0.f, 0.f);
+                            w[1] = dxl + 1 < K ? wrow[dxl + 1] : make_float2(0.f, 0.f);
+                        } else {
+                            const float4 ww = tw2[tp];
+                            w[0] = make_float2(ww.x, ww.y);
+                            w[1] = make_float2(ww.z, ww.w);
+                        }
                         // cell += w e as two packed FMAs: w.x (e.x, e.y) + (-w.y, w.y) (e.y, e.x)
-                        const float2 w = tapw[(nker > 1 ? a * KK : 0) + tap];
-                        const float2 wr = make_float2(w.x, w.x), wi = make_float2(-w.y, w.y);
+                        float2 wr[2], wi[2];
+#pragma unroll
+                        for (int u = 0; u < 2; u++) {
+                            wr[u] = make_float2(w[u].x, w[u].x);
+                            wi[u] = make_float2(-w[u].y, w[u].y);
+                        }
 #pragma unroll
                         for (int ts = 0; ts < TS; ts++) {
+                            float2 e[P];
                             if constexpr (P == 2) {
                                 const float4 e2 = reinterpret_cast<const float4 *>(es + ts * AP)[a];
-                                const float2 e0 = make_float2(e2.x, e2.y), e1 = make_float2(e2.z, e2.w);
-                                acc_g[ts][0] = pfma(wi, pswap(e0), pfma(wr, e0, acc_g[ts][0]));
-                                acc_g[ts][1] = pfma(wi, pswap(e1), pfma(wr, e1, acc_g[ts][1]));
+                                e[0] = make_float2(e2.x, e2.y);
+                                e[1] = make_float2(e2.z, e2.w);
                             } else {
-                                const float2 e0 = es[ts * AP + a];
-                                acc_g[ts][0] = pfma(wi, pswap(e0), pfma(wr, e0, acc_g[ts][0]));
+                                e[0] = es[ts * AP + a];
+                            }
+#pragma unroll
+                            for (int p = 0; p < P; p++) {
+                                const float2 esw = pswap(e[p]);
+#pragma unroll
+                                for (int u = 0; u < 2; u++)
+                                    acc_g[ts][p][u] = pfma(wi[u], esw, pfma(wr[u], e[p], acc_g[ts][p][u]));
                             }
                         }
                     }
@@ -276,7 +313,10 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
 #pragma unroll
                     for (int ts = 0; ts < TS; ts++)
 #pragma unroll
-                        for (int p = 0; p < P; p++) G[(ts * P + p) * BUF + cell] = acc_g[ts][p];
+                        for (int p = 0; p < P; p++) {
+                            G[(ts * P + p) * BUF + cell] = acc_g[ts][p][0];
+                            G[(ts * P + p) * BUF + cell + 1] = acc_g[ts][p][1];
+                        }
                 }
                 bt = next;
             }
@@ -367,6 +407,7 @@ size_t reg64_smem(int A, int K, int nker)
     const int AP = A * P;
     size_t b = sizeof(float2) * (static_cast<size_t>(TS) * P * M * (M + 1) + static_cast<size_t>(TS) * AP + AP +
                                  static_cast<size_t>(nker) * K * K);
+    b += sizeof(float4) * static_cast<size_t>(K) * (K + 1);
     b += sizeof(uint32_t) * TS * ((AP + 3) / 4);
     return (b + 15) & ~static_cast<size_t>(15);
 }

@@ -248,20 +248,24 @@ int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, int M, 
 }
 
 // Gather table of the FP32 register-transform kernel (fold side M = 64 or 48).
-// Per channel every folded cell lists the (antenna, tap) pairs whose footprints
-// cover it; a lane owns one cell, sums its list in registers and stores the
-// cell once, so the gridding reads no grid cell and needs no cleared grid.
-// Cells are sorted by list length and dealt in batches of 32 lanes (one list
-// step per warp iteration; a batch runs as long as its longest list).  Within
-// each group of lanes that one shared-memory request serves (8 for the 16-byte
-// dual-polarisation voltage loads, 16 for the 8-byte single-polarisation ones)
-// the list order is chosen greedily so that one step reads distinct banks.
-// Cells no footprint covers in rows that some footprint touches get zeros,
-// from per-warp lists of 32 cells per step; rows nobody touches are skipped by
-// the transform and need nothing.  Batches go to the warps longest first, each
-// to the warp with the least work so far, then the zero steps.
+// A lane owns a pair of horizontally adjacent folded cells (x = 2 xp, 2 xp + 1)
+// and sums, in registers, the (antenna, tap pair) entries whose footprints cover
+// either cell: one voltage load serves both cells, and an antenna whose row
+// segment covers only one of them brings a zero weight for the other.  Each
+// pair is stored once per plane, so the gridding reads no grid cell and needs
+// no cleared grid.  Pairs are sorted by list length and dealt in batches of 32
+// lanes (one list step per warp iteration; a batch runs as long as its longest
+// list).  Within each group of lanes that one shared-memory request serves (8
+// for the 16-byte dual-polarisation voltage loads, 16 for the 8-byte
+// single-polarisation ones) the list order is chosen greedily so that one step
+// reads distinct banks.  Cells of touched rows that no listed pair writes get
+// zeros, from per-warp lists of 32 cells per step; rows nobody touches are
+// skipped by the transform and need nothing.  Batches go to the warps longest
+// first, each to the warp with the least work so far, then the zero steps.
+//   entry: a << 8 | tp, tp = dyi (K + 1) + dxl + 1, dxl in [-1, K - 1] the tap column of the left
+//          cell (-1: only the right cell is covered; K - 1: only the left one)
 //   channel block: [zero lists of warps 0..7][gather batches of warps 0..7]
-//   gather batch:  [length d][32 cell offsets y (M + 1) + x, or ~0][d x 32 entries a << 8 | tap, or ~0]
+//   gather batch:  [length d][32 left-cell offsets y (M + 1) + 2 xp, or ~0][d x 32 entries, or ~0]
 //   idx[ci * 8 + w] = (zero list offset, zero steps, first batch offset, batches), offsets from the
 //   channel block's start; chan[ci] = (block start, block words)
 int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, int P, const std::vector<int> &chans,
@@ -269,7 +273,7 @@ int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, in
                        std::vector<unsigned long long> &rowmask)
 {
     constexpr int W = 8;
-    const int h = (K - 1) / 2, S = M + 1;
+    const int h = (K - 1) / 2, S = M + 1, MP = M / 2;
     if (A > 4096 || K > 15 || (M != 64 && M != 48)) return EPIC_ERR_UNSUPPORTED;
     const int nc = static_cast<int>(chans.size());
     const int grp = P == 2 ? 8 : 16;    // lanes per request; bank slot = a mod grp
@@ -279,27 +283,36 @@ int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, in
     rowmask.assign(nc, 0ull);
     for (int ci = 0; ci < nc; ci++) {
         const int c = chans[ci];
-        std::vector<std::vector<uint32_t>> list(M * M);   // per cell: a << 8 | tap
+        std::vector<std::vector<uint32_t>> list(M * MP);   // per pair: a << 8 | tp
         for (int a = 0; a < A; a++) {
             const short2 k = cells[static_cast<size_t>(c) * A + a];
             const int jx = k.x % M, jy = k.y % M;
+            const int x0 = ((jx - h) % M + M) % M;
             for (int dyi = 0; dyi < K; dyi++) {
                 const int y = ((jy + dyi - h) % M + M) % M;
                 rowmask[ci] |= 1ull << y;
+                int last = -1;
                 for (int dx = 0; dx < K; dx++) {
-                    const int x = ((jx + dx - h) % M + M) % M;
-                    list[y * M + x].push_back((static_cast<uint32_t>(a) << 8) | static_cast<uint32_t>(dyi * K + dx));
+                    const int x = (x0 + dx) % M, pr = x >> 1;
+                    if (pr == last) continue;   // the right cell of a pair already listed
+                    last = pr;
+                    const int dxl = dx - (x & 1);
+                    list[y * MP + pr].push_back((static_cast<uint32_t>(a) << 8) |
+                                                static_cast<uint32_t>(dyi * (K + 1) + dxl + 1));
                 }
             }
         }
         std::vector<int> touched, zero;
-        for (int i = 0; i < M * M; i++) {
+        for (int i = 0; i < M * MP; i++)
             if (!list[i].empty()) touched.push_back(i);
-            else if ((rowmask[ci] >> (i / M)) & 1ull) zero.push_back(i);
+        for (int i = 0; i < M * M; i++) {
+            const int y = i / M, x = i % M;
+            if (((rowmask[ci] >> y) & 1ull) && list[y * MP + x / 2].empty()) zero.push_back(i);
         }
         std::stable_sort(touched.begin(), touched.end(),
                          [&](int u, int v) { return list[u].size() > list[v].size(); });
         auto cell_word = [&](int i) { return static_cast<uint32_t>((i / M) * S + i % M); };
+        auto pair_word = [&](int i) { return static_cast<uint32_t>((i / MP) * S + 2 * (i % MP)); };
         std::vector<std::vector<uint32_t>> batches;
         for (size_t b0 = 0; b0 < touched.size(); b0 += 32) {
             const int nl = static_cast<int>(std::min<size_t>(32, touched.size() - b0));
@@ -307,7 +320,7 @@ int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, in
             for (int l = 0; l < nl; l++) d = std::max(d, static_cast<int>(list[touched[b0 + l]].size()));
             std::vector<uint32_t> words(1 + 32 + static_cast<size_t>(d) * 32, ~0u);
             words[0] = static_cast<uint32_t>(d);
-            for (int l = 0; l < nl; l++) words[1 + l] = cell_word(touched[b0 + l]);
+            for (int l = 0; l < nl; l++) words[1 + l] = pair_word(touched[b0 + l]);
             for (int g0 = 0; g0 < 32; g0 += grp) {
                 std::vector<std::vector<uint32_t>> rem(grp);
                 for (int l = 0; l < grp; l++)

@@ -1,8 +1,9 @@
 // Host-side checks of the two gridding tables the plan builds (no GPU needed):
 //  * build_gather_table: every (cell, antenna, tap) contribution of every footprint appears
-//    exactly once, under the lane that owns its cell; every cell of a touched row is written
-//    exactly once per sample (by a list or a zero step); block offsets stay inside the block;
-//    the warps' list steps are balanced;
+//    exactly once, under the lane that owns its cell pair (an entry's tap pair expanded to the
+//    covered cells); every cell of a touched row is written exactly once per sample (by a pair's
+//    store or a zero step); block offsets stay inside the block; the warps' list steps are
+//    balanced;
 //  * build_reg64_schedule: every footprint row segment appears once; no two segments of a round
 //    share a cell; the 16 lanes of a half-warp start on distinct (y + x0) mod 16 bank pairs;
 //    the first-write masks mark exactly one tap per touched cell.
@@ -70,7 +71,7 @@ int main(int argc, char **argv)
         CHECK(rows[ci] == want_rows, "channel %d: touched-row mask", ci);
         std::map<uint32_t, int> written;
         const long long base = chan[ci].x, end = base + chan[ci].y;
-        long long wmin = 1LL << 40, wmax = 0;
+        long long wmin = 1LL << 40, wmax = 0, dmax = 0;
         for (int w = 0; w < 8; w++) {
             const int4 ix = idx[ci * 8 + w];
             for (int r = 0; r < ix.y; r++)
@@ -85,17 +86,28 @@ int main(int argc, char **argv)
                 CHECK(off + 33 + 32LL * d <= end, "channel %d warp %d: batch outside its block", ci, w);
                 if (off + 33 + 32LL * d > end) break;
                 for (int l = 0; l < 32; l++) {
-                    const uint32_t cell = tab[off + 1 + l];
-                    if (cell != ~0u) written[cell]++;
+                    const uint32_t cell = tab[off + 1 + l];   // left cell of the pair
+                    if (cell != ~0u) {
+                        CHECK((cell % S) % 2 == 0, "channel %d: pair not starting at an even column", ci);
+                        written[cell]++;
+                        written[cell + 1]++;
+                    }
                     for (int j = 0; j < d; j++) {
                         const uint32_t e = tab[off + 33 + 32LL * j + l];
                         if (e == ~0u) continue;
                         CHECK(cell != ~0u, "channel %d: entry under an empty lane", ci);
-                        got.insert((static_cast<long long>(cell) << 32) | e);
+                        const long long a = e >> 8;
+                        const int tp = e & 0xFF, dyi = tp / (K + 1), dxl = tp % (K + 1) - 1;
+                        CHECK(dyi < K && (dxl >= 0 || dxl + 1 < K), "channel %d: tap pair %d", ci, tp);
+                        if (dxl >= 0)
+                            got.insert((static_cast<long long>(cell) << 32) | (a << 8) | (dyi * K + dxl));
+                        if (dxl + 1 < K)
+                            got.insert((static_cast<long long>(cell + 1) << 32) | (a << 8) | (dyi * K + dxl + 1));
                     }
                 }
                 off += 33 + 32LL * d;
                 steps += d;
+                dmax = std::max(dmax, static_cast<long long>(d));
             }
             wmin = std::min(wmin, steps);
             wmax = std::max(wmax, steps);
@@ -108,8 +120,10 @@ int main(int argc, char **argv)
                 CHECK(n == (((want_rows >> y) & 1ull) ? 1 : 0), "channel %d: cell (%d, %d) written %d times", ci, y,
                       x, n);
             }
-        // balance: the longest warp within one batch depth plus a few steps of the shortest
-        CHECK(wmax - wmin <= 2 + wmax / 8, "channel %d: warp list steps %lld .. %lld", ci, wmin, wmax);
+        // balance (longest batch first to the least-loaded warp): the warps' list steps differ by at
+        // most one batch
+        CHECK(wmax - wmin <= dmax, "channel %d: warp list steps %lld .. %lld (longest batch %lld)", ci, wmin,
+              wmax, dmax);
     }
 
     // ---- round schedule (tensor kernels)
