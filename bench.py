@@ -41,19 +41,19 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic of one launch of the dominant kernel from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload, with the
 # hash of the kernel source it was taken on; ignored once the source changes.
-# lwa: one full 64-channel launch captured: 35 510 528 B read (the 32.8 MB ci4
-# input plus tables) + 75 219 456 B written (time-chunk partial sums that spill
+# lwa: one full 64-channel launch captured: 35 249 664 B read (the 32.8 MB ci4
+# input plus tables) + 74 313 728 B written (time-chunk partial sums that spill
 # out of L2 before the epilogue reads them).
-NCU_TRAFFIC = {"lwa": (110_729_984, "93ce18d7a9f15ae1")}
-# What the same full-set capture shows about the kernel's limits: shared-memory
-# wavefronts per SM cycle at the capture's clock (against 1 per cycle, 128 B/clk),
-# issue and FMA-pipe activity.  With the gather gridding none of them is saturated:
-# 8 warps per SM (the register transforms take 226 registers) leave the kernel
-# bound by latency (stalls per issue: wait 1.14, short scoreboard 0.87).
-NCU_LIMITER = {"lwa": ({"unit": "shared-memory wavefronts per SM cycle", "achieved": 0.66, "peak": 1.0,
-                        "wavefronts_per_launch": 1_330_587_656, "issue_active_pct": 45.0,
-                        "fma_pipe_pct": 37.4},
-                       "93ce18d7a9f15ae1")}
+NCU_TRAFFIC = {"lwa": (109_563_392, "1dd260f9e71ea38a")}
+# What the same capture shows about the kernel's limits: shared-memory wavefronts
+# per SM cycle (against 1 per cycle, 128 B/clk) and issue activity.  Neither is
+# saturated: with 8 warps per SM (the register transforms take ~226 registers a
+# thread) the kernel is bound by latency; a phase probe puts 45 % of its time in
+# the gather gridding, which runs near 0.8 wavefronts per cycle.
+NCU_LIMITER = {"lwa": ({"unit": "shared-memory wavefronts per SM cycle", "achieved": 0.67, "peak": 1.0,
+                        "wavefronts_per_launch": 1_241_332_752, "issue_active_pct": 45.1,
+                        "warp_instructions_per_launch": 3_201_891_968},
+                       "1dd260f9e71ea38a")}
 
 
 def parse():
