@@ -119,7 +119,13 @@ enum {
  *                  EPIC_ANTENNA_KERNELS
  *
  * Uses the current CUDA device.  Allocates device memory (tables and
- * workspace) and returns EPIC_ERR_NOMEM if that fails.  Channels with a
+ * workspace) and returns EPIC_ERR_NOMEM if that fails.  The tables include,
+ * per channel, the gridding lists of the FP32 kernel (for every pair of
+ * adjacent folded cells, the antennas whose footprints cover it: 4 bytes per
+ * entry, about A * K * (K + 1) / 2 entries plus padding; 43 KB per channel at
+ * A = 256, K = 5), staged in shared memory by the kernel when they fit (the
+ * environment variable EPIC_GATHER_GLOBAL=1 reads them through L1 instead, a
+ * test hook; the result is bitwise the same).  Channels with a
  * 512 grid side and one shared kernel wider than one tap are imaged by
  * gridding each (channel, sample) once and folding the 64 pixel classes from
  * it: their workspace adds the folded class grids of one time batch, up to

@@ -43,7 +43,7 @@ struct GroupCfg {
     float *d_partial = nullptr;        // device: [tau_cap][n_items][M*M][NPF] partial sums
     // partial-sum pixel order: folded frequency m sits at R2 (m mod R1) + m / R1
     int R1 = 1, R2 = 1;
-    // M = 64 register-transform kernel: gridding schedule and samples per iteration
+    // register-transform kernels (fold side 64 or 48): gridding tables and samples per iteration
     bool reg64 = false;
     bool tensor = false;               // a tensor plan's group that folds to 64 runs the tensor kernel
     bool tc_regular = true;            // the tensor kernel's per-antenna buffers fit (else only the fold path)
