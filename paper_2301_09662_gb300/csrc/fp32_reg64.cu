@@ -13,8 +13,8 @@
 //    two cells;
 //  * the M-point transforms run in registers (one row or column per thread),
 //    so each axis costs one shared-memory read and one write;
-//  * two time samples per iteration share the schedule, the twiddles and the
-//    synchronisation;
+//  * two time samples per iteration share the gather lists (one entry and tap
+//    load serve both samples), the twiddles and the synchronisation;
 //  * the transforms and the gridding multiply-adds run on packed FP32 pairs
 //    (add/sub/mul/fma .f32x2: one instruction for both lanes of a float2).
 #include <type_traits>
