@@ -38,6 +38,9 @@ def checker(tmp_path_factory):
     (101, 3, 64, 2, 1),     # single polarisation: 16-lane bank groups
     (2048, 7, 512, 1, 2),   # dense: long lists
     (4096, 15, 128, 1, 1),  # limits: n_ant * n_pol = 4096, K = 15
+    (64, 3, 96, 2, 1),      # folded side 48, single polarisation
+    (500, 15, 96, 1, 2),    # folded side 48, footprints wider than a bank group
+    (37, 1, 64, 2, 1),      # point kernel, few antennas (fewer batches than warps)
 ])
 def test_tables(checker, A, K, N, C, P):
     r = subprocess.run([checker, str(A), str(K), str(N), str(C), str(P)], capture_output=True, text=True)
