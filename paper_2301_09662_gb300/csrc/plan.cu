@@ -10,6 +10,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <map>
 #include <new>
 
@@ -281,7 +283,11 @@ int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, in
     idx.assign(static_cast<size_t>(nc) * W, make_int4(0, 0, 0, 0));
     chan.assign(nc, make_int2(0, 0));
     rowmask.assign(nc, 0ull);
-    for (int ci = 0; ci < nc; ci++) {
+    // channels are independent: each builds its own block (offsets relative to the block), in
+    // parallel over host threads; the blocks are then laid end to end in channel order, so the
+    // table does not depend on the thread count
+    std::vector<std::vector<uint32_t>> blocks(nc);
+    auto build_one = [&](int ci) -> bool {
         const int c = chans[ci];
         std::vector<std::vector<uint32_t>> list(M * MP);   // per pair: a << 8 | tp
         for (int a = 0; a < A; a++) {
@@ -368,22 +374,51 @@ int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, in
             zsteps[w]++;
             load[w] += 1;
         }
-        const size_t start = tab.size();
-        if (start > 0x7FFFFFFFull) return EPIC_ERR_UNSUPPORTED;
+        std::vector<uint32_t> &blk = blocks[ci];
         size_t zi = 0;   // zero cells dealt in natural order: consecutive cells, distinct banks
         for (int w = 0; w < W; w++) {
-            idx[static_cast<size_t>(ci) * W + w].x = static_cast<int>(tab.size() - start);
+            idx[static_cast<size_t>(ci) * W + w].x = static_cast<int>(blk.size());
             idx[static_cast<size_t>(ci) * W + w].y = zsteps[w];
             for (int st = 0; st < zsteps[w]; st++)
-                for (int l = 0; l < 32; l++, zi++) tab.push_back(zi < zero.size() ? cell_word(zero[zi]) : ~0u);
+                for (int l = 0; l < 32; l++, zi++) blk.push_back(zi < zero.size() ? cell_word(zero[zi]) : ~0u);
         }
         for (int w = 0; w < W; w++) {
-            idx[static_cast<size_t>(ci) * W + w].z = static_cast<int>(tab.size() - start);
+            idx[static_cast<size_t>(ci) * W + w].z = static_cast<int>(blk.size());
             idx[static_cast<size_t>(ci) * W + w].w = static_cast<int>(per_warp[w].size());
-            for (int b : per_warp[w]) tab.insert(tab.end(), batches[b].begin(), batches[b].end());
+            for (int b : per_warp[w]) blk.insert(blk.end(), batches[b].begin(), batches[b].end());
+            if (blk.size() > 0x7FFFFFFFull) return false;
         }
-        if (tab.size() - start > 0x7FFFFFFFull) return EPIC_ERR_UNSUPPORTED;
-        chan[ci] = make_int2(static_cast<int>(start), static_cast<int>(tab.size() - start));
+        return true;
+    };
+    std::atomic<int> next{0};
+    std::atomic<bool> ok{true};
+    auto worker = [&]() {
+        for (int ci; ok && (ci = next++) < nc;) {
+            try {
+                if (!build_one(ci)) ok = false;
+            } catch (...) {
+                ok = false;
+            }
+        }
+    };
+    const int nt = std::max(1, std::min({nc, 16, static_cast<int>(std::thread::hardware_concurrency())}));
+    std::vector<std::thread> pool;
+    for (int i = 1; i < nt; i++) {
+        try {
+            pool.emplace_back(worker);
+        } catch (...) {
+            break;   // fewer threads: the calling thread takes the rest
+        }
+    }
+    worker();
+    for (auto &th : pool) th.join();
+    if (!ok) return EPIC_ERR_UNSUPPORTED;
+    for (int ci = 0; ci < nc; ci++) {
+        const size_t start = tab.size();
+        if (start + blocks[ci].size() > 0x7FFFFFFFull) return EPIC_ERR_UNSUPPORTED;
+        chan[ci] = make_int2(static_cast<int>(start), static_cast<int>(blocks[ci].size()));
+        tab.insert(tab.end(), blocks[ci].begin(), blocks[ci].end());
+        std::vector<uint32_t>().swap(blocks[ci]);
     }
     if (tab.empty()) tab.push_back(0);
     return EPIC_OK;
