@@ -267,9 +267,8 @@ def run_reference(args):
 
 
 def tensor_stages():
-    """DFT stages the tensor form runs as GEMMs: both (default), or the column
-    stage alone when EPIC_TC_PIPE=1 or EPIC_TC_SERIAL=1 selects an earlier form."""
-    return 1 if os.environ.get("EPIC_TC_PIPE") == "1" or os.environ.get("EPIC_TC_SERIAL") == "1" else 2
+    """DFT stages the tensor form runs as GEMMs: both, the row and the column stage."""
+    return 2
 
 
 def tensor_roofline(wl, form, img_ms, peaks):

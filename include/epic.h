@@ -72,7 +72,8 @@ enum {
     EPIC_FP32 = 0,              /* FP32 SIMT: shared-memory gridding and FFT */
     EPIC_TC_SPLIT_FP16 = 1,     /* tensor cores, split hi+lo FP16 operands, FP32 accumulate */
     EPIC_TC_FP16 = 2,           /* tensor cores, single FP16 operands */
-    EPIC_TC_SPLIT_BF16 = 3      /* tensor cores, three-term BF16 split */
+    EPIC_TC_SPLIT_BF16 = 3      /* tensor cores, two-part BF16 split (hi + lo, 3 MMAs per k-block): about
+                                   16 significant bits, bounded by 1e-4 of the peak, not 1e-5 */
 };
 
 /* flags */
@@ -98,6 +99,22 @@ enum {
 #define EPIC_ANTENNA_KERNELS 16u
 
 /*
+ * Diagnostic plan options, in the flags word from bit 8 up.  They exist for
+ * the library's own tests and measurements: each selects another route to the
+ * same result (or, for EPIC_DIAG_WITHHOLD_MMA, injects a fault), and nothing
+ * but an explicit flag turns one on.
+ */
+#define EPIC_DIAG_NO_GRAPH       (1u << 8)   /* launch each kernel directly instead of replaying a CUDA graph */
+#define EPIC_DIAG_GATHER_GLOBAL  (1u << 9)   /* FP32 register kernel: read the gather table through L1 instead
+                                                of staging it in shared memory (bitwise the same result) */
+#define EPIC_DIAG_NO_ALIAS       (1u << 10)  /* 512 grid sides: grid per pixel class instead of folding */
+#define EPIC_DIAG_WITHHOLD_MMA   (1u << 11)  /* fault injection: the tensor kernel issues no MMA, its bounded
+                                                wait (budget ~1 ms) runs out and epic_status reports
+                                                EPIC_ERR_TIMEOUT; the context stays usable */
+#define EPIC_DIAG_ALIAS_BATCH(n) ((((unsigned)(n)) & 255u) << 16)   /* fold path: at most n (1..255) samples
+                                                                        per time batch */
+
+/*
  * epic_plan -- validate the array geometry and build every table the imaging
  * calls need (Sec. 3.1 grid and antenna-to-cell map; Eq. 4 kernel image).
  *
@@ -116,21 +133,18 @@ enum {
  *   max_spectra    largest n_spectra an epic_image call will pass (>= 0)
  *   precision      EPIC_FP32 or one of the EPIC_TC_* forms
  *   flags          EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER | EPIC_STOKES |
- *                  EPIC_ANTENNA_KERNELS
+ *                  EPIC_ANTENNA_KERNELS, plus the EPIC_DIAG_* options above
  *
  * Uses the current CUDA device.  Allocates device memory (tables and
  * workspace) and returns EPIC_ERR_NOMEM if that fails.  The tables include,
  * per channel, the gridding lists of the FP32 kernel (for every pair of
  * adjacent folded cells, the antennas whose footprints cover it: 4 bytes per
  * entry, about A * K * (K + 1) / 2 entries plus padding; 43 KB per channel at
- * A = 256, K = 5), staged in shared memory by the kernel when they fit (the
- * environment variable EPIC_GATHER_GLOBAL=1 reads them through L1 instead, a
- * test hook; the result is bitwise the same).  Channels with a
- * 512 grid side and one shared kernel wider than one tap are imaged by
- * gridding each (channel, sample) once and folding the 64 pixel classes from
- * it: their workspace adds the folded class grids of one time batch, up to
- * 4 GiB (C * 64 * n_pol * 32 KB per spectrum, batched); the environment
- * variable EPIC_NO_ALIAS=1 keeps the per-class gridding instead.  Returns
+ * A = 256, K = 5), staged in shared memory by the kernel when they fit.
+ * Channels with a 512 grid side and one shared kernel wider than one tap are
+ * imaged by gridding each (channel, sample) once and folding the 64 pixel
+ * classes from it: their workspace adds the folded class grids of one time
+ * batch, up to 4 GiB (C * 64 * n_pol * 32 KB per spectrum, batched).  Returns
  * EPIC_ERR_OUT_OF_GRID when some antenna footprint k_a +- (K-1)/2 leaves
  * [0, N_c) in some channel; EPIC_ERR_UNSUPPORTED for a grid side, precision or
  * size this build does not provide.
@@ -365,12 +379,27 @@ typedef struct epic_search_s *epic_search_t;
  *   width_mask  boxcar widths of the single-pulse search: bit k = width 2^k,
  *               k < 6 (1 .. 32 samples); at least one bit
  *
+ * width_mask may also carry diagnostic options, from bit 8 up (tests and
+ * measurements only; the result is bitwise the same in every form):
+ *   EPIC_SEARCH_DIAG_DM32     blocks of 32 trial DMs where they fit (else 16)
+ *   EPIC_SEARCH_DIAG_DIRECT   the direct form (each warp loads its own sweep)
+ *   EPIC_SEARCH_DIAG_NO_PIX2  unit-stride cubes on the one-pixel staged form
+ *   EPIC_SEARCH_DIAG_NO_TMA   no tensor-memory-access copies (cp.async forms)
+ *   EPIC_SEARCH_DIAG_WITHHOLD_TMA  fault injection: the TMA form's producer
+ *       skips channel 0, the consumers' bounded wait (~1 ms) runs out and
+ *       epic_search_status reports EPIC_ERR_TIMEOUT
+ *
  * Channel c at trial d is delayed by s = floor(k_DM DM (f_c^-2 - f_max^-2) / dt
  * + 1/2) samples (f in MHz, k_DM = 4.148808e3 s MHz^2 pc^-1 cm^3, FP64 on the
  * host); t_out = n_time - max s output samples remain.  EPIC_ERR_ARG for bad
  * arguments, EPIC_ERR_TOO_LARGE when the largest delay leaves fewer output
  * samples than the smallest width.  The plan owns the device delay table.
  */
+#define EPIC_SEARCH_DIAG_DM32         (1u << 8)
+#define EPIC_SEARCH_DIAG_DIRECT       (1u << 9)
+#define EPIC_SEARCH_DIAG_NO_PIX2      (1u << 10)
+#define EPIC_SEARCH_DIAG_NO_TMA       (1u << 11)
+#define EPIC_SEARCH_DIAG_WITHHOLD_TMA (1u << 12)
 int epic_search_plan(epic_search_t *out, const double *freq_hz, int n_chan, double dt_s,
                      const double *dm, int n_dm, int n_pix, int n_time, unsigned width_mask);
 

@@ -203,10 +203,16 @@ int build_alias_tables(const std::vector<short2> &cells, int A, int K, int N, co
     return EPIC_OK;
 }
 
+// The cap is per kernel and process, and this plan's size depends on K: raise it
+// to the device's opt-in limit so a later plan with a smaller K cannot lower it.
 int prepare_alias(const epic_plan_s *plan)
 {
-    if (cudaFuncSetAttribute(alias_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(alias_smem(plan->K))) != cudaSuccess)
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return EPIC_ERR_CUDA;
+    if (alias_smem(plan->K) > static_cast<size_t>(optin) ||
+        cudaFuncSetAttribute(alias_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
         return EPIC_ERR_UNSUPPORTED;
     return prepare_fold64(plan->P);
 }

@@ -88,9 +88,7 @@ struct epic_plan_s {
     std::vector<int> grid_n;
     std::vector<long long> out_off;    // complex-element offset of each channel's image
     size_t out_floats = 0;
-    uint8_t *d_dft = nullptr;          // tensor form: column-DFT operand (hi, lo parts)
-    uint16_t *d_dft_rows = nullptr;    // pipelined tensor form: the same operand as plain rows
-    int tc_form = 2;                   // tensor kernel: 0 serial column DFT, 1 pipelined column DFT, 2 both DFTs
+    uint8_t *d_dft = nullptr;          // tensor form: the 64-point DFT operand (hi, lo parts)
     short2 *d_cells = nullptr;         // [C][A]
     float2 *d_kernel = nullptr;        // [K*K]
     int *d_autoint = nullptr;          // [C][A][4] exact integer auto sums
@@ -158,13 +156,8 @@ int launch_epilogue_series(epic_plan_s *plan, const GroupCfg &g, const float2 *g
 int launch_imaging(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                    cudaStream_t stream);
 
-// tensor-core form (tc_col64.cu)
-size_t tc_smem_bytes(int A, int K);
-int prepare_tc(const epic_plan_s *plan);
-int launch_tc(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
-              cudaStream_t stream);
+// tensor-core form, both 64-point DFT stages on tcgen05 (tc_dual64.cu)
 void build_dft_operand(bool bf16, std::vector<uint16_t> &words);
-size_t tc_pipe_smem_bytes(int A, int K);
 size_t tc_dual_smem_bytes(int A, int K);
 int prepare_tc_dual(const epic_plan_s *plan, size_t smem);
 size_t tc_dual_fold_smem_bytes();
@@ -172,10 +165,6 @@ int launch_tc_dual_fold(epic_plan_s *plan, const GroupCfg &g, const float2 *gain
                         bool accumulate, cudaStream_t stream);
 int launch_tc_dual(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                    cudaStream_t stream);
-int prepare_tc_pipe(const epic_plan_s *plan);
-int launch_tc_pipe(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
-                   cudaStream_t stream);
-void build_dft_rows(bool bf16, std::vector<uint16_t> &words);
 
 // Gather table of the FP32 register-transform kernel for the channels of one group (plan.cu).
 int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, int P, const std::vector<int> &chans,

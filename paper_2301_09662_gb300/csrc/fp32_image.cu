@@ -312,13 +312,28 @@ int launch_group(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
+// The dynamic shared-memory cap of a kernel holds for the whole process, so it
+// is raised to the device's opt-in limit rather than to one caller's size: a
+// later plan or static call that needs less must not lower it under a plan
+// that needs more.
+int raise_smem_cap(const void *kfn, size_t need)
+{
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return EPIC_ERR_CUDA;
+    if (need > static_cast<size_t>(optin)) return EPIC_ERR_UNSUPPORTED;
+    return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) == cudaSuccess
+               ? EPIC_OK
+               : EPIC_ERR_UNSUPPORTED;
+}
+
 template <int M, int P>
 int prepare_group(const epic_plan_s *plan)
 {
     auto kfn = fp32_image_kernel<M, P>;
     const size_t smem = smem_bytes<M, P>(plan->A, plan->K, plan->nker);
-    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
-        return EPIC_ERR_UNSUPPORTED;
+    if (const int rc = raise_smem_cap(reinterpret_cast<const void *>(kfn), smem); rc != EPIC_OK) return rc;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, smem) != cudaSuccess || per_sm < 1)
         return EPIC_ERR_UNSUPPORTED;
@@ -330,8 +345,7 @@ int launch_raw(const RawImage &r, const uint8_t *v, const float2 *gains, cudaStr
 {
     auto kfn = fp32_image_kernel<M, P>;
     const size_t smem = smem_bytes<M, P>(r.A, r.K);
-    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
-        return EPIC_ERR_UNSUPPORTED;
+    if (const int rc = raise_smem_cap(reinterpret_cast<const void *>(kfn), smem); rc != EPIC_OK) return rc;
     const dim3 grid(static_cast<unsigned>(r.n_items * r.n_tau));
     kfn<<<grid, kThreads, smem, stream>>>(v, gains, r.cells, r.kernel, r.K, r.chans, r.twN, r.A, r.C, r.T, r.N, r.Q1,
                                           r.n_items, r.n_tau, r.partial, r.status, 1, nullptr, nullptr);
@@ -396,9 +410,7 @@ int launch_imaging(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
     if (g.alias && plan->force_tau == 0) return launch_alias(plan, g, v, gains, T, n_tau, s);
     if (g.tensor && !g.tc_regular) return EPIC_ERR_UNSUPPORTED;   // e.g. an image series: no fold path there
     if (g.tensor)
-        return plan->tc_form == 2   ? launch_tc_dual(plan, g, v, gains, T, n_tau, s)
-               : plan->tc_form == 1 ? launch_tc_pipe(plan, g, v, gains, T, n_tau, s)
-                                    : launch_tc(plan, g, v, gains, T, n_tau, s);
+        return launch_tc_dual(plan, g, v, gains, T, n_tau, s);
     if (g.reg64) return launch_reg64(plan, g, v, gains, T, n_tau, s);
     switch (g.M * 4 + plan->P) {
     case 32 * 4 + 2: return launch_group<32, 2>(plan, g, v, gains, T, n_tau, s);

@@ -64,7 +64,6 @@ void free_plan(epic_plan_s *p)
     cudaFree(p->d_cells);
     cudaFree(p->d_kernel);
     cudaFree(p->d_dft);
-    cudaFree(p->d_dft_rows);
     cudaFree(p->d_bauto);
     cudaFree(p->d_autoint);
     cudaFree(p->d_status);
@@ -519,8 +518,12 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     if (n_ant < 1 || (n_pol != 1 && n_pol != 2) || K < 1 || (K % 2) == 0 || K > epic::kMaxK ||
         n_chan < 1 || !(du > 0.0) || du > 0.5 || max_spectra < 0)
         return EPIC_ERR_ARG;
-    if (flags & ~(EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER | EPIC_STOKES | EPIC_ANTENNA_KERNELS))
-        return EPIC_ERR_ARG;
+    constexpr unsigned kUser = EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER | EPIC_STOKES | EPIC_ANTENNA_KERNELS;
+    constexpr unsigned kDiag = EPIC_DIAG_NO_GRAPH | EPIC_DIAG_GATHER_GLOBAL | EPIC_DIAG_NO_ALIAS |
+                               EPIC_DIAG_WITHHOLD_MMA | EPIC_DIAG_ALIAS_BATCH(255);
+    if (flags & ~(kUser | kDiag)) return EPIC_ERR_ARG;
+    const unsigned diag = flags & kDiag;
+    flags &= kUser;
     if ((flags & EPIC_STOKES) && n_pol != 2) return EPIC_ERR_ARG;
     const bool ant_kernels = (flags & EPIC_ANTENNA_KERNELS) != 0;
     if (ant_kernels && (flags & EPIC_KERNEL_TAPER)) return EPIC_ERR_ARG;
@@ -675,14 +678,11 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         g.R2 = g.M / 8;
         const int ap = n_ant * n_pol;
         g.tensor = tensor && g.M == 64;
-        const char *na = std::getenv("EPIC_NO_ALIAS");
-        const bool fold_ok = g.Q1 == 8 && p->nker == 1 && p->K > 1 && !(na && na[0] == '1');
+        const bool fold_ok = g.Q1 == 8 && p->nker == 1 && p->K > 1 && !(diag & EPIC_DIAG_NO_ALIAS);
         if (g.tensor) {
             // + static shared memory of the kernel (barriers, TMEM slot, alignment); a large side
             // that can take the fold path needs only the operands and the grid there
-            g.tc_regular = std::max({epic::tc_smem_bytes(n_ant, p->K), epic::tc_pipe_smem_bytes(n_ant, p->K),
-                                     epic::tc_dual_smem_bytes(n_ant, p->K)}) + 2048 <=
-                           static_cast<size_t>(smem_optin);
+            g.tc_regular = epic::tc_dual_smem_bytes(n_ant, p->K) + 2048 <= static_cast<size_t>(smem_optin);
             if (!g.tc_regular && !(fold_ok && epic::tc_dual_fold_smem_bytes() + 2048 <= static_cast<size_t>(smem_optin)))
                 rc = EPIC_ERR_UNSUPPORTED;
             g.reg64 = true;   // same gridding schedule and natural pixel order
@@ -722,8 +722,7 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                 g.gstage = epic::reg64_smem_bytes(g.M, n_pol, g.ts, n_ant, p->K, p->nker) +
                                sizeof(uint32_t) * static_cast<size_t>(g.gwords) <=
                            static_cast<size_t>(smem_optin);
-                const char *ng = std::getenv("EPIC_GATHER_GLOBAL");   // test hook: the unstaged form
-                if (ng && ng[0] == '1') g.gstage = false;
+                if (diag & EPIC_DIAG_GATHER_GLOBAL) g.gstage = false;   // the unstaged form
             }
             if (rc == EPIC_OK) rc = dev_upload(&g.d_rowmask, rows.data(), rows.size());
             // large sides with one shared kernel of more than one tap: grid once per (channel,
@@ -739,9 +738,9 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                     const size_t per_sample = static_cast<size_t>(g.n_items) * n_pol * 64 * 64 * sizeof(float2);
                     constexpr size_t kBudget = size_t(4) << 30;   // folded grids of one time batch
                     g.alias_tb = static_cast<int>(std::max<size_t>(1, std::min<size_t>(max_spectra, kBudget / per_sample)));
-                    // EPIC_ALIAS_BATCH caps the time batch (tests: several batches on a small case)
-                    const char *ab = std::getenv("EPIC_ALIAS_BATCH");
-                    if (ab && std::atoi(ab) > 0) g.alias_tb = std::min(g.alias_tb, std::atoi(ab));
+                    // a diagnostic cap on the time batch (tests: several batches on a small case)
+                    const int cap_tb = static_cast<int>((diag >> 16) & 255u);
+                    if (cap_tb > 0) g.alias_tb = std::min(g.alias_tb, cap_tb);
                     rc = dev_upload(&g.d_j0, j0.data(), j0.size());
                     if (rc == EPIC_OK) rc = dev_upload(&g.d_bseg, bseg.data(), std::max<size_t>(1, bseg.size()));
                     if (rc == EPIC_OK) rc = dev_upload(&g.d_boff, boff.data(), boff.size());
@@ -780,30 +779,18 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         rc = dev_upload(&p->d_autoint, static_cast<const int *>(nullptr),
                         static_cast<size_t>(p->series_cap) * n_chan * n_ant * 4);
     if (rc == EPIC_OK && tensor) {
-        // both DFT stages on the tensor cores unless EPIC_TC_PIPE=1 (column stage only,
-        // pipelined) or EPIC_TC_SERIAL=1 (column stage only, one sample at a time) asks otherwise
-        const char *ser = std::getenv("EPIC_TC_SERIAL");
-        const char *pip = std::getenv("EPIC_TC_PIPE");
-        p->tc_form = (ser && ser[0] == '1') ? 0 : (pip && pip[0] == '1') ? 1 : 2;
+        // both 64-point DFT stages on the tensor cores (tc_dual64.cu)
         std::vector<uint16_t> ops;
-        if (p->tc_form == 1) {
-            epic::build_dft_rows(precision == EPIC_TC_SPLIT_BF16, ops);
-            rc = dev_upload(&p->d_dft_rows, ops.data(), ops.size());
-            if (rc == EPIC_OK) rc = epic::prepare_tc_pipe(p);
-        } else {
-            epic::build_dft_operand(precision == EPIC_TC_SPLIT_BF16, ops);
-            rc = dev_upload(&p->d_dft, reinterpret_cast<const uint8_t *>(ops.data()), ops.size() * 2);
-            // the dual kernel's dynamic shared memory: the largest any of its groups needs (a
-            // large side on the fold path needs the operands and the grid only)
-            size_t dual = 0;
-            for (const auto &g : p->groups)
-                if (g.tensor) {
-                    if (g.alias && p->tc_form != 2) rc = EPIC_ERR_UNSUPPORTED;   // only the two-stage form folds
-                    dual = std::max(dual, g.tc_regular ? epic::tc_dual_smem_bytes(n_ant, p->K)
-                                                       : epic::tc_dual_fold_smem_bytes());
-                }
-            if (rc == EPIC_OK) rc = p->tc_form == 2 ? epic::prepare_tc_dual(p, dual) : epic::prepare_tc(p);
-        }
+        epic::build_dft_operand(precision == EPIC_TC_SPLIT_BF16, ops);
+        rc = dev_upload(&p->d_dft, reinterpret_cast<const uint8_t *>(ops.data()), ops.size() * 2);
+        // the dual kernel's dynamic shared memory: the largest any of its groups needs (a
+        // large side on the fold path needs the operands and the grid only)
+        size_t dual = 0;
+        for (const auto &g : p->groups)
+            if (g.tensor)
+                dual = std::max(dual, g.tc_regular ? epic::tc_dual_smem_bytes(n_ant, p->K)
+                                                   : epic::tc_dual_fold_smem_bytes());
+        if (rc == EPIC_OK) rc = epic::prepare_tc_dual(p, dual);
     }
     for (const auto &g : p->groups) {
         if (rc != EPIC_OK) break;
@@ -811,13 +798,11 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         if (rc == EPIC_OK && g.alias) rc = epic::prepare_alias(p);
     }
     if (rc == EPIC_OK) {
-        const char *env = std::getenv("EPIC_NO_GRAPH");
-        p->use_graph = !(env && env[0] == '1');
+        p->use_graph = !(diag & EPIC_DIAG_NO_GRAPH);
         // Fault injection for the failure-detection test: the tensor kernel
         // issues no MMA, so its completion wait runs out after a short budget
         // and the plan's status word reports EPIC_ERR_TIMEOUT.
-        const char *inj = std::getenv("EPIC_TEST_WITHHOLD_MMA");
-        if (inj && inj[0] == '1') {
+        if (diag & EPIC_DIAG_WITHHOLD_MMA) {
             p->test_withhold_mma = 1;
             p->wait_budget = 2000000;   // ~1 ms
         }

@@ -688,6 +688,10 @@ int epic_search_plan(epic_search_t *out, const double *freq_hz, int n_chan, doub
     if (!out) return EPIC_ERR_ARG;
     *out = nullptr;
     if (!freq_hz || !dm || n_chan < 1 || n_dm < 1 || n_pix < 1 || n_time < 1 || !(dt_s > 0)) return EPIC_ERR_ARG;
+    constexpr unsigned kDiag = EPIC_SEARCH_DIAG_DM32 | EPIC_SEARCH_DIAG_DIRECT | EPIC_SEARCH_DIAG_NO_PIX2 |
+                               EPIC_SEARCH_DIAG_NO_TMA | EPIC_SEARCH_DIAG_WITHHOLD_TMA;
+    const unsigned diag = width_mask & kDiag;
+    width_mask &= ~kDiag;
     if ((width_mask & 63u) == 0 || (width_mask & ~63u)) return EPIC_ERR_ARG;
     double fmax = 0;
     for (int c = 0; c < n_chan; c++) {
@@ -722,9 +726,8 @@ int epic_search_plan(epic_search_t *out, const double *freq_hz, int n_chan, doub
     s->widths = width_mask;
     // the staged kernels hold a tile + (spread of the shifts over one block's DMs) rows per
     // channel.  Blocks of 16 trials (two blocks per SM) measured faster than 32 in every staged
-    // form; EPIC_SEARCH_DM_BLOCK=32 asks for 32-trial blocks where they fit, 0 for the direct form.
-    const char *env = std::getenv("EPIC_SEARCH_DM_BLOCK");
-    const int want = env && *env ? std::atoi(env) : 16;
+    // form; the diagnostic options ask for 32-trial blocks where they fit, or for the direct form.
+    const int want = (diag & EPIC_SEARCH_DIAG_DIRECT) ? 0 : (diag & EPIC_SEARCH_DIAG_DM32) ? 32 : 16;
     const int spread32 = epic::staged_spread(shift, n_dm, n_chan, 32);
     const int spread16 = epic::staged_spread(shift, n_dm, n_chan, 16);
     if (want == 32 && epic::kTS + spread32 <= epic::kRows) {
@@ -734,18 +737,14 @@ int epic_search_plan(epic_search_t *out, const double *freq_hz, int n_chan, doub
         s->dm_block = 16;
         s->spread = spread16;
     }
-    // EPIC_SEARCH_PIX2=0 keeps unit-stride cubes on the one-pixel staged form,
-    // EPIC_SEARCH_TMA=0 on the cp.async forms
-    const char *env2 = std::getenv("EPIC_SEARCH_PIX2");
-    s->pix2 = !(env2 && *env2 == '0');
-    const char *env3 = std::getenv("EPIC_SEARCH_TMA");
-    s->tma = !(env3 && *env3 == '0');
+    // diagnostics: keep unit-stride cubes on the one-pixel staged form, or on the cp.async forms
+    s->pix2 = !(diag & EPIC_SEARCH_DIAG_NO_PIX2);
+    s->tma = !(diag & EPIC_SEARCH_DIAG_NO_TMA);
     s->wait_budget = epic::kWaitBudget;
     // Fault injection for the failure-detection test: the TMA form's producer
     // skips channel 0, the consumers' wait runs out after a short budget and
     // the status word reports EPIC_ERR_TIMEOUT.
-    const char *inj = std::getenv("EPIC_TEST_WITHHOLD_TMA");
-    if (inj && inj[0] == '1') {
+    if (diag & EPIC_SEARCH_DIAG_WITHHOLD_TMA) {
         s->withhold = 1;
         s->wait_budget = 2000000;   // ~1 ms
     }

@@ -38,7 +38,9 @@
 #include "epic_internal.cuh"
 #include "tc_ptx.cuh"
 
+#include <cmath>
 #include <type_traits>
+#include <vector>
 
 namespace epic {
 namespace {
@@ -57,6 +59,13 @@ constexpr int kBarSimt = 5;
 __host__ __device__ constexpr uint32_t mn_off(int n, int k)
 {
     return static_cast<uint32_t>((n >> 3) * kSBO + (k >> 3) * kLBO + (k & 7) * 16 + (n & 7) * 2);
+}
+
+// byte offset of (row, k) in the K-major canonical layout of one 128 x 128 part
+// (8 consecutive k per 16 bytes, core matrices of 8 rows)
+__host__ __device__ constexpr uint32_t k_off(int row, int k)
+{
+    return static_cast<uint32_t>((row >> 3) * kSBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2);
 }
 
 __host__ __device__ constexpr uint32_t idesc_kk(int M, int N, bool bf16)
@@ -600,11 +609,18 @@ int dual_dispatch(int precision, int K, F &&f)
 
 size_t tc_dual_smem_bytes(int A, int K) { return dual_smem(A, K); }
 
+// The cap is per kernel and process: raise it to the device's opt-in limit so
+// that a later plan needing less cannot lower it under this one.
 int prepare_tc_dual(const epic_plan_s *plan, size_t smem)
 {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return EPIC_ERR_CUDA;
+    if (smem > static_cast<size_t>(optin)) return EPIC_ERR_UNSUPPORTED;
     return dual_dispatch(plan->precision, plan->K, [&](auto vv, auto kc) {
         return cudaFuncSetAttribute(tc_dual64_kernel<decltype(vv)::value, decltype(kc)::value>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) == cudaSuccess
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin) == cudaSuccess
                    ? EPIC_OK
                    : EPIC_ERR_UNSUPPORTED;
     });
@@ -627,6 +643,43 @@ int launch_tc_dual(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
     return dual_dispatch(plan->precision, plan->K, [&](auto vv, auto kc) {
         return launch_dual_t<decltype(vv)::value, decltype(kc)::value>(plan, g, v, gains, T, n_tau, stream);
     });
+}
+
+// The 64-point DFT X[r][k] in real 2 x 2 block form, hi and lo parts, K-major:
+// row r = 32 q + l -> (my = 16 q + l mod 16, part = l / 16), column k = 64 part' + j,
+// X = exp(+2 pi i j my / 64) as [[cos, -sin], [sin, cos]] over (part, part').
+// The lo part is what the hi part leaves of the FP64 value, rounded once more.
+void build_dft_operand(bool bf16, std::vector<uint16_t> &words)
+{
+    words.assign(2 * kPart / 2, 0);
+    auto to16 = [bf16](double x, double &back) -> uint16_t {
+        if (bf16) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(static_cast<float>(x));
+            back = static_cast<double>(__bfloat162float(h));
+            return __bfloat16_as_ushort(h);
+        }
+        const __half h = __float2half_rn(static_cast<float>(x));
+        back = static_cast<double>(__half2float(h));
+        return __half_as_ushort(h);
+    };
+    for (int r = 0; r < 128; r++) {
+        const int q = r / 32, l = r % 32;
+        const int my = 16 * q + (l % 16), part = l / 16;
+        for (int k = 0; k < 128; k++) {
+            const int j = k % 64;
+            const bool im_in = k >= 64;
+            const long e = (static_cast<long>(j) * my) % 64;
+            const double th = 2.0 * M_PI * static_cast<double>(e) / 64.0;
+            double a;
+            if (part == 0) a = im_in ? -std::sin(th) : std::cos(th);
+            else a = im_in ? std::cos(th) : std::sin(th);
+            double hi_back = 0, lo_back = 0;
+            const uint16_t hi = to16(a, hi_back);
+            const uint16_t lo = to16(a - hi_back, lo_back);
+            words[k_off(r, k) / 2] = hi;
+            words[(kPart + k_off(r, k)) / 2] = lo;
+        }
+    }
 }
 
 }  // namespace epic

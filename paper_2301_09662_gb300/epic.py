@@ -36,6 +36,23 @@ EPIC_STOKES = 8
 EPIC_ANTENNA_KERNELS = 16
 STOKES = ("I", "Q", "U", "V")
 
+# diagnostic plan options (tests and measurements only; include/epic.h)
+EPIC_DIAG_NO_GRAPH = 1 << 8
+EPIC_DIAG_GATHER_GLOBAL = 1 << 9
+EPIC_DIAG_NO_ALIAS = 1 << 10
+EPIC_DIAG_WITHHOLD_MMA = 1 << 11
+
+
+def EPIC_DIAG_ALIAS_BATCH(n: int) -> int:
+    return (int(n) & 255) << 16
+
+
+EPIC_SEARCH_DIAG_DM32 = 1 << 8
+EPIC_SEARCH_DIAG_DIRECT = 1 << 9
+EPIC_SEARCH_DIAG_NO_PIX2 = 1 << 10
+EPIC_SEARCH_DIAG_NO_TMA = 1 << 11
+EPIC_SEARCH_DIAG_WITHHOLD_TMA = 1 << 12
+
 PRODUCTS = ("XX", "YY", "XY", "YX")
 
 #: every symbol include/epic.h declares
@@ -355,9 +372,9 @@ class Search:
     """De-dispersion and single-pulse search of an intensity cube (epic_search_*).
 
     freq_hz [C], dt_s, dms [n_dm] (pc cm^-3), n_pix, n_time; widths: boxcar
-    widths, powers of two up to 32."""
+    widths, powers of two up to 32; diag: EPIC_SEARCH_DIAG_* options (tests)."""
 
-    def __init__(self, freq_hz, dt_s, dms, n_pix, n_time, widths=(1, 2, 4, 8, 16, 32)):
+    def __init__(self, freq_hz, dt_s, dms, n_pix, n_time, widths=(1, 2, 4, 8, 16, 32), diag=0):
         L = load()
         self._f = np.ascontiguousarray(freq_hz, np.float64)
         self._dm = np.ascontiguousarray(dms, np.float64)
@@ -370,7 +387,7 @@ class Search:
         self.C, self.n_dm, self.n_pix, self.n_time = len(self._f), len(self._dm), int(n_pix), int(n_time)
         self._h = ctypes.c_void_p()
         rc = L.epic_search_plan(ctypes.byref(self._h), self._f.ctypes.data, self.C, float(dt_s), self._dm.ctypes.data,
-                                self.n_dm, self.n_pix, self.n_time, mask)
+                                self.n_dm, self.n_pix, self.n_time, mask | int(diag))
         _check(rc, "epic_search_plan")
         t_out, smax = ctypes.c_int(), ctypes.c_int()
         _check(L.epic_search_info(self._h, ctypes.byref(t_out), ctypes.byref(smax)), "epic_search_info")

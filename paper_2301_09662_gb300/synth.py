@@ -299,16 +299,23 @@ def dense(T: int = 500, C: int = 256, seed_cfg: int = 5) -> Workload:
 
 def random_small(A: int, P: int, C: int, T: int, N: int, K: int, seed: int,
                  spread_cells: float | None = None, gains: bool = True,
-                 du: float = 0.5, f0: float = 50e6) -> Workload:
+                 du: float = 0.5, f0: float = 50e6, full_range: bool = False) -> Workload:
     """Small random case for parity/property tests: A antennas uniform in a disc
-    sized to spread over about `spread_cells` cells at f0, uniform random ci4."""
+    sized to spread over about `spread_cells` cells at f0, uniform random ci4
+    (parts in [-7, 7]; with full_range every byte value 0..255 is equally
+    likely, -8 included, and the first 256 bytes of the voltage array are the
+    256 values in order, so each one occurs)."""
     rng = np.random.default_rng(seed)
     lam = C0 / f0
     spread = spread_cells if spread_cells is not None else N / 2 - K
     radius = 0.5 * spread * du * lam
     ant = layout_disc(A, radius, rng)
     freq = f0 + 25e3 * np.arange(C)
-    v = random_ci4((T, C, A, P), rng)
+    v = random_ci4((T, C, A, P), rng, lo=-8 if full_range else -7)
+    if full_range:
+        flat = v.reshape(-1)
+        n = min(256, flat.size)
+        flat[:n] = np.arange(n, dtype=np.uint8)
     g = random_gains(C, A, P, rng) if gains else None
     kern = gaussian_kernel(K)
     if K > 1:

@@ -81,14 +81,13 @@ def test_fold48_register_kernel_taper():
 
 
 @pytest.mark.parametrize("A,P,N,K", [(100, 2, 128, 5), (64, 1, 96, 3)])
-def test_gather_table_staged_and_global_forms_agree(monkeypatch, A, P, N, K):
+def test_gather_table_staged_and_global_forms_agree(A, P, N, K):
     """The gather table read from shared memory (staged per channel) and through
     the L1 cache give bitwise the same image (same lists, same order), and both
     match the oracle."""
     wl = synth.random_small(A=A, P=P, C=2, T=9, N=N, K=K, seed=A + N)
     staged, _ = run_gpu(wl)
-    monkeypatch.setenv("EPIC_GATHER_GLOBAL", "1")
-    unstaged, _ = run_gpu(wl)
+    unstaged, _ = run_gpu(wl, flags=epic.EPIC_DIAG_GATHER_GLOBAL)
     assert np.array_equal(staged, unstaged)
     assert peak_rel_err(staged, _oracle(wl), wl.grid_n, P).max() < FP32_TOL
 
@@ -180,13 +179,12 @@ def test_graph_replay_follows_new_pointers_and_lengths():
         assert peak_rel_err(out.cpu().numpy().astype(np.complex128), ref, wl.grid_n, 2).max() < FP32_TOL
 
 
-def test_graph_and_direct_launches_agree(monkeypatch):
+def test_graph_and_direct_launches_agree():
     import torch
     wl = synth.random_small(A=90, P=2, C=3, T=6, N=64, K=5, seed=22)
     wl.grid_n = np.array([64, 96, 128], np.int32)
     g_out, _ = run_gpu(wl)
-    monkeypatch.setenv("EPIC_NO_GRAPH", "1")
-    d_out, _ = run_gpu(wl)
+    d_out, _ = run_gpu(wl, flags=epic.EPIC_DIAG_NO_GRAPH)
     assert peak_rel_err(g_out, d_out, wl.grid_n, 2).max() < 1e-6
 
 
@@ -198,30 +196,28 @@ def test_folded64_path_is_bitwise_deterministic():
     assert np.array_equal(a, b)
 
 
-def test_large_grid_fold_path_matches_per_class_path_and_is_deterministic(monkeypatch):
+def test_large_grid_fold_path_matches_per_class_path_and_is_deterministic():
     """At N = 512 the plan grids once per (channel, sample) and folds the 64
-    pixel classes with one 8 x 8 DFT per folded cell; EPIC_NO_ALIAS=1 keeps the
+    pixel classes with one 8 x 8 DFT per folded cell; EPIC_DIAG_NO_ALIAS keeps the
     per-class gridding.  Both agree to FP32 rounding, the fold path repeats bit
     for bit (no atomics), and it matches the oracle."""
     wl = synth.random_small(A=150, P=2, C=2, T=7, N=512, K=5, seed=31)
     a, p = run_gpu(wl)
     b, _ = run_gpu(wl, plan=p)
     assert np.array_equal(a, b)
-    monkeypatch.setenv("EPIC_NO_ALIAS", "1")
-    c, _ = run_gpu(wl)
+    c, _ = run_gpu(wl, flags=epic.EPIC_DIAG_NO_ALIAS)
     assert peak_rel_err(a, c, wl.grid_n, 2).max() < 1e-6
     ref = oracle.workload_image(wl)
     assert peak_rel_err(a, ref, wl.grid_n, 2).max() < FP32_TOL
 
 
 @pytest.mark.parametrize("P,precision", [(1, epic.EPIC_FP32), (2, epic.EPIC_FP32), (2, epic.EPIC_TC_SPLIT_FP16)])
-def test_large_grid_fold_path_in_time_batches(P, precision, monkeypatch):
+def test_large_grid_fold_path_in_time_batches(P, precision):
     """The fold path sums time batches into one partial slot: 7 spectra in
     batches of 3 (3 + 3 + 1) give the oracle's image, single and dual
     polarisation, FP32 and split-FP16 tensor kernels."""
-    monkeypatch.setenv("EPIC_ALIAS_BATCH", "3")
     wl = synth.random_small(A=92, P=P, C=2, T=7, N=512, K=3, seed=41 + P)   # A*P a multiple of 4: the M = 64 path
-    gpu, _ = run_gpu(wl, precision=precision)
+    gpu, _ = run_gpu(wl, precision=precision, flags=epic.EPIC_DIAG_ALIAS_BATCH(3))
     ref = oracle.workload_image(wl)
     assert peak_rel_err(gpu, ref, wl.grid_n, P).max() < FP32_TOL
 

@@ -22,6 +22,17 @@ def _cube(T, C, P, seed, pulses=()):
     return cube.astype(np.float32)
 
 
+def _diag(cap, pix2, tma):
+    """Search plan diagnostics for one kernel form: DM block ("32", "16" or "0" =
+    the direct form), two-pixel staged form ("1"/"0"), TMA form ("1"/"0")."""
+    d = {"32": epic.EPIC_SEARCH_DIAG_DM32, "16": 0, "0": epic.EPIC_SEARCH_DIAG_DIRECT}[cap]
+    if pix2 == "0":
+        d |= epic.EPIC_SEARCH_DIAG_NO_PIX2
+    if tma == "0":
+        d |= epic.EPIC_SEARCH_DIAG_NO_TMA
+    return d
+
+
 def _setup(T=150, C=20, P=300, n_dm=13, seed=1):
     f = 42.1e6 + 25e3 * np.arange(C)
     dms = np.linspace(0, 12, n_dm)
@@ -43,7 +54,7 @@ def test_dedisperse_parity_ragged():
 
 
 @pytest.mark.parametrize("grid", ["fine", "coarse", "unsorted"])
-def test_dedisperse_forms_agree_bitwise(grid, monkeypatch):
+def test_dedisperse_forms_agree_bitwise(grid):
     """The 32- and 16-trial staged blocks (TMA producer warp or cp.async
     staging; two pixels per lane with packed adds, or one) and the direct form
     sum every sweep in channel order, so they agree bit for bit; all match the
@@ -66,10 +77,7 @@ def test_dedisperse_forms_agree_bitwise(grid, monkeypatch):
     outs = []
     for cap, pix2, tma in (("32", "1", "1"), ("16", "1", "1"), ("32", "1", "0"), ("16", "1", "0"),
                            ("32", "0", "1"), ("16", "0", "1"), ("0", "1", "1")):
-        monkeypatch.setenv("EPIC_SEARCH_DM_BLOCK", cap)
-        monkeypatch.setenv("EPIC_SEARCH_PIX2", pix2)
-        monkeypatch.setenv("EPIC_SEARCH_TMA", tma)
-        s = epic.Search(f, dt, dms, P, T)
+        s = epic.Search(f, dt, dms, P, T, diag=_diag(cap, pix2, tma))
         outs.append(s.dedisperse(x_pad4, strides=(C * (P + 1), P + 1, 1)).cpu().numpy())
         outs.append(s.dedisperse(x).cpu().numpy())
         assert s.status() == epic.EPIC_OK
@@ -86,7 +94,7 @@ def test_dedisperse_forms_agree_bitwise(grid, monkeypatch):
     (90, 9, 130, 37, "tcp"),     # the same with an even pitch (two-pixel cp.async form)
     (80, 7, 64, 20, "ctp"),      # channel-major cube: the time stride is the smaller one
 ])
-def test_dedisperse_edge_shapes_all_forms(T, C, P, n_dm, layout, monkeypatch):
+def test_dedisperse_edge_shapes_all_forms(T, C, P, n_dm, layout):
     import torch
     f = 42.1e6 + 25e3 * np.arange(C)
     dms = np.linspace(0, 3, n_dm)
@@ -100,10 +108,7 @@ def test_dedisperse_edge_shapes_all_forms(T, C, P, n_dm, layout, monkeypatch):
         strides = (P, T * P, 1)
     outs = []
     for cap, pix2, tma in (("16", "1", "1"), ("16", "1", "0"), ("16", "0", "1"), ("32", "1", "1"), ("0", "1", "1")):
-        monkeypatch.setenv("EPIC_SEARCH_DM_BLOCK", cap)
-        monkeypatch.setenv("EPIC_SEARCH_PIX2", pix2)
-        monkeypatch.setenv("EPIC_SEARCH_TMA", tma)
-        s = epic.Search(f, 0.04, dms, P, T, widths=(1,))
+        s = epic.Search(f, 0.04, dms, P, T, widths=(1,), diag=_diag(cap, pix2, tma))
         outs.append(s.dedisperse(x, strides=strides).cpu().numpy())
         assert s.status() == epic.EPIC_OK
         s.close()
@@ -112,7 +117,7 @@ def test_dedisperse_edge_shapes_all_forms(T, C, P, n_dm, layout, monkeypatch):
         assert np.array_equal(outs[0], o)
 
 
-def test_dedisperse_wait_timeout_sets_status(monkeypatch):
+def test_dedisperse_wait_timeout_sets_status():
     """Failure detection without a fault: the TMA form's producer withholds
     channel 0, the consumers' bounded wait runs out, the plan's status word
     reads EPIC_ERR_TIMEOUT, and a fresh plan on the same context is correct."""
@@ -121,13 +126,11 @@ def test_dedisperse_wait_timeout_sets_status(monkeypatch):
     f, dms, dt, sh = _setup(T, C, P, n_dm=8)
     cube = _cube(T, C, P, 12)
     x = torch.from_numpy(cube).cuda()
-    monkeypatch.setenv("EPIC_TEST_WITHHOLD_TMA", "1")
-    s = epic.Search(f, dt, dms, P, T)
+    s = epic.Search(f, dt, dms, P, T, diag=epic.EPIC_SEARCH_DIAG_WITHHOLD_TMA)
     s.dedisperse(x)
     assert s.status() == epic.EPIC_ERR_TIMEOUT
     assert s.status() == epic.EPIC_OK               # reading clears it
     s.close()
-    monkeypatch.delenv("EPIC_TEST_WITHHOLD_TMA")
     s = epic.Search(f, dt, dms, P, T)
     dd = s.dedisperse(x).cpu().numpy()
     assert s.status() == epic.EPIC_OK

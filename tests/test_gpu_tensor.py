@@ -1,7 +1,9 @@
-"""Parity of the tensor-core forms (tcgen05 DFT-as-GEMM: both transform stages by
-default, the column stage alone with EPIC_TC_PIPE=1 or EPIC_TC_SERIAL=1) with the
-FP64 oracle, per operand precision: split FP16 within 1e-5 of the channel peak,
-single FP16 within 2e-3; the BF16 two-part split is reported and bounded."""
+"""Parity of the tensor-core form (tcgen05 DFT-as-GEMM, both 64-point transform
+stages) with the FP64 oracle, per operand precision: split FP16 within 1e-5 of
+the channel peak, single FP16 within 2e-3, and the two-part BF16 split within
+1e-4 (BF16 keeps 8 significant bits, so hi + lo carry about 16: a product
+error near 2^-16 ~ 1.5e-5 relative per operand element, summed over the
+transform; the bound is the one derived for that split, not the FP16 one)."""
 import numpy as np
 import pytest
 
@@ -70,7 +72,7 @@ def test_tensor_lwa_full_size_sampled_channels():
     assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16, channels=[3, 60]).max() < SPLIT_TOL
 
 
-def test_bounded_wait_reports_timeout_and_context_survives(monkeypatch):
+def test_bounded_wait_reports_timeout_and_context_survives():
     """Failure detection without a fault: the tensor kernel withholds its MMA,
     so the mbarrier it waits on never completes; the bounded wait gives up,
     the plan's status word reads EPIC_ERR_TIMEOUT, and the next plan on the
@@ -78,25 +80,14 @@ def test_bounded_wait_reports_timeout_and_context_survives(monkeypatch):
     import torch
     from gpu_helpers import torch_inputs
     wl = synth.random_small(A=40, P=2, C=1, T=3, N=64, K=3, seed=320)
-    monkeypatch.setenv("EPIC_TEST_WITHHOLD_MMA", "1")
-    p = epic.Plan.from_workload(wl, precision=epic.EPIC_TC_SPLIT_FP16)
+    p = epic.Plan.from_workload(wl, precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_DIAG_WITHHOLD_MMA)
     v, g = torch_inputs(wl)
     p.image(v, g)
     torch.cuda.synchronize()
     assert p.status() == epic.EPIC_ERR_TIMEOUT
     assert p.status() == epic.EPIC_OK          # reading clears it
     p.close()
-    monkeypatch.delenv("EPIC_TEST_WITHHOLD_MMA")
     assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16).max() < SPLIT_TOL
-
-
-@pytest.mark.parametrize("form", ["EPIC_TC_PIPE", "EPIC_TC_SERIAL"])
-@pytest.mark.parametrize("precision,tol", [(epic.EPIC_TC_SPLIT_FP16, SPLIT_TOL), (epic.EPIC_TC_SPLIT_BF16, BF16_TOL)])
-def test_column_stage_only_forms(monkeypatch, form, precision, tol):
-    """The earlier forms (column DFT on the tensor cores, row FFT in FP32) stay correct."""
-    wl = synth.random_small(A=48, P=2, C=2, T=21, N=128, K=5, seed=330)
-    monkeypatch.setenv(form, "1")
-    assert _cmp(wl, precision).max() < tol
 
 
 @pytest.mark.parametrize("T", [1, 2, 65])

@@ -11,6 +11,8 @@ P8  invariances (antenna / time permutation, one-cell translation, XX/YY real,
     YX = conj(XY), gain scaling, MEAN flag, empty integration)
 P9  the oracle's FFT vs a direct DFT and numpy.fft
 P10 ci4 unpacking vs a table built from the definition
+P11 antenna -> cell map (Sec. 3.1 nearest neighbour, reading 7) vs cell
+    indices worked out by hand from the definition
 """
 import os
 
@@ -439,3 +441,62 @@ def test_geometric_delays_recipe():
     assert np.allclose(tau[:, 0], -5.0 / synth.C0, rtol=0, atol=1e-20)
     assert np.allclose(tau[:, 1], 5.0 / synth.C0, rtol=0, atol=1e-20)
     assert np.all(tau[:, 2:] == 0)
+
+
+# ---------------------------------------------------------------- P11 cell map
+
+C0 = 299_792_458.0
+
+# Three antennas around the centroid (10, -4) m, at offsets that are exact in
+# binary: in cells of 0.5 m (du = 0.5 at f = c0) they sit at (+1.5, +2.5),
+# (-2.5, -1.5) and (+1, -1).  The x and y offsets differ (a swapped axis moves
+# them), the half-cell offsets are ties (rounding must go away from zero), and
+# the centroid is far from the origin (it must be subtracted).  Every quotient
+# x f / (c0 du) below is exactly representable, so the expected cells are
+# integers worked out by hand:
+#   k = llround((x - x_c) f / (c0 du)) + N / 2, per axis.
+P11_ANT = np.array([[10.75, -2.75], [8.75, -4.75], [10.5, -4.5]])
+P11_CASES = [
+    # (du, f (Hz), N, expected [A][2])
+    (0.5, C0, 32, [[18, 19], [13, 14], [17, 15]]),            # ties at +-1.5, +-2.5
+    (0.5, 2 * C0, 64, [[35, 37], [27, 29], [34, 30]]),        # offsets x2
+    (0.5, C0 / 2, 16, [[9, 9], [7, 7], [9, 7]]),              # +-0.75, +-1.25, ties at +-0.5
+    (0.25, C0, 32, [[19, 21], [11, 13], [18, 14]]),           # finer cells: offsets x2
+    (0.25, 2 * C0, 64, [[38, 42], [22, 26], [36, 28]]),       # offsets x4
+]
+
+
+@pytest.mark.parametrize("du,f,N,expect", P11_CASES)
+def test_p11_cell_map_by_hand(du, f, N, expect):
+    cells = oracle.cell_map(P11_ANT, np.array([f]), np.array([N], np.int32), du)
+    assert cells.shape == (1, 3, 2)
+    assert cells[0].tolist() == expect
+
+
+def test_p11_cell_map_channels_are_independent():
+    # all five channel set-ups of one du in one call give the same cells as one at a time
+    for du in (0.5, 0.25):
+        sel = [c for c in P11_CASES if c[0] == du]
+        f = np.array([c[1] for c in sel])
+        n = np.array([c[2] for c in sel], np.int32)
+        cells = oracle.cell_map(P11_ANT, f, n, du)
+        for i, c in enumerate(sel):
+            assert cells[i].tolist() == c[3]
+
+
+def test_p11_cell_map_plausible_mistakes_fail():
+    # what a dropped centroid, swapped axes, floor or ties-to-even rounding would give
+    # on the first case: none of them equals the hand-worked cells the oracle matches
+    du, f, N, expect = P11_CASES[0]
+    off = (P11_ANT - P11_ANT.mean(axis=0)) * f / (C0 * du)
+    rnd_away = np.sign(off) * np.floor(np.abs(off) + 0.5)
+    assert (rnd_away + N // 2).astype(int).tolist() == expect
+    wrong = {
+        "no centroid": np.sign(P11_ANT * f / (C0 * du)) * np.floor(np.abs(P11_ANT * f / (C0 * du)) + 0.5) + N // 2,
+        "swapped axes": rnd_away[:, ::-1] + N // 2,
+        "floor": np.floor(off) + N // 2,
+        "ties to even": np.rint(off) + N // 2,
+        "du ignored": np.sign(off * du) * np.floor(np.abs(off * du) + 0.5) + N // 2,
+    }
+    for name, w in wrong.items():
+        assert w.astype(int).tolist() != expect, name
