@@ -203,18 +203,12 @@ int build_alias_tables(const std::vector<short2> &cells, int A, int K, int N, co
     return EPIC_OK;
 }
 
-// The cap is per kernel and process, and this plan's size depends on K: raise it
-// to the device's opt-in limit so a later plan with a smaller K cannot lower it.
+// The cap is per kernel and process, and this plan's size depends on K
+// (raise_dyn_smem_cap: a later plan with a smaller K cannot lower it).
 int prepare_alias(const epic_plan_s *plan)
 {
-    int dev = 0, optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-        return EPIC_ERR_CUDA;
-    if (alias_smem(plan->K) > static_cast<size_t>(optin) ||
-        cudaFuncSetAttribute(alias_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
-        return EPIC_ERR_UNSUPPORTED;
-    return prepare_fold64(plan->P);
+    const int rc = raise_dyn_smem_cap(reinterpret_cast<const void *>(alias_fold_kernel), alias_smem(plan->K));
+    return rc != EPIC_OK ? rc : prepare_fold64(plan->P);
 }
 
 // One integration: per batch of alias_tb samples, fold every class of every

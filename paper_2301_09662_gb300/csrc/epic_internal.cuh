@@ -214,6 +214,9 @@ int launch_epilogue_raw(const RawImage &r, const float2 *gains, float2 *out, cud
 int host_cell_map(const double *ant_xy_m, int n_ant, const double *freq_hz, int n_chan, const int *grid_n,
                   double du, int K, std::vector<short2> &cells);
 void host_kernel_power(const float *kern, int K, int N, std::vector<double> &out);
+// raise a kernel's dynamic shared-memory cap to the device limit (less its static shared memory);
+// EPIC_ERR_UNSUPPORTED if `need` does not fit
+int raise_dyn_smem_cap(const void *kfn, size_t need);
 
 // device status bits
 constexpr int kStatusDevice = 1;

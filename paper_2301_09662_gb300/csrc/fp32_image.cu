@@ -312,28 +312,12 @@ int launch_group(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const f
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
-// The dynamic shared-memory cap of a kernel holds for the whole process, so it
-// is raised to the device's opt-in limit rather than to one caller's size: a
-// later plan or static call that needs less must not lower it under a plan
-// that needs more.
-int raise_smem_cap(const void *kfn, size_t need)
-{
-    int dev = 0, optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-        return EPIC_ERR_CUDA;
-    if (need > static_cast<size_t>(optin)) return EPIC_ERR_UNSUPPORTED;
-    return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) == cudaSuccess
-               ? EPIC_OK
-               : EPIC_ERR_UNSUPPORTED;
-}
-
 template <int M, int P>
 int prepare_group(const epic_plan_s *plan)
 {
     auto kfn = fp32_image_kernel<M, P>;
     const size_t smem = smem_bytes<M, P>(plan->A, plan->K, plan->nker);
-    if (const int rc = raise_smem_cap(reinterpret_cast<const void *>(kfn), smem); rc != EPIC_OK) return rc;
+    if (const int rc = raise_dyn_smem_cap(reinterpret_cast<const void *>(kfn), smem); rc != EPIC_OK) return rc;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, smem) != cudaSuccess || per_sm < 1)
         return EPIC_ERR_UNSUPPORTED;
@@ -345,7 +329,7 @@ int launch_raw(const RawImage &r, const uint8_t *v, const float2 *gains, cudaStr
 {
     auto kfn = fp32_image_kernel<M, P>;
     const size_t smem = smem_bytes<M, P>(r.A, r.K);
-    if (const int rc = raise_smem_cap(reinterpret_cast<const void *>(kfn), smem); rc != EPIC_OK) return rc;
+    if (const int rc = raise_dyn_smem_cap(reinterpret_cast<const void *>(kfn), smem); rc != EPIC_OK) return rc;
     const dim3 grid(static_cast<unsigned>(r.n_items * r.n_tau));
     kfn<<<grid, kThreads, smem, stream>>>(v, gains, r.cells, r.kernel, r.K, r.chans, r.twN, r.A, r.C, r.T, r.N, r.Q1,
                                           r.n_items, r.n_tau, r.partial, r.status, 1, nullptr, nullptr);

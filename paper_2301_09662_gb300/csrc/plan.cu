@@ -157,6 +157,26 @@ int host_cell_map(const double *ant_xy_m, int n_ant, const double *freq_hz, int 
 
 void host_kernel_power(const float *kern, int K, int N, std::vector<double> &out) { kernel_power(kern, K, N, out); }
 
+// A kernel's dynamic shared-memory cap holds for the whole process, so it is
+// raised to the most the device allows beside the kernel's static shared
+// memory rather than to one caller's size: a later plan or call that needs
+// less must not lower it under one that needs more.
+int raise_dyn_smem_cap(const void *kfn, size_t need)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kfn) != cudaSuccess)
+        return EPIC_ERR_CUDA;
+    const long long cap = static_cast<long long>(optin) - static_cast<long long>(fa.sharedSizeBytes);
+    if (cap < 0 || need > static_cast<size_t>(cap)) return EPIC_ERR_UNSUPPORTED;
+    return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(cap)) ==
+                   cudaSuccess
+               ? EPIC_OK
+               : EPIC_ERR_UNSUPPORTED;
+}
+
 // Gridding schedule of the register-transform kernels (fold side M = 64 or 48).
 // Each antenna footprint is cut into K row segments (one per dy) of K cells on
 // the folded M x M grid.  Warp w owns rows y = w (mod 8); its segments are

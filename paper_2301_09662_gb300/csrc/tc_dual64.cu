@@ -609,20 +609,13 @@ int dual_dispatch(int precision, int K, F &&f)
 
 size_t tc_dual_smem_bytes(int A, int K) { return dual_smem(A, K); }
 
-// The cap is per kernel and process: raise it to the device's opt-in limit so
-// that a later plan needing less cannot lower it under this one.
+// The cap is per kernel and process (raise_dyn_smem_cap): a later plan that
+// needs less cannot lower it under this one.
 int prepare_tc_dual(const epic_plan_s *plan, size_t smem)
 {
-    int dev = 0, optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-        return EPIC_ERR_CUDA;
-    if (smem > static_cast<size_t>(optin)) return EPIC_ERR_UNSUPPORTED;
     return dual_dispatch(plan->precision, plan->K, [&](auto vv, auto kc) {
-        return cudaFuncSetAttribute(tc_dual64_kernel<decltype(vv)::value, decltype(kc)::value>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin) == cudaSuccess
-                   ? EPIC_OK
-                   : EPIC_ERR_UNSUPPORTED;
+        return raise_dyn_smem_cap(
+            reinterpret_cast<const void *>(tc_dual64_kernel<decltype(vv)::value, decltype(kc)::value>), smem);
     });
 }
 
