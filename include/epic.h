@@ -113,6 +113,9 @@ enum {
                                                 EPIC_ERR_TIMEOUT; the context stays usable */
 #define EPIC_DIAG_ALIAS_BATCH(n) ((((unsigned)(n)) & 255u) << 16)   /* fold path: at most n (1..255) samples
                                                                         per time batch */
+#define EPIC_DIAG_NO_PAIR        (1u << 12)  /* tensor form, grid side 128: one pixel class per CTA (the
+                                                two-stage kernel of every side) instead of two classes
+                                                from one gridding */
 
 /*
  * epic_plan -- validate the array geometry and build every table the imaging

@@ -68,6 +68,14 @@ struct GroupCfg {
     short2 *d_j0 = nullptr;            // device: [n_chan] first occupied alias block (x, y)
     uint32_t *d_bseg = nullptr;        // device: footprint rows (a << 8 | dyi) per (channel, 8-row band)
     int *d_boff = nullptr;             // device: [n_chan * 8 + 1] offsets into d_bseg
+    // grid side 128 in a tensor plan: the pair kernel (tc_pair128.cu), two pixel classes per CTA
+    bool pair = false;
+    int launch_items = 0;              // CTAs per time chunk (n_items, or n_chan * 2 for the pair kernel)
+    int pwords = 0;                    // largest channel block of the pair lists (16-bit words)
+    uint16_t *d_ptab = nullptr;        // device: pair-kernel gather lists (build_pair_tables)
+    int2 *d_pchan = nullptr;           // device: [n_chan] (block start, block words)
+    int4 *d_pidx = nullptr;            // device: [n_chan][8 warps] (half 1 offset, batches, half 2 offset, batches)
+    unsigned long long *d_upper = nullptr;  // device: [n_chan] folded rows whose cells lie in unfolded rows 64..127
 };
 
 struct KernelTables {
@@ -164,6 +172,15 @@ size_t tc_dual_fold_smem_bytes();
 int launch_tc_dual_fold(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, const float2 *gf, int nb,
                         bool accumulate, cudaStream_t stream);
 int launch_tc_dual(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
+                   cudaStream_t stream);
+// grid side 128: two pixel classes per CTA from one gridding (tc_pair128.cu)
+int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
+                      const std::vector<uint32_t> &tab32, const std::vector<int4> &idx32,
+                      const std::vector<int2> &chan32, std::vector<uint16_t> &tab, std::vector<int4> &idx,
+                      std::vector<int2> &chan, std::vector<unsigned long long> &upper);
+size_t tc_pair_smem_bytes(int A, int K, int words);
+int prepare_tc_pair(const epic_plan_s *plan, size_t smem);
+int launch_tc_pair(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                    cudaStream_t stream);
 
 // Gather table of the FP32 register-transform kernel for the channels of one group (plan.cu).

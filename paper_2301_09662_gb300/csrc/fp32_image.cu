@@ -344,7 +344,7 @@ int choose_tau(const epic_plan_s *plan, const GroupCfg &g, int T)
 {
     int n = plan->force_tau > 0                       ? plan->force_tau
             : (g.tuned_tau > 0 && g.tuned_T == T) ? g.tuned_tau
-                                                  : pick_tau(g.n_items, T, plan->sm_count);
+                                                  : pick_tau(g.launch_items, T, plan->sm_count);
     return std::max(1, std::min(n, g.tau_cap));
 }
 
@@ -393,8 +393,7 @@ int launch_imaging(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
 {
     if (g.alias && plan->force_tau == 0) return launch_alias(plan, g, v, gains, T, n_tau, s);
     if (g.tensor && !g.tc_regular) return EPIC_ERR_UNSUPPORTED;   // e.g. an image series: no fold path there
-    if (g.tensor)
-        return launch_tc_dual(plan, g, v, gains, T, n_tau, s);
+    if (g.tensor) return g.pair ? launch_tc_pair(plan, g, v, gains, T, n_tau, s) : launch_tc_dual(plan, g, v, gains, T, n_tau, s);
     if (g.reg64) return launch_reg64(plan, g, v, gains, T, n_tau, s);
     switch (g.M * 4 + plan->P) {
     case 32 * 4 + 2: return launch_group<32, 2>(plan, g, v, gains, T, n_tau, s);

@@ -91,6 +91,10 @@ void free_plan(epic_plan_s *p)
         cudaFree(g.d_gchan);
         cudaFree(g.d_tw64);
         cudaFree(g.d_Y);
+        cudaFree(g.d_ptab);
+        cudaFree(g.d_pchan);
+        cudaFree(g.d_pidx);
+        cudaFree(g.d_upper);
     }
     delete p;
 }
@@ -540,7 +544,7 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         return EPIC_ERR_ARG;
     constexpr unsigned kUser = EPIC_MEAN | EPIC_NO_AUTOSUB | EPIC_KERNEL_TAPER | EPIC_STOKES | EPIC_ANTENNA_KERNELS;
     constexpr unsigned kDiag = EPIC_DIAG_NO_GRAPH | EPIC_DIAG_GATHER_GLOBAL | EPIC_DIAG_NO_ALIAS |
-                               EPIC_DIAG_WITHHOLD_MMA | EPIC_DIAG_ALIAS_BATCH(255);
+                               EPIC_DIAG_WITHHOLD_MMA | EPIC_DIAG_ALIAS_BATCH(255) | EPIC_DIAG_NO_PAIR;
     if (flags & ~(kUser | kDiag)) return EPIC_ERR_ARG;
     const unsigned diag = flags & kDiag;
     flags &= kUser;
@@ -770,7 +774,34 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                 }
             }
             if (rc == EPIC_OK && g.tensor && !g.tc_regular && !g.alias) rc = EPIC_ERR_UNSUPPORTED;
+            // grid side 128 in a tensor plan: two pixel classes per CTA from one gridding when the
+            // aperture's rows fold without overlap and the lists fit in shared memory
+            if (rc == EPIC_OK && g.tensor && g.N == 128 && n_pol == 2 && p->nker == 1 &&
+                !(diag & EPIC_DIAG_NO_PAIR)) {
+                std::vector<uint32_t> tab32;
+                std::vector<int4> idx32, pidx;
+                std::vector<int2> chan32, pchan;
+                std::vector<unsigned long long> rows32, upper;
+                std::vector<uint16_t> ptab;
+                if (epic::build_gather_table(cells, n_ant, p->K, 64, 2, g.chans, tab32, idx32, chan32, rows32) ==
+                        EPIC_OK &&
+                    epic::build_pair_tables(cells, n_ant, p->K, g.chans, tab32, idx32, chan32, ptab, pidx, pchan,
+                                            upper) == EPIC_OK) {
+                    int words = 0;
+                    for (const int2 &ch : pchan) words = std::max(words, ch.y);
+                    if (epic::tc_pair_smem_bytes(n_ant, p->K, words) + 2048 <= static_cast<size_t>(smem_optin)) {
+                        g.pair = true;
+                        g.pwords = words;
+                        rc = dev_upload(&g.d_ptab, ptab.data(), ptab.size());
+                        if (rc == EPIC_OK) rc = dev_upload(&g.d_pidx, pidx.data(), pidx.size());
+                        if (rc == EPIC_OK) rc = dev_upload(&g.d_pchan, pchan.data(), pchan.size());
+                        if (rc == EPIC_OK) rc = dev_upload(&g.d_upper, upper.data(), upper.size());
+                    }
+                }
+            }
         }
+        g.launch_items = g.pair ? g.n_chan * 2 : g.n_items;
+        if (g.pair) g.tau_cap = std::max(g.tau_cap, epic::fp32_pick_tau(g.launch_items, max_spectra, p->sm_count));
         if (rc == EPIC_OK) rc = dev_upload(&g.d_chans, g.chans.data(), g.chans.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_out_off, offs.data(), offs.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_wpow, wpow.data(), wpow.size());
@@ -811,6 +842,10 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                 dual = std::max(dual, g.tc_regular ? epic::tc_dual_smem_bytes(n_ant, p->K)
                                                    : epic::tc_dual_fold_smem_bytes());
         if (rc == EPIC_OK) rc = epic::prepare_tc_dual(p, dual);
+        size_t pair = 0;
+        for (const auto &g : p->groups)
+            if (g.pair) pair = std::max(pair, epic::tc_pair_smem_bytes(n_ant, p->K, g.pwords));
+        if (rc == EPIC_OK && pair) rc = epic::prepare_tc_pair(p, pair);
     }
     for (const auto &g : p->groups) {
         if (rc != EPIC_OK) break;
@@ -913,10 +948,10 @@ int epic_autotune(epic_plan_t plan, int n_spectra, void *stream)
         auto add = [&](int n) {
             if (n >= 1 && n <= cap && std::find(cand.begin(), cand.end(), n) == cand.end()) cand.push_back(n);
         };
-        const int c0 = epic::fp32_pick_tau(g.n_items, n_spectra, plan->sm_count);
+        const int c0 = epic::fp32_pick_tau(g.launch_items, n_spectra, plan->sm_count);
         for (int d = -2; d <= 2; d++) add(c0 + d);
         for (int waves = 1; waves <= 4; waves++)
-            add(static_cast<int>((static_cast<long long>(waves) * plan->sm_count) / std::max(1, g.n_items)));
+            add(static_cast<int>((static_cast<long long>(waves) * plan->sm_count) / std::max(1, g.launch_items)));
         float best = 1e30f;
         int best_n = c0;
         for (int n : cand) {

@@ -1,0 +1,689 @@
+// Tensor-core form for grid side 128 (dual polarisation): one CTA images two
+// pixel classes of one channel from a single gridding of each sample.
+//
+// With l = 2 m + h (h in {0, 1}^2) the image of class h is the 64-point 2-D DFT
+// of the folded aperture Gf_h(j) = sum_{k = j mod 64} G(k) w_128^{k.h}.  The
+// class phase is separable, w_128^{kx hx} w_128^{ky hy}.  A CTA owns the two
+// classes (hx, 0) and (hx, 1): the x factor goes into the gridding (into the
+// gains per antenna and the taps per column), so both classes share one
+// gridded sample and one row transform; the y factor is applied to each
+// folded row after the row transform.  That needs one unfolded row ky per
+// folded row jy among the cells any footprint touches (the aperture spans at
+// most 64 rows, as with 2x padding); the plan checks it per channel and lists
+// the rows with ky >= 64, and then w_128^{ky} = w_128^{jy} (-1)^{ky >= 64}.
+//
+//   row stage     D1[(pol, jy)][r] = sum_k G16[(pol, jy)][k] X[r][k]
+//                 G16 = the gridded sample in FP16 hi + lo (shared memory,
+//                 K-major, A operand), X = the 64-point DFT in real 2 x 2 block
+//                 form (shared memory, K-major, B operand)
+//   column stage  D2_hy[r][(mx, pol)] = sum_k X[r][k] H16_hy[(mx, pol)][k]
+//                 H16_hy = D1 with row jy turned by w_128^{ky hy}, as FP16 hi + lo
+//                 (shared memory, MN-major, B operand); hy = 0 then 1 in one
+//                 buffer
+//
+// Both stages take three MMAs per 16-deep k-block (hi hi + hi lo + lo hi).
+//
+// Gridding is a gather (the FP32 register kernel's lists, 16-bit entries): a
+// lane sums the (antenna, tap pair) list of one pair of horizontally adjacent
+// folded cells in FP32 registers and writes both cells' hi and lo straight into
+// G16, so there is no FP32 grid and no conversion pass.  The lists write the
+// same cells every sample and the transforms run in TMEM, so cells no list
+// names stay zero from the start.
+//
+// TMEM columns: D1 [0,128), D2 of class hy = 0 [128,256), of hy = 1
+// [256,384), the time sums of class hy = 1 [384,512); class hy = 0 keeps its
+// time sums in registers.  Shared memory: X, G16 and H16 (64 KB each, hi and
+// lo), the channel's gather lists, calibrated voltages, gains, tap pairs.
+//
+// Warps 0-7 (SIMT), iteration t: wait for the row stage of t, D1 -> H16 (hy 0)
+// and arrive on bar_h; unpack sample t+1 and grid the first half of its lists;
+// wait for the column stage of (t, 0), D1 -> H16 (hy 1) and arrive on bar_h;
+// grid the second half and arrive on bar_g; products of (t, 0); wait for the
+// column stage of (t, 1) and add its products.  Warp 8 issues, in order, the
+// row stage of t after bar_g, the column stage of (t, 0) after bar_h, that of
+// (t, 1) after the next bar_h, each committed to its own mbarrier.  Every wait
+// is bounded; a timeout is recorded in the plan's status word and stops the CTA.
+#include <algorithm>
+
+#include "dft_small.cuh"
+#include "epic_internal.cuh"
+#include "tc_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace epic {
+namespace {
+
+using namespace tcc;
+
+constexpr int kSimtP = kThreads;                 // warps 0-7
+constexpr int kPairThreads = kSimtP + 32;        // + the MMA warp
+constexpr int kBarP = 6;                         // named barrier of the SIMT warps
+constexpr uint32_t kColD1 = 0, kColD2a = 128, kColD2b = 256, kColAcc1 = 384;
+constexpr uint16_t kNone = 0xFFFFu;
+
+// XX, YY, XY of one sample added to the time sums of one class: TMEM lanes
+// 32 (w mod 4) + l = (my, part), columns 32 hh .. of each polarisation
+// (hh = w / 4) of D2 at column d2.  Lane l keeps pixels mx = 32 hh + 16 part + j,
+// j < 16; Re and Im of a pixel are exchanged between lanes l and l ^ 16 by one
+// shuffle.  Two halves of 8 pixels (x8 loads of the own and the partner's
+// columns) bound the live registers.  Class hy = 0 sums into registers (acc),
+// class hy = 1 into TMEM columns kColAcc1 + 64 hh .. (4 per pixel).
+template <bool REG>
+__device__ __forceinline__ void products(uint32_t lane_addr, uint32_t d2, int hh, int part, float4 (&acc)[16])
+{
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+        // own columns 16 part + 8 half .., the partner's 16 (1 - part) + 8 half ..
+        uint32_t ox[8], oy[8], sx[8], sy[8];
+        const uint32_t base = lane_addr + d2 + 32 * hh + 8 * half;
+        tc::tmem_ld8_issue(base + 16 * part, ox);
+        tc::tmem_ld8_issue(base + 64 + 16 * part, oy);
+        tc::tmem_ld8_issue(base + 16 * (1 - part), sx);
+        tc::tmem_ld8_issue(base + 64 + 16 * (1 - part), sy);
+        uint32_t s[32];
+        const uint32_t at = lane_addr + kColAcc1 + 64 * hh + 32 * half;
+        if constexpr (!REG) tc::tmem_ld32_issue(at, s);
+        tc::tmem_wait_ld();
+        tc::reg_fence8(ox);
+        tc::reg_fence8(oy);
+        tc::reg_fence8(sx);
+        tc::reg_fence8(sy);
+        if constexpr (!REG) tc::reg_fence32(s);
+#pragma unroll
+        for (int jj = 0; jj < 8; jj++) {
+            const float gx = __shfl_xor_sync(0xffffffffu, __uint_as_float(sx[jj]), 16);
+            const float gy = __shfl_xor_sync(0xffffffffu, __uint_as_float(sy[jj]), 16);
+            const float o1 = __uint_as_float(ox[jj]), o2 = __uint_as_float(oy[jj]);
+            const float xr = part ? gx : o1, xi = part ? o1 : gx;
+            const float yr = part ? gy : o2, yi = part ? o2 : gy;
+            if constexpr (REG) {
+                float4 &a = acc[8 * half + jj];
+                a.x = fmaf(xr, xr, fmaf(xi, xi, a.x));
+                a.y = fmaf(yr, yr, fmaf(yi, yi, a.y));
+                a.z = fmaf(xr, yr, fmaf(xi, yi, a.z));
+                a.w = fmaf(xi, yr, fmaf(-xr, yi, a.w));
+            } else {
+                uint32_t *a4 = s + 4 * jj;
+                a4[0] = __float_as_uint(fmaf(xr, xr, fmaf(xi, xi, __uint_as_float(a4[0]))));
+                a4[1] = __float_as_uint(fmaf(yr, yr, fmaf(yi, yi, __uint_as_float(a4[1]))));
+                a4[2] = __float_as_uint(fmaf(xr, yr, fmaf(xi, yi, __uint_as_float(a4[2]))));
+                a4[3] = __float_as_uint(fmaf(xi, yr, fmaf(-xr, yi, __uint_as_float(a4[3]))));
+            }
+        }
+        if constexpr (!REG) {
+            tc::tmem_st32_issue(at, s);
+            tc::tmem_wait_st();
+        }
+    }
+}
+
+// Shared memory (dynamic, 1024-aligned): X, G16, H16 (each hi then lo), then
+// es [A*P], gp [A*P], tw2 [K (K + 1)] (float4), stage [(A*P + 3) / 4] (u32),
+// the channel's lists [words] (u16).
+template <int VAR>
+__global__ void __launch_bounds__(kPairThreads, 1)
+tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
+                  const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K,
+                  const int *__restrict__ chans, const float2 *__restrict__ twN,
+                  const uint16_t *__restrict__ ptab, const int2 *__restrict__ pchan, const int4 *__restrict__ pidx,
+                  const unsigned long long *__restrict__ upper,
+                  const uint8_t *__restrict__ dft_ops, int A, int C, int T, int n_items_out, int n_tau,
+                  float *__restrict__ partial, int *__restrict__ status, long long wait_budget, int withhold_mma,
+                  const float *__restrict__ dfreq, const float4 *__restrict__ dtab)
+{
+    constexpr int P = 2;
+    constexpr int N = 128;
+    constexpr bool kBF16 = VAR == 2;
+    constexpr bool kSplit = VAR != 1;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *opX = smem;                                      // [2 parts][32 KB] K-major
+    uint8_t *opG = smem + 2 * kPart;                          // [2 parts][32 KB] K-major
+    uint8_t *opH = smem + 4 * kPart;                          // [2 parts][32 KB] MN-major
+    const int AP = A * P, KK = K * K, hk = (K - 1) / 2;
+    const int APW = (AP + 3) >> 2;
+    float2 *es = reinterpret_cast<float2 *>(smem + 6 * kPart);
+    float2 *gp = es + AP;
+    float4 *tw2 = reinterpret_cast<float4 *>(gp + AP);
+    uint32_t *stage = reinterpret_cast<uint32_t *>(tw2 + K * (K + 1));
+    uint16_t *stab = reinterpret_cast<uint16_t *>(stage + APW);
+    __shared__ __align__(8) uint64_t bar_x, bar_g, bar_h, bar_m1, bar_m2a, bar_m2b;
+    __shared__ uint32_t tmem_slot;
+    __shared__ float red[kSimtP / 32];
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool simt = warp < 8;
+    const int n_pairs = gridDim.x / n_tau;                    // CTAs per time chunk: channels x 2
+    const int item = blockIdx.x % n_pairs;
+    const int tau = blockIdx.x / n_pairs;
+    const int ci = item >> 1, hx = item & 1;
+    const int c = chans[ci];
+    const int t0 = static_cast<int>(static_cast<long long>(T) * tau / n_tau);
+    const int t1 = static_cast<int>(static_cast<long long>(T) * (tau + 1) / n_tau);
+    const int2 my_chan = pchan[ci];
+
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
+    if (tid == 0) {
+        abort_flag = 0;
+        tc::mbar_init(&bar_x, 1);
+        tc::mbar_init(&bar_g, kSimtP);
+        tc::mbar_init(&bar_h, kSimtP);
+        tc::mbar_init(&bar_m1, 1);
+        tc::mbar_init(&bar_m2a, 1);
+        tc::mbar_init(&bar_m2b, 1);
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {   // the DFT operand, hi and lo, one bulk copy each
+        tc::mbar_expect_tx(&bar_x, 2 * kPart);
+        tc::bulk_g2s(opX, dft_ops, kPart, &bar_x);
+        tc::bulk_g2s(opX + kPart, dft_ops + kPart, kPart, &bar_x);
+    }
+
+    // ---- set-up: gains and taps with the class-x phase, the largest gain for the FP16 scale,
+    // a zero G16, the channel's lists, the bytes of the first sample
+    float gmax = 0.f;
+    for (int a = simt ? tid : A; a < A; a += kSimtP) {
+        const short2 k = cells[static_cast<size_t>(c) * A + a];
+        if (k.x < hk || k.x >= N - hk || k.y < hk || k.y >= N - hk) atomicOr(status, kStatusDevice);
+        const float2 ph = twN[(k.x * hx) & (N - 1)];
+        for (int p = 0; p < P; p++) {
+            const float2 g = gains ? gains[(static_cast<size_t>(c) * A + a) * P + p] : make_float2(1.f, 0.f);
+            const float2 gg = cmul(g, ph);
+            gp[a * P + p] = gg;
+            gmax = fmaxf(gmax, sqrtf(gg.x * gg.x + gg.y * gg.y));
+        }
+    }
+    // tap pairs (w(dy, dxl), w(dy, dxl + 1)), zero outside the footprint row, with w_128^{dx hx}
+    for (int i = simt ? tid : K * (K + 1); i < K * (K + 1); i += kSimtP) {
+        const int dyi = i / (K + 1), j = i % (K + 1);
+        float2 w[2];
+        for (int u = 0; u < 2; u++) {
+            const int dx = j - 1 + u;
+            w[u] = (dx >= 0 && dx < K) ? cmul(kern[dyi * K + dx], twN[((dx - hk) * hx) & (N - 1)])
+                                       : make_float2(0.f, 0.f);
+        }
+        tw2[i] = make_float4(w[0].x, w[0].y, w[1].x, w[1].y);
+    }
+    for (int i = simt ? tid : 2 * static_cast<int>(kPart) / 16; i < 2 * static_cast<int>(kPart) / 16; i += kSimtP)
+        reinterpret_cast<uint4 *>(opG)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = simt ? tid : my_chan.y; i < my_chan.y; i += kSimtP) stab[i] = __ldg(ptab + my_chan.x + i);
+    if (simt && t0 < t1) {
+        const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(t0) * C + c) * AP);
+        for (int w = tid; w < APW; w += kSimtP) stage[w] = row[w];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    if (simt && lane == 0) red[warp] = gmax;
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = tmem_slot;
+    const uint32_t lane_addr = taddr + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+    float scale = 1.f;
+    if constexpr (!kBF16) {
+        // |H| <= sum_a |e~_a| sum_taps |w| bounds both stages' operands: keep it below 2^13
+        float gm = 0.f;
+        for (int w = 0; w < kSimtP / 32; w++) gm = fmaxf(gm, red[w]);
+        float wsum = 0.f;
+        for (int i = 0; i < KK; i++) wsum += sqrtf(kern[i].x * kern[i].x + kern[i].y * kern[i].y);
+        const float bound = 2.f * static_cast<float>(A) * 11.3137085f * gm * wsum;
+        int e2 = 0;
+        if (bound > 0.f) e2 = static_cast<int>(floorf(log2f(16384.f / bound)));
+        scale = ldexpf(1.f, max(-40, min(40, e2)));
+    }
+    for (int i = simt ? tid : AP; i < AP; i += kSimtP) gp[i] = cscale(gp[i], scale);
+    if (simt) {
+        // zero the TMEM time sums of class hy = 1: lanes 32 (w mod 4) .., columns kColAcc1 + 64 (w / 4) ..
+        uint32_t z[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) z[j] = 0u;
+        const uint32_t acc = lane_addr + kColAcc1 + 64 * (warp >> 2);
+        tc::tmem_st32_issue(acc, z);
+        tc::tmem_st32_issue(acc + 32, z);
+        tc::tmem_wait_st();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+
+    constexpr uint32_t idesc_row = idesc_kk(128, 128, kBF16);
+    constexpr uint32_t idesc_col = idesc_kmn(128, 128, kBF16);
+    const uint32_t x_base = tc::smem_u32(opX), g_base = tc::smem_u32(opG), h_base = tc::smem_u32(opH);
+
+    if (!simt) {
+        // ---- the MMA warp: row stage of t after bar_g, column stages of (t, 0) and (t, 1)
+        // after the next two completions of bar_h
+        if (lane == 0) {
+            bool ok = tc::mbar_wait(&bar_x, 0, wait_budget);
+            uint32_t pg = 0, ph = 0;
+            for (int t = t0; t < t1 && ok; t++) {
+                ok = tc::mbar_wait(&bar_g, pg, wait_budget) && !abort_flag;
+                pg ^= 1u;
+                if (!ok) break;
+                tc::fence_after_sync();
+                if (!withhold_mma) {
+#pragma unroll
+                    for (int kb = 0; kb < 8; kb++) {
+                        const uint64_t g_hi = tc::smem_desc(g_base + kb * 256, kLBO, kSBO);
+                        const uint64_t x_hi = tc::smem_desc(x_base + kb * 256, kLBO, kSBO);
+                        tc::mma_f16(taddr + kColD1, g_hi, x_hi, idesc_row, kb > 0 ? 1u : 0u);
+                        if constexpr (kSplit) {
+                            const uint64_t g_lo = tc::smem_desc(g_base + kPart + kb * 256, kLBO, kSBO);
+                            const uint64_t x_lo = tc::smem_desc(x_base + kPart + kb * 256, kLBO, kSBO);
+                            tc::mma_f16(taddr + kColD1, g_hi, x_lo, idesc_row, 1u);
+                            tc::mma_f16(taddr + kColD1, g_lo, x_hi, idesc_row, 1u);
+                        }
+                    }
+                    tc::mma_commit(&bar_m1);
+                }
+                for (int hy = 0; hy < 2 && ok; hy++) {
+                    ok = tc::mbar_wait(&bar_h, ph, wait_budget) && !abort_flag;
+                    ph ^= 1u;
+                    if (!ok) break;
+                    tc::fence_after_sync();
+                    if (!withhold_mma) {
+                        const uint32_t d2 = taddr + (hy ? kColD2b : kColD2a);
+#pragma unroll
+                        for (int kb = 0; kb < 8; kb++) {
+                            const uint64_t x_hi = tc::smem_desc(x_base + kb * 256, kLBO, kSBO);
+                            const uint64_t h_hi = tc::smem_desc(h_base + kb * 256, kLBO, kSBO);
+                            tc::mma_f16(d2, x_hi, h_hi, idesc_col, kb > 0 ? 1u : 0u);
+                            if constexpr (kSplit) {
+                                const uint64_t x_lo = tc::smem_desc(x_base + kPart + kb * 256, kLBO, kSBO);
+                                const uint64_t h_lo = tc::smem_desc(h_base + kPart + kb * 256, kLBO, kSBO);
+                                tc::mma_f16(d2, x_hi, h_lo, idesc_col, 1u);
+                                tc::mma_f16(d2, x_lo, h_hi, idesc_col, 1u);
+                            }
+                        }
+                        tc::mma_commit(hy ? &bar_m2b : &bar_m2a);
+                    }
+                }
+            }
+            if (!ok) {
+                atomicOr(status, kStatusTimeout);
+                abort_flag = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        constexpr int kPreW = kMaxAP / 4 / kSimtP;
+        const int m = 32 * (warp & 3) + lane;          // this thread's TMEM lane: (pol, jy) in D1, (my, part) in D2
+        const int hp = warp >> 2;                       // which half of the columns
+        const int part = lane >> 4;
+        const int pol = m >> 6, jy = m & 63;
+        // the class-y turn of row jy: w_128^{ky}, ky = jy + 64 [row listed as upper]
+        const int ky = jy + (((upper[ci] >> jy) & 1ull) ? 64 : 0);
+        const float2 turn = twN[ky];
+        const int4 my_idx = pidx[ci * 8 + warp];        // (first batch, batches in half 1, second half's start, batches in half 2)
+
+        // a1, a2: unpack and calibrate sample t from the staged bytes
+        auto unpack = [&](int t) {
+            for (int i = tid; i < AP; i += kSimtP) {
+                const uint32_t b = reinterpret_cast<const uint8_t *>(stage)[i];
+                float2 e = cmul(gp[i], ci4_decode(b));
+                if (dtab) e = cmul(e, delay_phase(dtab[static_cast<size_t>(t) * A + i / P], dfreq[c]));
+                es[i] = e;
+            }
+        };
+        // a3: gather gridding of n batches from offset `at` (u16 units) straight into G16
+        auto gather = [&](int at, int n) {
+            const uint16_t *bt = stab + at;
+            for (int b = 0; b < n; b++) {
+                const int d = bt[0];
+                const uint32_t pos = bt[1 + lane];
+                const uint16_t *ent = bt + 33 + lane;
+                float2 acc[P][2];
+#pragma unroll
+                for (int p = 0; p < P; p++) acc[p][0] = acc[p][1] = make_float2(0.f, 0.f);
+                uint32_t en = d > 0 ? ent[0] : kNone;
+                for (int j = 0; j < d; j++) {
+                    const uint32_t cur = en;
+                    if (j + 1 < d) en = ent[(j + 1) * 32];
+                    if (cur != kNone) {
+                        const int a = static_cast<int>(cur & 1023u), tp = static_cast<int>(cur >> 10);
+                        const float4 ww = tw2[tp];
+                        const float4 e2 = reinterpret_cast<const float4 *>(es)[a];
+                        const float2 e[2] = {make_float2(e2.x, e2.y), make_float2(e2.z, e2.w)};
+                        const float2 wr[2] = {make_float2(ww.x, ww.x), make_float2(ww.z, ww.z)};
+                        const float2 wi[2] = {make_float2(-ww.y, ww.y), make_float2(-ww.w, ww.w)};
+#pragma unroll
+                        for (int p = 0; p < P; p++) {
+                            const float2 esw = pswap(e[p]);
+#pragma unroll
+                            for (int u = 0; u < 2; u++) acc[p][u] = pfma(wi[u], esw, pfma(wr[u], e[p], acc[p][u]));
+                        }
+                    }
+                }
+                if (pos != kNone) {
+                    const int y = static_cast<int>(pos >> 5), x = 2 * static_cast<int>(pos & 31u);
+#pragma unroll
+                    for (int p = 0; p < P; p++) {
+                        uint32_t rh, rl, ih, il;
+                        split_pair<kBF16, kSplit>(acc[p][0].x, acc[p][1].x, rh, rl);
+                        split_pair<kBF16, kSplit>(acc[p][0].y, acc[p][1].y, ih, il);
+                        const int row = 64 * p + y;
+                        *reinterpret_cast<uint32_t *>(opG + k_off(row, x)) = rh;
+                        *reinterpret_cast<uint32_t *>(opG + k_off(row, 64 + x)) = ih;
+                        if constexpr (kSplit) {
+                            *reinterpret_cast<uint32_t *>(opG + kPart + k_off(row, x)) = rl;
+                            *reinterpret_cast<uint32_t *>(opG + kPart + k_off(row, 64 + x)) = il;
+                        }
+                    }
+                }
+                bt += 33 + 32 * d;
+            }
+        };
+        // D1 (row transform of the sample) -> H16 for class hy: row jy turned by w_128^{ky hy}.
+        // Thread: lane m = (pol, jy), columns 64 hp .. 64 hp + 63 = Re and Im of mx = 32 hp .. 32 hp + 31.
+        auto to_h16 = [&](int hy) {
+            const float2 f = hy ? turn : make_float2(1.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                uint32_t d[32];
+                tc::tmem_ld32_issue(lane_addr + kColD1 + 64 * hp + 32 * q, d);
+                tc::tmem_wait_ld();
+                tc::reg_fence32(d);
+#pragma unroll
+                for (int g8 = 0; g8 < 2; g8++) {
+                    uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+                    for (int w = 0; w < 4; w++) {
+                        float2 z[2];
+#pragma unroll
+                        for (int u = 0; u < 2; u++) {
+                            const int i = 8 * g8 + 2 * w + u;
+                            z[u] = make_float2(__uint_as_float(d[i]), __uint_as_float(d[16 + i]));
+                            if (hy) z[u] = cmul(z[u], f);
+                        }
+                        split_pair<kBF16, kSplit>(z[0].x, z[1].x, rh[w], rl[w]);
+                        split_pair<kBF16, kSplit>(z[0].y, z[1].y, ih[w], il[w]);
+                    }
+                    const int n0 = 32 * hp + 16 * q + 8 * g8 + 64 * pol;
+                    *reinterpret_cast<uint4 *>(opH + mn_off(n0, jy)) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+                    *reinterpret_cast<uint4 *>(opH + mn_off(n0, 64 + jy)) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+                    if constexpr (kSplit) {
+                        *reinterpret_cast<uint4 *>(opH + kPart + mn_off(n0, jy)) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+                        *reinterpret_cast<uint4 *>(opH + kPart + mn_off(n0, 64 + jy)) =
+                            make_uint4(il[0], il[1], il[2], il[3]);
+                    }
+                }
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            tc::mbar_arrive(&bar_h);
+        };
+        auto load_stage = [&](int t, uint32_t (&pre)[kPreW]) {
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(t) * C + c) * AP);
+#pragma unroll
+            for (int r = 0; r < kPreW; r++) {
+                const int w = tid + r * kSimtP;
+                pre[r] = (t < t1 && w < APW) ? __ldg(row + w) : 0u;
+            }
+        };
+        auto put_stage = [&](const uint32_t (&pre)[kPreW]) {
+#pragma unroll
+            for (int r = 0; r < kPreW; r++) {
+                const int w = tid + r * kSimtP;
+                if (w < APW) stage[w] = pre[r];
+            }
+        };
+        auto fail = [&]() {
+            atomicOr(status, kStatusTimeout);
+            abort_flag = 1;
+        };
+
+        float4 acc0[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) acc0[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+        // prologue: sample t0 gridded into G16, the bytes of t0 + 1 staged
+        if (t0 < t1) {
+            unpack(t0);
+            tc::named_bar_sync(kBarP, kSimtP);
+            uint32_t pre[kPreW];
+            load_stage(t0 + 1, pre);
+            gather(my_idx.x, my_idx.y);
+            gather(my_idx.z, my_idx.w);
+            put_stage(pre);
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            tc::mbar_arrive(&bar_g);
+            tc::named_bar_sync(kBarP, kSimtP);
+        }
+        uint32_t p1 = 0, p2a = 0, p2b = 0;
+        for (int t = t0; t < t1; t++) {
+            const bool nxt = t + 1 < t1;
+            uint32_t pre[kPreW];
+            load_stage(t + 2, pre);
+            // row stage of t done: D1 -> H16 for class hy = 0 (G16 is free for sample t + 1)
+            if (!abort_flag) {
+                if (!tc::mbar_wait(&bar_m1, p1, wait_budget)) fail();
+                else {
+                    tc::fence_after_sync();
+                    to_h16(0);
+                }
+            }
+            p1 ^= 1u;
+            if (nxt) unpack(t + 1);
+            tc::named_bar_sync(kBarP, kSimtP);          // es of t + 1 complete; the staged bytes are free
+            put_stage(pre);
+            if (nxt && !abort_flag) gather(my_idx.x, my_idx.y);
+            // column stage of (t, 0) done: H16 is free -> H16 for class hy = 1
+            if (!abort_flag) {
+                if (!tc::mbar_wait(&bar_m2a, p2a, wait_budget)) fail();
+                else {
+                    tc::fence_after_sync();
+                    to_h16(1);
+                }
+            }
+            p2a ^= 1u;
+            if (nxt && !abort_flag) {
+                gather(my_idx.z, my_idx.w);
+                tc::fence_proxy_async();
+                tc::fence_before_sync();
+                tc::mbar_arrive(&bar_g);
+            }
+            // a5, a6: products of (t, 0) from D2a (complete: waited above), then of (t, 1)
+            if (!abort_flag) products<true>(lane_addr, kColD2a, hp, part, acc0);
+            if (!abort_flag) {
+                if (!tc::mbar_wait(&bar_m2b, p2b, wait_budget)) fail();
+                else {
+                    tc::fence_after_sync();
+                    products<false>(lane_addr, kColD2b, hp, part, acc0);
+                }
+            }
+            p2b ^= 1u;
+            tc::fence_before_sync();
+            tc::named_bar_sync(kBarP, kSimtP);
+            if (abort_flag) break;
+        }
+
+        // ---- partial images of both classes (undo the FP16 scale exactly)
+        tc::fence_after_sync();
+        const float inv = 1.f / (scale * scale);
+        const int my = 16 * (warp & 3) + (lane & 15);
+        float4 *dst0 = reinterpret_cast<float4 *>(partial) +
+                       (static_cast<size_t>(tau) * n_items_out + ci * 4 + hx) * (64 * 64);
+        float4 *dst1 = reinterpret_cast<float4 *>(partial) +
+                       (static_cast<size_t>(tau) * n_items_out + ci * 4 + 2 + hx) * (64 * 64);
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const int mx = 32 * hp + 16 * part + j;
+            dst0[my * 64 + mx] = make_float4(acc0[j].x * inv, acc0[j].y * inv, acc0[j].z * inv, acc0[j].w * inv);
+        }
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+            uint32_t s[32];
+            tc::tmem_ld32_issue(lane_addr + kColAcc1 + 64 * hp + 32 * half, s);
+            tc::tmem_wait_ld();
+            tc::reg_fence32(s);
+#pragma unroll
+            for (int jj = 0; jj < 8; jj++) {
+                const int mx = 32 * hp + 16 * part + 8 * half + jj;
+                dst1[my * 64 + mx] = make_float4(__uint_as_float(s[4 * jj]) * inv, __uint_as_float(s[4 * jj + 1]) * inv,
+                                                 __uint_as_float(s[4 * jj + 2]) * inv,
+                                                 __uint_as_float(s[4 * jj + 3]) * inv);
+            }
+        }
+    }
+    // an aborted CTA may still have MMAs in flight: give them a bounded chance to land
+    if (tid == kSimtP && abort_flag) {
+        tc::mbar_wait(&bar_m1, 0, wait_budget);
+        tc::mbar_wait(&bar_m1, 1, wait_budget);
+        tc::mbar_wait(&bar_m2a, 0, wait_budget);
+        tc::mbar_wait(&bar_m2a, 1, wait_budget);
+        tc::mbar_wait(&bar_m2b, 0, wait_budget);
+        tc::mbar_wait(&bar_m2b, 1, wait_budget);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(taddr, 512);
+}
+
+size_t pair_smem(int A, int K, int words)
+{
+    const int AP = A * 2;
+    size_t b = 6 * static_cast<size_t>(kPart);
+    b += sizeof(float2) * 2 * static_cast<size_t>(AP) + sizeof(float4) * static_cast<size_t>(K) * (K + 1);
+    b += sizeof(uint32_t) * ((AP + 3) / 4) + sizeof(uint16_t) * static_cast<size_t>(words);
+    return (b + 15) & ~static_cast<size_t>(15);
+}
+
+template <class F>
+int pair_dispatch(int precision, F &&f)
+{
+    switch (precision) {
+    case EPIC_TC_SPLIT_FP16: return f(std::integral_constant<int, 0>{});
+    case EPIC_TC_FP16: return f(std::integral_constant<int, 1>{});
+    default: return f(std::integral_constant<int, 2>{});
+    }
+}
+
+}  // namespace
+
+// The gather lists of the pair kernel from the FP32 kernel's table of the same
+// channels (build_gather_table, fold side 64, dual polarisation): batches of 32
+// cell pairs keep their order and their bank-aware step order, each as
+// [list length d][32 pair positions y * 32 + x / 2][d x 32 entries tp << 10 | a]
+// in 16-bit words (0xFFFF: none), without the zero lists (G16 keeps the cells
+// no list names at zero).  Each warp's batches are split in two halves of
+// about equal work (list steps) for the two gridding phases of an iteration:
+// idx[ci * 8 + w] = (first half's offset, its batches, second half's offset,
+// its batches), offsets in words from the channel block's start; chan[ci] =
+// (block start, block words).  The upper mask of a channel lists the folded
+// rows whose cells lie in unfolded rows 64..127; EPIC_ERR_UNSUPPORTED when a
+// folded row holds cells of both halves, when A > 1024, or when K (K + 1) > 64.
+int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
+                      const std::vector<uint32_t> &tab32, const std::vector<int4> &idx32,
+                      const std::vector<int2> &chan32, std::vector<uint16_t> &tab, std::vector<int4> &idx,
+                      std::vector<int2> &chan, std::vector<unsigned long long> &upper)
+{
+    constexpr int M = 64, S = M + 1, W = 8;
+    if (A > 1024 || K * (K + 1) > 63) return EPIC_ERR_UNSUPPORTED;
+    const int nc = static_cast<int>(chans.size()), h = (K - 1) / 2;
+    tab.clear();
+    idx.assign(static_cast<size_t>(nc) * W, make_int4(0, 0, 0, 0));
+    chan.assign(nc, make_int2(0, 0));
+    upper.assign(nc, 0ull);
+    for (int ci = 0; ci < nc; ci++) {
+        unsigned long long lo_rows = 0, hi_rows = 0;
+        for (int a = 0; a < A; a++) {
+            const short2 k = cells[static_cast<size_t>(chans[ci]) * A + a];
+            for (int dy = -h; dy <= h; dy++) {
+                const int ky = k.y + dy;
+                if (ky < 0 || ky >= 2 * M) return EPIC_ERR_UNSUPPORTED;
+                if (ky >= M) hi_rows |= 1ull << (ky - M);
+                else lo_rows |= 1ull << ky;
+            }
+        }
+        if (lo_rows & hi_rows) return EPIC_ERR_UNSUPPORTED;
+        upper[ci] = hi_rows;
+        const size_t start = tab.size();
+        const uint32_t *blk = tab32.data() + chan32[ci].x;
+        for (int w = 0; w < W; w++) {
+            const int4 i32 = idx32[static_cast<size_t>(ci) * W + w];
+            // this warp's batches: their offsets and list steps
+            std::vector<std::pair<int, int>> bs;
+            int at = i32.z;
+            for (int b = 0; b < i32.w; b++) {
+                const int d = static_cast<int>(blk[at]);
+                bs.push_back({at, d});
+                at += 33 + 32 * d;
+            }
+            long long total = 0;
+            for (auto &x : bs) total += 4 * x.second + 2;
+            long long run = 0;
+            size_t split = 0;
+            while (split < bs.size() && 2 * (run + 4 * bs[split].second + 2) <= total) run += 4 * bs[split++].second + 2;
+            int4 &o = idx[static_cast<size_t>(ci) * W + w];
+            for (int half = 0; half < 2; half++) {
+                const size_t b0 = half ? split : 0, b1 = half ? bs.size() : split;
+                const int off = static_cast<int>(tab.size() - start);
+                if (half) {
+                    o.z = off;
+                    o.w = static_cast<int>(b1 - b0);
+                } else {
+                    o.x = off;
+                    o.y = static_cast<int>(b1 - b0);
+                }
+                for (size_t b = b0; b < b1; b++) {
+                    const int bat = bs[b].first, d = bs[b].second;
+                    tab.push_back(static_cast<uint16_t>(d));
+                    for (int l = 0; l < 32; l++) {
+                        const uint32_t cw = blk[bat + 1 + l];
+                        if (cw == ~0u) {
+                            tab.push_back(0xFFFFu);
+                            continue;
+                        }
+                        const int y = static_cast<int>(cw / S), x = static_cast<int>(cw % S);
+                        tab.push_back(static_cast<uint16_t>(y * 32 + x / 2));
+                    }
+                    for (int e = 0; e < 32 * d; e++) {
+                        const uint32_t en = blk[bat + 33 + e];
+                        if (en == ~0u) {
+                            tab.push_back(0xFFFFu);
+                            continue;
+                        }
+                        const uint32_t a = en >> 8, tp = en & 0xFFu;
+                        tab.push_back(static_cast<uint16_t>((tp << 10) | a));
+                    }
+                }
+            }
+        }
+        const size_t words = tab.size() - start;
+        if (words > 0xFFFFFFull || start > 0x7FFFFFFFull) return EPIC_ERR_UNSUPPORTED;
+        chan[ci] = make_int2(static_cast<int>(start), static_cast<int>(words));
+    }
+    if (tab.empty()) tab.push_back(0);
+    return EPIC_OK;
+}
+
+size_t tc_pair_smem_bytes(int A, int K, int words) { return pair_smem(A, K, words); }
+
+int prepare_tc_pair(const epic_plan_s *plan, size_t smem)
+{
+    return pair_dispatch(plan->precision, [&](auto vv) {
+        return raise_dyn_smem_cap(reinterpret_cast<const void *>(tc_pair128_kernel<decltype(vv)::value>), smem);
+    });
+}
+
+int launch_tc_pair(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau_out,
+                   cudaStream_t stream)
+{
+    int n_tau = choose_tau(plan, g, T);
+    if (n_tau > g.tau_cap) n_tau = g.tau_cap;
+    *n_tau_out = n_tau;
+    const dim3 grid(static_cast<unsigned>(g.n_chan * 2 * n_tau));
+    const size_t smem = pair_smem(plan->A, plan->K, g.pwords);
+    return pair_dispatch(plan->precision, [&](auto vv) {
+        tc_pair128_kernel<decltype(vv)::value><<<grid, kPairThreads, smem, stream>>>(
+            v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN, g.d_ptab, g.d_pchan, g.d_pidx,
+            g.d_upper, plan->d_dft, plan->A, plan->C, T, g.n_items, n_tau, g.d_partial, plan->d_status,
+            plan->wait_budget, plan->test_withhold_mma, plan->d_dfreq, plan->delays ? plan->d_dtab : nullptr);
+        return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+    });
+}
+
+}  // namespace epic

@@ -41,6 +41,7 @@ EPIC_DIAG_NO_GRAPH = 1 << 8
 EPIC_DIAG_GATHER_GLOBAL = 1 << 9
 EPIC_DIAG_NO_ALIAS = 1 << 10
 EPIC_DIAG_WITHHOLD_MMA = 1 << 11
+EPIC_DIAG_NO_PAIR = 1 << 12
 
 
 def EPIC_DIAG_ALIAS_BATCH(n: int) -> int:

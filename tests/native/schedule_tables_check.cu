@@ -166,7 +166,97 @@ int main(int argc, char **argv)
             for (auto &kv : first_taps) CHECK(kv.second == 1, "channel %d: cell with %d first writes", ci, kv.second);
         }
     }
-    std::printf("%s: A=%d K=%d N=%d C=%d P=%d, %zu table words, %ld failures\n", g_bad ? "FAIL" : "ok", A, K, N, C,
-                P, tab.size(), g_bad);
+    // ---- pair lists of the grid-side-128 tensor kernel, for a layout whose rows fold without
+    // overlap (a 60-row band): the same (cell pair, antenna, tap pair) entries as the FP32 table,
+    // each warp's batches split in two halves that cover them once, offsets inside the block, the
+    // upper-row mask, and no list for a layout whose rows overlap after folding
+    long long pair_words = -1;
+    if (N == 128 && P == 2 && K * (K + 1) <= 63 && A <= 1024) {
+        std::vector<short2> band(cells);
+        for (auto &c : band) c.y = static_cast<short>(N / 2 - 30 + ((c.y - h) % (60 - 2 * h)) + h);
+        std::vector<uint32_t> t32;
+        std::vector<int4> i32, pidx;
+        std::vector<int2> c32, pchan;
+        std::vector<unsigned long long> r32, upper;
+        std::vector<uint16_t> ptab;
+        CHECK(epic::build_gather_table(band, A, K, M, P, chans, t32, i32, c32, r32) == EPIC_OK, "band table");
+        CHECK(epic::build_pair_tables(band, A, K, chans, t32, i32, c32, ptab, pidx, pchan, upper) == EPIC_OK,
+              "pair lists build failed");
+        for (int ci = 0; ci < C && g_bad == 0; ci++) {
+            unsigned long long up = 0;
+            for (int a = 0; a < A; a++)
+                for (int dy = -h; dy <= h; dy++) {
+                    const int ky = band[static_cast<size_t>(ci) * A + a].y + dy;
+                    if (ky >= 64) up |= 1ull << (ky - 64);
+                }
+            CHECK(up == upper[ci], "channel %d: upper-row mask", ci);
+            std::multiset<long long> want, got;
+            const uint32_t *blk = t32.data() + c32[ci].x;
+            for (int w = 0; w < 8; w++) {
+                const int4 q = i32[static_cast<size_t>(ci) * 8 + w];
+                long long off = q.z;
+                for (int b = 0; b < q.w; b++) {
+                    const int d = static_cast<int>(blk[off]);
+                    for (int l = 0; l < 32; l++) {
+                        const uint32_t cw = blk[off + 1 + l];
+                        for (int j = 0; j < d; j++) {
+                            const uint32_t e = blk[off + 33 + 32LL * j + l];
+                            if (e == ~0u || cw == ~0u) continue;
+                            const long long pos = (cw / S) * 32 + (cw % S) / 2;
+                            want.insert((((static_cast<long long>(w) << 16) | pos) << 24) | ((e >> 8) << 8) | (e & 0xFF));
+                        }
+                    }
+                    off += 33 + 32LL * d;
+                }
+            }
+            const uint16_t *pb = ptab.data() + pchan[ci].x;
+            for (int w = 0; w < 8; w++) {
+                const int4 q = pidx[static_cast<size_t>(ci) * 8 + w];
+                for (int half = 0; half < 2; half++) {
+                    long long off = half ? q.z : q.x;
+                    const int nb = half ? q.w : q.y;
+                    for (int b = 0; b < nb; b++) {
+                        CHECK(off + 33 <= pchan[ci].y, "channel %d: batch header outside the block", ci);
+                        const int d = pb[off];
+                        CHECK(off + 33 + 32LL * d <= pchan[ci].y, "channel %d: batch outside the block", ci);
+                        for (int l = 0; l < 32; l++) {
+                            const uint16_t pos = pb[off + 1 + l];
+                            for (int j = 0; j < d; j++) {
+                                const uint16_t e = pb[off + 33 + 32LL * j + l];
+                                if (e == 0xFFFFu) continue;
+                                CHECK(pos != 0xFFFFu && pos < 64 * 32, "channel %d: entry under an empty lane", ci);
+                                const long long a = e & 1023, tp = e >> 10;
+                                CHECK(a < A && tp < K * (K + 1), "channel %d: entry out of range", ci);
+                                got.insert((((static_cast<long long>(w) << 16) | pos) << 24) | (a << 8) | tp);
+                            }
+                        }
+                        off += 33 + 32LL * d;
+                    }
+                }
+            }
+            CHECK(want == got, "channel %d: pair lists differ from the FP32 table (%zu vs %zu)", ci, want.size(),
+                  got.size());
+            pair_words = std::max<long long>(pair_words, pchan[ci].y);
+        }
+        // rows that overlap after folding (one footprint in rows 0.., one in rows 64..): no pair lists
+        if (A > 1) {
+            std::vector<short2> wide(band);
+            for (int ci = 0; ci < C; ci++) {
+                wide[static_cast<size_t>(ci) * A].y = static_cast<short>(h);
+                wide[static_cast<size_t>(ci) * A + 1].y = static_cast<short>(64 + h);
+            }
+            std::vector<uint32_t> t2;
+            std::vector<int4> i2, pidx2;
+            std::vector<int2> c2, pchan2;
+            std::vector<unsigned long long> r2, up2;
+            std::vector<uint16_t> pt2;
+            CHECK(epic::build_gather_table(wide, A, K, M, P, chans, t2, i2, c2, r2) == EPIC_OK, "wide table");
+            CHECK(epic::build_pair_tables(wide, A, K, chans, t2, i2, c2, pt2, pidx2, pchan2, up2) ==
+                      EPIC_ERR_UNSUPPORTED,
+                  "rows that overlap after folding were accepted");
+        }
+    }
+    std::printf("%s: A=%d K=%d N=%d C=%d P=%d, %zu table words, %lld pair words, %ld failures\n", g_bad ? "FAIL" : "ok",
+                A, K, N, C, P, tab.size(), pair_words, g_bad);
     return g_bad ? 1 : 0;
 }

@@ -105,3 +105,93 @@ def test_mixed_grid_sides_in_a_tensor_plan(precision, tol):
     wl = synth.random_small(A=40, P=2, C=3, T=17, N=64, K=5, seed=350)
     wl.grid_n = np.array([64, 96, 128], np.int32)
     assert _cmp(wl, precision).max() < tol
+
+
+# ---- grid side 128: two pixel classes per CTA from one gridding (the pair kernel)
+
+PAIR_CASES = [
+    # A,  C, T,  K
+    (64, 2, 9, 5),
+    (256, 2, 6, 5),
+    (100, 3, 13, 3),     # A * P not a multiple of 32: partial bank groups
+    (256, 1, 7, 7),
+    (120, 2, 5, 1),      # point kernel
+]
+
+
+@pytest.mark.parametrize("A,C,T,K", PAIR_CASES)
+@pytest.mark.parametrize("precision,tol", [(epic.EPIC_TC_SPLIT_FP16, SPLIT_TOL), (epic.EPIC_TC_FP16, FP16_TOL),
+                                           (epic.EPIC_TC_SPLIT_BF16, BF16_TOL)])
+def test_pair_kernel_matches_oracle(A, C, T, K, precision, tol):
+    wl = synth.random_small(A=A, P=2, C=C, T=T, N=128, K=K, seed=600 + A + K + T)
+    assert _cmp(wl, precision).max() < tol
+
+
+def test_pair_kernel_agrees_with_single_class_kernel():
+    """The two-classes-per-CTA kernel and the one-class kernel (EPIC_DIAG_NO_PAIR)
+    compute the same images up to FP32 rounding of different summation orders."""
+    wl = synth.random_small(A=200, P=2, C=2, T=11, N=128, K=5, seed=610)
+    a, pa = run_gpu(wl, precision=epic.EPIC_TC_SPLIT_FP16)
+    b, pb = run_gpu(wl, precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_DIAG_NO_PAIR)
+    pa.close()
+    pb.close()
+    assert peak_rel_err(a, b, wl.grid_n, 2).max() < 5e-6
+    assert peak_rel_err(a, oracle.workload_image(wl), wl.grid_n, 2).max() < SPLIT_TOL
+
+
+@pytest.mark.parametrize("T", [1, 2, 3, 64])
+def test_pair_kernel_sample_counts(T):
+    """One sample (prologue only), two, three, and many over several time chunks:
+    the gather / row stage / two column stages pipeline drains every sample."""
+    wl = synth.random_small(A=48, P=2, C=1, T=T, N=128, K=3, seed=620 + T)
+    assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16).max() < SPLIT_TOL
+
+
+def test_pair_kernel_with_taper_and_flags():
+    wl = synth.random_small(A=96, P=2, C=2, T=8, N=128, K=5, seed=630)
+    for flags in (epic.EPIC_KERNEL_TAPER, epic.EPIC_MEAN, epic.EPIC_NO_AUTOSUB, epic.EPIC_STOKES):
+        assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16, flags=flags).max() < SPLIT_TOL
+
+
+def test_wide_aperture_at_side_128_keeps_parity():
+    """An aperture spanning more than 64 rows at side 128 folds rows onto each
+    other; the plan then images that side with one class per CTA, still exact."""
+    wl = synth.random_small(A=90, P=2, C=2, T=5, N=128, K=3, seed=640, spread_cells=100)
+    assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16).max() < SPLIT_TOL
+
+
+def test_pair_kernel_bounded_wait_reports_timeout():
+    """Failure detection in the pair kernel without a fault: no MMA is issued,
+    the bounded waits give up, the status reads EPIC_ERR_TIMEOUT, and a fresh
+    plan images correctly afterwards."""
+    import torch
+    from gpu_helpers import torch_inputs
+    wl = synth.random_small(A=40, P=2, C=1, T=3, N=128, K=3, seed=650)
+    p = epic.Plan.from_workload(wl, precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_DIAG_WITHHOLD_MMA)
+    v, g = torch_inputs(wl)
+    p.image(v, g)
+    torch.cuda.synchronize()
+    assert p.status() == epic.EPIC_ERR_TIMEOUT
+    p.close()
+    assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16).max() < SPLIT_TOL
+
+
+def test_pair_kernel_series_and_delays():
+    """Image series (one time chunk per image) and delay correction through the pair kernel."""
+    import torch
+    from gpu_helpers import torch_inputs
+    wl = synth.random_small(A=64, P=2, C=2, T=12, N=128, K=5, seed=660)
+    p = epic.Plan.from_workload(wl, precision=epic.EPIC_TC_SPLIT_FP16)
+    v, g = torch_inputs(wl)
+    imgs = p.image_series(v, 4, g).cpu().numpy().astype(np.complex128)
+    tau = synth.geometric_delays(wl.ant_xy, wl.T, dl=1e-3)
+    d = torch.from_numpy(tau).cuda()
+    withd = p.image(v, g, delays=d).cpu().numpy().astype(np.complex128)
+    torch.cuda.synchronize()
+    assert p.status() == epic.EPIC_OK
+    p.close()
+    for i in range(3):
+        sub = synth.Workload(wl.name, wl.ant_xy, 2, wl.kernel, wl.grid_n, wl.freq_hz, wl.du, 4,
+                             wl.v[4 * i:4 * i + 4], wl.gains, {})
+        assert peak_rel_err(imgs[i], oracle.workload_image(sub), wl.grid_n, 2).max() < SPLIT_TOL
+    assert peak_rel_err(withd, oracle.workload_image(wl, delays=tau), wl.grid_n, 2).max() < SPLIT_TOL

@@ -118,8 +118,10 @@ def test_static_call_between_plans_keeps_larger_plans_working():
     torch.cuda.synchronize()
     assert plan.status() == epic.EPIC_OK
     plan.close()
-    assert np.array_equal(again.cpu().numpy().astype(np.complex128), first)
-    assert _peak_rel(first, oracle.workload_image(big), big.C, 4) < FP32_TOL
+    ref = oracle.workload_image(big)
+    # the side-32 kernel grids with shared-memory atomics, so repeats agree to rounding, not bit for bit
+    assert _peak_rel(again.cpu().numpy().astype(np.complex128), ref, big.C, 4) < FP32_TOL
+    assert _peak_rel(first, ref, big.C, 4) < FP32_TOL
     assert _peak_rel(got.cpu().numpy().astype(np.complex128), oracle.workload_image(small), small.C, 4) < FP32_TOL
 
 
