@@ -15,6 +15,9 @@ readings of points the paper leaves open):
   epic_fx         O2, Eq. 1-3 (FX correlator + gridding with W (x) W^*)
                   (both take one [K][K] kernel or per-antenna [A][K][K] kernels, Eq. 3)
   grid_energy     sum_t sum_k |G_p(k, t)|^2 with O1's gridding (Parseval pin)
+  epic_efield     O1's steps a1-a4 alone: the electric-field image F_p(l, t) of
+                  every sample (the abstract and Sec. 1, "electric field or
+                  intensity images"), fft-shifted, no products
 """
 from __future__ import annotations
 
@@ -63,6 +66,8 @@ def lib():
                 f = getattr(L, name)
                 f.argtypes = [P, P, i, i, i, i, P, P, P, i, i, P, P, ctypes.c_uint, P]
                 f.restype = i
+            L.oracle_epic_efield.argtypes = [P, P, i, i, i, i, P, P, P, i, i, P, P, P]
+            L.oracle_epic_efield.restype = i
             L.oracle_grid_energy.argtypes = [P, P, i, i, i, i, P, P, P, i, i, P]
             L.oracle_grid_energy.restype = i
             L.oracle_threads.restype = i
@@ -170,6 +175,35 @@ def epic_direct(v, gains, cells, grid_n, W, flags: int = 0, freq=None, delays=No
 def epic_fx(v, gains, cells, grid_n, W, flags: int = 0, freq=None, delays=None) -> np.ndarray:
     """O2: same output as epic_direct, by the FX-correlator route."""
     return _run("oracle_epic_fx", v, gains, cells, grid_n, W, flags, freq, delays)
+
+
+def epic_efield(v, gains, cells, grid_n, W, freq=None, delays=None) -> np.ndarray:
+    """E-field images F_p(l, t): complex128 [T][sum_c P N_c^2], per sample the
+    channels packed in order, each [P][N][N] on the fft-shifted layout."""
+    v, g, cells, n, w, T, C, A, P = _common(v, gains, cells, grid_n, W)
+    f = d = None
+    if delays is not None:
+        f = np.ascontiguousarray(freq, np.float64)
+        d = np.ascontiguousarray(delays, np.float64)
+        if f.shape != (C,) or d.shape != (T, A):
+            raise ValueError("freq must be [C] and delays [T][A]")
+    per = int(sum(P * int(N) * int(N) for N in n))
+    out = np.zeros((T, per), np.complex128)
+    rc = lib().oracle_epic_efield(_ptr(v), _ptr(g), T, C, A, P, _ptr(cells), _ptr(n), _ptr(w), w.shape[-1],
+                                  int(w.ndim == 3), _ptr(f), _ptr(d), _ptr(out))
+    if rc:
+        raise ValueError("oracle_epic_efield: bad arguments")
+    return out
+
+
+def workload_efield(wl, channels=None) -> np.ndarray:
+    """epic_efield on a synth.Workload (optionally a subset of channels)."""
+    cells = cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    v, g, grid_n = wl.v, wl.gains, wl.grid_n
+    if channels is not None:
+        ch = np.asarray(channels)
+        v, g, cells, grid_n = v[:, ch], (None if g is None else g[ch]), cells[ch], grid_n[ch]
+    return epic_efield(v, g, cells, grid_n, wl.kernel)
 
 
 def grid_energy(v, gains, cells, grid_n, W) -> np.ndarray:

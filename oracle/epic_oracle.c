@@ -386,6 +386,59 @@ int oracle_epic_direct(const uint8_t *v, const double *gains_il, int T, int C, i
     return 0;
 }
 
+/* ------------------------------------------------------------ O1 E-field images */
+
+/* The electric-field images themselves (the abstract and Sec. 1: EPIC makes
+ * "electric field or intensity images"): O1's steps a1-a4 only -- calibrate,
+ * grid, inverse transform -- written per sample, channel and polarisation on
+ * the fft-shifted layout, with no products, no time sum and no autocorrelation
+ * term.  out: complex [T][sum_c P N_c^2], per sample the channels packed in
+ * order, each [P][N_c][N_c]. */
+int oracle_epic_efield(const uint8_t *v, const double *gains_il, int T, int C, int A, int P,
+                       const int *cells, const int *grid_n, const double *W_il, int K,
+                       int per_antenna, const double *freq_hz, const double *delays, double *out_il)
+{
+    if (check_args(T, C, A, P, K, grid_n)) return -1;
+    if (delays && !freq_hz) return -1;
+    const cplx *g = (const cplx *)gains_il;
+    const cplx *W = (const cplx *)W_il;
+    cplx *out = (cplx *)out_il;
+    int h = (K - 1) / 2;
+    size_t per_sample = channel_offset(grid_n, C, P);
+
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < C; c++) {
+        int N = grid_n[c];
+        size_t NN = (size_t)N * N;
+        cplx *G = malloc(sizeof(cplx) * NN);
+        cplx *buf = malloc(sizeof(cplx) * (size_t)(6 * N + 64));
+        cplx *tw = make_twiddles(N, +1);
+        fft_ctx ctx = {N, tw};
+        for (int t = 0; t < T; t++) {
+            cplx *ot = out + (size_t)t * per_sample + channel_offset(grid_n, c, P);
+            for (int p = 0; p < P; p++) {
+                memset(G, 0, sizeof(cplx) * NN);
+                for (int a = 0; a < A; a++) {
+                    cplx e = ci4_value(v[(((size_t)t * C + c) * A + a) * P + p]);
+                    if (g) e *= g[((size_t)c * A + a) * P + p];
+                    if (delays) e *= delay_factor(freq_hz, delays, A, t, c, a);
+                    int kx = cells[((size_t)c * A + a) * 2 + 0];
+                    int ky = cells[((size_t)c * A + a) * 2 + 1];
+                    for (int dy = -h; dy <= h; dy++)
+                        for (int dx = -h; dx <= h; dx++)
+                            G[(size_t)wrap(ky + dy, N) * N + wrap(kx + dx, N)] += wtap(W, K, per_antenna, a, dy, dx) * e;
+                }
+                ifft2(&ctx, G, buf);
+                for (int i = 0; i < N; i++)
+                    for (int j = 0; j < N; j++)
+                        ot[(size_t)p * NN + (size_t)i * N + j] = G[(size_t)wrap(i - N / 2, N) * N + wrap(j - N / 2, N)];
+            }
+        }
+        free(G); free(buf); free(tw);
+    }
+    return 0;
+}
+
 /* Per-(c, p) grid energy sum_t sum_k |G_p(k, t)|^2 with the O1 gridding, for
  * the Parseval pin. */
 int oracle_grid_energy(const uint8_t *v, const double *gains_il, int T, int C, int A, int P,

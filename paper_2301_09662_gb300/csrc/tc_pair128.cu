@@ -73,27 +73,31 @@ __device__ __forceinline__ void products(uint32_t lane_addr, uint32_t d2, int hh
 {
 #pragma unroll
     for (int half = 0; half < 2; half++) {
-        // own columns 16 part + 8 half .., the partner's 16 (1 - part) + 8 half ..
-        uint32_t ox[8], oy[8], sx[8], sy[8];
+        // columns 8 half .. (part 0's pixels) and 16 + 8 half .. (part 1's) of each polarisation;
+        // a TMEM load's address is warp-uniform, so each lane then picks its own part and the
+        // one its partner needs
+        uint32_t x0[8], y0[8], x1[8], y1[8];
         const uint32_t base = lane_addr + d2 + 32 * hh + 8 * half;
-        tc::tmem_ld8_issue(base + 16 * part, ox);
-        tc::tmem_ld8_issue(base + 64 + 16 * part, oy);
-        tc::tmem_ld8_issue(base + 16 * (1 - part), sx);
-        tc::tmem_ld8_issue(base + 64 + 16 * (1 - part), sy);
+        tc::tmem_ld8_issue(base, x0);
+        tc::tmem_ld8_issue(base + 16, x1);
+        tc::tmem_ld8_issue(base + 64, y0);
+        tc::tmem_ld8_issue(base + 64 + 16, y1);
         uint32_t s[32];
         const uint32_t at = lane_addr + kColAcc1 + 64 * hh + 32 * half;
         if constexpr (!REG) tc::tmem_ld32_issue(at, s);
         tc::tmem_wait_ld();
-        tc::reg_fence8(ox);
-        tc::reg_fence8(oy);
-        tc::reg_fence8(sx);
-        tc::reg_fence8(sy);
+        tc::reg_fence8(x0);
+        tc::reg_fence8(x1);
+        tc::reg_fence8(y0);
+        tc::reg_fence8(y1);
         if constexpr (!REG) tc::reg_fence32(s);
 #pragma unroll
         for (int jj = 0; jj < 8; jj++) {
-            const float gx = __shfl_xor_sync(0xffffffffu, __uint_as_float(sx[jj]), 16);
-            const float gy = __shfl_xor_sync(0xffffffffu, __uint_as_float(sy[jj]), 16);
-            const float o1 = __uint_as_float(ox[jj]), o2 = __uint_as_float(oy[jj]);
+            const uint32_t ox = part ? x1[jj] : x0[jj], oy = part ? y1[jj] : y0[jj];
+            const uint32_t sx = part ? x0[jj] : x1[jj], sy = part ? y0[jj] : y1[jj];
+            const float gx = __shfl_xor_sync(0xffffffffu, __uint_as_float(sx), 16);
+            const float gy = __shfl_xor_sync(0xffffffffu, __uint_as_float(sy), 16);
+            const float o1 = __uint_as_float(ox), o2 = __uint_as_float(oy);
             const float xr = part ? gx : o1, xi = part ? o1 : gx;
             const float yr = part ? gy : o2, yi = part ? o2 : gy;
             if constexpr (REG) {

@@ -149,8 +149,17 @@ def test_pair_kernel_sample_counts(T):
 
 def test_pair_kernel_with_taper_and_flags():
     wl = synth.random_small(A=96, P=2, C=2, T=8, N=128, K=5, seed=630)
-    for flags in (epic.EPIC_KERNEL_TAPER, epic.EPIC_MEAN, epic.EPIC_NO_AUTOSUB, epic.EPIC_STOKES):
+    for flags in (epic.EPIC_KERNEL_TAPER, epic.EPIC_MEAN, epic.EPIC_NO_AUTOSUB):
         assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16, flags=flags).max() < SPLIT_TOL
+    # Stokes: I = XX + YY, Q = XX - YY, U = 2 Re XY, V = 2 Im XY from the oracle's products
+    st, p = run_gpu(wl, precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_STOKES)
+    p.close()
+    ref = oracle.workload_image(wl)
+    for a, b in zip(oracle.split_channels(st, wl.grid_n, 2), oracle.split_channels(ref, wl.grid_n, 2)):
+        xx, yy, xy = b[0].real, b[1].real, b[2]
+        stokes = np.stack([xx + yy, xx - yy, 2 * xy.real, 2 * xy.imag])
+        peak = max(np.max(np.abs(xx)), np.max(np.abs(yy)))
+        assert np.max(np.abs(a.real - stokes)) / peak < 2 * SPLIT_TOL
 
 
 def test_wide_aperture_at_side_128_keeps_parity():

@@ -500,3 +500,63 @@ def test_p11_cell_map_plausible_mistakes_fail():
     }
     for name, w in wrong.items():
         assert w.astype(int).tolist() != expect, name
+
+
+# ---------------------------------------------------------------- E-field images
+
+def beamformer_field(v, g, cells, N, W):
+    """Brute-force F_p(l, t) = W^(l) sum_a e~_a exp(2 pi i k_a.l / N) for one
+    channel, [T][P][N][N] on the shifted layout (no grid, no FFT)."""
+    e = unpack_np(v)                                  # [T][A][P]
+    if g is not None:
+        e = e * g[None]
+    l = np.arange(N) - N // 2
+    ph_x = np.exp(2j * np.pi * np.outer(cells[:, 0], l) / N)
+    ph_y = np.exp(2j * np.pi * np.outer(cells[:, 1], l) / N)
+    return np.einsum("tap,ai,aj->tpij", e, ph_y, ph_x) * what(W, N)[None, None]
+
+
+@pytest.mark.parametrize("A,P,K,N", [(5, 1, 1, 8), (9, 2, 3, 16), (12, 2, 5, 32)])
+def test_efield_brute_force_beamformer(A, P, K, N):
+    wl = synth.random_small(A=A, P=P, C=2, T=3, N=N, K=K, seed=1200 + A)
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    F = oracle.epic_efield(wl.v, wl.gains, cells, wl.grid_n, wl.kernel)
+    per = P * N * N
+    for c in range(2):
+        ref = beamformer_field(wl.v[:, c], wl.gains[c], cells[c], N, wl.kernel)
+        got = F[:, c * per:(c + 1) * per].reshape(wl.T, P, N, N)
+        assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_efield_parseval_per_sample():
+    # sum_l |F_p(l, t)|^2 = N^2 sum_k |G_p(k, t)|^2 for every sample (one sample per call)
+    wl = synth.random_small(A=20, P=2, C=2, T=4, N=32, K=3, seed=1210)
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    F = oracle.epic_efield(wl.v, wl.gains, cells, wl.grid_n, wl.kernel).reshape(wl.T, 2, 2, 32 * 32)
+    for t in range(wl.T):
+        en = oracle.grid_energy(wl.v[t:t + 1], wl.gains, cells, wl.grid_n, wl.kernel)   # [C][P]
+        got = np.sum(np.abs(F[t]) ** 2, axis=-1)
+        assert np.allclose(got, 32 * 32 * en, rtol=1e-12)
+
+
+def test_efield_quarter_field_closed_form():
+    # e_a = s_t (-i)^{kx + ky}: F(l = (N/4, N/4), t) = s_t A W^(l), the peak of |F|
+    wl, _, s, N, A = _point_source_case(True)
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    F = oracle.epic_efield(wl.v, None, cells, wl.grid_n, wl.kernel).reshape(len(s), N, N)
+    Wh = what(wl.kernel, N)
+    i = j = N // 2 + N // 4
+    assert np.allclose(F[:, i, j], s * A * Wh[i, j], rtol=1e-13, atol=1e-12)
+    for t in range(len(s)):
+        assert np.argmax(np.abs(F[t])) == i * N + j
+
+
+def test_efield_products_give_the_unsubtracted_image():
+    # sum_t F_p F_q^* over the E-field images is the integration before autocorrelation removal
+    wl = synth.random_small(A=15, P=2, C=2, T=5, N=16, K=3, seed=1220)
+    cells = oracle.cell_map(wl.ant_xy, wl.freq_hz, wl.grid_n, wl.du)
+    F = oracle.epic_efield(wl.v, wl.gains, cells, wl.grid_n, wl.kernel).reshape(wl.T, 2, 2, 16 * 16)
+    ref = beamformer_image(wl.v[:, 0], wl.gains[0], cells[0], 16, wl.kernel, autosub=False)
+    X, Y = F[:, 0, 0], F[:, 0, 1]
+    S = [np.sum(X * X.conj(), 0), np.sum(Y * Y.conj(), 0), np.sum(X * Y.conj(), 0), np.sum(Y * X.conj(), 0)]
+    assert np.max(np.abs(np.array(S).reshape(ref.shape) - ref)) < 1e-11 * np.max(np.abs(ref))
