@@ -266,23 +266,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def tensor_stages():
-    """DFT stages the tensor form runs as GEMMs: both, the row and the column stage."""
-    return 2
-
-
-def tensor_roofline(wl, form, img_ms, peaks):
-    """Executed tensor FLOPs of the tensor-core imaging launch over its time:
-    per CTA (pixel class), sample and DFT stage, 8 k-blocks x terms MMAs of
-    128 x 128 x 16."""
+def tensor_roofline(wl, form, img_ms, peaks, pair=True):
+    """Executed tensor FLOPs of the tensor-core imaging launch over its time.
+    Each 64-point DFT stage of one sample is 8 k-blocks x terms MMAs of
+    128 x 128 x 16.  Grid side 128 runs two pixel classes per CTA from one row
+    stage (pair kernel): 3 stage GEMMs per two classes; other sides (and
+    side 128 with EPIC_DIAG_NO_PAIR): 2 per class.  Also the method's
+    algorithmic FLOPs (the FP32 FFT form's count) over the same time."""
     terms = 1 if form == "tc_fp16" else 3
-    n_items = sum((int(n) // 64) ** 2 for n in wl.grid_n)
-    flops = n_items * wl.T * tensor_stages() * 8 * terms * 2.0 * 128 * 128 * 16
+    stage = 8 * terms * 2.0 * 128 * 128 * 16
+    stages = 0.0
+    for n in wl.grid_n:
+        classes = (int(n) // 64) ** 2
+        stages += classes * (1.5 if (pair and int(n) == 128) else 2.0)
+    flops = stages * wl.T * stage
     ach = flops / (img_ms / 1e3) / 1e12
     peak = float(peaks.get("bf16_tflops", 1892.1))
+    alg = sum(fp32_flops_per_spectrum(wl.A, wl.K, int(n)) for n in wl.grid_n) * wl.T * wl.n_pol
     return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": None, "executed_flops_per_launch": flops, "ms_per_launch": img_ms,
-            "dft_stages_on_tensor_cores": tensor_stages(),
+            "stage_gemms_per_class_and_sample": stages / max(1, sum((int(n) // 64) ** 2 for n in wl.grid_n)),
+            "algorithmic_flops_per_launch": alg, "algorithmic_tflops": alg / (img_ms / 1e3) / 1e12,
             "peak_source": "MEASURED_PEAKS bf16_tflops burst (dense FP16 rate equals BF16)"}
 
 
@@ -301,15 +305,19 @@ def time_variants(wl, v, g, out, flush, args, stream):
              "tc_fp16": dict(precision=epic.EPIC_TC_FP16),
              "tc_split_bf16": dict(precision=epic.EPIC_TC_SPLIT_BF16),
              "tc_split_fp16_taper": dict(precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_KERNEL_TAPER),
+             "tc_split_fp16_one_class": dict(precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_DIAG_NO_PAIR),
              "fp32_delays": dict(),
              "fp32_antenna_kernels": dict(flags=epic.EPIC_ANTENNA_KERNELS),
              "fp32_series_stokes": dict(flags=epic.EPIC_STOKES)}
     notes = {"kernel_taper": "FP32; image-domain |W^|^2 taper with point gridding (exact for one shared kernel)",
              "tc_split_fp16": "row and column DFTs on tcgen05, FP16 hi+lo operands (3 MMAs per k-block), "
-                              "FP32 accumulate in TMEM",
+                              "FP32 accumulate in TMEM; at grid side 128 two pixel classes per CTA share one "
+                              "gather gridding and one row stage",
              "tc_fp16": "row and column DFTs on tcgen05, single FP16 operands",
              "tc_split_bf16": "row and column DFTs on tcgen05, BF16 hi+lo operands (3 MMAs per k-block)",
              "tc_split_fp16_taper": "tc_split_fp16 with the image-domain kernel taper",
+             "tc_split_fp16_one_class": "tc_split_fp16 with one pixel class per CTA at grid side 128 (each class "
+                                        "grids the sample itself; the form before the pair kernel)",
              "fp32_delays": "FP32 literal form with per-(t, antenna) geometric-delay phases (epic_image_ex; "
                             "[T][A] FP64 delays resident in HBM, phases formed in the kernel)",
              "fp32_antenna_kernels": "FP32 literal form with a kernel per antenna (seeded Gaussians of +-20 % "
@@ -367,7 +375,8 @@ def time_variants(wl, v, g, out, flush, args, stream):
         if name.startswith("tc_") and stages:
             img = max((v for k, v in stages.items() if k.startswith("image[")), default=None)
             if img:
-                entry["roofline"] = tensor_roofline(wl, name.replace("_taper", ""), img, peaks)
+                entry["roofline"] = tensor_roofline(wl, name.replace("_taper", "").replace("_one_class", ""), img,
+                                                    peaks, pair=name != "tc_split_fp16_one_class")
         res[name] = entry
         p.close()
     return res
