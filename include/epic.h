@@ -266,6 +266,37 @@ int epic_image_host(epic_plan_t plan, const uint8_t *ci4_host, const float *gain
 int epic_image_series(epic_plan_t plan, const uint8_t *ci4, const float *gains_c64,
                       int n_spectra, int spectra_per_image, float *out_c64, void *cuda_stream);
 
+/*
+ * epic_image_efield -- the electric-field images themselves, one per sample (the
+ * abstract and Sec. 1: EPIC forms "electric field or intensity images"; the
+ * transient mode of Sec. 4 images every sample):
+ *
+ *   F_p(l, t) = sum_k G_p(k, t) exp(+2 pi i k.l / N_c),
+ *   G_p(k, t) = sum_a sum_d W(d) g_{c,a,p} e_{t,c,a,p} [k = k_a(c) + d]
+ *
+ * for every sample t, channel c and polarisation p: calibrate, grid, transform
+ * (steps a1-a4 of epic_image), with no products, no time sum and no
+ * autocorrelation term (plan flags other than the kernel choice do not apply).
+ *
+ *   out_c64     device complex64 [n_spectra][epic_efield_floats(plan) / 2]: per
+ *               sample the channels packed in channel order, each
+ *               [n_pol][N_c][N_c] on the fft-shifted layout of epic_image
+ *               (pixel (i, j) holds l = (j - N_c/2, i - N_c/2)); overwritten
+ *   (the other arguments as for epic_image)
+ *
+ * The output is n_spectra x 8 sum_c n_pol N_c^2 bytes (16.8 GB for 1000 samples
+ * of 64 channels of 128 x 128 dual polarisation), written once.  FP32 plans
+ * whose grid sides all run the register-transform kernel (sides 64, 96, 128,
+ * 256, 512 with n_ant * n_pol a multiple of 4); EPIC_ERR_UNSUPPORTED for
+ * others.  Asynchronous; allocates nothing; direct launches (no graph).
+ */
+int epic_image_efield(epic_plan_t plan, const uint8_t *ci4, const float *gains_c64, int n_spectra,
+                      float *out_c64, void *cuda_stream);
+
+/* Floats of one sample of epic_image_efield's output (2 per complex value), or
+ * 0 for a NULL plan. */
+size_t epic_efield_floats(epic_plan_t plan);
+
 /* Number of floats of one epic_image output (2 per complex value), or 0 for a
  * NULL plan. */
 size_t epic_out_floats(epic_plan_t plan);

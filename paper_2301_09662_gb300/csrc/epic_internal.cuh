@@ -41,8 +41,9 @@ struct GroupCfg {
     int n_items = 0;                   // n_chan * Q
     int tau_cap = 1;                   // time chunks the partial buffer holds
     float *d_partial = nullptr;        // device: [tau_cap][n_items][M*M][NPF] partial sums
-    // partial-sum pixel order: folded frequency m sits at R2 (m mod R1) + m / R1
+    // partial-sum pixel order: folded frequency m sits at up (R2 (m mod R1) + m / R1)
     int R1 = 1, R2 = 1;
+    int up = 1;                        // 2: a side-32 group transformed zero-padded to 64 points (tensor form)
     // register-transform kernels (fold side 64 or 48): gridding tables and samples per iteration
     bool reg64 = false;
     bool tensor = false;               // a tensor plan's group that folds to 64 runs the tensor kernel
@@ -76,6 +77,7 @@ struct GroupCfg {
     int2 *d_pchan = nullptr;           // device: [n_chan] (block start, block words)
     int4 *d_pidx = nullptr;            // device: [n_chan][8 warps] (half 1 offset, batches, half 2 offset, batches)
     unsigned long long *d_upper = nullptr;  // device: [n_chan] folded rows whose cells lie in unfolded rows 64..127
+    long long *d_ef_off = nullptr;     // device (E-field images): per group channel, complex offset within a sample
 };
 
 struct KernelTables {
@@ -96,6 +98,7 @@ struct epic_plan_s {
     std::vector<int> grid_n;
     std::vector<long long> out_off;    // complex-element offset of each channel's image
     size_t out_floats = 0;
+    long long ef_stride = 0;           // E-field images: complex elements per sample (sum_c P N_c^2)
     uint8_t *d_dft = nullptr;          // tensor form: the 64-point DFT operand (hi, lo parts)
     short2 *d_cells = nullptr;         // [C][A]
     float2 *d_kernel = nullptr;        // [K*K]
@@ -191,6 +194,9 @@ int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, in
 size_t reg64_smem_bytes(int M, int P, int TS, int A, int K, int nker);
 int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                  cudaStream_t stream);
+// E-field images through the register kernel: out complex [T][stride], channel offsets in g.d_ef_off
+int launch_reg64_efield(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T,
+                        float2 *out, long long stride, cudaStream_t stream);
 // Gridding schedule of the register-transform kernels for the channels of one group (plan.cu).
 int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, int M, const std::vector<int> &chans,
                          std::vector<uint32_t> &desc, std::vector<int> &nrounds, int &rmax,

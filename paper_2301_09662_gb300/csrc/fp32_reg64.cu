@@ -102,6 +102,45 @@ __device__ __forceinline__ void transform_products(float2 *G, unsigned long long
     }
 }
 
+// E-field images (epic_image_efield): the same two transform passes, then each
+// of the TS x P transformed planes is written out as F_p(l, t) on the shifted
+// layout instead of being squared and summed.  Class (hx, hy) pixel (my, mx) is
+// l = (Q1 mx + hx, Q1 my + hy), stored at out[t][off_c + p N^2 + i N + j] with
+// (i, j) = (l_y + N/2, l_x + N/2) mod N.
+template <int M, int P, int TS>
+__device__ __forceinline__ void transform_store(float2 *G, unsigned long long rows_used, float2 *__restrict__ out,
+                                                long long stride, long long off_c, int t, int t1, int N, int Q1,
+                                                int hx, int hy, int tid)
+{
+    constexpr int S = M + 1, BUF = M * S;
+    for (int q = tid; q < TS * P * M; q += kThreads) {
+        if (!((rows_used >> (q % M)) & 1ull)) continue;
+        float2 *line = G + (q / M) * BUF + (q % M) * S;
+        float2 x[M];
+#pragma unroll
+        for (int i = 0; i < M; i++) x[i] = line[i];
+        fft_reg<M>(x, [&](int k, float2 val) { line[k] = val; });
+    }
+    __syncthreads();
+    for (int q = tid; q < TS * P * M; q += kThreads) {
+        float2 *col = G + (q / M) * BUF + (q % M);
+        float2 x[M];
+#pragma unroll
+        for (int i = 0; i < M; i++) x[i] = ((rows_used >> i) & 1ull) ? col[i * S] : make_float2(0.f, 0.f);
+        fft_reg<M>(x, [&](int k, float2 val) { col[k * S] = val; });
+    }
+    __syncthreads();
+    const long long NN = static_cast<long long>(N) * N;
+    for (int e = tid; e < TS * P * M * M; e += kThreads) {
+        const int pos = e % (M * M), plane = e / (M * M), ts = plane / P, p = plane % P;
+        if (t + ts >= t1) continue;
+        const int my = pos / M, mx = pos % M;
+        const int i = (Q1 * my + hy + N / 2) % N, j = (Q1 * mx + hx + N / 2) % N;
+        out[static_cast<long long>(t + ts) * stride + off_c + p * NN + static_cast<long long>(i) * N + j] =
+            G[plane * BUF + my * S + mx];
+    }
+}
+
 // Folded side M (64, or 48 for grid side 96).  Grid buffers: G[ts][p][y][x] with
 // x < M at stride M + 1.  DL: voltages take the geometric-delay phase of the
 // per-integration table dtab (Sec. 2.2 delay correction), once per antenna.
@@ -111,7 +150,10 @@ __device__ __forceinline__ void transform_products(float2 *G, unsigned long long
 // fits beside the grids), else it is read through the L1 cache.  rowmask[ci]
 // marks the folded rows any footprint touches: the others are never written
 // and their transforms are skipped.
-template <int M, int P, int TS, bool DL, bool GS>
+// EF: write the E-field images (transform_store) instead of summing products;
+// ef_out / ef_off / ef_stride are its output, per-channel offsets and per-sample
+// stride (complex elements), unused otherwise.
+template <int M, int P, int TS, bool DL, bool GS, bool EF>
 __global__ void __launch_bounds__(kThreads, 1)
 fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
                   const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K,
@@ -120,7 +162,8 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                   const unsigned long long *__restrict__ rowmask,
                   int A, int C, int T, int N, int Q1, int n_items, int n_tau,
                   float *__restrict__ partial, int *__restrict__ status, int nker,
-                  const float *__restrict__ dfreq, const float4 *__restrict__ dtab)
+                  const float *__restrict__ dfreq, const float4 *__restrict__ dtab,
+                  float2 *__restrict__ ef_out, const long long *__restrict__ ef_off, long long ef_stride)
 {
     constexpr int NPOS = M * M / kThreads;       // pixels per thread (16 at M = 64, 9 at 48)
     constexpr int S = M + 1;                     // padded row stride (float2)
@@ -324,8 +367,11 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         __syncthreads();
 
         // ---- a4, a5, a6: transforms, products summed over time (the next gather overwrites
-        // every cell of the touched rows, so nothing is cleared)
-        transform_products<M, P, TS, false>(G, rows_used, acc, tid);
+        // every cell of the touched rows, so nothing is cleared); or the E-field images
+        if constexpr (EF)
+            transform_store<M, P, TS>(G, rows_used, ef_out, ef_stride, ef_off[ci], t, t1, N, Q1, hx, hy, tid);
+        else
+            transform_products<M, P, TS, false>(G, rows_used, acc, tid);
 #pragma unroll
         for (int ts = 0; ts < TS; ts++)
 #pragma unroll
@@ -336,12 +382,14 @@ fp32_reg64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         __syncthreads();
     }
 
-    float *dst = partial + (static_cast<size_t>(tau) * n_items + item) * (M * M) * (P == 2 ? 4 : 1);
+    if constexpr (!EF) {
+        float *dst = partial + (static_cast<size_t>(tau) * n_items + item) * (M * M) * (P == 2 ? 4 : 1);
 #pragma unroll
-    for (int r = 0; r < NPOS; r++) {
-        const int pos = tid + r * kThreads;
-        if constexpr (P == 2) reinterpret_cast<float4 *>(dst)[pos] = acc[r];
-        else dst[pos] = acc[r];
+        for (int r = 0; r < NPOS; r++) {
+            const int pos = tid + r * kThreads;
+            if constexpr (P == 2) reinterpret_cast<float4 *>(dst)[pos] = acc[r];
+            else dst[pos] = acc[r];
+        }
     }
 }
 
@@ -412,11 +460,11 @@ size_t reg64_smem(int A, int K, int nker)
     return (b + 15) & ~static_cast<size_t>(15);
 }
 
-template <int M, int P, int TS, bool DL, bool GS>
+template <int M, int P, int TS, bool DL, bool GS, bool EF = false>
 int launch_reg64_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau_out,
-                   cudaStream_t stream)
+                   cudaStream_t stream, float2 *ef_out = nullptr, long long ef_stride = 0)
 {
-    auto kfn = fp32_reg64_kernel<M, P, TS, DL, GS>;
+    auto kfn = fp32_reg64_kernel<M, P, TS, DL, GS, EF>;
     const size_t smem = reg64_smem<M, P, TS>(plan->A, plan->K, plan->nker) +
                         (GS ? sizeof(uint32_t) * static_cast<size_t>(g.gwords) : 0);
     int n_tau = choose_tau(plan, g, T);
@@ -426,7 +474,7 @@ int launch_reg64_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
     kfn<<<grid, kThreads, smem, stream>>>(v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN,
                                           g.d_gtab, g.d_gidx, g.d_gchan, g.d_rowmask, plan->A, plan->C, T, g.N,
                                           g.Q1, g.n_items, n_tau, g.d_partial, plan->d_status, plan->nker,
-                                          plan->d_dfreq, DL ? plan->d_dtab : nullptr);
+                                          plan->d_dfreq, DL ? plan->d_dtab : nullptr, ef_out, g.d_ef_off, ef_stride);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -444,9 +492,11 @@ int prepare_reg64_t(const epic_plan_s *plan, const GroupCfg &g)
                         (GS ? sizeof(uint32_t) * static_cast<size_t>(g.gwords) : 0);
     if (need > static_cast<size_t>(optin)) return EPIC_ERR_UNSUPPORTED;
     const int smem = optin;
-    const bool ok = cudaFuncSetAttribute(fp32_reg64_kernel<M, P, TS, false, GS>,
+    const bool ok = cudaFuncSetAttribute(fp32_reg64_kernel<M, P, TS, false, GS, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
-                    cudaFuncSetAttribute(fp32_reg64_kernel<M, P, TS, true, GS>,
+                    cudaFuncSetAttribute(fp32_reg64_kernel<M, P, TS, true, GS, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+                    cudaFuncSetAttribute(fp32_reg64_kernel<M, P, TS, false, GS, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
     return ok ? EPIC_OK : EPIC_ERR_UNSUPPORTED;
 }
@@ -508,6 +558,17 @@ int launch_fold64(const GroupCfg &g, int P, const float2 *gf, int nb, bool accum
     if (P == 2) fp32_fold64_kernel<2><<<grid, kThreads, smem, stream>>>(gf, nb, accumulate ? 1 : 0, g.d_partial);
     else fp32_fold64_kernel<1><<<grid, kThreads, smem, stream>>>(gf, nb, accumulate ? 1 : 0, g.d_partial);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
+}
+
+int launch_reg64_efield(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T,
+                        float2 *out, long long stride, cudaStream_t stream)
+{
+    return reg64_dispatch(plan, g, [&](auto m_, auto p_, auto ts_, auto gs_) {
+        constexpr int M = decltype(m_)::value, P = decltype(p_)::value, TS = decltype(ts_)::value;
+        constexpr bool GS = decltype(gs_)::value != 0;
+        int n_tau = 1;
+        return launch_reg64_t<M, P, TS, false, GS, true>(plan, g, v, gains, T, &n_tau, stream, out, stride);
+    });
 }
 
 int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,

@@ -60,7 +60,9 @@ autopower_kernel(const uint8_t *__restrict__ v, int T, int C, int A, int P, int 
 // grid (pixel tiles, group channels).  Partial layout written by the imaging
 // kernels: [tau][item][pos][NPF] with item = ci * Q + (hy * Q1 + hx) and
 // pos = py * M + px, where folded frequency m sits at digit position
-// R2 (m mod R1) + m / R1 (R1 = 1, R2 = M for natural order).
+// up (R2 (m mod R1) + m / R1) (R1 = 1, R2 = M for natural order; up = 2 when a
+// side-32 grid was transformed zero-padded to 64 points, whose even
+// frequencies are the 32-point transform).
 template <int M, int P>
 __global__ void __launch_bounds__(kThreads)
 epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N, int Q1, int R1, int R2,
@@ -68,7 +70,7 @@ epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N
                 const double *__restrict__ wpow, const int *__restrict__ autoint,
                 const float2 *__restrict__ gains, int A, int T, unsigned flags, float2 *__restrict__ out,
                 size_t auto_stride, long long out_stride,
-                const double2 *__restrict__ Yauto, const double2 *__restrict__ tw64, int K)
+                const double2 *__restrict__ Yauto, const double2 *__restrict__ tw64, int K, int up)
 {
     // blockIdx.z = image: it sums time chunks [z n_tau, (z + 1) n_tau) and uses
     // the auto sums and output block of index z (one image unless a series)
@@ -129,7 +131,7 @@ epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N
         const int ly = (i + N / 2) % N, lx = (j + N / 2) % N;   // (i - N/2) mod N
         const int hx = lx % Q1, mx = lx / Q1, hy = ly % Q1, my = ly / Q1;
         const int item = ci * Q + hy * Q1 + hx;
-        const int px = R2 * (mx % R1) + mx / R1, py = R2 * (my % R1) + my / R1;
+        const int px = up * (R2 * (mx % R1) + mx / R1), py = up * (R2 * (my % R1) + my / R1);
         const size_t pos = static_cast<size_t>(py) * M + px;
         // time chunks added in time order as compensated FP32 (hi, lo) pairs: TwoSum keeps
         // hi + lo equal to the exact running sum up to the roundings of lo, far below FP32;
@@ -287,7 +289,7 @@ int launch_epi(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T,
                                                          g.d_chans,
                                                          g.d_out_off, g.d_wpow, plan->d_autoint, gains, plan->A, T,
                                                          plan->flags, out, 0, 0,
-                                                         plan->nker > 1 ? g.d_Y : nullptr, g.d_tw64, plan->K);
+                                                         plan->nker > 1 ? g.d_Y : nullptr, g.d_tw64, plan->K, g.up);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -300,7 +302,7 @@ int launch_epi_raw(const RawImage &r, const float2 *gains, float2 *out, cudaStre
     epilogue_kernel<M, P><<<grid, kThreads, 0, stream>>>(r.partial, r.n_tau, r.n_items, r.N, r.Q1, 8, M / 8,
                                                          r.chans,
                                                          r.out_off, r.wpow, r.autoint, gains, r.A, r.T, r.flags,
-                                                         out, 0, 0, nullptr, nullptr, 0);
+                                                         out, 0, 0, nullptr, nullptr, 0, 1);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -356,7 +358,7 @@ int launch_epi_series(epic_plan_s *plan, const GroupCfg &g, const float2 *gains,
                                                          plan->flags, out,
                                                          static_cast<size_t>(plan->C) * plan->A * 4,
                                                          static_cast<long long>(plan->out_floats / 2), nullptr,
-                                                         nullptr, 0);
+                                                         nullptr, 0, g.up);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 

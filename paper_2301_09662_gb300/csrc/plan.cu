@@ -95,6 +95,7 @@ void free_plan(epic_plan_s *p)
         cudaFree(g.d_pchan);
         cudaFree(g.d_pidx);
         cudaFree(g.d_upper);
+        cudaFree(g.d_ef_off);
     }
     delete p;
 }
@@ -555,11 +556,12 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     if (precision < EPIC_FP32 || precision > EPIC_TC_SPLIT_BF16) return EPIC_ERR_ARG;
     const bool tensor = precision != EPIC_FP32;
     if (tensor) {
-        // the tensor form exists for dual polarisation on folded side 64; channel groups of
-        // other sides (32, 96) in the same plan run the FP32 kernel, but at least one must fold
-        if (n_pol != 2 || (n_ant * n_pol) % 4 != 0) return EPIC_ERR_UNSUPPORTED;
+        // the tensor form runs on 64-point transforms: sides 64, 128, 256, 512 fold to them and
+        // side 32 is transformed zero-padded; channel groups of side 96 in the same plan run the
+        // FP32 kernel, but at least one group must be of another side
+        if ((n_ant * n_pol) % 4 != 0) return EPIC_ERR_UNSUPPORTED;
         bool any = false;
-        for (int c = 0; c < n_chan; c++) any = any || (grid_n[c] != 32 && grid_n[c] != 96);
+        for (int c = 0; c < n_chan; c++) any = any || grid_n[c] != 96;
         if (!any) return EPIC_ERR_UNSUPPORTED;
     }
     if (static_cast<long long>(n_ant) * n_pol > epic::kMaxAP) return EPIC_ERR_UNSUPPORTED;
@@ -619,6 +621,11 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         off += static_cast<long long>(p->NP) * grid_n[c] * grid_n[c];
     }
     p->out_floats = static_cast<size_t>(off) * 2;
+    std::vector<long long> ef_off(n_chan);     // E-field images: channel offsets within one sample
+    for (int c = 0; c < n_chan; c++) {
+        ef_off[c] = p->ef_stride;
+        p->ef_stride += static_cast<long long>(n_pol) * grid_n[c] * grid_n[c];
+    }
 
     int smem_optin = 0;
     if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device) != cudaSuccess) {
@@ -683,6 +690,12 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         g.N = kv.first;
         g.Q1 = fold_for(g.N);
         g.M = g.N / g.Q1;
+        if (tensor && g.N == 32) {
+            // the tensor kernel's 64-point DFT of the zero-padded 32 x 32 grid: its even
+            // frequencies 2 l are the 32-point transform at l (cells lie in [0, 32))
+            g.M = 64;
+            g.up = 2;
+        }
         g.Q = g.Q1 * g.Q1;
         g.chans = kv.second;
         g.n_chan = static_cast<int>(g.chans.size());
@@ -702,7 +715,9 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         g.R2 = g.M / 8;
         const int ap = n_ant * n_pol;
         g.tensor = tensor && g.M == 64;
-        const bool fold_ok = g.Q1 == 8 && p->nker == 1 && p->K > 1 && !(diag & EPIC_DIAG_NO_ALIAS);
+        // (the tensor kernel's fold path is written for dual polarisation)
+        const bool fold_ok = g.Q1 == 8 && p->nker == 1 && p->K > 1 && !(diag & EPIC_DIAG_NO_ALIAS) &&
+                             !(tensor && n_pol == 1);
         if (g.tensor) {
             // + static shared memory of the kernel (barriers, TMEM slot, alignment); a large side
             // that can take the fold path needs only the operands and the grid there
@@ -804,6 +819,11 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         if (g.pair) g.tau_cap = std::max(g.tau_cap, epic::fp32_pick_tau(g.launch_items, max_spectra, p->sm_count));
         if (rc == EPIC_OK) rc = dev_upload(&g.d_chans, g.chans.data(), g.chans.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_out_off, offs.data(), offs.size());
+        if (rc == EPIC_OK) {
+            std::vector<long long> eo(g.n_chan);
+            for (int i = 0; i < g.n_chan; i++) eo[i] = ef_off[g.chans[i]];
+            rc = dev_upload(&g.d_ef_off, eo.data(), eo.size());
+        }
         if (rc == EPIC_OK) rc = dev_upload(&g.d_wpow, wpow.data(), wpow.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_twN, tw.data(), tw.size());
         if (rc == EPIC_OK && ant_kernels) {
@@ -1021,6 +1041,28 @@ int epic_image_series_ex(epic_plan_t plan, const uint8_t *ci4, const float *gain
         plan->delays = nullptr;
     }
     return rc;
+}
+
+size_t epic_efield_floats(epic_plan_t plan) { return plan ? static_cast<size_t>(plan->ef_stride) * 2 : 0; }
+
+int epic_image_efield(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra, float *out, void *stream)
+{
+    if (!plan || !out) return EPIC_ERR_ARG;
+    if (n_spectra < 0 || n_spectra > plan->max_spectra) return EPIC_ERR_ARG;
+    if (n_spectra > 0 && !ci4) return EPIC_ERR_ARG;
+    if (plan->precision != EPIC_FP32) return EPIC_ERR_UNSUPPORTED;
+    for (const auto &g : plan->groups)
+        if (!g.reg64 || g.tensor) return EPIC_ERR_UNSUPPORTED;
+    if (n_spectra == 0) return EPIC_OK;
+    auto s = static_cast<cudaStream_t>(stream);
+    auto *o = reinterpret_cast<float2 *>(out);
+    const auto *g2 = reinterpret_cast<const float2 *>(gains);
+    plan->delays = nullptr;
+    for (const auto &g : plan->groups) {
+        const int rc = epic::launch_reg64_efield(plan, g, ci4, g2, n_spectra, o, plan->ef_stride, s);
+        if (rc != EPIC_OK) return rc;
+    }
+    return EPIC_OK;
 }
 
 int epic_image_series(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra, int spi, float *out,

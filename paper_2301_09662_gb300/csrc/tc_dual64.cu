@@ -102,9 +102,10 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
                  const uint8_t *__restrict__ dft_ops, int A, int C, int T, int N, int Q1, int n_items, int n_tau,
                  float *__restrict__ partial, int *__restrict__ status, long long wait_budget, int withhold_mma,
                  const float *__restrict__ dfreq, const float4 *__restrict__ dtab,
-                 const uint16_t *__restrict__ first, const float2 *__restrict__ gf, int accumulate)
+                 const uint16_t *__restrict__ first, const float2 *__restrict__ gf, int accumulate, int npol)
 {
-    constexpr int P = 2;
+    // npol = 1: single polarisation; the Y rows of the operands stay zero and only XX is written
+    const int P = npol;
     constexpr bool kBF16 = VAR == 2;
     constexpr bool kSplit = VAR != 1;
     constexpr int BUF = M64 * S64;
@@ -112,10 +113,10 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *opX = smem;                                              // [2 parts][32 KB] K-major
     uint8_t *opH = smem + 2 * kPart;                                  // [2 parts][32 KB] MN-major
-    float2 *G = reinterpret_cast<float2 *>(smem + 4 * kPart);         // [P][64][65]
+    float2 *G = reinterpret_cast<float2 *>(smem + 4 * kPart);         // [2][64][65] (X, Y)
     const int AP = A * P, KK = K * K, hk = (K - 1) / 2;
     const int APW = (AP + 3) >> 2;
-    float2 *es = G + P * BUF;
+    float2 *es = G + 2 * BUF;
     float2 *gp = es + AP;
     float2 *tapw = gp + AP;
     uint32_t *stage = reinterpret_cast<uint32_t *>(tapw + KK);
@@ -177,7 +178,7 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
         const int dy = i / K - hk, dx = i % K - hk;
         tapw[i] = cmul(kern[i], twN[((dx * hx + dy * hy) % N + N) % N]);
     }
-    for (int i = simt ? tid : P * BUF; i < P * BUF; i += kSimt) G[i] = make_float2(0.f, 0.f);
+    for (int i = simt ? tid : 2 * BUF; i < 2 * BUF; i += kSimt) G[i] = make_float2(0.f, 0.f);
     if (simt && t0 < t1 && !lg) {
         const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(t0) * C + c) * AP);
         for (int w = tid; w < APW; w += kSimt) stage[w] = row[w];
@@ -296,7 +297,7 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
                     const int dyi = static_cast<int>((d >> 12) & 0xFu);
                     const int y = static_cast<int>((d >> 16) & 0x3Fu);
                     const int x0 = static_cast<int>((d >> 22) & 0x3Fu);
-                    const float2 e0 = es[a * P], e1 = es[a * P + 1];
+                    const float2 e0 = es[a * P], e1 = P == 2 ? es[a * P + 1] : make_float2(0.f, 0.f);
                     const float2 e0s = pswap(e0), e1s = pswap(e1);
                     const float2 *wrow = tapw + dyi * K;
                     float2 *gy = G + y * S64;
@@ -310,7 +311,7 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
                         const bool fresh = (fm >> dx) & 1u;
                         const float2 z = make_float2(0.f, 0.f);
                         gy[x] = pfma(wi, e0s, pfma(wr, e0, fresh ? z : gy[x]));
-                        gy[BUF + x] = pfma(wi, e1s, pfma(wr, e1, fresh ? z : gy[BUF + x]));
+                        if (P == 2) gy[BUF + x] = pfma(wi, e1s, pfma(wr, e1, fresh ? z : gy[BUF + x]));
                     }
                 }
                 __syncwarp();
@@ -471,6 +472,11 @@ tc_dual64_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains
             const uint32_t *a4 = j < 8 ? s0 + 4 * j : s1 + 4 * (j - 8);
             float4 o = make_float4(__uint_as_float(a4[0]) * inv, __uint_as_float(a4[1]) * inv,
                                    __uint_as_float(a4[2]) * inv, __uint_as_float(a4[3]) * inv);
+            if (P == 1) {                                  // XX only: one float per pixel
+                float *d1 = partial + (static_cast<size_t>(tau) * n_items + item) * (M64 * M64);
+                d1[my * M64 + mx] = accumulate ? d1[my * M64 + mx] + o.x : o.x;
+                continue;
+            }
             if (accumulate) {                              // a later time batch of a large-side group
                 const float4 q = dst[my * M64 + mx];
                 o = make_float4(q.x + o.x, q.y + o.y, q.z + o.z, q.w + o.w);
@@ -512,7 +518,7 @@ int launch_dual_t(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const 
         v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN, g.d_sched, g.d_nrounds, g.rmax,
         plan->d_dft, plan->A, plan->C, T, g.N, g.Q1, g.n_items, n_tau, g.d_partial, plan->d_status,
         plan->wait_budget, plan->test_withhold_mma, plan->d_dfreq, plan->delays ? plan->d_dtab : nullptr,
-        g.d_first, nullptr, 0);
+        g.d_first, nullptr, 0, plan->P);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 
@@ -529,7 +535,7 @@ int launch_dual_fold_t(epic_plan_s *plan, const GroupCfg &g, const float2 *gains
     tc_dual64_kernel<VAR, KC><<<grid, kDualThreads, dual_fold_smem(), stream>>>(
         nullptr, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN, g.d_sched, g.d_nrounds, g.rmax,
         plan->d_dft, plan->A, plan->C, nb, g.N, g.Q1, g.n_items, 1, g.d_partial, plan->d_status,
-        plan->wait_budget, plan->test_withhold_mma, plan->d_dfreq, nullptr, g.d_first, gf, accumulate ? 1 : 0);
+        plan->wait_budget, plan->test_withhold_mma, plan->d_dfreq, nullptr, g.d_first, gf, accumulate ? 1 : 0, 2);
     return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
 }
 

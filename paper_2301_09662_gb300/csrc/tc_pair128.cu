@@ -95,23 +95,24 @@ __device__ __forceinline__ void products(uint32_t lane_addr, uint32_t d2, int hh
         for (int jj = 0; jj < 8; jj++) {
             const uint32_t ox = part ? x1[jj] : x0[jj], oy = part ? y1[jj] : y0[jj];
             const uint32_t sx = part ? x0[jj] : x1[jj], sy = part ? y0[jj] : y1[jj];
-            const float gx = __shfl_xor_sync(0xffffffffu, __uint_as_float(sx), 16);
-            const float gy = __shfl_xor_sync(0xffffffffu, __uint_as_float(sy), 16);
-            const float o1 = __uint_as_float(ox), o2 = __uint_as_float(oy);
-            const float xr = part ? gx : o1, xi = part ? o1 : gx;
-            const float yr = part ? gy : o2, yi = part ? o2 : gy;
+            // (a, b) = (own, partner's) parts of F_X, (c, d) of F_Y: (Re, Im) on part-0 lanes,
+            // (Im, Re) on part-1 lanes.  XX, YY and Re XY are symmetric in that swap; Im XY =
+            // b c - a d on part-0 lanes and its negative on part-1 lanes, fixed at the end.
+            const float b = __shfl_xor_sync(0xffffffffu, __uint_as_float(sx), 16);
+            const float d = __shfl_xor_sync(0xffffffffu, __uint_as_float(sy), 16);
+            const float a = __uint_as_float(ox), c = __uint_as_float(oy);
             if constexpr (REG) {
-                float4 &a = acc[8 * half + jj];
-                a.x = fmaf(xr, xr, fmaf(xi, xi, a.x));
-                a.y = fmaf(yr, yr, fmaf(yi, yi, a.y));
-                a.z = fmaf(xr, yr, fmaf(xi, yi, a.z));
-                a.w = fmaf(xi, yr, fmaf(-xr, yi, a.w));
+                float4 &q = acc[8 * half + jj];
+                q.x = fmaf(a, a, fmaf(b, b, q.x));
+                q.y = fmaf(c, c, fmaf(d, d, q.y));
+                q.z = fmaf(a, c, fmaf(b, d, q.z));
+                q.w = fmaf(b, c, fmaf(-a, d, q.w));
             } else {
                 uint32_t *a4 = s + 4 * jj;
-                a4[0] = __float_as_uint(fmaf(xr, xr, fmaf(xi, xi, __uint_as_float(a4[0]))));
-                a4[1] = __float_as_uint(fmaf(yr, yr, fmaf(yi, yi, __uint_as_float(a4[1]))));
-                a4[2] = __float_as_uint(fmaf(xr, yr, fmaf(xi, yi, __uint_as_float(a4[2]))));
-                a4[3] = __float_as_uint(fmaf(xi, yr, fmaf(-xr, yi, __uint_as_float(a4[3]))));
+                a4[0] = __float_as_uint(fmaf(a, a, fmaf(b, b, __uint_as_float(a4[0]))));
+                a4[1] = __float_as_uint(fmaf(c, c, fmaf(d, d, __uint_as_float(a4[1]))));
+                a4[2] = __float_as_uint(fmaf(a, c, fmaf(b, d, __uint_as_float(a4[2]))));
+                a4[3] = __float_as_uint(fmaf(b, c, fmaf(-a, d, __uint_as_float(a4[3]))));
             }
         }
         if constexpr (!REG) {
@@ -506,6 +507,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         // ---- partial images of both classes (undo the FP16 scale exactly)
         tc::fence_after_sync();
         const float inv = 1.f / (scale * scale);
+        const float inv_im = part ? -inv : inv;        // Im XY was summed with the lane's part sign
         const int my = 16 * (warp & 3) + (lane & 15);
         float4 *dst0 = reinterpret_cast<float4 *>(partial) +
                        (static_cast<size_t>(tau) * n_items_out + ci * 4 + hx) * (64 * 64);
@@ -514,7 +516,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
 #pragma unroll
         for (int j = 0; j < 16; j++) {
             const int mx = 32 * hp + 16 * part + j;
-            dst0[my * 64 + mx] = make_float4(acc0[j].x * inv, acc0[j].y * inv, acc0[j].z * inv, acc0[j].w * inv);
+            dst0[my * 64 + mx] = make_float4(acc0[j].x * inv, acc0[j].y * inv, acc0[j].z * inv, acc0[j].w * inv_im);
         }
 #pragma unroll
         for (int half = 0; half < 2; half++) {
@@ -527,7 +529,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 const int mx = 32 * hp + 16 * part + 8 * half + jj;
                 dst1[my * 64 + mx] = make_float4(__uint_as_float(s[4 * jj]) * inv, __uint_as_float(s[4 * jj + 1]) * inv,
                                                  __uint_as_float(s[4 * jj + 2]) * inv,
-                                                 __uint_as_float(s[4 * jj + 3]) * inv);
+                                                 __uint_as_float(s[4 * jj + 3]) * inv_im);
             }
         }
     }

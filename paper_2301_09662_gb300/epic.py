@@ -57,7 +57,7 @@ EPIC_SEARCH_DIAG_WITHHOLD_TMA = 1 << 12
 PRODUCTS = ("XX", "YY", "XY", "YX")
 
 #: every symbol include/epic.h declares
-EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_autotune", "epic_solve_gains", "epic_image_series_ex", "epic_image_host", "epic_out_floats", "epic_status",
+EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_image_efield", "epic_efield_floats", "epic_autotune", "epic_solve_gains", "epic_image_series_ex", "epic_image_host", "epic_out_floats", "epic_status",
            "epic_set_profiling", "epic_stage_times", "epic_image_static", "epic_image_series", "epic_destroy",
            "epic_strerror", "epic_search_plan", "epic_search_info", "epic_dedisperse", "epic_single_pulse",
            "epic_search_status", "epic_search_destroy")
@@ -97,6 +97,10 @@ def load():
     L.epic_solve_gains.restype = i
     L.epic_image_series_ex.argtypes = [vp, vp, vp, vp, i, i, vp, vp]
     L.epic_image_series_ex.restype = i
+    L.epic_image_efield.argtypes = [vp, vp, vp, i, vp, vp]
+    L.epic_image_efield.restype = i
+    L.epic_efield_floats.argtypes = [vp]
+    L.epic_efield_floats.restype = ctypes.c_size_t
     L.epic_out_floats.argtypes = [vp]
     L.epic_out_floats.restype = ctypes.c_size_t
     L.epic_status.argtypes = [vp]
@@ -233,6 +237,23 @@ class Plan:
             rc = load().epic_image_ex(self._h, v.data_ptr(), g, delays.data_ptr(), int(v.shape[0]), out.data_ptr(),
                                       self._stream(stream))
             _check(rc, "epic_image_ex")
+        return out
+
+    def image_efield(self, v, gains=None, out=None, stream=None):
+        """E-field images of every sample (epic_image_efield): a complex64
+        device tensor [T][epic_efield_floats/2], per sample the channels packed,
+        each [P][N][N] fft-shifted."""
+        import torch
+        self._check_inputs(v, gains, device=True)
+        T = int(v.shape[0])
+        per = int(load().epic_efield_floats(self._h)) // 2
+        if out is None:
+            out = torch.empty((T, per), dtype=torch.complex64, device=v.device)
+        elif out.dtype != torch.complex64 or out.numel() != T * per or not out.is_contiguous():
+            raise ValueError("out must be a contiguous complex64 tensor of T x epic_efield_floats/2 elements")
+        rc = load().epic_image_efield(self._h, v.data_ptr(), gains.data_ptr() if gains is not None else None, T,
+                                      out.data_ptr(), self._stream(stream))
+        _check(rc, "epic_image_efield")
         return out
 
     def autotune(self, n_spectra, stream=None):

@@ -53,10 +53,9 @@ def _fringe_workload(f, N, cells, P):
 
 
 @pytest.mark.parametrize("f,N,cells", HAND)
-@pytest.mark.parametrize("P,precision", [(1, epic.EPIC_FP32), (2, epic.EPIC_FP32), (2, epic.EPIC_TC_SPLIT_FP16)])
+@pytest.mark.parametrize("P,precision", [(1, epic.EPIC_FP32), (2, epic.EPIC_FP32), (1, epic.EPIC_TC_SPLIT_FP16),
+                                         (2, epic.EPIC_TC_SPLIT_FP16)])
 def test_cell_map_hand_worked_quarter_field_peak(f, N, cells, P, precision):
-    if precision != epic.EPIC_FP32 and N == 32:
-        pytest.skip("the tensor form needs a folded side of 64")
     wl, s2 = _fringe_workload(f, N, cells, P)
     A = ANT.shape[0]
     gpu, plan = run_gpu(wl, precision=precision)
@@ -78,6 +77,7 @@ FULL_RANGE_CASES = [
     (256, 2, 2, 9, 128, 5, epic.EPIC_TC_SPLIT_FP16, 0),
     (256, 2, 2, 9, 128, 5, epic.EPIC_TC_SPLIT_FP16, epic.EPIC_KERNEL_TAPER),
     (64, 1, 2, 9, 32, 3, epic.EPIC_FP32, 0),
+    (64, 1, 2, 9, 32, 3, epic.EPIC_TC_SPLIT_FP16, 0),
     (100, 2, 2, 9, 96, 5, epic.EPIC_FP32, 0),
 ]
 

@@ -204,3 +204,37 @@ def test_pair_kernel_series_and_delays():
                              wl.v[4 * i:4 * i + 4], wl.gains, {})
         assert peak_rel_err(imgs[i], oracle.workload_image(sub), wl.grid_n, 2).max() < SPLIT_TOL
     assert peak_rel_err(withd, oracle.workload_image(wl, delays=tau), wl.grid_n, 2).max() < SPLIT_TOL
+
+
+# ---- the precision form on the tiny configuration's shapes: single polarisation and grid side 32
+# (side 32 is transformed zero-padded to 64 points; its even frequencies are the 32-point image)
+
+def _cmp_p(wl, precision, flags=0):
+    gpu, p = run_gpu(wl, precision=precision, flags=flags)
+    p.close()
+    return peak_rel_err(gpu, oracle.workload_image(wl, flags=flags), wl.grid_n, wl.n_pol)
+
+
+@pytest.mark.parametrize("precision,tol", [(epic.EPIC_TC_SPLIT_FP16, SPLIT_TOL), (epic.EPIC_TC_FP16, FP16_TOL),
+                                           (epic.EPIC_TC_SPLIT_BF16, BF16_TOL)])
+def test_tensor_form_on_the_tiny_workload(precision, tol):
+    """16 single-pol antennas, 4 channels at 40-41 MHz, 3 x 3 kernel, 32 x 32 grid,
+    64 spectra: the tensor form against both oracles (O1 direct, O2 FX)."""
+    wl = synth.tiny()
+    gpu, p = run_gpu(wl, precision=precision)
+    p.close()
+    assert peak_rel_err(gpu, oracle.workload_image(wl), wl.grid_n, 1).max() < tol
+    assert peak_rel_err(gpu, oracle.workload_image(wl, form="fx"), wl.grid_n, 1).max() < tol
+
+
+@pytest.mark.parametrize("A,P,C,T,N,K", [(64, 1, 2, 9, 128, 5), (100, 1, 2, 7, 64, 3), (40, 2, 2, 6, 32, 3),
+                                         (24, 1, 3, 5, 32, 1), (64, 1, 1, 4, 256, 5)])
+def test_tensor_single_polarisation_and_side_32(A, P, C, T, N, K):
+    wl = synth.random_small(A=A, P=P, C=C, T=T, N=N, K=K, seed=700 + A + N)
+    assert _cmp_p(wl, epic.EPIC_TC_SPLIT_FP16).max() < SPLIT_TOL
+
+
+def test_tensor_side_32_with_flags_and_taper():
+    wl = synth.random_small(A=40, P=2, C=2, T=6, N=32, K=3, seed=720)
+    for flags in (epic.EPIC_MEAN, epic.EPIC_NO_AUTOSUB, epic.EPIC_KERNEL_TAPER):
+        assert _cmp_p(wl, epic.EPIC_TC_SPLIT_FP16, flags=flags).max() < SPLIT_TOL
