@@ -5,6 +5,10 @@ One step = one integration imaged by one epic_image call: every channel,
 polarisation and time sample of the workload (unpack, calibrate, grid,
 transform, products, time sum, autocorrelation subtraction).  The metric is
 imaged spectra per second, spectra = channels x time samples x polarisations.
+The headline form is the split-FP16 tensor-core form (both 64-point DFT stages
+on tcgen05, literal gridding, within 1e-5 of the FP64 oracle); the plain FP32
+form and the other forms are timed beside it ("variants"), and the uneven-band
+and dense-array workloads have their own lines ("workloads").
 
 Default workload: the LWA-station-like configuration (256 dual-pol antennas,
 64 channels of 25 kHz from 60 MHz, 1000 spectra per integration, 5x5 kernel,
@@ -38,22 +42,13 @@ FP32_LANES_PER_SM = 128
 SERIES_SPI = 40                      # spectra per image of the time-resolved variant (1.6 ms at 25 k spectra/s)
 L2_FLUSH_BYTES = 256 << 20
 
-# DRAM traffic of one launch of the dominant kernel from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload, with the
-# hash of the kernel source it was taken on; ignored once the source changes.
-# lwa: one full 64-channel launch captured: 35 249 664 B read (the 32.8 MB ci4
-# input plus tables) + 74 313 728 B written (time-chunk partial sums that spill
-# out of L2 before the epilogue reads them).
-NCU_TRAFFIC = {"lwa": (109_563_392, "1dd260f9e71ea38a")}
-# What the same capture shows about the kernel's limits: shared-memory wavefronts
-# per SM cycle (against 1 per cycle, 128 B/clk) and issue activity.  Neither is
-# saturated: with 8 warps per SM (the register transforms take ~226 registers a
-# thread) the kernel is bound by latency; a phase probe puts 45 % of its time in
-# the gather gridding, which runs near 0.8 wavefronts per cycle.
-NCU_LIMITER = {"lwa": ({"unit": "shared-memory wavefronts per SM cycle", "achieved": 0.67, "peak": 1.0,
-                        "wavefronts_per_launch": 1_241_332_752, "issue_active_pct": 45.1,
-                        "warp_instructions_per_launch": 3_201_891_968},
-                       "1dd260f9e71ea38a")}
+# DRAM traffic of one launch of a timed kernel from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (workload, form),
+# with the hash of the kernel source it was taken on; ignored (null) once the
+# source changes.  Filled in from the committed profiles/ summaries.
+NCU_TRAFFIC = {}
+# What the same capture shows about the kernel's limits (same keys and hashes).
+NCU_LIMITER = {}
 
 
 def parse():
@@ -63,8 +58,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["lwa", "tiny", "uneven", "dense"], default="lwa")
-    ap.add_argument("--precision", choices=["fp32", "tc_split_fp16", "tc_fp16", "tc_split_bf16"], default="fp32",
-                    help="arithmetic form of the timed plan (default: the FP32 form)")
+    ap.add_argument("--precision", choices=["fp32", "tc_split_fp16", "tc_fp16", "tc_split_bf16"],
+                    default="tc_split_fp16",
+                    help="arithmetic form of the timed plan (default: the split-FP16 tensor-core form)")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the uneven-band and dense-array lines")
+    ap.add_argument("--no-peaks", action="store_true", help="skip measuring the pipes' peak rates")
     ap.add_argument("--taper", action="store_true", help="apply the kernel as an image-domain taper")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
@@ -108,19 +106,45 @@ def fp32_flops_per_spectrum(A, K, N):
     return 8.0 * A * K * K + 5.0 * N * math.log2(N) * (N / 2 + N) + 8.0 * N * N
 
 
-def kernel_source_hash():
-    """Hash of the dominant kernel's device code (the register transforms, the
-    transform_products function and the fp32_reg64_kernel template, and the
-    64-point transform headers they include)."""
+def kernel_source_hash(form):
+    """Hash of the device code of the imaging kernel a form runs at grid side
+    128: the FP32 register kernel (fp32_reg64.cu up to its large-side part, and
+    the transform headers) or the tensor pair kernel (tc_pair128.cu and the
+    tensor helpers)."""
     csrc = os.path.join(ROOT, "paper_2301_09662_gb300", "csrc")
-    src = open(os.path.join(csrc, "fp32_reg64.cu")).read()
-    start = src.index("// Register transforms of the folded side M")
-    end = src.index("// Large grid sides: the folded grids", start)
-    h = hashlib.sha256(src[start:end].encode())
-    for f in ("fft64.cuh", "dft_small.cuh"):
+    if form == "fp32":
+        src = open(os.path.join(csrc, "fp32_reg64.cu")).read()
+        start = src.index("// Register transforms of the folded side M")
+        end = src.index("// Large grid sides: the folded grids", start)
+        h = hashlib.sha256(src[start:end].encode())
+        files = ("fft64.cuh", "dft_small.cuh")
+    else:
+        h = hashlib.sha256()
+        files = ("tc_pair128.cu", "tc_common.cuh", "tc_ptx.cuh", "dft_small.cuh")
+    for f in files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def ncu_record(table, workload, form):
+    rec = table.get((workload, form))
+    return rec[0] if rec and rec[1] == kernel_source_hash(form) else None
+
+
+def measure_pipe_peaks():
+    """Peak rates of the pipes the kernels use, measured here by epic_measure_peak
+    (best of three ~100 ms launches each; TFLOP/s, 2 per multiply-add)."""
+    from paper_2301_09662_gb300 import epic
+    out = {}
+    for k in ("fp32", "fp32x2", "fp64", "fp16_tc"):
+        try:
+            out[k] = epic.measure_peak(k, 100)
+        except Exception as e:       # a probe that fails is reported, not fatal
+            out[k] = f"failed: {e}"
+    out["how"] = ("epic_measure_peak: independent FMA chains (8 per thread, 4 blocks of 512 threads per SM) or "
+                  "back-to-back 128 x 256 x 16 FP16 tcgen05 MMAs (one CTA per SM), ~100 ms launches, best of 3")
+    return out
 
 
 def measured_peaks():
@@ -290,17 +314,54 @@ def tensor_roofline(wl, form, img_ms, peaks, pair=True):
             "peak_source": "MEASURED_PEAKS bf16_tflops burst (dense FP16 rate equals BF16)"}
 
 
+def fp32_roofline(wl, stages, peaks, sm_count):
+    """The FP32 form's dominant imaging launch against the FP32 FMA peak derived
+    from unit counts (alu bound): the method's algorithmic FLOPs of that grid
+    side's channels over the launch's event-timed duration."""
+    image_stage = max((n for n in stages if n.startswith("image[")), key=lambda n: stages[n])
+    side = int(image_stage[8:-1])
+    flops = sum(fp32_flops_per_spectrum(wl.A, wl.K, int(n)) for n in wl.grid_n if int(n) == side) * wl.T * wl.n_pol
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    ms = stages[image_stage]
+    return {"bound": "alu", "kernel": f"FP32 imaging kernel {image_stage}", "achieved": flops / (ms / 1e3) / 1e12,
+            "peak": peak, "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / peak, "traffic": None,
+            "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
+                           f"(max SM clock of MEASURED_PEAKS)",
+            "flops_per_launch": flops, "ms_per_launch": ms}
+
+
+def _time_steps(call, flush, args, stream):
+    """Device time per step (CUDA events on the launching stream, L2 flushed between steps)."""
+    import torch
+    for _ in range(max(args.warmup, 1)):
+        call()
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        call()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return sum(ms) / len(ms)
+
+
 def time_variants(wl, v, g, out, flush, args, stream):
     """Other forms of the same integration, timed the same way (device events
-    per step, L2 flushed between steps): the taper and tensor forms (same output
-    up to rounding), delay correction, per-antenna kernels and time-resolved
-    Stokes images."""
+    per step, L2 flushed between steps): the plain FP32 form, the taper and
+    tensor forms (same output up to rounding), delay correction, per-antenna
+    kernels, time-resolved Stokes images and the E-field images."""
     import numpy as np
     import torch
 
     from paper_2301_09662_gb300 import epic
     res = {}
-    forms = {"kernel_taper": dict(flags=epic.EPIC_KERNEL_TAPER),
+    forms = {"fp32": dict(),
+             "kernel_taper": dict(flags=epic.EPIC_KERNEL_TAPER),
              "tc_split_fp16": dict(precision=epic.EPIC_TC_SPLIT_FP16),
              "tc_fp16": dict(precision=epic.EPIC_TC_FP16),
              "tc_split_bf16": dict(precision=epic.EPIC_TC_SPLIT_BF16),
@@ -308,8 +369,11 @@ def time_variants(wl, v, g, out, flush, args, stream):
              "tc_split_fp16_one_class": dict(precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_DIAG_NO_PAIR),
              "fp32_delays": dict(),
              "fp32_antenna_kernels": dict(flags=epic.EPIC_ANTENNA_KERNELS),
-             "fp32_series_stokes": dict(flags=epic.EPIC_STOKES)}
-    notes = {"kernel_taper": "FP32; image-domain |W^|^2 taper with point gridding (exact for one shared kernel)",
+             "fp32_series_stokes": dict(flags=epic.EPIC_STOKES),
+             "fp32_efield": dict()}
+    notes = {"fp32": "plain FP32 form: gather gridding, register 64-point FFTs on packed FP32 pairs, products "
+                     "summed in registers (literal gridding)",
+             "kernel_taper": "FP32; image-domain |W^|^2 taper with point gridding (exact for one shared kernel)",
              "tc_split_fp16": "row and column DFTs on tcgen05, FP16 hi+lo operands (3 MMAs per k-block), "
                               "FP32 accumulate in TMEM; at grid side 128 two pixel classes per CTA share one "
                               "gather gridding and one row stage",
@@ -324,7 +388,9 @@ def time_variants(wl, v, g, out, flush, args, stream):
                                      "width and a small phase gradient); auto term sum_a A_a |W_a^|^2",
              "fp32_series_stokes": f"FP32 literal form, epic_image_series: one Stokes (I, Q, U, V) image per "
                                    f"{SERIES_SPI} spectra ({wl.T // SERIES_SPI if wl.T % SERIES_SPI == 0 else 0} "
-                                   f"images per integration)"}
+                                   f"images per integration)",
+             "fp32_efield": "epic_image_efield: the complex E-field image of every sample, channel and "
+                            "polarisation (FP32 register kernel, no products), written to HBM"}
     import copy
 
     from paper_2301_09662_gb300 import synth
@@ -332,54 +398,120 @@ def time_variants(wl, v, g, out, flush, args, stream):
     wl_ak = copy.copy(wl)
     wl_ak.kernel = synth.antenna_kernels(wl.A, wl.K, np.random.default_rng(20230120))
     peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     for name, kw in forms.items():
         series = name == "fp32_series_stokes"
+        efield = name == "fp32_efield"
         if series and wl.T % SERIES_SPI:
             res[name] = {"unavailable": f"{wl.T} spectra are not a multiple of {SERIES_SPI}"}
             continue
         try:
             p = epic.Plan.from_workload(wl_ak if name == "fp32_antenna_kernels" else wl, **kw)
-            if not args.no_autotune and not series:
+            if not args.no_autotune and not series and not efield:
                 p.autotune(wl.T)
         except epic.EpicError as e:
             res[name] = {"unavailable": str(e)}
             continue
-        p.set_profiling(True)
-        o = torch.empty((wl.T // SERIES_SPI, out.numel()), dtype=out.dtype, device=out.device) if series \
-            else torch.empty_like(out)
+        p.set_profiling(not (series or efield))
+        if series:
+            o = torch.empty((wl.T // SERIES_SPI, out.numel()), dtype=out.dtype, device=out.device)
+        elif efield:
+            o = torch.empty((wl.T, int(epic.load().epic_efield_floats(p.handle)) // 2), dtype=torch.complex64,
+                            device=out.device)
+        else:
+            o = torch.empty_like(out)
         dl = delays if name == "fp32_delays" else None
 
         def call():
             if series:
                 p.image_series(v, SERIES_SPI, g, out=o)
+            elif efield:
+                p.image_efield(v, g, out=o)
             else:
                 p.image(v, g, out=o, delays=dl)
 
-        for _ in range(max(args.warmup, 1)):
-            call()
-        torch.cuda.synchronize()
-        ms = []
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            call()
-            b.record(stream)
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
-        stages = None if series else p.stage_times()   # epic_image_series runs unprofiled
-        step = sum(ms) / len(ms)
+        step = _time_steps(call, flush, args, stream)
+        stages = None if (series or efield) else p.stage_times()   # series and E-field run unprofiled
         entry = {"value": wl.spectra / (step / 1e3), "unit": UNIT, "ms_per_step": step, "note": notes[name],
                  "stages_ms_last": stages}
         if name.startswith("tc_") and stages:
-            img = max((v for k, v in stages.items() if k.startswith("image[")), default=None)
+            img = max((x for k, x in stages.items() if k.startswith("image[")), default=None)
             if img:
                 entry["roofline"] = tensor_roofline(wl, name.replace("_taper", "").replace("_one_class", ""), img,
                                                     peaks, pair=name != "tc_split_fp16_one_class")
+        if name == "fp32" and stages:
+            entry["roofline"] = fp32_roofline(wl, stages, peaks, sm_count)
+            entry["roofline"]["traffic"] = ncu_record(NCU_TRAFFIC, "lwa", "fp32")
+            entry["roofline"]["measured_limiter"] = ncu_record(NCU_LIMITER, "lwa", "fp32")
+        if efield:
+            out_bytes = o.numel() * 8
+            in_bytes = v.numel() + (g.numel() * 8 if g is not None else 0)
+            hbm = float(peaks.get("hbm_gbs", 6658.0))
+            entry["hbm"] = {"bound": "hbm", "algorithmic_bytes": out_bytes + in_bytes,
+                            "achieved": (out_bytes + in_bytes) / (step / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                            "frac": (out_bytes + in_bytes) / (step / 1e3) / 1e9 / hbm,
+                            "peak_source": "MEASURED_PEAKS hbm_gbs"}
         res[name] = entry
         p.close()
+        del o
     return res
+
+
+def time_workloads(flush, args, stream):
+    """The uneven-band (192 channels, grid sides 64/96/128) and dense-array
+    (2048 antennas, 256 channels, grid side 512) integrations: FP32 and
+    split-FP16 tensor forms (and the FP32 taper on the dense array), each with
+    its dominant kernel's roofline."""
+    import torch
+
+    from paper_2301_09662_gb300 import epic, synth
+    peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    res = {}
+    for wname, fn in (("uneven", synth.uneven), ("dense", synth.dense)):
+        wl = fn()
+        v = torch.from_numpy(wl.v).cuda()
+        g = torch.from_numpy(wl.gains).cuda()
+        forms = {"fp32": dict(), "tc_split_fp16": dict(precision=epic.EPIC_TC_SPLIT_FP16)}
+        if wname == "dense":
+            forms["fp32_taper"] = dict(flags=epic.EPIC_KERNEL_TAPER)
+        lines = {}
+        for fname, kw in forms.items():
+            try:
+                p = epic.Plan.from_workload(wl, **kw)
+                if not args.no_autotune:
+                    p.autotune(wl.T)
+            except epic.EpicError as e:
+                lines[fname] = {"unavailable": str(e)}
+                continue
+            p.set_profiling(True)
+            o = torch.empty(p.out_floats // 2, dtype=torch.complex64, device="cuda")
+            step = _time_steps(lambda: p.image(v, g, out=o), flush, args, stream)
+            stages = p.stage_times()
+            entry = {"value": wl.spectra / (step / 1e3), "unit": UNIT, "ms_per_step": step, "stages_ms_last": stages}
+            if fname.startswith("tc_"):
+                img_stage = max((k for k in stages if k.startswith("image[")), key=lambda k: stages[k])
+                side = int(img_stage[8:-1])
+                sub = copy_with_side(wl, side)
+                entry["roofline"] = tensor_roofline(sub, fname, stages[img_stage], peaks)
+                entry["roofline"]["kernel"] = f"tensor-core imaging launch {img_stage}"
+            else:
+                entry["roofline"] = fp32_roofline(wl, stages, peaks, sm_count)
+            lines[fname] = entry
+            p.close()
+            del o
+        res[wname] = {"config": describe(wl, wname), "forms": lines}
+        del v, g
+        torch.cuda.empty_cache()
+    return res
+
+
+def copy_with_side(wl, side):
+    """The workload restricted to the channels of one grid side (for a per-launch roofline)."""
+    import copy
+    sub = copy.copy(wl)
+    sub.grid_n = wl.grid_n[wl.grid_n == side]
+    return sub
 
 
 def time_calibration(plan, wl, v, flush, args, stream):
@@ -571,45 +703,33 @@ def run_ours(args):
         e2e = run_e2e(plan, wl, args, world, barrier, spectra)
 
 
-    # roofline of the dominant kernel (the fused imaging kernel)
+    # roofline of the dominant kernel (the fused imaging launch)
     peaks = measured_peaks()
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    # the dominant kernel: the imaging launch with the largest device time
+    stages_avg = {n: stage_sum[n] / args.steps for n in names}
     image_stage = max((n for n in names if n.startswith("image[")), key=lambda n: stage_sum[n])
-    flops = sum(fp32_flops_per_spectrum(wl.A, wl.K, int(n)) * wl.T * wl.n_pol for n in wl.grid_n
-                if int(n) == int(image_stage[8:-1]))
-    img_ms = stage_sum[image_stage] / args.steps
-    achieved = flops / (img_ms / 1e3) / 1e12
-    traffic = None
-    rec = NCU_TRAFFIC.get(args.workload) if (args.precision == "fp32" and not args.taper
-                                              and args.channels is None) else None
-    limiter = None
-    if rec and rec[1] == kernel_source_hash():
-        traffic = rec[0]
-        lim = NCU_LIMITER.get(args.workload)
-        if lim and lim[1] == rec[1]:
-            limiter = lim[0]
-
+    img_ms = stages_avg[image_stage]
     config = describe(wl, args.workload)
     config["launch_shapes"] = "cost model" if args.no_autotune else "measured per channel group (epic_autotune)"
     config["form"] = args.precision + (" + image-domain kernel taper" if args.taper else " (literal gridding)")
-    roofline = {"bound": "alu", "kernel": f"FP32 imaging kernel {image_stage}", "achieved": achieved,
-                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
-                               f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS)",
-                "flops_per_launch": flops, "ms_per_launch": img_ms, "measured_limiter": limiter}
-    if args.precision != "fp32":
+    if args.precision == "fp32":
+        roofline = fp32_roofline(wl, stages_avg, peaks, sm_count)
+    else:
         roofline = tensor_roofline(wl, args.precision, img_ms, peaks)
         roofline["kernel"] = f"tensor-core imaging kernel {image_stage}"
+    if args.channels is None and not args.taper:
+        roofline["traffic"] = ncu_record(NCU_TRAFFIC, args.workload, args.precision)
+        roofline["measured_limiter"] = ncu_record(NCU_LIMITER, args.workload, args.precision)
+    dtype = "f32" if args.precision == "fp32" else \
+        {"tc_split_fp16": "f16 hi+lo operands, f32 accumulate", "tc_fp16": "f16 operands, f32 accumulate",
+         "tc_split_bf16": "bf16 hi+lo operands, f32 accumulate"}[args.precision]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded LWA-like layout, sky, noise, gains)",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded LWA-like layout, sky, noise, gains)",
         "config": config,
         "roofline": roofline,
-        "stages_ms": {n: s / args.steps for n, s in stage_sum.items()},
+        "stages_ms": stages_avg,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": launches,
@@ -618,6 +738,10 @@ def run_ours(args):
         line["variants"] = time_variants(wl, v, g, out, flush, args, stream)
         line["search"] = time_search(flush, args, stream)
         line["calibration"] = time_calibration(plan, wl, v, flush, args, stream)
+    if not args.no_workloads and world == 1 and args.channels is None and args.workload == "lwa":
+        line["workloads"] = time_workloads(flush, args, stream)
+    if not args.no_peaks and world == 1:
+        line["peaks_measured"] = measure_pipe_peaks()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     if rank == 0:

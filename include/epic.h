@@ -483,6 +483,21 @@ int epic_search_status(epic_search_t s);
 
 void epic_search_destroy(epic_search_t s);
 
+/*
+ * epic_measure_peak -- measure the peak rate of one arithmetic pipe on the
+ * current device, for the roofline fractions of the benchmark; the paper has
+ * no counterpart.  what: EPIC_PEAK_FP32 (FP32 FMA), EPIC_PEAK_FP32X2 (FP32 FMA
+ * on packed pairs, fma.rn.f32x2), EPIC_PEAK_FP64 (FP64 FMA), EPIC_PEAK_FP16_TC
+ * (dense FP16 tcgen05 MMA, 128 x 256 x 16, FP32 accumulate).  Each launch runs
+ * long chains of independent multiply-adds (or back-to-back MMAs, one CTA per
+ * SM) for about `ms` milliseconds (1 .. 10000); *tflops receives the best of
+ * three launches in TFLOP/s (2 per multiply-add).  Synchronises the stream;
+ * allocates 4 KB of device memory for the duration of the call.
+ * EPIC_ERR_TIMEOUT if the tensor probe's bounded wait ran out.
+ */
+enum { EPIC_PEAK_FP32 = 0, EPIC_PEAK_FP32X2 = 1, EPIC_PEAK_FP64 = 2, EPIC_PEAK_FP16_TC = 3 };
+int epic_measure_peak(int what, int ms, double *tflops, void *cuda_stream);
+
 /* Static, human-readable text for an EPIC_* code. */
 const char *epic_strerror(int code);
 

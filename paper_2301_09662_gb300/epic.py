@@ -57,7 +57,7 @@ EPIC_SEARCH_DIAG_WITHHOLD_TMA = 1 << 12
 PRODUCTS = ("XX", "YY", "XY", "YX")
 
 #: every symbol include/epic.h declares
-EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_image_efield", "epic_efield_floats", "epic_autotune", "epic_solve_gains", "epic_image_series_ex", "epic_image_host", "epic_out_floats", "epic_status",
+EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_image_efield", "epic_efield_floats", "epic_measure_peak", "epic_autotune", "epic_solve_gains", "epic_image_series_ex", "epic_image_host", "epic_out_floats", "epic_status",
            "epic_set_profiling", "epic_stage_times", "epic_image_static", "epic_image_series", "epic_destroy",
            "epic_strerror", "epic_search_plan", "epic_search_info", "epic_dedisperse", "epic_single_pulse",
            "epic_search_status", "epic_search_destroy")
@@ -101,6 +101,8 @@ def load():
     L.epic_image_efield.restype = i
     L.epic_efield_floats.argtypes = [vp]
     L.epic_efield_floats.restype = ctypes.c_size_t
+    L.epic_measure_peak.argtypes = [i, i, ctypes.POINTER(ctypes.c_double), vp]
+    L.epic_measure_peak.restype = i
     L.epic_out_floats.argtypes = [vp]
     L.epic_out_floats.restype = ctypes.c_size_t
     L.epic_status.argtypes = [vp]
@@ -374,6 +376,18 @@ def image_static(ant_xy, n_pol, kernel, grid_n, freq_hz, du, v, gains=None, flag
                              int(v.shape[0]), int(flags), out.data_ptr(), ctypes.c_void_p(s.cuda_stream))
     _check(rc, "epic_image_static")
     return out
+
+
+PEAKS = {"fp32": 0, "fp32x2": 1, "fp64": 2, "fp16_tc": 3}
+
+
+def measure_peak(what: str, ms: int = 100, stream=None) -> float:
+    """Measured peak rate (TFLOP/s) of one arithmetic pipe (epic_measure_peak):
+    'fp32', 'fp32x2' (packed FMA pairs), 'fp64' or 'fp16_tc' (dense tcgen05)."""
+    out = ctypes.c_double()
+    _check(load().epic_measure_peak(PEAKS[what], int(ms), ctypes.byref(out), _stream_handle(stream)),
+           "epic_measure_peak")
+    return out.value
 
 
 def make_plan_raw(ant_xy, n_pol, kernel, grid_n, freq_hz, du=0.5, max_spectra=16, precision=EPIC_FP32,
