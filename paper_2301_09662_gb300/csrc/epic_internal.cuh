@@ -15,6 +15,8 @@ constexpr int kThreads = 256;          // threads per CTA of the imaging kernels
 constexpr int kMaxTau = 64;            // most time chunks one channel item is split into
 constexpr int kMaxK = 15;
 constexpr int kMaxAP = 4096;           // n_ant * n_pol handled by one CTA's staging
+constexpr int kPairHelpers = 3;        // pair kernel (tc_pair128.cu): gridding-only warps beside its 8 TMEM warps
+constexpr int kPairGatherWarps = 8 + kPairHelpers;
 
 // How one grid side N is imaged by the FP32 kernel: the sky is split into
 // Q1 x Q1 pixel classes l = (Q1 m + h) and each CTA owns one class, so it grids

@@ -35,14 +35,19 @@
 // time sums in registers.  Shared memory: X, G16 and H16 (64 KB each, hi and
 // lo), the channel's gather lists, calibrated voltages, gains, tap pairs.
 //
-// Warps 0-7 (SIMT), iteration t: wait for the row stage of t, D1 -> H16 (hy 0)
-// and arrive on bar_h; unpack sample t+1 and grid the first half of its lists;
-// wait for the column stage of (t, 0), D1 -> H16 (hy 1) and arrive on bar_h;
-// grid the second half and arrive on bar_g; products of (t, 0); wait for the
-// column stage of (t, 1) and add its products.  Warp 8 issues, in order, the
+// Warps 0-7 (TMEM warps), iteration t: wait for the row stage of t, D1 -> H16
+// (hy 0) and arrive on bar_h; unpack sample t+1 and grid the first half of
+// their lists; wait for the column stage of (t, 0), D1 -> H16 (hy 1) and arrive
+// on bar_h; grid the second half and arrive on bar_g; products of (t, 0); wait
+// for the column stage of (t, 1) and add its products.  Warps 8-10 only grid:
+// after the row stage of t they take a larger share of sample t+1's lists (the
+// plan deals the lists so that each warp's work, conversions and products
+// included, is about equal) and arrive on bar_g.  Warp 11 issues, in order, the
 // row stage of t after bar_g, the column stage of (t, 0) after bar_h, that of
 // (t, 1) after the next bar_h, each committed to its own mbarrier.  Every wait
 // is bounded; a timeout is recorded in the plan's status word and stops the CTA.
+// Twelve warps cost no registers over nine: a scheduler holding three warps
+// already limits a thread to 168.
 #include <algorithm>
 
 #include "dft_small.cuh"
@@ -55,9 +60,13 @@ namespace {
 
 using namespace tcc;
 
-constexpr int kSimtP = kThreads;                 // warps 0-7
-constexpr int kPairThreads = kSimtP + 32;        // + the MMA warp
-constexpr int kBarP = 6;                         // named barrier of the SIMT warps
+constexpr int kTmemWarps = 8;                    // warps 0-7: grid, convert the row stage, form products
+constexpr int kGathW = kTmemWarps + kPairHelpers; // + warps that only grid
+constexpr int kSimtP = kTmemWarps * 32;          // threads that touch TMEM (bar_h arrivals)
+constexpr int kGath = kGathW * 32;               // threads that grid (bar_g arrivals, the named barrier)
+constexpr int kMmaWarp = kGathW;                 // the MMA-issuing warp
+constexpr int kPairThreads = (kGathW + 1) * 32;
+constexpr int kBarP = 6;                         // named barrier of the gridding warps
 constexpr uint32_t kColD1 = 0, kColD2a = 128, kColD2b = 256, kColAcc1 = 384;
 constexpr uint16_t kNone = 0xFFFFu;
 
@@ -123,8 +132,10 @@ __device__ __forceinline__ void products(uint32_t lane_addr, uint32_t d2, int hh
 }
 
 // Shared memory (dynamic, 1024-aligned): X, G16, H16 (each hi then lo), then
-// es [A*P], gp [A*P], tw2 [K (K + 1)] (float4), stage [(A*P + 3) / 4] (u32),
-// the channel's lists [words] (u16).
+// es [A*P], gp [A*P], tw2 [K (K + 1) + 1][8] (float4: eight interleaved copies,
+// lane l reads copy l mod 8, so the eight lanes of one 16-byte request never
+// share a bank group; the last slot is zero, for the lists' empty steps),
+// stage [(A*P + 3) / 4] (u32), the channel's lists [words] (u16).
 template <int VAR>
 __global__ void __launch_bounds__(kPairThreads, 1)
 tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
@@ -149,15 +160,17 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     float2 *es = reinterpret_cast<float2 *>(smem + 6 * kPart);
     float2 *gp = es + AP;
     float4 *tw2 = reinterpret_cast<float4 *>(gp + AP);
-    uint32_t *stage = reinterpret_cast<uint32_t *>(tw2 + K * (K + 1));
+    const int TPN = K * (K + 1);                             // the zero tap slot
+    uint32_t *stage = reinterpret_cast<uint32_t *>(tw2 + 8 * (TPN + 1));
     uint16_t *stab = reinterpret_cast<uint16_t *>(stage + APW);
     __shared__ __align__(8) uint64_t bar_x, bar_g, bar_h, bar_m1, bar_m2a, bar_m2b;
     __shared__ uint32_t tmem_slot;
-    __shared__ float red[kSimtP / 32];
+    __shared__ float red[kGathW];
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool simt = warp < 8;
+    const bool simt = warp < kGathW;             // a gridding warp (TMEM warps included)
+    const bool tmw = warp < kTmemWarps;
     const int n_pairs = gridDim.x / n_tau;                    // CTAs per time chunk: channels x 2
     const int item = blockIdx.x % n_pairs;
     const int tau = blockIdx.x / n_pairs;
@@ -171,7 +184,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     if (tid == 0) {
         abort_flag = 0;
         tc::mbar_init(&bar_x, 1);
-        tc::mbar_init(&bar_g, kSimtP);
+        tc::mbar_init(&bar_g, kGath);
         tc::mbar_init(&bar_h, kSimtP);
         tc::mbar_init(&bar_m1, 1);
         tc::mbar_init(&bar_m2a, 1);
@@ -188,7 +201,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     // ---- set-up: gains and taps with the class-x phase, the largest gain for the FP16 scale,
     // a zero G16, the channel's lists, the bytes of the first sample
     float gmax = 0.f;
-    for (int a = simt ? tid : A; a < A; a += kSimtP) {
+    for (int a = simt ? tid : A; a < A; a += kGath) {
         const short2 k = cells[static_cast<size_t>(c) * A + a];
         if (k.x < hk || k.x >= N - hk || k.y < hk || k.y >= N - hk) atomicOr(status, kStatusDevice);
         const float2 ph = twN[(k.x * hx) & (N - 1)];
@@ -200,22 +213,22 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         }
     }
     // tap pairs (w(dy, dxl), w(dy, dxl + 1)), zero outside the footprint row, with w_128^{dx hx}
-    for (int i = simt ? tid : K * (K + 1); i < K * (K + 1); i += kSimtP) {
-        const int dyi = i / (K + 1), j = i % (K + 1);
+    for (int i = simt ? tid : 8 * (TPN + 1); i < 8 * (TPN + 1); i += kGath) {
+        const int tp = i >> 3, dyi = tp / (K + 1), j = tp % (K + 1);
         float2 w[2];
         for (int u = 0; u < 2; u++) {
             const int dx = j - 1 + u;
-            w[u] = (dx >= 0 && dx < K) ? cmul(kern[dyi * K + dx], twN[((dx - hk) * hx) & (N - 1)])
-                                       : make_float2(0.f, 0.f);
+            w[u] = (tp < TPN && dx >= 0 && dx < K) ? cmul(kern[dyi * K + dx], twN[((dx - hk) * hx) & (N - 1)])
+                                                   : make_float2(0.f, 0.f);
         }
         tw2[i] = make_float4(w[0].x, w[0].y, w[1].x, w[1].y);
     }
-    for (int i = simt ? tid : 2 * static_cast<int>(kPart) / 16; i < 2 * static_cast<int>(kPart) / 16; i += kSimtP)
+    for (int i = simt ? tid : 2 * static_cast<int>(kPart) / 16; i < 2 * static_cast<int>(kPart) / 16; i += kGath)
         reinterpret_cast<uint4 *>(opG)[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int i = simt ? tid : my_chan.y; i < my_chan.y; i += kSimtP) stab[i] = __ldg(ptab + my_chan.x + i);
+    for (int i = simt ? tid : my_chan.y; i < my_chan.y; i += kGath) stab[i] = __ldg(ptab + my_chan.x + i);
     if (simt && t0 < t1) {
         const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(t0) * C + c) * AP);
-        for (int w = tid; w < APW; w += kSimtP) stage[w] = row[w];
+        for (int w = tid; w < APW; w += kGath) stage[w] = row[w];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
@@ -229,7 +242,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     if constexpr (!kBF16) {
         // |H| <= sum_a |e~_a| sum_taps |w| bounds both stages' operands: keep it below 2^13
         float gm = 0.f;
-        for (int w = 0; w < kSimtP / 32; w++) gm = fmaxf(gm, red[w]);
+        for (int w = 0; w < kGathW; w++) gm = fmaxf(gm, red[w]);
         float wsum = 0.f;
         for (int i = 0; i < KK; i++) wsum += sqrtf(kern[i].x * kern[i].x + kern[i].y * kern[i].y);
         const float bound = 2.f * static_cast<float>(A) * 11.3137085f * gm * wsum;
@@ -237,8 +250,8 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         if (bound > 0.f) e2 = static_cast<int>(floorf(log2f(16384.f / bound)));
         scale = ldexpf(1.f, max(-40, min(40, e2)));
     }
-    for (int i = simt ? tid : AP; i < AP; i += kSimtP) gp[i] = cscale(gp[i], scale);
-    if (simt) {
+    for (int i = simt ? tid : AP; i < AP; i += kGath) gp[i] = cscale(gp[i], scale);
+    if (tmw) {
         // zero the TMEM time sums of class hy = 1: lanes 32 (w mod 4) .., columns kColAcc1 + 64 (w / 4) ..
         uint32_t z[32];
 #pragma unroll
@@ -257,7 +270,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     const uint32_t x_base = tc::smem_u32(opX), g_base = tc::smem_u32(opG), h_base = tc::smem_u32(opH);
 
     if (!simt) {
-        // ---- the MMA warp: row stage of t after bar_g, column stages of (t, 0) and (t, 1)
+        // ---- the MMA warp (kMmaWarp): row stage of t after bar_g, column stages of (t, 0) and (t, 1)
         // after the next two completions of bar_h
         if (lane == 0) {
             bool ok = tc::mbar_wait(&bar_x, 0, wait_budget);
@@ -312,67 +325,77 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         }
         __syncwarp();
     } else {
-        constexpr int kPreW = kMaxAP / 4 / kSimtP;
-        const int m = 32 * (warp & 3) + lane;          // this thread's TMEM lane: (pol, jy) in D1, (my, part) in D2
-        const int hp = warp >> 2;                       // which half of the columns
+        constexpr int kPreW = (kMaxAP / 4 + kGath - 1) / kGath;
+        const int m = 32 * (warp & 3) + lane;          // TMEM warps: lane m = (pol, jy) in D1, (my, part) in D2
+        const int hp = (warp >> 2) & 1;                 // which half of the columns
         const int part = lane >> 4;
         const int pol = m >> 6, jy = m & 63;
         // the class-y turn of row jy: w_128^{ky}, ky = jy + 64 [row listed as upper]
         const int ky = jy + (((upper[ci] >> jy) & 1ull) ? 64 : 0);
         const float2 turn = twN[ky];
-        const int4 my_idx = pidx[ci * 8 + warp];        // (first batch, batches in half 1, second half's start, batches in half 2)
+        const int4 my_idx = pidx[ci * kGathW + warp];   // (first batch, batches in half 1, second half's start, batches in half 2)
 
         // a1, a2: unpack and calibrate sample t from the staged bytes
         auto unpack = [&](int t) {
-            for (int i = tid; i < AP; i += kSimtP) {
+            for (int i = tid; i < AP; i += kGath) {
                 const uint32_t b = reinterpret_cast<const uint8_t *>(stage)[i];
                 float2 e = cmul(gp[i], ci4_decode(b));
                 if (dtab) e = cmul(e, delay_phase(dtab[static_cast<size_t>(t) * A + i / P], dfreq[c]));
                 es[i] = e;
             }
         };
-        // a3: gather gridding of n batches from offset `at` (u16 units) straight into G16
+        // a3: gather gridding of n batches from offset `at` (u16 units) straight into G16.  A
+        // batch is [d][32 G16 byte offsets of the lanes' cell pairs (pol 0, Re, hi part), or
+        // 0xFFFF][d x 32 entries tp << 10 | a]; empty steps name the zero tap slot and antenna 0.
         auto gather = [&](int at, int n) {
             const uint16_t *bt = stab + at;
+            const float4 *es4 = reinterpret_cast<const float4 *>(es);
+            const float4 *tw8 = tw2 + (lane & 7);
+            const uint32_t empty = static_cast<uint32_t>(TPN) << 10;
             for (int b = 0; b < n; b++) {
                 const int d = bt[0];
-                const uint32_t pos = bt[1 + lane];
+                const uint32_t off = bt[1 + lane];
                 const uint16_t *ent = bt + 33 + lane;
                 float2 acc[P][2];
 #pragma unroll
                 for (int p = 0; p < P; p++) acc[p][0] = acc[p][1] = make_float2(0.f, 0.f);
-                uint32_t en = d > 0 ? ent[0] : kNone;
+                // software-pipelined: the entry two steps ahead and the taps and voltages one step
+                // ahead are in flight while the current step's multiply-adds run
+                uint32_t en1 = d > 1 ? ent[32] : empty;
+                const uint32_t e0 = d > 0 ? ent[0] : empty;
+                float4 ww = tw8[(e0 >> 10) << 3];
+                float4 ee = es4[e0 & 1023u];
                 for (int j = 0; j < d; j++) {
-                    const uint32_t cur = en;
-                    if (j + 1 < d) en = ent[(j + 1) * 32];
-                    if (cur != kNone) {
-                        const int a = static_cast<int>(cur & 1023u), tp = static_cast<int>(cur >> 10);
-                        const float4 ww = tw2[tp];
-                        const float4 e2 = reinterpret_cast<const float4 *>(es)[a];
-                        const float2 e[2] = {make_float2(e2.x, e2.y), make_float2(e2.z, e2.w)};
-                        const float2 wr[2] = {make_float2(ww.x, ww.x), make_float2(ww.z, ww.z)};
-                        const float2 wi[2] = {make_float2(-ww.y, ww.y), make_float2(-ww.w, ww.w)};
+                    const uint32_t en2 = j + 2 < d ? ent[(j + 2) * 32] : empty;
+                    const float4 wwn = tw8[(en1 >> 10) << 3];
+                    const float4 een = es4[en1 & 1023u];
+                    // cell u += w_u e_p (complex), as scalar FMAs with the sign folded in
+                    const float wr[2] = {ww.x, ww.z}, wi[2] = {ww.y, ww.w};
+                    const float er[2] = {ee.x, ee.z}, ei[2] = {ee.y, ee.w};
 #pragma unroll
-                        for (int p = 0; p < P; p++) {
-                            const float2 esw = pswap(e[p]);
+                    for (int p = 0; p < P; p++)
 #pragma unroll
-                            for (int u = 0; u < 2; u++) acc[p][u] = pfma(wi[u], esw, pfma(wr[u], e[p], acc[p][u]));
+                        for (int u = 0; u < 2; u++) {
+                            acc[p][u].x = fmaf(-wi[u], ei[p], fmaf(wr[u], er[p], acc[p][u].x));
+                            acc[p][u].y = fmaf(wi[u], er[p], fmaf(wr[u], ei[p], acc[p][u].y));
                         }
-                    }
+                    ww = wwn;
+                    ee = een;
+                    en1 = en2;
                 }
-                if (pos != kNone) {
-                    const int y = static_cast<int>(pos >> 5), x = 2 * static_cast<int>(pos & 31u);
+                if (off != kNone) {
+                    // Re at off, Im at + 1024 (K + 64), polarisation 1 at + 16384 (rows + 64)
 #pragma unroll
                     for (int p = 0; p < P; p++) {
                         uint32_t rh, rl, ih, il;
                         split_pair<kBF16, kSplit>(acc[p][0].x, acc[p][1].x, rh, rl);
                         split_pair<kBF16, kSplit>(acc[p][0].y, acc[p][1].y, ih, il);
-                        const int row = 64 * p + y;
-                        *reinterpret_cast<uint32_t *>(opG + k_off(row, x)) = rh;
-                        *reinterpret_cast<uint32_t *>(opG + k_off(row, 64 + x)) = ih;
+                        uint8_t *at0 = opG + off + 16384 * p;
+                        *reinterpret_cast<uint32_t *>(at0) = rh;
+                        *reinterpret_cast<uint32_t *>(at0 + 1024) = ih;
                         if constexpr (kSplit) {
-                            *reinterpret_cast<uint32_t *>(opG + kPart + k_off(row, x)) = rl;
-                            *reinterpret_cast<uint32_t *>(opG + kPart + k_off(row, 64 + x)) = il;
+                            *reinterpret_cast<uint32_t *>(at0 + kPart) = rl;
+                            *reinterpret_cast<uint32_t *>(at0 + kPart + 1024) = il;
                         }
                     }
                 }
@@ -422,14 +445,14 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(t) * C + c) * AP);
 #pragma unroll
             for (int r = 0; r < kPreW; r++) {
-                const int w = tid + r * kSimtP;
+                const int w = tid + r * kGath;
                 pre[r] = (t < t1 && w < APW) ? __ldg(row + w) : 0u;
             }
         };
         auto put_stage = [&](const uint32_t (&pre)[kPreW]) {
 #pragma unroll
             for (int r = 0; r < kPreW; r++) {
-                const int w = tid + r * kSimtP;
+                const int w = tid + r * kGath;
                 if (w < APW) stage[w] = pre[r];
             }
         };
@@ -445,7 +468,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         // prologue: sample t0 gridded into G16, the bytes of t0 + 1 staged
         if (t0 < t1) {
             unpack(t0);
-            tc::named_bar_sync(kBarP, kSimtP);
+            tc::named_bar_sync(kBarP, kGath);
             uint32_t pre[kPreW];
             load_stage(t0 + 1, pre);
             gather(my_idx.x, my_idx.y);
@@ -454,87 +477,94 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             tc::fence_proxy_async();
             tc::fence_before_sync();
             tc::mbar_arrive(&bar_g);
-            tc::named_bar_sync(kBarP, kSimtP);
+            tc::named_bar_sync(kBarP, kGath);
         }
         uint32_t p1 = 0, p2a = 0, p2b = 0;
         for (int t = t0; t < t1; t++) {
             const bool nxt = t + 1 < t1;
             uint32_t pre[kPreW];
             load_stage(t + 2, pre);
-            // row stage of t done: D1 -> H16 for class hy = 0 (G16 is free for sample t + 1)
+            // row stage of t done: G16 is free for sample t + 1; the TMEM warps convert D1 -> H16
+            // for class hy = 0
             if (!abort_flag) {
                 if (!tc::mbar_wait(&bar_m1, p1, wait_budget)) fail();
-                else {
+                else if (tmw) {
                     tc::fence_after_sync();
                     to_h16(0);
                 }
             }
             p1 ^= 1u;
             if (nxt) unpack(t + 1);
-            tc::named_bar_sync(kBarP, kSimtP);          // es of t + 1 complete; the staged bytes are free
+            tc::named_bar_sync(kBarP, kGath);           // es of t + 1 complete; the staged bytes are free
             put_stage(pre);
-            if (nxt && !abort_flag) gather(my_idx.x, my_idx.y);
-            // column stage of (t, 0) done: H16 is free -> H16 for class hy = 1
-            if (!abort_flag) {
-                if (!tc::mbar_wait(&bar_m2a, p2a, wait_budget)) fail();
-                else {
-                    tc::fence_after_sync();
-                    to_h16(1);
+            if (tmw) {
+                if (nxt && !abort_flag) gather(my_idx.x, my_idx.y);
+                // column stage of (t, 0) done: H16 is free -> H16 for class hy = 1
+                if (!abort_flag) {
+                    if (!tc::mbar_wait(&bar_m2a, p2a, wait_budget)) fail();
+                    else {
+                        tc::fence_after_sync();
+                        to_h16(1);
+                    }
                 }
+                p2a ^= 1u;
             }
-            p2a ^= 1u;
             if (nxt && !abort_flag) {
-                gather(my_idx.z, my_idx.w);
+                if (tmw) gather(my_idx.z, my_idx.w);
+                else gather(my_idx.x, my_idx.y);
                 tc::fence_proxy_async();
                 tc::fence_before_sync();
                 tc::mbar_arrive(&bar_g);
             }
-            // a5, a6: products of (t, 0) from D2a (complete: waited above), then of (t, 1)
-            if (!abort_flag) products<true>(lane_addr, kColD2a, hp, part, acc0);
-            if (!abort_flag) {
-                if (!tc::mbar_wait(&bar_m2b, p2b, wait_budget)) fail();
-                else {
-                    tc::fence_after_sync();
-                    products<false>(lane_addr, kColD2b, hp, part, acc0);
+            if (tmw) {
+                // a5, a6: products of (t, 0) from D2a (complete: waited above), then of (t, 1)
+                if (!abort_flag) products<true>(lane_addr, kColD2a, hp, part, acc0);
+                if (!abort_flag) {
+                    if (!tc::mbar_wait(&bar_m2b, p2b, wait_budget)) fail();
+                    else {
+                        tc::fence_after_sync();
+                        products<false>(lane_addr, kColD2b, hp, part, acc0);
+                    }
                 }
+                p2b ^= 1u;
             }
-            p2b ^= 1u;
             tc::fence_before_sync();
-            tc::named_bar_sync(kBarP, kSimtP);
-            if (abort_flag) break;
+            if (tc::named_bar_or(kBarP, kGath, abort_flag != 0)) break;   // the same answer in every warp
         }
 
         // ---- partial images of both classes (undo the FP16 scale exactly)
         tc::fence_after_sync();
-        const float inv = 1.f / (scale * scale);
-        const float inv_im = part ? -inv : inv;        // Im XY was summed with the lane's part sign
-        const int my = 16 * (warp & 3) + (lane & 15);
-        float4 *dst0 = reinterpret_cast<float4 *>(partial) +
-                       (static_cast<size_t>(tau) * n_items_out + ci * 4 + hx) * (64 * 64);
-        float4 *dst1 = reinterpret_cast<float4 *>(partial) +
-                       (static_cast<size_t>(tau) * n_items_out + ci * 4 + 2 + hx) * (64 * 64);
+        if (tmw) {
+            const float inv = 1.f / (scale * scale);
+            const float inv_im = part ? -inv : inv;        // Im XY was summed with the lane's part sign
+            const int my = 16 * (warp & 3) + (lane & 15);
+            float4 *dst0 = reinterpret_cast<float4 *>(partial) +
+                           (static_cast<size_t>(tau) * n_items_out + ci * 4 + hx) * (64 * 64);
+            float4 *dst1 = reinterpret_cast<float4 *>(partial) +
+                           (static_cast<size_t>(tau) * n_items_out + ci * 4 + 2 + hx) * (64 * 64);
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
-            const int mx = 32 * hp + 16 * part + j;
-            dst0[my * 64 + mx] = make_float4(acc0[j].x * inv, acc0[j].y * inv, acc0[j].z * inv, acc0[j].w * inv_im);
-        }
+            for (int j = 0; j < 16; j++) {
+                const int mx = 32 * hp + 16 * part + j;
+                dst0[my * 64 + mx] = make_float4(acc0[j].x * inv, acc0[j].y * inv, acc0[j].z * inv, acc0[j].w * inv_im);
+            }
 #pragma unroll
-        for (int half = 0; half < 2; half++) {
-            uint32_t s[32];
-            tc::tmem_ld32_issue(lane_addr + kColAcc1 + 64 * hp + 32 * half, s);
-            tc::tmem_wait_ld();
-            tc::reg_fence32(s);
+            for (int half = 0; half < 2; half++) {
+                uint32_t s[32];
+                tc::tmem_ld32_issue(lane_addr + kColAcc1 + 64 * hp + 32 * half, s);
+                tc::tmem_wait_ld();
+                tc::reg_fence32(s);
 #pragma unroll
-            for (int jj = 0; jj < 8; jj++) {
-                const int mx = 32 * hp + 16 * part + 8 * half + jj;
-                dst1[my * 64 + mx] = make_float4(__uint_as_float(s[4 * jj]) * inv, __uint_as_float(s[4 * jj + 1]) * inv,
-                                                 __uint_as_float(s[4 * jj + 2]) * inv,
-                                                 __uint_as_float(s[4 * jj + 3]) * inv_im);
+                for (int jj = 0; jj < 8; jj++) {
+                    const int mx = 32 * hp + 16 * part + 8 * half + jj;
+                    dst1[my * 64 + mx] = make_float4(__uint_as_float(s[4 * jj]) * inv, __uint_as_float(s[4 * jj + 1]) * inv,
+                                                     __uint_as_float(s[4 * jj + 2]) * inv,
+                                                     __uint_as_float(s[4 * jj + 3]) * inv_im);
+                }
             }
         }
     }
     // an aborted CTA may still have MMAs in flight: give them a bounded chance to land
-    if (tid == kSimtP && abort_flag) {
+    if (tid == kMmaWarp * 32 && abort_flag) {
         tc::mbar_wait(&bar_m1, 0, wait_budget);
         tc::mbar_wait(&bar_m1, 1, wait_budget);
         tc::mbar_wait(&bar_m2a, 0, wait_budget);
@@ -552,7 +582,7 @@ size_t pair_smem(int A, int K, int words)
 {
     const int AP = A * 2;
     size_t b = 6 * static_cast<size_t>(kPart);
-    b += sizeof(float2) * 2 * static_cast<size_t>(AP) + sizeof(float4) * static_cast<size_t>(K) * (K + 1);
+    b += sizeof(float2) * 2 * static_cast<size_t>(AP) + sizeof(float4) * 8 * (static_cast<size_t>(K) * (K + 1) + 1);
     b += sizeof(uint32_t) * ((AP + 3) / 4) + sizeof(uint16_t) * static_cast<size_t>(words);
     return (b + 15) & ~static_cast<size_t>(15);
 }
@@ -569,24 +599,39 @@ int pair_dispatch(int precision, F &&f)
 
 }  // namespace
 
-// The gather lists of the pair kernel from the FP32 kernel's table of the same
-// channels (build_gather_table, fold side 64, dual polarisation): batches of 32
-// cell pairs keep their order and their bank-aware step order, each as
-// [list length d][32 pair positions y * 32 + x / 2][d x 32 entries tp << 10 | a]
-// in 16-bit words (0xFFFF: none), without the zero lists (G16 keeps the cells
-// no list names at zero).  Each warp's batches are split in two halves of
-// about equal work (list steps) for the two gridding phases of an iteration:
-// idx[ci * 8 + w] = (first half's offset, its batches, second half's offset,
-// its batches), offsets in words from the channel block's start; chan[ci] =
-// (block start, block words).  The upper mask of a channel lists the folded
-// rows whose cells lie in unfolded rows 64..127; EPIC_ERR_UNSUPPORTED when a
-// folded row holds cells of both halves, when A > 1024, or when K (K + 1) > 64.
+// The gather lists of the pair kernel, rebuilt from the FP32 kernel's table of
+// the same channels (build_gather_table, fold side 64, dual polarisation: per
+// pair of adjacent folded cells, the (antenna, tap pair) entries of the
+// footprints that cover it).  Batches of 32 cell pairs are formed again for
+// this kernel: pairs sorted by list length, and each batch takes, from a
+// window of the next pairs, ones whose 32-bit stores into G16 fall in distinct
+// banks -- a pair (y, 2 xp) is stored at bank 4 (y mod 8) + xp mod 4 of every
+// part, so 32 pairs with distinct (y mod 8, xp mod 4) store without conflicts.
+// Within each group of 8 lanes (one 16-byte request of the voltage loads) the
+// step order is then chosen so that one step reads distinct banks, antenna
+// a mod 8, as far as the lists allow.  Storage: [list length d][32 G16 byte
+// offsets k_off(y, 2 xp) of the pairs (0xFFFF: an empty lane)][d x 32 entries
+// tp << 10 | a] in 16-bit words, an empty step naming tap slot K (K + 1)
+// (zeros) and antenna 0; no zero lists (G16 keeps the cells no list names at
+// zero).  The
+// batches are dealt to the kernel's gridding warps longest first, each to the
+// warp with the least work so far (a batch costs 4 d + 6, about 37 cycles a
+// unit): the 8 TMEM warps start with kTmemLoad units for their conversions and
+// products, the gridding-only warps with none.  A TMEM warp's batches are split
+// in two halves of about equal work for the two gridding phases of an
+// iteration; a gridding-only warp has one list.  idx[ci * kPairGatherWarps + w]
+// = (first half's offset, its batches, second half's offset, its batches),
+// offsets in words from the channel block's start; chan[ci] = (block start,
+// block words).  The upper mask of a channel lists the folded rows whose cells
+// lie in unfolded rows 64..127; EPIC_ERR_UNSUPPORTED when a folded row holds
+// cells of both halves, when A > 1024, or when K (K + 1) > 63.
 int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
                       const std::vector<uint32_t> &tab32, const std::vector<int4> &idx32,
                       const std::vector<int2> &chan32, std::vector<uint16_t> &tab, std::vector<int4> &idx,
                       std::vector<int2> &chan, std::vector<unsigned long long> &upper)
 {
-    constexpr int M = 64, S = M + 1, W = 8;
+    constexpr int M = 64, S = M + 1, W32 = 8, W = kPairGatherWarps, kWindow = 96;
+    constexpr long long kTmemLoad = 90;
     if (A > 1024 || K * (K + 1) > 63) return EPIC_ERR_UNSUPPORTED;
     const int nc = static_cast<int>(chans.size()), h = (K - 1) / 2;
     tab.clear();
@@ -606,26 +651,129 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
         }
         if (lo_rows & hi_rows) return EPIC_ERR_UNSUPPORTED;
         upper[ci] = hi_rows;
-        const size_t start = tab.size();
+        // every cell pair of the channel with its entries (tp << 10 | a)
         const uint32_t *blk = tab32.data() + chan32[ci].x;
-        for (int w = 0; w < W; w++) {
-            const int4 i32 = idx32[static_cast<size_t>(ci) * W + w];
-            // this warp's batches: their offsets and list steps
-            std::vector<std::pair<int, int>> bs;
+        std::vector<std::pair<int, std::vector<uint16_t>>> pairs;   // (y * 32 + xp, entries)
+        for (int w = 0; w < W32; w++) {
+            const int4 i32 = idx32[static_cast<size_t>(ci) * W32 + w];
             int at = i32.z;
             for (int b = 0; b < i32.w; b++) {
                 const int d = static_cast<int>(blk[at]);
-                bs.push_back({at, d});
+                for (int l = 0; l < 32; l++) {
+                    const uint32_t cw = blk[at + 1 + l];
+                    if (cw == ~0u) continue;
+                    std::vector<uint16_t> ent;
+                    for (int j = 0; j < d; j++) {
+                        const uint32_t en = blk[at + 33 + 32 * j + l];
+                        if (en != ~0u) ent.push_back(static_cast<uint16_t>(((en & 0xFFu) << 10) | (en >> 8)));
+                    }
+                    pairs.push_back({static_cast<int>(cw / S) * 32 + static_cast<int>(cw % S) / 2, std::move(ent)});
+                }
                 at += 33 + 32 * d;
             }
+        }
+        std::stable_sort(pairs.begin(), pairs.end(),
+                         [](const auto &u, const auto &v) { return u.second.size() > v.second.size(); });
+        // batches of 32 pairs with distinct store banks where the window allows
+        std::vector<std::vector<int>> batches;
+        std::vector<char> taken(pairs.size(), 0);
+        size_t first = 0;
+        while (first < pairs.size()) {
+            std::vector<int> bt;
+            bool bank[32] = {};
+            for (size_t q = first; q < pairs.size() && q < first + kWindow && bt.size() < 32; q++) {
+                if (taken[q]) continue;
+                const int pos = pairs[q].first, r = 4 * ((pos >> 5) & 7) + (pos & 3);
+                if (bank[r]) continue;
+                bank[r] = true;
+                taken[q] = 1;
+                bt.push_back(static_cast<int>(q));
+            }
+            for (size_t q = first; q < pairs.size() && bt.size() < 32; q++)   // fill: conflicts allowed
+                if (!taken[q]) {
+                    taken[q] = 1;
+                    bt.push_back(static_cast<int>(q));
+                }
+            while (first < pairs.size() && taken[first]) first++;
+            batches.push_back(std::move(bt));
+        }
+        // each batch as words: length, positions, then the steps with distinct voltage banks per
+        // group of 8 lanes where possible
+        std::vector<std::vector<uint16_t>> words(batches.size());
+        std::vector<int> blen(batches.size());
+        for (size_t b = 0; b < batches.size(); b++) {
+            const auto &bt = batches[b];
+            int d = 0;
+            for (int q : bt) d = std::max(d, static_cast<int>(pairs[q].second.size()));
+            blen[b] = d;
+            auto &wd = words[b];
+            const uint16_t empty = static_cast<uint16_t>((K * (K + 1)) << 10);   // zero tap slot, antenna 0
+            wd.assign(1 + 32 + static_cast<size_t>(d) * 32, empty);
+            wd[0] = static_cast<uint16_t>(d);
+            for (int l = 0; l < 32; l++) {
+                if (l >= static_cast<int>(bt.size())) {
+                    wd[1 + l] = 0xFFFFu;
+                    continue;
+                }
+                const int pos = pairs[bt[l]].first;
+                wd[1 + l] = static_cast<uint16_t>(k_off(pos >> 5, 2 * (pos & 31)));   // pol 0, Re, hi part
+            }
+            for (int g0 = 0; g0 < 32; g0 += 8) {
+                std::vector<std::vector<uint16_t>> rem(8);
+                for (int l = 0; l < 8; l++)
+                    if (g0 + l < static_cast<int>(bt.size())) rem[l] = pairs[bt[g0 + l]].second;
+                for (int j = 0; j < d; j++) {
+                    std::vector<int> order(8);
+                    for (int l = 0; l < 8; l++) order[l] = l;
+                    std::stable_sort(order.begin(), order.end(),
+                                     [&](int u, int v) { return rem[u].size() > rem[v].size(); });
+                    int slot[8];
+                    for (int &x : slot) x = -1;
+                    for (int l : order) {
+                        auto &r = rem[l];
+                        if (r.empty()) continue;
+                        const bool must = static_cast<int>(r.size()) >= d - j;
+                        int pick = -1;
+                        for (size_t q = 0; q < r.size() && pick < 0; q++) {
+                            const int a = r[q] & 1023, sl = a & 7;
+                            if (slot[sl] < 0 || slot[sl] == a) pick = static_cast<int>(q);
+                        }
+                        if (pick < 0 && must) pick = 0;
+                        if (pick < 0) continue;
+                        const uint16_t e = r[pick];
+                        r.erase(r.begin() + pick);
+                        slot[(e & 1023) & 7] = e & 1023;
+                        wd[1 + 32 + static_cast<size_t>(j) * 32 + g0 + l] = e;
+                    }
+                }
+            }
+        }
+        // deal to the gridding warps
+        std::vector<int> ord(batches.size());
+        for (size_t b = 0; b < ord.size(); b++) ord[b] = static_cast<int>(b);
+        std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) { return blen[u] > blen[v]; });
+        std::vector<std::vector<int>> per(W);
+        std::vector<long long> load(W, 0);
+        for (int w = 0; w < 8; w++) load[w] = kTmemLoad;
+        for (int b : ord) {
+            const int w = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+            per[w].push_back(b);
+            load[w] += 4LL * blen[b] + 6;
+        }
+        const size_t start = tab.size();
+        for (int w = 0; w < W; w++) {
             long long total = 0;
-            for (auto &x : bs) total += 4 * x.second + 2;
-            long long run = 0;
-            size_t split = 0;
-            while (split < bs.size() && 2 * (run + 4 * bs[split].second + 2) <= total) run += 4 * bs[split++].second + 2;
+            for (int b : per[w]) total += 4LL * blen[b] + 6;
+            size_t split = per[w].size();   // gridding-only warps: one list
+            if (w < 8) {
+                long long run = 0;
+                split = 0;
+                while (split < per[w].size() && 2 * (run + 4LL * blen[per[w][split]] + 6) <= total)
+                    run += 4LL * blen[per[w][split++]] + 6;
+            }
             int4 &o = idx[static_cast<size_t>(ci) * W + w];
             for (int half = 0; half < 2; half++) {
-                const size_t b0 = half ? split : 0, b1 = half ? bs.size() : split;
+                const size_t b0 = half ? split : 0, b1 = half ? per[w].size() : split;
                 const int off = static_cast<int>(tab.size() - start);
                 if (half) {
                     o.z = off;
@@ -634,33 +782,12 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
                     o.x = off;
                     o.y = static_cast<int>(b1 - b0);
                 }
-                for (size_t b = b0; b < b1; b++) {
-                    const int bat = bs[b].first, d = bs[b].second;
-                    tab.push_back(static_cast<uint16_t>(d));
-                    for (int l = 0; l < 32; l++) {
-                        const uint32_t cw = blk[bat + 1 + l];
-                        if (cw == ~0u) {
-                            tab.push_back(0xFFFFu);
-                            continue;
-                        }
-                        const int y = static_cast<int>(cw / S), x = static_cast<int>(cw % S);
-                        tab.push_back(static_cast<uint16_t>(y * 32 + x / 2));
-                    }
-                    for (int e = 0; e < 32 * d; e++) {
-                        const uint32_t en = blk[bat + 33 + e];
-                        if (en == ~0u) {
-                            tab.push_back(0xFFFFu);
-                            continue;
-                        }
-                        const uint32_t a = en >> 8, tp = en & 0xFFu;
-                        tab.push_back(static_cast<uint16_t>((tp << 10) | a));
-                    }
-                }
+                for (size_t q = b0; q < b1; q++) tab.insert(tab.end(), words[per[w][q]].begin(), words[per[w][q]].end());
             }
         }
-        const size_t words = tab.size() - start;
-        if (words > 0xFFFFFFull || start > 0x7FFFFFFFull) return EPIC_ERR_UNSUPPORTED;
-        chan[ci] = make_int2(static_cast<int>(start), static_cast<int>(words));
+        const size_t nwords = tab.size() - start;
+        if (nwords > 0xFFFFFFull || start > 0x7FFFFFFFull) return EPIC_ERR_UNSUPPORTED;
+        chan[ci] = make_int2(static_cast<int>(start), static_cast<int>(nwords));
     }
     if (tab.empty()) tab.push_back(0);
     return EPIC_OK;

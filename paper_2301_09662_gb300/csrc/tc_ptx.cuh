@@ -218,5 +218,18 @@ __device__ __forceinline__ void named_bar_sync(int id, int count)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// The same barrier, returning whether `pred` held in any participating thread
+// (one answer for all of them, so a loop can leave it uniformly).
+__device__ __forceinline__ bool named_bar_or(int id, int count, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 q, %3, 0;\n bar.red.or.pred p, %1, %2, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(r)
+        : "r"(id), "r"(count), "r"(static_cast<uint32_t>(pred))
+        : "memory");
+    return r != 0;
+}
+
 }  // namespace tc
 }  // namespace epic

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "epic_internal.cuh"
+#include "tc_common.cuh"
 
 static long g_bad = 0;
 #define CHECK(cond, ...)                  \
@@ -203,15 +204,16 @@ int main(int argc, char **argv)
                             const uint32_t e = blk[off + 33 + 32LL * j + l];
                             if (e == ~0u || cw == ~0u) continue;
                             const long long pos = (cw / S) * 32 + (cw % S) / 2;
-                            want.insert((((static_cast<long long>(w) << 16) | pos) << 24) | ((e >> 8) << 8) | (e & 0xFF));
+                            want.insert((pos << 24) | ((e >> 8) << 8) | (e & 0xFF));
                         }
                     }
                     off += 33 + 32LL * d;
                 }
             }
             const uint16_t *pb = ptab.data() + pchan[ci].x;
-            for (int w = 0; w < 8; w++) {
-                const int4 q = pidx[static_cast<size_t>(ci) * 8 + w];
+            for (int w = 0; w < epic::kPairGatherWarps; w++) {
+                const int4 q = pidx[static_cast<size_t>(ci) * epic::kPairGatherWarps + w];
+                CHECK(w < 8 || q.w == 0, "channel %d: a gridding-only warp with a second list", ci);
                 for (int half = 0; half < 2; half++) {
                     long long off = half ? q.z : q.x;
                     const int nb = half ? q.w : q.y;
@@ -220,14 +222,23 @@ int main(int argc, char **argv)
                         const int d = pb[off];
                         CHECK(off + 33 + 32LL * d <= pchan[ci].y, "channel %d: batch outside the block", ci);
                         for (int l = 0; l < 32; l++) {
-                            const uint16_t pos = pb[off + 1 + l];
+                            // the lane's G16 byte offset (pol 0, Re, hi part) back to its cell pair
+                            const uint16_t go = pb[off + 1 + l];
+                            const int y = (go / 2048) * 8 + (go % 128) / 16;
+                            const int k = ((go % 2048) / 128) * 8 + (go % 16) / 2;
+                            const bool lane_ok = go != 0xFFFFu && y < 64 && k < 64 && k % 2 == 0 &&
+                                                 epic::tcc::k_off(y, k) == go;
                             for (int j = 0; j < d; j++) {
                                 const uint16_t e = pb[off + 33 + 32LL * j + l];
-                                if (e == 0xFFFFu) continue;
-                                CHECK(pos != 0xFFFFu && pos < 64 * 32, "channel %d: entry under an empty lane", ci);
                                 const long long a = e & 1023, tp = e >> 10;
-                                CHECK(a < A && tp < K * (K + 1), "channel %d: entry out of range", ci);
-                                got.insert((((static_cast<long long>(w) << 16) | pos) << 24) | (a << 8) | tp);
+                                CHECK(a < A && tp <= K * (K + 1), "channel %d: entry out of range", ci);
+                                if (tp == K * (K + 1)) {   // an empty step: the zero tap slot, antenna 0
+                                    CHECK(a == 0, "channel %d: empty step with an antenna", ci);
+                                    continue;
+                                }
+                                CHECK(lane_ok, "channel %d: entry under an empty or bad lane offset", ci);
+                                const long long pos = y * 32 + k / 2;
+                                got.insert((pos << 24) | (a << 8) | tp);
                             }
                         }
                         off += 33 + 32LL * d;
