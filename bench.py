@@ -14,7 +14,10 @@ Default workload: the LWA-station-like configuration (256 dual-pol antennas,
 64 channels of 25 kHz from 60 MHz, 1000 spectra per integration, 5x5 kernel,
 128x128 grid), seeded synthetic inputs resident in HBM.  L2 is flushed by a
 256 MiB write between timed steps.  Under torchrun each rank images its own
-band of the same shape (weak scaling, no collective on the data path).
+band of the same shape (weak scaling, no collective on the data path); with
+--split-band the ranks split one fixed band by channel instead (strong
+scaling) and the finished images are gathered to rank 0 after the timed
+region.
 
 --impl reference times the FP64 CPU oracle (the correctness reference) on the
 host cores instead, on a bounded sample of the same workload.
@@ -67,6 +70,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     ap.add_argument("--no-variants", action="store_true", help="skip timing the other forms")
+    ap.add_argument("--split-band", action="store_true",
+                    help="under torchrun: split one fixed band across the ranks (strong scaling) instead of "
+                         "giving every rank its own band (weak scaling)")
     ap.add_argument("--channels", type=int, default=None,
                     help="shrink the workload to this many channels (profiling captures only)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
@@ -610,7 +616,7 @@ def time_search(flush, args, stream):
     return res
 
 
-def run_e2e(plan, wl, args, world, barrier, spectra):
+def run_e2e(plan, wl, args, world, barrier, spectra, band_spectra=None):
     """Same metric through epic_image_host: every step copies the pinned host
     voltages and gains in and the image out, inside the timed region."""
     import torch
@@ -629,7 +635,8 @@ def run_e2e(plan, wl, args, world, barrier, spectra):
         times.append(time.perf_counter() - t0)
     barrier()
     step_s = shard.max_over_ranks(sum(times) / len(times), device="cuda")
-    return {"value": shard.whole_job_rate(spectra, world, step_s), "unit": UNIT,
+    rate = shard.whole_job_rate(spectra, world, step_s) if band_spectra is None else band_spectra / step_s
+    return {"value": rate, "unit": UNIT,
             "h2d_bytes_per_step": vh.numel() + (gh.numel() * 8 if gh is not None else 0),
             "d2h_bytes_per_step": oh.numel() * 8}
 
@@ -652,7 +659,17 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    wl = make_workload(args.workload, args.channels, rank)
+    band = None
+    if args.split_band and world > 1:
+        # one fixed band: every rank plans and images its cost-balanced block of channels
+        from paper_2301_09662_gb300 import synth
+        band = make_workload(args.workload, args.channels, 0)
+        mine, _, _ = shard.band_slice(band.grid_n, band.n_pol, world, rank)
+        if not mine:
+            raise SystemExit(f"rank {rank}: no channel of the {band.C}-channel band is left for this rank")
+        wl = synth.select_channels(band, mine)
+    else:
+        wl = make_workload(args.workload, args.channels, rank)
     precision = {"fp32": epic.EPIC_FP32, "tc_split_fp16": epic.EPIC_TC_SPLIT_FP16, "tc_fp16": epic.EPIC_TC_FP16,
                  "tc_split_bf16": epic.EPIC_TC_SPLIT_BF16}[args.precision]
     plan = epic.Plan.from_workload(wl, precision=precision, flags=epic.EPIC_KERNEL_TAPER if args.taper else 0)
@@ -693,14 +710,21 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     max_total_ms = shard.max_over_ranks(sum(step_ms), device="cuda")
     ms_per_step = max_total_ms / args.steps
-    value = shard.whole_job_rate(spectra, world, ms_per_step / 1e3)
+    if band is None:
+        value = shard.whole_job_rate(spectra, world, ms_per_step / 1e3)
+    else:
+        value = band.spectra / (ms_per_step / 1e3)
+        # the finished band collected on rank 0, once, after the timed region
+        whole = shard.assemble_band(out, band.grid_n, band.n_pol)
+        if rank == 0 and whole.numel() != shard.packed_offsets(band.grid_n, band.n_pol)[-1]:
+            raise RuntimeError("assembled band has the wrong size")
     launches = len(names) * args.steps
 
     # end to end through the host-buffer entry point: pinned inputs copied in,
     # image copied out, every step
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(plan, wl, args, world, barrier, spectra)
+        e2e = run_e2e(plan, wl, args, world, barrier, spectra, None if band is None else band.spectra)
 
 
     # roofline of the dominant kernel (the fused imaging launch)
@@ -709,7 +733,9 @@ def run_ours(args):
     stages_avg = {n: stage_sum[n] / args.steps for n in names}
     image_stage = max((n for n in names if n.startswith("image[")), key=lambda n: stage_sum[n])
     img_ms = stages_avg[image_stage]
-    config = describe(wl, args.workload)
+    config = describe(wl if band is None else band, args.workload)
+    if band is not None:
+        config["parallelism"] = f"one band split across {world} ranks by channel (cost-balanced), images gathered to rank 0"
     config["launch_shapes"] = "cost model" if args.no_autotune else "measured per channel group (epic_autotune)"
     config["form"] = args.precision + (" + image-domain kernel taper" if args.taper else " (literal gridding)")
     if args.precision == "fp32":
@@ -725,7 +751,8 @@ def run_ours(args):
          "tc_split_bf16": "bf16 hi+lo operands, f32 accumulate"}[args.precision]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak" if band is None else "strong",
         "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded LWA-like layout, sky, noise, gains)",
         "config": config,
         "roofline": roofline,

@@ -8,10 +8,14 @@ with no exchange on the data path.  Two uses:
 * weak scaling: every rank images a band of the same shape next to the others
   (`rank_first_channel`);
 * a fixed band split across ranks (`shard_channels`), balanced by the
-  per-channel cost N^2 log2 N of the grid side.
+  per-channel cost N^2 log2 N of the grid side.  Each rank plans and images
+  only its channels (`band_slice` gives their place in the whole band's packed
+  output) and `assemble_band` collects the slices into the band's packed
+  layout once the integration is done.
 
-The only collective is on the control path: the slowest rank's time
-(`max_over_ranks`).
+Imaging itself needs no exchange.  The collectives are the slowest rank's time
+(`max_over_ranks`) and, for a split band, the one gather of the finished
+images (`assemble_band`).
 """
 from __future__ import annotations
 
@@ -52,6 +56,65 @@ def shard_channels(grid_n, world: int, rank: int) -> list[int]:
         bounds.append(c)
     bounds.append(len(costs))
     return list(range(bounds[rank], bounds[rank + 1]))
+
+
+def packed_offsets(grid_n, n_pol: int) -> list[int]:
+    """Offsets (complex elements) of every channel's [NP][N][N] block in a
+    plan's packed output, with the total size as the last entry (NP = 4 products
+    for dual polarisation, 1 for single)."""
+    NP = 4 if int(n_pol) == 2 else 1
+    offs = [0]
+    for n in grid_n:
+        offs.append(offs[-1] + NP * int(n) * int(n))
+    return offs
+
+
+def band_slice(grid_n, n_pol: int, world: int, rank: int) -> tuple[list[int], int, int]:
+    """Rank `rank`'s part of a fixed band split across `world` ranks: its
+    channels (`shard_channels`) and the [start, stop) range of complex elements
+    their images occupy in the whole band's packed output.  A plan made of
+    exactly these channels, in this order, writes that range contiguously."""
+    ch = shard_channels(grid_n, world, rank)
+    offs = packed_offsets(grid_n, n_pol)
+    if not ch:
+        return ch, 0, 0
+    return ch, offs[ch[0]], offs[ch[-1] + 1]
+
+
+def assemble_band(local, grid_n, n_pol: int, dst: int = 0, group=None):
+    """Collect every rank's packed slice (a 1-D complex tensor from a plan of
+    its `band_slice` channels; empty for a rank without channels) into the whole
+    band's packed output on rank `dst` (None on the others).
+
+    One all_gather of equal-length buffers (each slice padded to the longest),
+    as complex values viewed as float pairs so that gloo and NCCL both carry it;
+    without torch.distributed (one rank) the slice is the band."""
+    import torch
+    import torch.distributed as dist
+    offs = packed_offsets(grid_n, n_pol)
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:
+        if local.numel() != offs[-1]:
+            raise ValueError("a single rank's slice must be the whole band")
+        return local
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    spans = [band_slice(grid_n, n_pol, world, r)[1:] for r in range(world)]
+    mine = spans[rank][1] - spans[rank][0]
+    if local.numel() != mine:
+        raise ValueError(f"rank {rank}: slice has {local.numel()} elements, its channels need {mine}")
+    longest = max(b - a for a, b in spans)
+    buf = torch.zeros(max(longest, 1), 2, dtype=torch.float32, device=local.device)
+    if mine:
+        buf[:mine] = torch.view_as_real(local.reshape(-1).to(torch.complex64))
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(parts, buf, group=group)
+    if rank != dst:
+        return None
+    out = torch.empty(offs[-1], dtype=torch.complex64, device=local.device)
+    for (a, b), part in zip(spans, parts):
+        if b > a:
+            out[a:b] = torch.view_as_complex(part[:b - a].contiguous())
+    return out
 
 
 def max_over_ranks(value: float, device=None) -> float:

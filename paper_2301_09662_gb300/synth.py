@@ -219,6 +219,18 @@ class Workload:
         return self.T * self.C * self.n_pol
 
 
+def select_channels(wl: Workload, channels) -> Workload:
+    """The same workload restricted to the given channels (in that order):
+    voltages, gains, grid sides and frequencies are sliced, nothing is redrawn."""
+    ch = np.asarray(list(channels), np.int64)
+    if ch.size == 0:
+        raise ValueError("select_channels needs at least one channel")
+    return Workload(f"{wl.name}[ch {ch[0]}..{ch[-1]}]", wl.ant_xy, wl.n_pol, wl.kernel,
+                    np.ascontiguousarray(wl.grid_n[ch]), np.ascontiguousarray(wl.freq_hz[ch]), wl.du, wl.T,
+                    np.ascontiguousarray(wl.v[:, ch]),
+                    None if wl.gains is None else np.ascontiguousarray(wl.gains[ch]), dict(wl.meta))
+
+
 def _lm_uniform_disc(n, rmax, rng):
     r = rmax * np.sqrt(rng.random(n))
     th = 2 * np.pi * rng.random(n)
