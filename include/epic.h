@@ -347,13 +347,17 @@ int epic_stage_times(epic_plan_t plan, float *ms, int max_stages);
  * is queued (e.g. 64 channels of 128 x 128 dual polarisation fit; 128 do not).
  *
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the array and overwrites what the previous call
- * left in it (what must start at zero is cleared on the call's stream), so
- * calls whose GPU work overlaps -- different streams, different host threads
- * -- race; order them.  The geometry tables are copied from pageable host
- * memory on the stream, so the call may block the host briefly.  Asynchronous
- * otherwise.  Other errors are those of epic_plan and epic_image.
+ * device, with that device current).  Every call shares the array and
+ * overwrites what the previous call left in it (what must start at zero is
+ * cleared on the call's stream), so calls whose GPU work overlaps -- different
+ * streams, different host threads -- race; order them.  The geometry tables
+ * are copied from pageable host memory on the stream, so the call may block
+ * the host briefly, and it must not be made while the stream is being captured
+ * into a CUDA graph.  Asynchronous otherwise.  The return value covers the
+ * checks and launches only: the device-side status word that epic_status
+ * reports for a plan (e.g. a bounded wait that ran out) lives in the shared
+ * array and is not reported to a static caller.  Other errors are those of
+ * epic_plan and epic_image.
  */
 int epic_image_static(const double *ant_xy_m, int n_ant, int n_pol,
                       const float *kernel_c64, int K, int grid_n,

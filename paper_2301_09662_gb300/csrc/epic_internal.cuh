@@ -188,10 +188,11 @@ int prepare_tc_pair(const epic_plan_s *plan, size_t smem);
 int launch_tc_pair(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                    cudaStream_t stream);
 
-// Gather table of the FP32 register-transform kernel for the channels of one group (plan.cu).
+// Gather table of the FP32 register-transform kernel for the channels of one group (plan.cu),
+// built on up to `threads` host threads (0: automatic); the result does not depend on it.
 int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, int P, const std::vector<int> &chans,
                        std::vector<uint32_t> &tab, std::vector<int4> &idx, std::vector<int2> &chan,
-                       std::vector<unsigned long long> &rowmask);
+                       std::vector<unsigned long long> &rowmask, int threads = 0);
 // Register-transform kernels, fold side M = 64 or 48 (fp32_reg64.cu)
 size_t reg64_smem_bytes(int M, int P, int TS, int A, int K, int nker);
 int launch_reg64(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,

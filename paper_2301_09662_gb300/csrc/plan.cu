@@ -294,9 +294,12 @@ int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, int M, 
 //   gather batch:  [length d][32 left-cell offsets y (M + 1) + 2 xp, or ~0][d x 32 entries, or ~0]
 //   idx[ci * 8 + w] = (zero list offset, zero steps, first batch offset, batches), offsets from the
 //   channel block's start; chan[ci] = (block start, block words)
+// Channels are built in parallel on up to `threads` host threads (0: up to 16, or the hardware's
+// count); the table does not depend on the thread count.  A host allocation failure returns
+// EPIC_ERR_NOMEM, a layout the format cannot hold EPIC_ERR_UNSUPPORTED.
 int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, int P, const std::vector<int> &chans,
                        std::vector<uint32_t> &tab, std::vector<int4> &idx, std::vector<int2> &chan,
-                       std::vector<unsigned long long> &rowmask)
+                       std::vector<unsigned long long> &rowmask, int threads)
 {
     constexpr int W = 8;
     const int h = (K - 1) / 2, S = M + 1, MP = M / 2;
@@ -415,17 +418,21 @@ int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, in
         return true;
     };
     std::atomic<int> next{0};
-    std::atomic<bool> ok{true};
+    std::atomic<bool> ok{true}, nomem{false};
     auto worker = [&]() {
         for (int ci; ok && (ci = next++) < nc;) {
             try {
                 if (!build_one(ci)) ok = false;
+            } catch (const std::bad_alloc &) {
+                nomem = true;
+                ok = false;
             } catch (...) {
                 ok = false;
             }
         }
     };
-    const int nt = std::max(1, std::min({nc, 16, static_cast<int>(std::thread::hardware_concurrency())}));
+    const int nt = threads > 0 ? std::min(nc, threads)
+                               : std::max(1, std::min({nc, 16, static_cast<int>(std::thread::hardware_concurrency())}));
     std::vector<std::thread> pool;
     for (int i = 1; i < nt; i++) {
         try {
@@ -436,7 +443,7 @@ int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, in
     }
     worker();
     for (auto &th : pool) th.join();
-    if (!ok) return EPIC_ERR_UNSUPPORTED;
+    if (!ok) return nomem ? EPIC_ERR_NOMEM : EPIC_ERR_UNSUPPORTED;
     for (int ci = 0; ci < nc; ci++) {
         const size_t start = tab.size();
         if (start + blocks[ci].size() > 0x7FFFFFFFull) return EPIC_ERR_UNSUPPORTED;

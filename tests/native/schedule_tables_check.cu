@@ -56,6 +56,21 @@ int main(int argc, char **argv)
     std::vector<int2> chan;
     std::vector<unsigned long long> rows;
     CHECK(epic::build_gather_table(cells, A, K, M, P, chans, tab, idx, chan, rows) == EPIC_OK, "gather build failed");
+    {   // the same table from one host thread and from three
+        for (int nt : {1, 3}) {
+            std::vector<uint32_t> tab1;
+            std::vector<int4> idx1;
+            std::vector<int2> chan1;
+            std::vector<unsigned long long> rows1;
+            CHECK(epic::build_gather_table(cells, A, K, M, P, chans, tab1, idx1, chan1, rows1, nt) == EPIC_OK,
+                  "gather build on %d threads failed", nt);
+            bool same = tab1 == tab && rows1 == rows && idx1.size() == idx.size() && chan1.size() == chan.size();
+            for (size_t i = 0; same && i < idx.size(); i++)
+                same = idx1[i].x == idx[i].x && idx1[i].y == idx[i].y && idx1[i].z == idx[i].z && idx1[i].w == idx[i].w;
+            for (size_t i = 0; same && i < chan.size(); i++) same = chan1[i].x == chan[i].x && chan1[i].y == chan[i].y;
+            CHECK(same, "gather table built on %d threads differs from the default build", nt);
+        }
+    }
     for (int ci = 0; ci < C && g_bad == 0; ci++) {
         std::multiset<long long> want, got;
         unsigned long long want_rows = 0;
