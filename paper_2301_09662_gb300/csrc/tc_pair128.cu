@@ -36,13 +36,17 @@
 // lo), the channel's gather lists, calibrated voltages, gains, tap pairs.
 //
 // Warps 0-7 (TMEM warps), iteration t: wait for the row stage of t, D1 -> H16
-// (hy 0) and arrive on bar_h; unpack sample t+1 and grid the first half of
-// their lists; wait for the column stage of (t, 0), D1 -> H16 (hy 1) and arrive
-// on bar_h; grid the second half and arrive on bar_g; products of (t, 0); wait
+// (hy 0) and arrive on bar_h; grid the first half of their lists of sample
+// t+1; wait for the column stage of (t, 0), D1 -> H16 (hy 1) and arrive on
+// bar_h; grid the second half and arrive on bar_g; products of (t, 0); wait
 // for the column stage of (t, 1) and add its products.  Warps 8-10 only grid:
 // after the row stage of t they take a larger share of sample t+1's lists (the
 // plan deals the lists so that each warp's work, conversions and products
-// included, is about equal) and arrive on bar_g.  Warp 11 issues, in order, the
+// included, is about equal) and arrive on bar_g; then, while the TMEM warps
+// form products, they unpack and calibrate sample t+2 (its bytes copied
+// asynchronously since the iteration began) into the other of two voltage
+// buffers, so no unpacking lies between a row stage and the next gridding.
+// Warp 11 issues, in order, the
 // row stage of t after bar_g, the column stage of (t, 0) after bar_h, that of
 // (t, 1) after the next bar_h, each committed to its own mbarrier.  Every wait
 // is bounded; a timeout is recorded in the plan's status word and stops the CTA.
@@ -67,6 +71,7 @@ constexpr int kGath = kGathW * 32;               // threads that grid (bar_g arr
 constexpr int kMmaWarp = kGathW;                 // the MMA-issuing warp
 constexpr int kPairThreads = (kGathW + 1) * 32;
 constexpr int kBarP = 6;                         // named barrier of the gridding warps
+constexpr int kBarH = 7;                         // named barrier of the gridding-only warps
 constexpr uint32_t kColD1 = 0, kColD2a = 128, kColD2b = 256, kColAcc1 = 384;
 constexpr uint16_t kNone = 0xFFFFu;
 
@@ -132,7 +137,7 @@ __device__ __forceinline__ void products(uint32_t lane_addr, uint32_t d2, int hh
 }
 
 // Shared memory (dynamic, 1024-aligned): X, G16, H16 (each hi then lo), then
-// es [A*P], gp [A*P], tw2 [K (K + 1) + 1][8] (float4: eight interleaved copies,
+// es [2][A*P], gp [A*P], tw2 [K (K + 1) + 1][8] (float4: eight interleaved copies,
 // lane l reads copy l mod 8, so the eight lanes of one 16-byte request never
 // share a bank group; the last slot is zero, for the lists' empty steps),
 // stage [(A*P + 3) / 4] (u32), the channel's lists [words] (u16).
@@ -157,8 +162,8 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     uint8_t *opH = smem + 4 * kPart;                          // [2 parts][32 KB] MN-major
     const int AP = A * P, KK = K * K, hk = (K - 1) / 2;
     const int APW = (AP + 3) >> 2;
-    float2 *es = reinterpret_cast<float2 *>(smem + 6 * kPart);
-    float2 *gp = es + AP;
+    float2 *es = reinterpret_cast<float2 *>(smem + 6 * kPart);   // sample t in es + (t & 1) AP
+    float2 *gp = es + 2 * AP;
     float4 *tw2 = reinterpret_cast<float4 *>(gp + AP);
     const int TPN = K * (K + 1);                             // the zero tap slot
     uint32_t *stage = reinterpret_cast<uint32_t *>(tw2 + 8 * (TPN + 1));
@@ -226,10 +231,6 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     for (int i = simt ? tid : 2 * static_cast<int>(kPart) / 16; i < 2 * static_cast<int>(kPart) / 16; i += kGath)
         reinterpret_cast<uint4 *>(opG)[i] = make_uint4(0u, 0u, 0u, 0u);
     for (int i = simt ? tid : my_chan.y; i < my_chan.y; i += kGath) stab[i] = __ldg(ptab + my_chan.x + i);
-    if (simt && t0 < t1) {
-        const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(t0) * C + c) * AP);
-        for (int w = tid; w < APW; w += kGath) stage[w] = row[w];
-    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
     if (simt && lane == 0) red[warp] = gmax;
@@ -325,7 +326,6 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         }
         __syncwarp();
     } else {
-        constexpr int kPreW = (kMaxAP / 4 + kGath - 1) / kGath;
         const int m = 32 * (warp & 3) + lane;          // TMEM warps: lane m = (pol, jy) in D1, (my, part) in D2
         const int hp = (warp >> 2) & 1;                 // which half of the columns
         const int part = lane >> 4;
@@ -335,21 +335,25 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         const float2 turn = twN[ky];
         const int4 my_idx = pidx[ci * kGathW + warp];   // (first batch, batches in half 1, second half's start, batches in half 2)
 
-        // a1, a2: unpack and calibrate sample t from the staged bytes
-        auto unpack = [&](int t) {
-            for (int i = tid; i < AP; i += kGath) {
-                const uint32_t b = reinterpret_cast<const uint8_t *>(stage)[i];
-                float2 e = cmul(gp[i], ci4_decode(b));
+        // a1, a2: unpack and calibrate sample t into es + (t & 1) AP, from the bytes at `src`
+        // (global or staged), by threads first, first + stride, ...
+        auto unpack = [&](int t, const uint8_t *src, int first, int stride) {
+            float2 *dst = es + (t & 1) * AP;
+            for (int i = first; i < AP; i += stride) {
+                float2 e = cmul(gp[i], ci4_decode(src[i]));
                 if (dtab) e = cmul(e, delay_phase(dtab[static_cast<size_t>(t) * A + i / P], dfreq[c]));
-                es[i] = e;
+                dst[i] = e;
             }
         };
+        auto bytes_of = [&](int t) { return v + (static_cast<size_t>(t) * C + c) * AP; };
+        const bool helper = !tmw;
+        const int htid = tid - kSimtP;                  // helpers: 0 .. 32 kPairHelpers - 1
         // a3: gather gridding of n batches from offset `at` (u16 units) straight into G16.  A
         // batch is [d][32 G16 byte offsets of the lanes' cell pairs (pol 0, Re, hi part), or
         // 0xFFFF][d x 32 entries tp << 10 | a]; empty steps name the zero tap slot and antenna 0.
-        auto gather = [&](int at, int n) {
+        auto gather = [&](int at, int n, int t) {
             const uint16_t *bt = stab + at;
-            const float4 *es4 = reinterpret_cast<const float4 *>(es);
+            const float4 *es4 = reinterpret_cast<const float4 *>(es + (t & 1) * AP);
             const float4 *tw8 = tw2 + (lane & 7);
             const uint32_t empty = static_cast<uint32_t>(TPN) << 10;
             for (int b = 0; b < n; b++) {
@@ -441,20 +445,11 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             tc::fence_before_sync();
             tc::mbar_arrive(&bar_h);
         };
-        auto load_stage = [&](int t, uint32_t (&pre)[kPreW]) {
-            const uint32_t *row = reinterpret_cast<const uint32_t *>(v + (static_cast<size_t>(t) * C + c) * AP);
-#pragma unroll
-            for (int r = 0; r < kPreW; r++) {
-                const int w = tid + r * kGath;
-                pre[r] = (t < t1 && w < APW) ? __ldg(row + w) : 0u;
-            }
-        };
-        auto put_stage = [&](const uint32_t (&pre)[kPreW]) {
-#pragma unroll
-            for (int r = 0; r < kPreW; r++) {
-                const int w = tid + r * kGath;
-                if (w < APW) stage[w] = pre[r];
-            }
+        // helpers: the bytes of sample t copied asynchronously into the stage
+        auto stage_async = [&](int t) {
+            if (t >= t1) return;
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(bytes_of(t));
+            for (int w = htid; w < APW; w += 32 * kPairHelpers) tc::cp_async4(stage + w, row + w);
         };
         auto fail = [&]() {
             atomicOr(status, kStatusTimeout);
@@ -465,15 +460,13 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
 #pragma unroll
         for (int j = 0; j < 16; j++) acc0[j] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-        // prologue: sample t0 gridded into G16, the bytes of t0 + 1 staged
+        // prologue: samples t0 and t0 + 1 unpacked, t0 gridded into G16
         if (t0 < t1) {
-            unpack(t0);
+            unpack(t0, bytes_of(t0), tid, kGath);
+            if (t0 + 1 < t1) unpack(t0 + 1, bytes_of(t0 + 1), tid, kGath);
             tc::named_bar_sync(kBarP, kGath);
-            uint32_t pre[kPreW];
-            load_stage(t0 + 1, pre);
-            gather(my_idx.x, my_idx.y);
-            gather(my_idx.z, my_idx.w);
-            put_stage(pre);
+            gather(my_idx.x, my_idx.y, t0);
+            gather(my_idx.z, my_idx.w, t0);
             tc::fence_proxy_async();
             tc::fence_before_sync();
             tc::mbar_arrive(&bar_g);
@@ -482,8 +475,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         uint32_t p1 = 0, p2a = 0, p2b = 0;
         for (int t = t0; t < t1; t++) {
             const bool nxt = t + 1 < t1;
-            uint32_t pre[kPreW];
-            load_stage(t + 2, pre);
+            if (helper) stage_async(t + 2);
             // row stage of t done: G16 is free for sample t + 1; the TMEM warps convert D1 -> H16
             // for class hy = 0
             if (!abort_flag) {
@@ -494,11 +486,8 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 }
             }
             p1 ^= 1u;
-            if (nxt) unpack(t + 1);
-            tc::named_bar_sync(kBarP, kGath);           // es of t + 1 complete; the staged bytes are free
-            put_stage(pre);
             if (tmw) {
-                if (nxt && !abort_flag) gather(my_idx.x, my_idx.y);
+                if (nxt && !abort_flag) gather(my_idx.x, my_idx.y, t + 1);
                 // column stage of (t, 0) done: H16 is free -> H16 for class hy = 1
                 if (!abort_flag) {
                     if (!tc::mbar_wait(&bar_m2a, p2a, wait_budget)) fail();
@@ -510,11 +499,18 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 p2a ^= 1u;
             }
             if (nxt && !abort_flag) {
-                if (tmw) gather(my_idx.z, my_idx.w);
-                else gather(my_idx.x, my_idx.y);
+                if (tmw) gather(my_idx.z, my_idx.w, t + 1);
+                else gather(my_idx.x, my_idx.y, t + 1);
                 tc::fence_proxy_async();
                 tc::fence_before_sync();
                 tc::mbar_arrive(&bar_g);
+            }
+            if (helper && t + 2 < t1) {
+                // sample t + 2 into the buffer sample t used (all gridding of t ended at the last
+                // iteration's closing barrier); the closing barrier below publishes it
+                tc::cp_async_wait_all();
+                tc::named_bar_sync(kBarH, 32 * kPairHelpers);   // every helper's copies landed
+                unpack(t + 2, reinterpret_cast<const uint8_t *>(stage), htid, 32 * kPairHelpers);
             }
             if (tmw) {
                 // a5, a6: products of (t, 0) from D2a (complete: waited above), then of (t, 1)
@@ -532,6 +528,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             if (tc::named_bar_or(kBarP, kGath, abort_flag != 0)) break;   // the same answer in every warp
         }
 
+        if (helper) tc::cp_async_wait_all();             // no copy outlives the loop
         // ---- partial images of both classes (undo the FP16 scale exactly)
         tc::fence_after_sync();
         if (tmw) {
@@ -582,7 +579,7 @@ size_t pair_smem(int A, int K, int words)
 {
     const int AP = A * 2;
     size_t b = 6 * static_cast<size_t>(kPart);
-    b += sizeof(float2) * 2 * static_cast<size_t>(AP) + sizeof(float4) * 8 * (static_cast<size_t>(K) * (K + 1) + 1);
+    b += sizeof(float2) * 3 * static_cast<size_t>(AP) + sizeof(float4) * 8 * (static_cast<size_t>(K) * (K + 1) + 1);
     b += sizeof(uint32_t) * ((AP + 3) / 4) + sizeof(uint16_t) * static_cast<size_t>(words);
     return (b + 15) & ~static_cast<size_t>(15);
 }

@@ -231,5 +231,13 @@ __device__ __forceinline__ bool named_bar_or(int id, int count, bool pred)
     return r != 0;
 }
 
+// 4-byte asynchronous global -> shared copy (both 4-byte aligned), and the wait
+// for all of this thread's copies
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 }  // namespace tc
 }  // namespace epic
