@@ -6,20 +6,23 @@
 // class phase is separable, w_128^{kx hx} w_128^{ky hy}.  A CTA owns the two
 // classes (hx, 0) and (hx, 1): the x factor goes into the gridding (into the
 // gains per antenna and the taps per column), so both classes share one
-// gridded sample and one row transform; the y factor is applied to each
-// folded row after the row transform.  That needs one unfolded row ky per
-// folded row jy among the cells any footprint touches (the aperture spans at
-// most 64 rows, as with 2x padding); the plan checks it per channel and lists
-// the rows with ky >= 64, and then w_128^{ky} = w_128^{jy} (-1)^{ky >= 64}.
+// gridded sample, one row transform and one conversion of its result; the y
+// factor turns each folded input row of the column transform, and so goes
+// into that transform's operand.  That needs one unfolded row ky per folded
+// row jy among the cells any footprint touches (the aperture spans at most 64
+// rows, as with 2x padding); the plan checks it per channel and lists the rows
+// with ky >= 64, and then w_128^{ky} = w_128^{jy} (-1)^{ky >= 64}.
 //
 //   row stage     D1[(pol, jy)][r] = sum_k G16[(pol, jy)][k] X[r][k]
 //                 G16 = the gridded sample in FP16 hi + lo (shared memory,
 //                 K-major, A operand), X = the 64-point DFT in real 2 x 2 block
 //                 form (shared memory, K-major, B operand)
-//   column stage  D2_hy[r][(mx, pol)] = sum_k X[r][k] H16_hy[(mx, pol)][k]
-//                 H16_hy = D1 with row jy turned by w_128^{ky hy}, as FP16 hi + lo
-//                 (shared memory, MN-major, B operand); hy = 0 then 1 in one
-//                 buffer
+//   column stage  D2_hy[r][n] = sum_k X_hy[r][k] H16[n][k],  n = (mx, pol)
+//                 H16 = D1 as FP16 hi + lo (shared memory, MN-major, B
+//                 operand); X_0 = X (shared memory), X_1 = X with input row jy
+//                 turned by w_128^{ky} (TMEM, A operand, built once per CTA).
+//                 The two classes' column stages run back to back, class 1's
+//                 into D1's columns (D1 has been converted by then).
 //
 // Both stages take three MMAs per 16-deep k-block (hi hi + hi lo + lo hi).
 //
@@ -30,28 +33,28 @@
 // same cells every sample and the transforms run in TMEM, so cells no list
 // names stay zero from the start.
 //
-// TMEM columns: D1 [0,128), D2 of class hy = 0 [128,256), of hy = 1
+// TMEM columns: D1, later D2_1 [0,128), X_1 [128,256) (hi, lo), D2_0
 // [256,384), the time sums of class hy = 1 [384,512); class hy = 0 keeps its
-// time sums in registers.  Shared memory: X, G16 and H16 (64 KB each, hi and
-// lo), the channel's gather lists, calibrated voltages, gains, tap pairs.
+// time sums in registers.  Shared memory: X, G16 and
+// H16 (64 KB each, hi and lo), the channel's gather lists, calibrated
+// voltages (two samples), gains, tap pairs.
 //
 // Warps 0-7 (TMEM warps), iteration t: wait for the row stage of t, D1 -> H16
-// (hy 0) and arrive on bar_h; grid the first half of their lists of sample
-// t+1; wait for the column stage of (t, 0), D1 -> H16 (hy 1) and arrive on
-// bar_h; grid the second half and arrive on bar_g; products of (t, 0); wait
-// for the column stage of (t, 1) and add its products.  Warps 8-10 only grid:
-// after the row stage of t they take a larger share of sample t+1's lists (the
-// plan deals the lists so that each warp's work, conversions and products
-// included, is about equal) and arrive on bar_g; then, while the TMEM warps
-// form products, they unpack and calibrate sample t+2 (its bytes copied
-// asynchronously since the iteration began) into the other of two voltage
-// buffers, so no unpacking lies between a row stage and the next gridding.
-// Warp 11 issues, in order, the
-// row stage of t after bar_g, the column stage of (t, 0) after bar_h, that of
-// (t, 1) after the next bar_h, each committed to its own mbarrier.  Every wait
-// is bounded; a timeout is recorded in the plan's status word and stops the CTA.
-// Twelve warps cost no registers over nine: a scheduler holding three warps
-// already limits a thread to 168.
+// and arrive on bar_h; grid the first half of their lists of sample t+1; wait
+// for class 0's column stage and add its products; grid the second half and
+// arrive on bar_g; wait for class 1's column stage, add its products and
+// arrive on bar_free (D1's columns are free again).  Warps 8-10 only grid: after the row stage of t
+// they take a larger share of sample t+1's lists (the plan deals the lists so
+// that each warp's work, conversions and products included, is about equal)
+// and arrive on bar_g; then, while the TMEM warps form products, they unpack
+// and calibrate sample t+2 (its bytes copied asynchronously since the
+// iteration began) into the other of two voltage buffers, so no unpacking lies
+// between a row stage and the next gridding.  Warp 11 issues, in order, the
+// row stage of t after bar_g (and, from the second sample on, bar_free), then
+// after bar_h the column stages of classes 0 and 1, each committed to its own
+// mbarrier.  Every wait is bounded; a timeout is recorded in the plan's
+// status word and stops the CTA.  Twelve warps cost no registers over nine: a
+// scheduler holding three warps already limits a thread to 168.
 #include <algorithm>
 
 #include "dft_small.cuh"
@@ -72,12 +75,12 @@ constexpr int kMmaWarp = kGathW;                 // the MMA-issuing warp
 constexpr int kPairThreads = (kGathW + 1) * 32;
 constexpr int kBarP = 6;                         // named barrier of the gridding warps
 constexpr int kBarH = 7;                         // named barrier of the gridding-only warps
-constexpr uint32_t kColD1 = 0, kColD2a = 128, kColD2b = 256, kColAcc1 = 384;
+constexpr uint32_t kColD1 = 0, kColXt = 128, kColD2 = 256, kColAcc1 = 384;
 constexpr uint16_t kNone = 0xFFFFu;
 
 // XX, YY, XY of one sample added to the time sums of one class: TMEM lanes
-// 32 (w mod 4) + l = (my, part), columns 32 hh .. of each polarisation
-// (hh = w / 4) of D2 at column d2.  Lane l keeps pixels mx = 32 hh + 16 part + j,
+// 32 (w mod 4) + l = (my, part), the column block 64 hh .. (hh = w / 4,
+// pixels mx = 32 hh ..) of the column stage's result at column d2.  Lane l keeps pixels mx = 32 hh + 16 part + j,
 // j < 16; Re and Im of a pixel are exchanged between lanes l and l ^ 16 by one
 // shuffle.  Two halves of 8 pixels (x8 loads of the own and the partner's
 // columns) bound the live registers.  Class hy = 0 sums into registers (acc),
@@ -87,15 +90,15 @@ __device__ __forceinline__ void products(uint32_t lane_addr, uint32_t d2, int hh
 {
 #pragma unroll
     for (int half = 0; half < 2; half++) {
-        // columns 8 half .. (part 0's pixels) and 16 + 8 half .. (part 1's) of each polarisation;
-        // a TMEM load's address is warp-uniform, so each lane then picks its own part and the
-        // one its partner needs
+        // columns 8 half .. (part 0's pixels) and 16 + 8 half .. (part 1's) of each polarisation
+        // in the column block 64 hh .. of D2 (polarisation 0 at + 0-31, 1 at + 32-63); a TMEM load's
+        // address is warp-uniform, so each lane then picks its own part and the one its partner needs
         uint32_t x0[8], y0[8], x1[8], y1[8];
-        const uint32_t base = lane_addr + d2 + 32 * hh + 8 * half;
+        const uint32_t base = lane_addr + d2 + 64 * hh + 8 * half;
         tc::tmem_ld8_issue(base, x0);
         tc::tmem_ld8_issue(base + 16, x1);
-        tc::tmem_ld8_issue(base + 64, y0);
-        tc::tmem_ld8_issue(base + 64 + 16, y1);
+        tc::tmem_ld8_issue(base + 32, y0);
+        tc::tmem_ld8_issue(base + 48, y1);
         uint32_t s[32];
         const uint32_t at = lane_addr + kColAcc1 + 64 * hh + 32 * half;
         if constexpr (!REG) tc::tmem_ld32_issue(at, s);
@@ -168,7 +171,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     const int TPN = K * (K + 1);                             // the zero tap slot
     uint32_t *stage = reinterpret_cast<uint32_t *>(tw2 + 8 * (TPN + 1));
     uint16_t *stab = reinterpret_cast<uint16_t *>(stage + APW);
-    __shared__ __align__(8) uint64_t bar_x, bar_g, bar_h, bar_m1, bar_m2a, bar_m2b;
+    __shared__ __align__(8) uint64_t bar_x, bar_g, bar_h, bar_free, bar_m1, bar_m2[2];
     __shared__ uint32_t tmem_slot;
     __shared__ float red[kGathW];
     __shared__ int abort_flag;
@@ -192,8 +195,9 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         tc::mbar_init(&bar_g, kGath);
         tc::mbar_init(&bar_h, kSimtP);
         tc::mbar_init(&bar_m1, 1);
-        tc::mbar_init(&bar_m2a, 1);
-        tc::mbar_init(&bar_m2b, 1);
+        tc::mbar_init(&bar_free, kSimtP);
+        tc::mbar_init(&bar_m2[0], 1);
+        tc::mbar_init(&bar_m2[1], 1);
         tc::fence_mbar_init();
     }
     __syncthreads();
@@ -260,6 +264,27 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         const uint32_t acc = lane_addr + kColAcc1 + 64 * (warp >> 2);
         tc::tmem_st32_issue(acc, z);
         tc::tmem_st32_issue(acc + 32, z);
+        // the column-stage operand of class hy = 1 (A operand in TMEM): X with input row jy
+        // turned by w_128^{ky}, ky = jy + 64 [row listed as upper], i.e. the rotation by
+        // w_128^{2 jy my + ky} in real 2 x 2 form.  Lane = output (my, part), columns k / 2 of
+        // k = 64 im_in + jy (hi, then lo 64 columns on); warp half w / 4 = im_in.
+        const int myo = 16 * (warp & 3) + (lane & 15), prt = lane >> 4, imin = warp >> 2;
+        const unsigned long long up = upper[ci];
+        uint32_t xh[32], xl[32];
+#pragma unroll
+        for (int w = 0; w < 32; w++) {
+            float a2[2];
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                const int j = 2 * w + u;
+                const int kyj = j + (((up >> j) & 1ull) ? 64 : 0);
+                const float2 e = twN[(2 * j * myo + kyj) & (N - 1)];
+                a2[u] = prt == 0 ? (imin ? -e.y : e.x) : (imin ? e.x : e.y);
+            }
+            split_pair<kBF16, kSplit>(a2[0], a2[1], xh[w], xl[w]);
+        }
+        tc::tmem_st32_issue(lane_addr + kColXt + 32 * imin, xh);
+        if constexpr (kSplit) tc::tmem_st32_issue(lane_addr + kColXt + 64 + 32 * imin, xl);
         tc::tmem_wait_st();
     }
     tc::fence_before_sync();
@@ -275,10 +300,14 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         // after the next two completions of bar_h
         if (lane == 0) {
             bool ok = tc::mbar_wait(&bar_x, 0, wait_budget);
-            uint32_t pg = 0, ph = 0;
+            uint32_t pg = 0, ph = 0, pf = 0;
             for (int t = t0; t < t1 && ok; t++) {
                 ok = tc::mbar_wait(&bar_g, pg, wait_budget) && !abort_flag;
                 pg ^= 1u;
+                if (ok && t > t0) {   // the products of (t - 1, 1) have read D1's columns
+                    ok = tc::mbar_wait(&bar_free, pf, wait_budget) && !abort_flag;
+                    pf ^= 1u;
+                }
                 if (!ok) break;
                 tc::fence_after_sync();
                 if (!withhold_mma) {
@@ -296,26 +325,37 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                     }
                     tc::mma_commit(&bar_m1);
                 }
-                for (int hy = 0; hy < 2 && ok; hy++) {
-                    ok = tc::mbar_wait(&bar_h, ph, wait_budget) && !abort_flag;
-                    ph ^= 1u;
-                    if (!ok) break;
-                    tc::fence_after_sync();
-                    if (!withhold_mma) {
-                        const uint32_t d2 = taddr + (hy ? kColD2b : kColD2a);
+                ok = tc::mbar_wait(&bar_h, ph, wait_budget) && !abort_flag;
+                ph ^= 1u;
+                if (!ok) break;
+                tc::fence_after_sync();
+                if (!withhold_mma) {
+                    // class hy = 0: A = X (shared memory) into D2; class hy = 1: A = the turned X in
+                    // TMEM into D1's columns (D1 has been converted)
+                    for (int hy = 0; hy < 2; hy++) {
+                        const uint32_t d2 = taddr + (hy ? kColD1 : kColD2);
 #pragma unroll
                         for (int kb = 0; kb < 8; kb++) {
-                            const uint64_t x_hi = tc::smem_desc(x_base + kb * 256, kLBO, kSBO);
                             const uint64_t h_hi = tc::smem_desc(h_base + kb * 256, kLBO, kSBO);
-                            tc::mma_f16(d2, x_hi, h_hi, idesc_col, kb > 0 ? 1u : 0u);
-                            if constexpr (kSplit) {
-                                const uint64_t x_lo = tc::smem_desc(x_base + kPart + kb * 256, kLBO, kSBO);
-                                const uint64_t h_lo = tc::smem_desc(h_base + kPart + kb * 256, kLBO, kSBO);
-                                tc::mma_f16(d2, x_hi, h_lo, idesc_col, 1u);
-                                tc::mma_f16(d2, x_lo, h_hi, idesc_col, 1u);
+                            const uint64_t h_lo = tc::smem_desc(h_base + kPart + kb * 256, kLBO, kSBO);
+                            if (hy == 0) {
+                                const uint64_t x_hi = tc::smem_desc(x_base + kb * 256, kLBO, kSBO);
+                                tc::mma_f16(d2, x_hi, h_hi, idesc_col, kb > 0 ? 1u : 0u);
+                                if constexpr (kSplit) {
+                                    const uint64_t x_lo = tc::smem_desc(x_base + kPart + kb * 256, kLBO, kSBO);
+                                    tc::mma_f16(d2, x_hi, h_lo, idesc_col, 1u);
+                                    tc::mma_f16(d2, x_lo, h_hi, idesc_col, 1u);
+                                }
+                            } else {
+                                const uint32_t a_hi = taddr + kColXt + kb * 8;
+                                mma_ts(d2, a_hi, h_hi, idesc_col, kb > 0 ? 1u : 0u);
+                                if constexpr (kSplit) {
+                                    mma_ts(d2, a_hi, h_lo, idesc_col, 1u);
+                                    mma_ts(d2, a_hi + 64, h_hi, idesc_col, 1u);
+                                }
                             }
                         }
-                        tc::mma_commit(hy ? &bar_m2b : &bar_m2a);
+                        tc::mma_commit(&bar_m2[hy]);
                     }
                 }
             }
@@ -330,9 +370,6 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         const int hp = (warp >> 2) & 1;                 // which half of the columns
         const int part = lane >> 4;
         const int pol = m >> 6, jy = m & 63;
-        // the class-y turn of row jy: w_128^{ky}, ky = jy + 64 [row listed as upper]
-        const int ky = jy + (((upper[ci] >> jy) & 1ull) ? 64 : 0);
-        const float2 turn = twN[ky];
         const int4 my_idx = pidx[ci * kGathW + warp];   // (first batch, batches in half 1, second half's start, batches in half 2)
 
         // a1, a2: unpack and calibrate sample t into es + (t & 1) AP, from the bytes at `src`
@@ -406,10 +443,11 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 bt += 33 + 32 * d;
             }
         };
-        // D1 (row transform of the sample) -> H16 for class hy: row jy turned by w_128^{ky hy}.
-        // Thread: lane m = (pol, jy), columns 64 hp .. 64 hp + 63 = Re and Im of mx = 32 hp .. 32 hp + 31.
-        auto to_h16 = [&](int hy) {
-            const float2 f = hy ? turn : make_float2(1.f, 0.f);
+        // D1 (row transform of the sample) -> H16, shared by both classes (class hy = 1's turn is in
+        // its column-stage operand).  Thread: lane m = (pol, jy), columns 64 hp .. 64 hp + 63 = Re
+        // and Im of mx = 32 hp .. 32 hp + 31; H16 row n = 64 hp + 32 pol + (mx - 32 hp), so each
+        // half buffer of the column stage reads one contiguous N = 64 block.
+        auto to_h16 = [&]() {
 #pragma unroll
             for (int q = 0; q < 2; q++) {
                 uint32_t d[32];
@@ -421,17 +459,11 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                     uint32_t rh[4], rl[4], ih[4], il[4];
 #pragma unroll
                     for (int w = 0; w < 4; w++) {
-                        float2 z[2];
-#pragma unroll
-                        for (int u = 0; u < 2; u++) {
-                            const int i = 8 * g8 + 2 * w + u;
-                            z[u] = make_float2(__uint_as_float(d[i]), __uint_as_float(d[16 + i]));
-                            if (hy) z[u] = cmul(z[u], f);
-                        }
-                        split_pair<kBF16, kSplit>(z[0].x, z[1].x, rh[w], rl[w]);
-                        split_pair<kBF16, kSplit>(z[0].y, z[1].y, ih[w], il[w]);
+                        const int i = 8 * g8 + 2 * w;
+                        split_pair<kBF16, kSplit>(__uint_as_float(d[i]), __uint_as_float(d[i + 1]), rh[w], rl[w]);
+                        split_pair<kBF16, kSplit>(__uint_as_float(d[16 + i]), __uint_as_float(d[17 + i]), ih[w], il[w]);
                     }
-                    const int n0 = 32 * hp + 16 * q + 8 * g8 + 64 * pol;
+                    const int n0 = 64 * hp + 32 * pol + 16 * q + 8 * g8;
                     *reinterpret_cast<uint4 *>(opH + mn_off(n0, jy)) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
                     *reinterpret_cast<uint4 *>(opH + mn_off(n0, 64 + jy)) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
                     if constexpr (kSplit) {
@@ -472,31 +504,29 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             tc::mbar_arrive(&bar_g);
             tc::named_bar_sync(kBarP, kGath);
         }
-        uint32_t p1 = 0, p2a = 0, p2b = 0;
+        uint32_t p1 = 0, p2 = 0;
         for (int t = t0; t < t1; t++) {
             const bool nxt = t + 1 < t1;
             if (helper) stage_async(t + 2);
             // row stage of t done: G16 is free for sample t + 1; the TMEM warps convert D1 -> H16
-            // for class hy = 0
             if (!abort_flag) {
                 if (!tc::mbar_wait(&bar_m1, p1, wait_budget)) fail();
                 else if (tmw) {
                     tc::fence_after_sync();
-                    to_h16(0);
+                    to_h16();
                 }
             }
             p1 ^= 1u;
             if (tmw) {
                 if (nxt && !abort_flag) gather(my_idx.x, my_idx.y, t + 1);
-                // column stage of (t, 0) done: H16 is free -> H16 for class hy = 1
+                // a5, a6: products of (t, 0)
                 if (!abort_flag) {
-                    if (!tc::mbar_wait(&bar_m2a, p2a, wait_budget)) fail();
+                    if (!tc::mbar_wait(&bar_m2[0], p2, wait_budget)) fail();
                     else {
                         tc::fence_after_sync();
-                        to_h16(1);
+                        products<true>(lane_addr, kColD2, hp, part, acc0);
                     }
                 }
-                p2a ^= 1u;
             }
             if (nxt && !abort_flag) {
                 if (tmw) gather(my_idx.z, my_idx.w, t + 1);
@@ -512,18 +542,17 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 tc::named_bar_sync(kBarH, 32 * kPairHelpers);   // every helper's copies landed
                 unpack(t + 2, reinterpret_cast<const uint8_t *>(stage), htid, 32 * kPairHelpers);
             }
-            if (tmw) {
-                // a5, a6: products of (t, 0) from D2a (complete: waited above), then of (t, 1)
-                if (!abort_flag) products<true>(lane_addr, kColD2a, hp, part, acc0);
-                if (!abort_flag) {
-                    if (!tc::mbar_wait(&bar_m2b, p2b, wait_budget)) fail();
-                    else {
-                        tc::fence_after_sync();
-                        products<false>(lane_addr, kColD2b, hp, part, acc0);
-                    }
+            if (tmw && !abort_flag) {
+                // products of (t, 1), from D1's columns, which are then free for the row stage of t + 1
+                if (!tc::mbar_wait(&bar_m2[1], p2, wait_budget)) fail();
+                else {
+                    tc::fence_after_sync();
+                    products<false>(lane_addr, kColD1, hp, part, acc0);
+                    tc::fence_before_sync();
+                    tc::mbar_arrive(&bar_free);
                 }
-                p2b ^= 1u;
             }
+            p2 ^= 1u;
             tc::fence_before_sync();
             if (tc::named_bar_or(kBarP, kGath, abort_flag != 0)) break;   // the same answer in every warp
         }
@@ -564,10 +593,10 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     if (tid == kMmaWarp * 32 && abort_flag) {
         tc::mbar_wait(&bar_m1, 0, wait_budget);
         tc::mbar_wait(&bar_m1, 1, wait_budget);
-        tc::mbar_wait(&bar_m2a, 0, wait_budget);
-        tc::mbar_wait(&bar_m2a, 1, wait_budget);
-        tc::mbar_wait(&bar_m2b, 0, wait_budget);
-        tc::mbar_wait(&bar_m2b, 1, wait_budget);
+        for (int i = 0; i < 2; i++) {
+            tc::mbar_wait(&bar_m2[i], 0, wait_budget);
+            tc::mbar_wait(&bar_m2[i], 1, wait_budget);
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -615,8 +644,9 @@ int pair_dispatch(int precision, F &&f)
 // warp with the least work so far (a batch costs 4 d + 6, about 37 cycles a
 // unit): the 8 TMEM warps start with kTmemLoad units for their conversions and
 // products, the gridding-only warps with none.  A TMEM warp's batches are split
-// in two halves of about equal work for the two gridding phases of an
-// iteration; a gridding-only warp has one list.  idx[ci * kPairGatherWarps + w]
+// in two parts for the two gridding phases of an iteration, about two thirds
+// of the work in the first (it overlaps class 0's column stage, the second
+// only class 1's); a gridding-only warp has one list.  idx[ci * kPairGatherWarps + w]
 // = (first half's offset, its batches, second half's offset, its batches),
 // offsets in words from the channel block's start; chan[ci] = (block start,
 // block words).  The upper mask of a channel lists the folded rows whose cells
@@ -628,7 +658,7 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
                       std::vector<int2> &chan, std::vector<unsigned long long> &upper)
 {
     constexpr int M = 64, S = M + 1, W32 = 8, W = kPairGatherWarps, kWindow = 96;
-    constexpr long long kTmemLoad = 90;
+    constexpr long long kTmemLoad = 120;
     if (A > 1024 || K * (K + 1) > 63) return EPIC_ERR_UNSUPPORTED;
     const int nc = static_cast<int>(chans.size()), h = (K - 1) / 2;
     tab.clear();
@@ -765,7 +795,7 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
             if (w < 8) {
                 long long run = 0;
                 split = 0;
-                while (split < per[w].size() && 2 * (run + 4LL * blen[per[w][split]] + 6) <= total)
+                while (split < per[w].size() && 3 * (run + 4LL * blen[per[w][split]] + 6) <= 2 * total)
                     run += 4LL * blen[per[w][split++]] + 6;
             }
             int4 &o = idx[static_cast<size_t>(ci) * W + w];
