@@ -22,7 +22,11 @@
 //                 operand); X_0 = X (shared memory), X_1 = X with input row jy
 //                 turned by w_128^{ky} (TMEM, A operand, built once per CTA).
 //                 The two classes' column stages run back to back, class 1's
-//                 into D1's columns (D1 has been converted by then).
+//                 into D1's columns (D1 has been converted by then), class 0's
+//                 into a second buffer; the next sample's row stage takes that
+//                 one once class 0's products have read it, so the two buffers
+//                 swap roles every sample and no stage waits for the products
+//                 of the stage before it.
 //
 // Both stages take three MMAs per 16-deep k-block (hi hi + hi lo + lo hi).
 //
@@ -33,29 +37,31 @@
 // same cells every sample and the transforms run in TMEM, so cells no list
 // names stay zero from the start.
 //
-// TMEM columns: D1, later D2_1 [0,128), X_1 [128,256) (hi, lo), D2_0
-// [256,384), the time sums of class hy = 1 [384,512); class hy = 0 keeps its
-// time sums in registers.  Shared memory: X, G16 and
+// TMEM columns: buffers P [0,128) and Q [256,384) (sample t: D1 and then D2_1
+// in R(t), D2_0 in A(t); R = P for even t, Q for odd), X_1 [128,256) (hi, lo),
+// the time sums of class hy = 1 [384,512); class hy = 0 keeps its time sums in
+// registers.  Shared memory: X, G16 and
 // H16 (64 KB each, hi and lo), the channel's gather lists, calibrated
 // voltages (two samples), gains, tap pairs.
 //
 // Warps 0-7 (TMEM warps), iteration t: wait for the row stage of t, D1 -> H16
-// and arrive on bar_h; grid the first half of their lists of sample t+1; wait
-// for class 0's column stage and add its products; grid the second half and
-// arrive on bar_g; wait for class 1's column stage, add its products and
-// arrive on bar_free (D1's columns are free again).  Warps 8-10 only grid: after the row stage of t
+// and arrive on bar_h; grid the first part of their lists of sample t+1; wait
+// for class 0's column stage, add its products and arrive on bar_fa; grid the
+// second part and arrive on bar_g; wait for class 1's column stage, add its
+// products and arrive on bar_fb.  Warps 8-10 only grid: after the row stage of t
 // they take a larger share of sample t+1's lists (the plan deals the lists so
 // that each warp's work, conversions and products included, is about equal)
 // and arrive on bar_g; then, while the TMEM warps form products, they unpack
 // and calibrate sample t+2 (its bytes copied asynchronously since the
 // iteration began) into the other of two voltage buffers, so no unpacking lies
 // between a row stage and the next gridding.  Warp 11 issues, in order, the
-// row stage of t after bar_g (and, from the second sample on, bar_free), then
-// after bar_h the column stages of classes 0 and 1, each committed to its own
-// mbarrier.  Every wait is bounded; a timeout is recorded in the plan's
+// row stage of t after bar_g (and, from the second sample on, bar_fa of
+// t - 1), then after bar_h (and bar_fb of t - 1) the column stages of classes
+// 0 and 1, each committed to its own mbarrier.  Every wait is bounded; a timeout is recorded in the plan's
 // status word and stops the CTA.  Twelve warps cost no registers over nine: a
 // scheduler holding three warps already limits a thread to 168.
 #include <algorithm>
+#include <cstdlib>
 
 #include "dft_small.cuh"
 #include "epic_internal.cuh"
@@ -75,7 +81,11 @@ constexpr int kMmaWarp = kGathW;                 // the MMA-issuing warp
 constexpr int kPairThreads = (kGathW + 1) * 32;
 constexpr int kBarP = 6;                         // named barrier of the gridding warps
 constexpr int kBarH = 7;                         // named barrier of the gridding-only warps
-constexpr uint32_t kColD1 = 0, kColXt = 128, kColD2 = 256, kColAcc1 = 384;
+constexpr uint32_t kColP = 0, kColXt = 128, kColQ = 256, kColAcc1 = 384;
+// sample t's row stage and class 1's column stage use buffer R(t), class 0's column stage A(t);
+// the two swap every sample
+__device__ __forceinline__ uint32_t col_r(int t) { return (t & 1) ? kColQ : kColP; }
+__device__ __forceinline__ uint32_t col_a(int t) { return (t & 1) ? kColP : kColQ; }
 constexpr uint16_t kNone = 0xFFFFu;
 
 // XX, YY, XY of one sample added to the time sums of one class: TMEM lanes
@@ -171,7 +181,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     const int TPN = K * (K + 1);                             // the zero tap slot
     uint32_t *stage = reinterpret_cast<uint32_t *>(tw2 + 8 * (TPN + 1));
     uint16_t *stab = reinterpret_cast<uint16_t *>(stage + APW);
-    __shared__ __align__(8) uint64_t bar_x, bar_g, bar_h, bar_free, bar_m1, bar_m2[2];
+    __shared__ __align__(8) uint64_t bar_x, bar_g, bar_h, bar_fa, bar_fb, bar_m1, bar_m2[2];
     __shared__ uint32_t tmem_slot;
     __shared__ float red[kGathW];
     __shared__ int abort_flag;
@@ -195,7 +205,8 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         tc::mbar_init(&bar_g, kGath);
         tc::mbar_init(&bar_h, kSimtP);
         tc::mbar_init(&bar_m1, 1);
-        tc::mbar_init(&bar_free, kSimtP);
+        tc::mbar_init(&bar_fa, kSimtP);
+        tc::mbar_init(&bar_fb, kSimtP);
         tc::mbar_init(&bar_m2[0], 1);
         tc::mbar_init(&bar_m2[1], 1);
         tc::fence_mbar_init();
@@ -304,10 +315,8 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             for (int t = t0; t < t1 && ok; t++) {
                 ok = tc::mbar_wait(&bar_g, pg, wait_budget) && !abort_flag;
                 pg ^= 1u;
-                if (ok && t > t0) {   // the products of (t - 1, 1) have read D1's columns
-                    ok = tc::mbar_wait(&bar_free, pf, wait_budget) && !abort_flag;
-                    pf ^= 1u;
-                }
+                if (ok && t > t0)   // R(t) = A(t - 1): the products of (t - 1, 0) have read it
+                    ok = tc::mbar_wait(&bar_fa, pf, wait_budget) && !abort_flag;
                 if (!ok) break;
                 tc::fence_after_sync();
                 if (!withhold_mma) {
@@ -315,25 +324,28 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                     for (int kb = 0; kb < 8; kb++) {
                         const uint64_t g_hi = tc::smem_desc(g_base + kb * 256, kLBO, kSBO);
                         const uint64_t x_hi = tc::smem_desc(x_base + kb * 256, kLBO, kSBO);
-                        tc::mma_f16(taddr + kColD1, g_hi, x_hi, idesc_row, kb > 0 ? 1u : 0u);
+                        tc::mma_f16(taddr + col_r(t), g_hi, x_hi, idesc_row, kb > 0 ? 1u : 0u);
                         if constexpr (kSplit) {
                             const uint64_t g_lo = tc::smem_desc(g_base + kPart + kb * 256, kLBO, kSBO);
                             const uint64_t x_lo = tc::smem_desc(x_base + kPart + kb * 256, kLBO, kSBO);
-                            tc::mma_f16(taddr + kColD1, g_hi, x_lo, idesc_row, 1u);
-                            tc::mma_f16(taddr + kColD1, g_lo, x_hi, idesc_row, 1u);
+                            tc::mma_f16(taddr + col_r(t), g_hi, x_lo, idesc_row, 1u);
+                            tc::mma_f16(taddr + col_r(t), g_lo, x_hi, idesc_row, 1u);
                         }
                     }
                     tc::mma_commit(&bar_m1);
                 }
                 ok = tc::mbar_wait(&bar_h, ph, wait_budget) && !abort_flag;
                 ph ^= 1u;
+                if (ok && t > t0)   // A(t) = R(t - 1): the products of (t - 1, 1) have read it
+                    ok = tc::mbar_wait(&bar_fb, pf, wait_budget) && !abort_flag;
+                if (t > t0) pf ^= 1u;
                 if (!ok) break;
                 tc::fence_after_sync();
                 if (!withhold_mma) {
-                    // class hy = 0: A = X (shared memory) into D2; class hy = 1: A = the turned X in
-                    // TMEM into D1's columns (D1 has been converted)
+                    // class hy = 0: A = X (shared memory) into A(t); class hy = 1: A = the turned X in
+                    // TMEM into R(t) (converted to H16 by now)
                     for (int hy = 0; hy < 2; hy++) {
-                        const uint32_t d2 = taddr + (hy ? kColD1 : kColD2);
+                        const uint32_t d2 = taddr + (hy ? col_r(t) : col_a(t));
 #pragma unroll
                         for (int kb = 0; kb < 8; kb++) {
                             const uint64_t h_hi = tc::smem_desc(h_base + kb * 256, kLBO, kSBO);
@@ -447,11 +459,11 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         // its column-stage operand).  Thread: lane m = (pol, jy), columns 64 hp .. 64 hp + 63 = Re
         // and Im of mx = 32 hp .. 32 hp + 31; H16 row n = 64 hp + 32 pol + (mx - 32 hp), so each
         // half buffer of the column stage reads one contiguous N = 64 block.
-        auto to_h16 = [&]() {
+        auto to_h16 = [&](uint32_t d1) {
 #pragma unroll
             for (int q = 0; q < 2; q++) {
                 uint32_t d[32];
-                tc::tmem_ld32_issue(lane_addr + kColD1 + 64 * hp + 32 * q, d);
+                tc::tmem_ld32_issue(lane_addr + d1 + 64 * hp + 32 * q, d);
                 tc::tmem_wait_ld();
                 tc::reg_fence32(d);
 #pragma unroll
@@ -513,7 +525,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 if (!tc::mbar_wait(&bar_m1, p1, wait_budget)) fail();
                 else if (tmw) {
                     tc::fence_after_sync();
-                    to_h16();
+                    to_h16(col_r(t));
                 }
             }
             p1 ^= 1u;
@@ -524,7 +536,9 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                     if (!tc::mbar_wait(&bar_m2[0], p2, wait_budget)) fail();
                     else {
                         tc::fence_after_sync();
-                        products<true>(lane_addr, kColD2, hp, part, acc0);
+                        products<true>(lane_addr, col_a(t), hp, part, acc0);
+                        tc::fence_before_sync();
+                        tc::mbar_arrive(&bar_fa);
                     }
                 }
             }
@@ -543,13 +557,13 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 unpack(t + 2, reinterpret_cast<const uint8_t *>(stage), htid, 32 * kPairHelpers);
             }
             if (tmw && !abort_flag) {
-                // products of (t, 1), from D1's columns, which are then free for the row stage of t + 1
+                // products of (t, 1), from R(t), which is then free for class 0's column stage of t + 1
                 if (!tc::mbar_wait(&bar_m2[1], p2, wait_budget)) fail();
                 else {
                     tc::fence_after_sync();
-                    products<false>(lane_addr, kColD1, hp, part, acc0);
+                    products<false>(lane_addr, col_r(t), hp, part, acc0);
                     tc::fence_before_sync();
-                    tc::mbar_arrive(&bar_free);
+                    tc::mbar_arrive(&bar_fb);
                 }
             }
             p2 ^= 1u;
@@ -644,9 +658,10 @@ int pair_dispatch(int precision, F &&f)
 // warp with the least work so far (a batch costs 4 d + 6, about 37 cycles a
 // unit): the 8 TMEM warps start with kTmemLoad units for their conversions and
 // products, the gridding-only warps with none.  A TMEM warp's batches are split
-// in two parts for the two gridding phases of an iteration, about two thirds
+// in two parts for the two gridding phases of an iteration, about four fifths
 // of the work in the first (it overlaps class 0's column stage, the second
-// only class 1's); a gridding-only warp has one list.  idx[ci * kPairGatherWarps + w]
+// only part of class 1's, after class 0's products); a gridding-only warp has
+// one list.  idx[ci * kPairGatherWarps + w]
 // = (first half's offset, its batches, second half's offset, its batches),
 // offsets in words from the channel block's start; chan[ci] = (block start,
 // block words).  The upper mask of a channel lists the folded rows whose cells
@@ -658,7 +673,7 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
                       std::vector<int2> &chan, std::vector<unsigned long long> &upper)
 {
     constexpr int M = 64, S = M + 1, W32 = 8, W = kPairGatherWarps, kWindow = 96;
-    constexpr long long kTmemLoad = 120;
+    constexpr long long kTmemLoad = 90;
     if (A > 1024 || K * (K + 1) > 63) return EPIC_ERR_UNSUPPORTED;
     const int nc = static_cast<int>(chans.size()), h = (K - 1) / 2;
     tab.clear();
@@ -793,10 +808,16 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
             for (int b : per[w]) total += 4LL * blen[b] + 6;
             size_t split = per[w].size();   // gridding-only warps: one list
             if (w < 8) {
-                long long run = 0;
-                split = 0;
-                while (split < per[w].size() && 3 * (run + 4LL * blen[per[w][split]] + 6) <= 2 * total)
-                    run += 4LL * blen[per[w][split++]] + 6;
+                // the prefix closest to four fifths of the warp's gridding
+                long long run = 0, best = -1;
+                for (size_t i = 0; i <= per[w].size(); i++) {
+                    const long long dev = std::llabs(5 * run - 4 * total);
+                    if (best < 0 || dev < best) {
+                        best = dev;
+                        split = i;
+                    }
+                    if (i < per[w].size()) run += 4LL * blen[per[w][i]] + 6;
+                }
             }
             int4 &o = idx[static_cast<size_t>(ci) * W + w];
             for (int half = 0; half < 2; half++) {
