@@ -797,8 +797,9 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
             }
             if (rc == EPIC_OK && g.tensor && !g.tc_regular && !g.alias) rc = EPIC_ERR_UNSUPPORTED;
             // grid side 128 in a tensor plan: two pixel classes per CTA from one gridding when the
-            // aperture's rows fold without overlap and the lists fit in shared memory
-            if (rc == EPIC_OK && g.tensor && g.N == 128 && n_pol == 2 && p->nker == 1 &&
+            // aperture's rows fold without overlap and the lists fit in shared memory; grid side 64:
+            // the same kernel with its one class
+            if (rc == EPIC_OK && g.tensor && (g.N == 128 || g.N == 64) && n_pol == 2 && p->nker == 1 &&
                 !(diag & EPIC_DIAG_NO_PAIR)) {
                 std::vector<uint32_t> tab32;
                 std::vector<int4> idx32, pidx;
@@ -822,7 +823,7 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                 }
             }
         }
-        g.launch_items = g.pair ? g.n_chan * 2 : g.n_items;
+        g.launch_items = g.pair ? g.n_chan * (g.N == 128 ? 2 : 1) : g.n_items;
         if (g.pair) g.tau_cap = std::max(g.tau_cap, epic::fp32_pick_tau(g.launch_items, max_spectra, p->sm_count));
         if (rc == EPIC_OK) rc = dev_upload(&g.d_chans, g.chans.data(), g.chans.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_out_off, offs.data(), offs.size());

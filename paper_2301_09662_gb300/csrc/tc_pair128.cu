@@ -1,5 +1,7 @@
 // Tensor-core form for grid side 128 (dual polarisation): one CTA images two
-// pixel classes of one channel from a single gridding of each sample.
+// pixel classes of one channel from a single gridding of each sample.  The same
+// kernel with CLS = 1 images grid side 64 (one class, no folding): the row
+// stage, class 0's column stage and its products, nothing of class 1.
 //
 // With l = 2 m + h (h in {0, 1}^2) the image of class h is the 64-point 2-D DFT
 // of the folded aperture Gf_h(j) = sum_{k = j mod 64} G(k) w_128^{k.h}.  The
@@ -154,7 +156,7 @@ __device__ __forceinline__ void products(uint32_t lane_addr, uint32_t d2, int hh
 // lane l reads copy l mod 8, so the eight lanes of one 16-byte request never
 // share a bank group; the last slot is zero, for the lists' empty steps),
 // stage [(A*P + 3) / 4] (u32), the channel's lists [words] (u16).
-template <int VAR>
+template <int VAR, int CLS>
 __global__ void __launch_bounds__(kPairThreads, 1)
 tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
                   const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K,
@@ -166,7 +168,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                   const float *__restrict__ dfreq, const float4 *__restrict__ dtab)
 {
     constexpr int P = 2;
-    constexpr int N = 128;
+    constexpr int N = CLS == 2 ? 128 : 64;   // grid side: two classes of side 128, or side 64 unfolded
     constexpr bool kBF16 = VAR == 2;
     constexpr bool kSplit = VAR != 1;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -189,10 +191,10 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool simt = warp < kGathW;             // a gridding warp (TMEM warps included)
     const bool tmw = warp < kTmemWarps;
-    const int n_pairs = gridDim.x / n_tau;                    // CTAs per time chunk: channels x 2
+    const int n_pairs = gridDim.x / n_tau;                    // CTAs per time chunk: channels x CLS
     const int item = blockIdx.x % n_pairs;
     const int tau = blockIdx.x / n_pairs;
-    const int ci = item >> 1, hx = item & 1;
+    const int ci = CLS == 2 ? item >> 1 : item, hx = CLS == 2 ? item & 1 : 0;
     const int c = chans[ci];
     const int t0 = static_cast<int>(static_cast<long long>(T) * tau / n_tau);
     const int t1 = static_cast<int>(static_cast<long long>(T) * (tau + 1) / n_tau);
@@ -267,7 +269,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         scale = ldexpf(1.f, max(-40, min(40, e2)));
     }
     for (int i = simt ? tid : AP; i < AP; i += kGath) gp[i] = cscale(gp[i], scale);
-    if (tmw) {
+    if (CLS == 2 && tmw) {
         // zero the TMEM time sums of class hy = 1: lanes 32 (w mod 4) .., columns kColAcc1 + 64 (w / 4) ..
         uint32_t z[32];
 #pragma unroll
@@ -336,7 +338,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 }
                 ok = tc::mbar_wait(&bar_h, ph, wait_budget) && !abort_flag;
                 ph ^= 1u;
-                if (ok && t > t0)   // A(t) = R(t - 1): the products of (t - 1, 1) have read it
+                if (CLS == 2 && ok && t > t0)   // A(t) = R(t - 1): the products of (t - 1, 1) have read it
                     ok = tc::mbar_wait(&bar_fb, pf, wait_budget) && !abort_flag;
                 if (t > t0) pf ^= 1u;
                 if (!ok) break;
@@ -344,7 +346,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 if (!withhold_mma) {
                     // class hy = 0: A = X (shared memory) into A(t); class hy = 1: A = the turned X in
                     // TMEM into R(t) (converted to H16 by now)
-                    for (int hy = 0; hy < 2; hy++) {
+                    for (int hy = 0; hy < CLS; hy++) {
                         const uint32_t d2 = taddr + (hy ? col_r(t) : col_a(t));
 #pragma unroll
                         for (int kb = 0; kb < 8; kb++) {
@@ -556,7 +558,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 tc::named_bar_sync(kBarH, 32 * kPairHelpers);   // every helper's copies landed
                 unpack(t + 2, reinterpret_cast<const uint8_t *>(stage), htid, 32 * kPairHelpers);
             }
-            if (tmw && !abort_flag) {
+            if (CLS == 2 && tmw && !abort_flag) {
                 // products of (t, 1), from R(t), which is then free for class 0's column stage of t + 1
                 if (!tc::mbar_wait(&bar_m2[1], p2, wait_budget)) fail();
                 else {
@@ -578,8 +580,9 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             const float inv = 1.f / (scale * scale);
             const float inv_im = part ? -inv : inv;        // Im XY was summed with the lane's part sign
             const int my = 16 * (warp & 3) + (lane & 15);
+            // items: channel ci's classes h = 2 hy + hx (side 128), or channel ci (side 64)
             float4 *dst0 = reinterpret_cast<float4 *>(partial) +
-                           (static_cast<size_t>(tau) * n_items_out + ci * 4 + hx) * (64 * 64);
+                           (static_cast<size_t>(tau) * n_items_out + (CLS == 2 ? ci * 4 + hx : ci)) * (64 * 64);
             float4 *dst1 = reinterpret_cast<float4 *>(partial) +
                            (static_cast<size_t>(tau) * n_items_out + ci * 4 + 2 + hx) * (64 * 64);
 #pragma unroll
@@ -588,7 +591,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 dst0[my * 64 + mx] = make_float4(acc0[j].x * inv, acc0[j].y * inv, acc0[j].z * inv, acc0[j].w * inv_im);
             }
 #pragma unroll
-            for (int half = 0; half < 2; half++) {
+            for (int half = 0; half < (CLS == 2 ? 2 : 0); half++) {
                 uint32_t s[32];
                 tc::tmem_ld32_issue(lane_addr + kColAcc1 + 64 * hp + 32 * half, s);
                 tc::tmem_wait_ld();
@@ -635,6 +638,13 @@ int pair_dispatch(int precision, F &&f)
     case EPIC_TC_FP16: return f(std::integral_constant<int, 1>{});
     default: return f(std::integral_constant<int, 2>{});
     }
+}
+
+template <int VAR>
+const void *pair_kernel(int cls)
+{
+    return cls == 2 ? reinterpret_cast<const void *>(tc_pair128_kernel<VAR, 2>)
+                    : reinterpret_cast<const void *>(tc_pair128_kernel<VAR, 1>);
 }
 
 }  // namespace
@@ -846,7 +856,8 @@ size_t tc_pair_smem_bytes(int A, int K, int words) { return pair_smem(A, K, word
 int prepare_tc_pair(const epic_plan_s *plan, size_t smem)
 {
     return pair_dispatch(plan->precision, [&](auto vv) {
-        return raise_dyn_smem_cap(reinterpret_cast<const void *>(tc_pair128_kernel<decltype(vv)::value>), smem);
+        const int rc = raise_dyn_smem_cap(pair_kernel<decltype(vv)::value>(2), smem);
+        return rc != EPIC_OK ? rc : raise_dyn_smem_cap(pair_kernel<decltype(vv)::value>(1), smem);
     });
 }
 
@@ -856,10 +867,13 @@ int launch_tc_pair(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
     int n_tau = choose_tau(plan, g, T);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
-    const dim3 grid(static_cast<unsigned>(g.n_chan * 2 * n_tau));
+    const int cls = g.N == 128 ? 2 : 1;
+    const dim3 grid(static_cast<unsigned>(g.n_chan * cls * n_tau));
     const size_t smem = pair_smem(plan->A, plan->K, g.pwords);
     return pair_dispatch(plan->precision, [&](auto vv) {
-        tc_pair128_kernel<decltype(vv)::value><<<grid, kPairThreads, smem, stream>>>(
+        constexpr int V = decltype(vv)::value;
+        auto kfn = cls == 2 ? tc_pair128_kernel<V, 2> : tc_pair128_kernel<V, 1>;
+        kfn<<<grid, kPairThreads, smem, stream>>>(
             v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN, g.d_ptab, g.d_pchan, g.d_pidx,
             g.d_upper, plan->d_dft, plan->A, plan->C, T, g.n_items, n_tau, g.d_partial, plan->d_status,
             plan->wait_budget, plan->test_withhold_mma, plan->d_dfreq, plan->delays ? plan->d_dtab : nullptr);

@@ -127,10 +127,12 @@ def test_pair_kernel_matches_oracle(A, C, T, K, precision, tol):
     assert _cmp(wl, precision).max() < tol
 
 
-def test_pair_kernel_agrees_with_single_class_kernel():
-    """The two-classes-per-CTA kernel and the one-class kernel (EPIC_DIAG_NO_PAIR)
+@pytest.mark.parametrize("N", [128, 64])
+def test_pair_kernel_agrees_with_single_class_kernel(N):
+    """The gather-gridding pair kernel (two classes per CTA at side 128, its
+    one-class form at side 64) and the older one-class kernel (EPIC_DIAG_NO_PAIR)
     compute the same images up to FP32 rounding of different summation orders."""
-    wl = synth.random_small(A=200, P=2, C=2, T=11, N=128, K=5, seed=610)
+    wl = synth.random_small(A=200 if N == 128 else 90, P=2, C=2, T=11, N=N, K=5, seed=610 + N)
     a, pa = run_gpu(wl, precision=epic.EPIC_TC_SPLIT_FP16)
     b, pb = run_gpu(wl, precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_DIAG_NO_PAIR)
     pa.close()
@@ -139,11 +141,12 @@ def test_pair_kernel_agrees_with_single_class_kernel():
     assert peak_rel_err(a, oracle.workload_image(wl), wl.grid_n, 2).max() < SPLIT_TOL
 
 
+@pytest.mark.parametrize("N", [128, 64])
 @pytest.mark.parametrize("T", [1, 2, 3, 64])
-def test_pair_kernel_sample_counts(T):
+def test_pair_kernel_sample_counts(T, N):
     """One sample (prologue only), two, three, and many over several time chunks:
-    the gather / row stage / two column stages pipeline drains every sample."""
-    wl = synth.random_small(A=48, P=2, C=1, T=T, N=128, K=3, seed=620 + T)
+    the gather / row stage / column stages pipeline drains every sample."""
+    wl = synth.random_small(A=48, P=2, C=1, T=T, N=N, K=3, seed=620 + T + N)
     assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16).max() < SPLIT_TOL
 
 
