@@ -113,9 +113,10 @@ enum {
                                                 EPIC_ERR_TIMEOUT; the context stays usable */
 #define EPIC_DIAG_ALIAS_BATCH(n) ((((unsigned)(n)) & 255u) << 16)   /* fold path: at most n (1..255) samples
                                                                         per time batch */
-#define EPIC_DIAG_NO_PAIR        (1u << 12)  /* tensor form, grid side 128: one pixel class per CTA (the
-                                                two-stage kernel of every side) instead of two classes
-                                                from one gridding */
+#define EPIC_DIAG_NO_PAIR        (1u << 12)  /* tensor form, grid sides 128 and 64: the two-stage kernel of
+                                                every side (one pixel class per CTA, scheduled gridding)
+                                                instead of the gather-gridding pair kernel (two classes
+                                                from one gridding at side 128, its one class at 64) */
 
 /*
  * epic_plan -- validate the array geometry and build every table the imaging

@@ -67,9 +67,25 @@ def test_tensor_split_fp16_with_taper_and_flags():
         assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16, flags=flags).max() < SPLIT_TOL
 
 
-def test_tensor_lwa_full_size_sampled_channels():
+@pytest.mark.parametrize("precision,tol", [(epic.EPIC_TC_SPLIT_FP16, SPLIT_TOL), (epic.EPIC_TC_FP16, FP16_TOL),
+                                           (epic.EPIC_TC_SPLIT_BF16, BF16_TOL)])
+def test_tensor_lwa_full_size_sampled_channels(precision, tol):
+    """The full LWA-like integration (256 dual-pol antennas, 64 channels, 1000
+    spectra, grid 128) in each tensor precision, two channels against the oracle."""
     wl = synth.lwa()
-    assert _cmp(wl, epic.EPIC_TC_SPLIT_FP16, channels=[3, 60]).max() < SPLIT_TOL
+    assert _cmp(wl, precision, channels=[3, 60]).max() < tol
+
+
+@pytest.mark.parametrize("precision,tol", [(epic.EPIC_TC_SPLIT_FP16, SPLIT_TOL), (epic.EPIC_TC_SPLIT_BF16, BF16_TOL)])
+def test_tensor_uneven_workload_full_size_sampled_channels(precision, tol):
+    """The full uneven band (192 channels over 30-80 MHz, grid sides 64/96/128,
+    1000 spectra) in one tensor plan: side 64 on the pair kernel's one-class form,
+    96 on the FP32 register kernel, 128 on the pair kernel; one channel of each
+    group against the oracle."""
+    wl = synth.uneven()
+    chans = [0, 100, 191]
+    assert sorted(set(int(wl.grid_n[c]) for c in chans)) == [64, 96, 128]
+    assert _cmp(wl, precision, channels=chans).max() < tol
 
 
 def test_bounded_wait_reports_timeout_and_context_survives():
