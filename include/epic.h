@@ -251,6 +251,27 @@ int epic_image_host(epic_plan_t plan, const uint8_t *ci4_host, const float *gain
                     int n_spectra, float *out_c64_host, void *cuda_stream);
 
 /*
+ * epic_image_host_async / epic_host_wait -- the host-buffer integration as a
+ * pipeline for a stream of integrations (the paper's deployment images gulp
+ * after gulp, Sec. 2.2): epic_image_host_async queues the upload of this
+ * integration's ci4 and gains (on a plan-owned upload stream, into one of two
+ * plan-owned device slots), its imaging on cuda_stream, and the download of the
+ * image into out_c64_host (on a plan-owned download stream), and returns
+ * without waiting, so the upload of the next integration and the download of
+ * the previous one overlap this one's imaging.  epic_host_wait blocks until
+ * every queued upload and download has finished; until then the caller must
+ * neither change the host inputs nor read the host outputs of the queued calls.
+ * Host buffers should be pinned (pageable memory makes the copies synchronous).
+ * Argument meanings, layouts and checks are those of epic_image_host; device
+ * buffers are allocated on the first call (EPIC_ERR_NOMEM), copy errors are
+ * reported by this call or by epic_host_wait (EPIC_ERR_CUDA), device-side
+ * status by epic_status.  The paper has no counterpart.
+ */
+int epic_image_host_async(epic_plan_t plan, const uint8_t *ci4_host, const float *gains_c64_host,
+                          int n_spectra, float *out_c64_host, void *cuda_stream);
+int epic_host_wait(epic_plan_t plan);
+
+/*
  * epic_image_series -- time-resolved imaging for transient searches (the
  * millisecond imaging of Sec. 1 and Sec. 4): n_spectra = n_img *
  * spectra_per_image, and image i is the integration of spectra

@@ -135,6 +135,16 @@ struct epic_plan_s {
     uint8_t *d_stage_v = nullptr;
     float *d_stage_g = nullptr;
     float *d_stage_out = nullptr;
+    // pipelined host-buffer entry point (epic_image_host_async; allocated on first use): two
+    // slots of upload and download buffers, an upload and a download stream, and the events
+    // that order them against the imaging on the caller's stream
+    uint8_t *d_ring_v[2] = {nullptr, nullptr};
+    float *d_ring_g[2] = {nullptr, nullptr};
+    float *d_ring_out[2] = {nullptr, nullptr};
+    cudaStream_t s_up = nullptr, s_down = nullptr;
+    cudaEvent_t ev_up[2] = {nullptr, nullptr}, ev_in_free[2] = {nullptr, nullptr};
+    cudaEvent_t ev_img[2] = {nullptr, nullptr}, ev_out_free[2] = {nullptr, nullptr};
+    long long n_async = 0;
 };
 
 namespace epic {

@@ -72,6 +72,17 @@ void free_plan(epic_plan_s *p)
     cudaFree(p->d_stage_v);
     cudaFree(p->d_stage_g);
     cudaFree(p->d_stage_out);
+    if (p->s_up) cudaStreamSynchronize(p->s_up);
+    if (p->s_down) cudaStreamSynchronize(p->s_down);
+    for (int i = 0; i < 2; i++) {
+        cudaFree(p->d_ring_v[i]);
+        cudaFree(p->d_ring_g[i]);
+        cudaFree(p->d_ring_out[i]);
+        for (cudaEvent_t e : {p->ev_up[i], p->ev_in_free[i], p->ev_img[i], p->ev_out_free[i]})
+            if (e) cudaEventDestroy(e);
+    }
+    if (p->s_up) cudaStreamDestroy(p->s_up);
+    if (p->s_down) cudaStreamDestroy(p->s_down);
     for (auto &g : p->groups) {
         cudaFree(g.d_chans);
         cudaFree(g.d_out_off);
@@ -1079,6 +1090,67 @@ int epic_image_series(epic_plan_t plan, const uint8_t *ci4, const float *gains, 
     return epic_image_series_ex(plan, ci4, gains, nullptr, n_spectra, spi, out, stream);
 }
 
+namespace {
+
+// the device staging of the host-buffer entry points (the imaging graph's fixed pointers)
+int ensure_stage(epic_plan_s *plan)
+{
+    if (plan->d_stage_out) return EPIC_OK;
+    const size_t vbytes = static_cast<size_t>(plan->max_spectra) * plan->C * plan->A * plan->P;
+    const size_t gfloats = static_cast<size_t>(plan->C) * plan->A * plan->P * 2;
+    if (cudaMalloc(&plan->d_stage_v, vbytes ? vbytes : 16) != cudaSuccess ||
+        cudaMalloc(&plan->d_stage_g, gfloats * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&plan->d_stage_out, plan->out_floats * sizeof(float)) != cudaSuccess) {
+        cudaFree(plan->d_stage_v);
+        cudaFree(plan->d_stage_g);
+        cudaFree(plan->d_stage_out);
+        plan->d_stage_v = nullptr;
+        plan->d_stage_g = nullptr;
+        plan->d_stage_out = nullptr;
+        return EPIC_ERR_NOMEM;
+    }
+    return EPIC_OK;
+}
+
+// the two upload / download slots, streams and events of epic_image_host_async
+int ensure_ring(epic_plan_s *plan)
+{
+    if (plan->s_down) return EPIC_OK;
+    const size_t vbytes = static_cast<size_t>(plan->max_spectra) * plan->C * plan->A * plan->P;
+    const size_t gfloats = static_cast<size_t>(plan->C) * plan->A * plan->P * 2;
+    bool ok = true;
+    for (int i = 0; i < 2 && ok; i++) {
+        ok = cudaMalloc(&plan->d_ring_v[i], vbytes ? vbytes : 16) == cudaSuccess &&
+             cudaMalloc(&plan->d_ring_g[i], gfloats * sizeof(float)) == cudaSuccess &&
+             cudaMalloc(&plan->d_ring_out[i], plan->out_floats * sizeof(float)) == cudaSuccess;
+        for (cudaEvent_t *e : {&plan->ev_up[i], &plan->ev_in_free[i], &plan->ev_img[i], &plan->ev_out_free[i]})
+            ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    }
+    ok = ok && cudaStreamCreateWithFlags(&plan->s_up, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&plan->s_down, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) return EPIC_OK;
+    for (int i = 0; i < 2; i++) {
+        cudaFree(plan->d_ring_v[i]);
+        cudaFree(plan->d_ring_g[i]);
+        cudaFree(plan->d_ring_out[i]);
+        plan->d_ring_v[i] = nullptr;
+        plan->d_ring_g[i] = nullptr;
+        plan->d_ring_out[i] = nullptr;
+        for (cudaEvent_t *e : {&plan->ev_up[i], &plan->ev_in_free[i], &plan->ev_img[i], &plan->ev_out_free[i]})
+            if (*e) {
+                cudaEventDestroy(*e);
+                *e = nullptr;
+            }
+    }
+    if (plan->s_up) cudaStreamDestroy(plan->s_up);
+    plan->s_up = nullptr;
+    if (plan->s_down) cudaStreamDestroy(plan->s_down);
+    plan->s_down = nullptr;
+    return EPIC_ERR_NOMEM;
+}
+
+}  // namespace
+
 int epic_image_host(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra,
                     float *out, void *stream)
 {
@@ -1086,21 +1158,8 @@ int epic_image_host(epic_plan_t plan, const uint8_t *ci4, const float *gains, in
     if (n_spectra < 0 || n_spectra > plan->max_spectra) return EPIC_ERR_ARG;
     if (n_spectra > 0 && !ci4) return EPIC_ERR_ARG;
     auto s = static_cast<cudaStream_t>(stream);
-    const size_t vbytes = static_cast<size_t>(plan->max_spectra) * plan->C * plan->A * plan->P;
     const size_t gfloats = static_cast<size_t>(plan->C) * plan->A * plan->P * 2;
-    if (!plan->d_stage_out) {
-        if (cudaMalloc(&plan->d_stage_v, vbytes ? vbytes : 16) != cudaSuccess ||
-            cudaMalloc(&plan->d_stage_g, gfloats * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&plan->d_stage_out, plan->out_floats * sizeof(float)) != cudaSuccess) {
-            cudaFree(plan->d_stage_v);
-            cudaFree(plan->d_stage_g);
-            cudaFree(plan->d_stage_out);
-            plan->d_stage_v = nullptr;
-            plan->d_stage_g = nullptr;
-            plan->d_stage_out = nullptr;
-            return EPIC_ERR_NOMEM;
-        }
-    }
+    if (const int rc = ensure_stage(plan); rc != EPIC_OK) return rc;
     const size_t nbytes = static_cast<size_t>(n_spectra) * plan->C * plan->A * plan->P;
     if (nbytes && cudaMemcpyAsync(plan->d_stage_v, ci4, nbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return EPIC_ERR_CUDA;
@@ -1112,6 +1171,57 @@ int epic_image_host(epic_plan_t plan, const uint8_t *ci4, const float *gains, in
     if (cudaMemcpyAsync(out, plan->d_stage_out, plan->out_floats * sizeof(float), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return EPIC_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return EPIC_ERR_CUDA;
+    return EPIC_OK;
+}
+
+int epic_image_host_async(epic_plan_t plan, const uint8_t *ci4, const float *gains, int n_spectra, float *out,
+                          void *stream)
+{
+    if (!plan || !out) return EPIC_ERR_ARG;
+    if (n_spectra < 0 || n_spectra > plan->max_spectra) return EPIC_ERR_ARG;
+    if (n_spectra > 0 && !ci4) return EPIC_ERR_ARG;
+    if (const int rc = ensure_stage(plan); rc != EPIC_OK) return rc;
+    if (const int rc = ensure_ring(plan); rc != EPIC_OK) return rc;
+    auto s = static_cast<cudaStream_t>(stream);
+    const int k = static_cast<int>(plan->n_async++ & 1);
+    const size_t nbytes = static_cast<size_t>(n_spectra) * plan->C * plan->A * plan->P;
+    const size_t gbytes = static_cast<size_t>(plan->C) * plan->A * plan->P * 2 * sizeof(float);
+    const size_t obytes = plan->out_floats * sizeof(float);
+    auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+    // upload into slot k once the imaging two calls back has taken its inputs out of it
+    if (!ok(cudaStreamWaitEvent(plan->s_up, plan->ev_in_free[k], 0)) ||
+        (nbytes && !ok(cudaMemcpyAsync(plan->d_ring_v[k], ci4, nbytes, cudaMemcpyHostToDevice, plan->s_up))) ||
+        (gains && !ok(cudaMemcpyAsync(plan->d_ring_g[k], gains, gbytes, cudaMemcpyHostToDevice, plan->s_up))) ||
+        !ok(cudaEventRecord(plan->ev_up[k], plan->s_up)))
+        return EPIC_ERR_CUDA;
+    // on the caller's stream: inputs into the imaging graph's fixed buffers, image, result into
+    // slot k once the download two calls back has emptied it
+    if (!ok(cudaStreamWaitEvent(s, plan->ev_up[k], 0)) ||
+        (nbytes && !ok(cudaMemcpyAsync(plan->d_stage_v, plan->d_ring_v[k], nbytes, cudaMemcpyDeviceToDevice, s))) ||
+        (gains && !ok(cudaMemcpyAsync(plan->d_stage_g, plan->d_ring_g[k], gbytes, cudaMemcpyDeviceToDevice, s))) ||
+        !ok(cudaEventRecord(plan->ev_in_free[k], s)))
+        return EPIC_ERR_CUDA;
+    int rc = epic::run_image(plan, plan->d_stage_v, gains ? reinterpret_cast<const float2 *>(plan->d_stage_g) : nullptr,
+                             n_spectra, reinterpret_cast<float2 *>(plan->d_stage_out), s);
+    if (rc != EPIC_OK) return rc;
+    if (!ok(cudaStreamWaitEvent(s, plan->ev_out_free[k], 0)) ||
+        !ok(cudaMemcpyAsync(plan->d_ring_out[k], plan->d_stage_out, obytes, cudaMemcpyDeviceToDevice, s)) ||
+        !ok(cudaEventRecord(plan->ev_img[k], s)))
+        return EPIC_ERR_CUDA;
+    // download slot k into the caller's host buffer
+    if (!ok(cudaStreamWaitEvent(plan->s_down, plan->ev_img[k], 0)) ||
+        !ok(cudaMemcpyAsync(out, plan->d_ring_out[k], obytes, cudaMemcpyDeviceToHost, plan->s_down)) ||
+        !ok(cudaEventRecord(plan->ev_out_free[k], plan->s_down)))
+        return EPIC_ERR_CUDA;
+    return EPIC_OK;
+}
+
+int epic_host_wait(epic_plan_t plan)
+{
+    if (!plan) return EPIC_ERR_ARG;
+    if (!plan->s_down) return EPIC_OK;
+    if (cudaStreamSynchronize(plan->s_up) != cudaSuccess || cudaStreamSynchronize(plan->s_down) != cudaSuccess)
+        return EPIC_ERR_CUDA;
     return EPIC_OK;
 }
 

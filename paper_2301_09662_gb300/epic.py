@@ -57,7 +57,7 @@ EPIC_SEARCH_DIAG_WITHHOLD_TMA = 1 << 12
 PRODUCTS = ("XX", "YY", "XY", "YX")
 
 #: every symbol include/epic.h declares
-EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_image_efield", "epic_efield_floats", "epic_measure_peak", "epic_autotune", "epic_solve_gains", "epic_image_series_ex", "epic_image_host", "epic_out_floats", "epic_status",
+EXPORTS = ("epic_plan", "epic_image", "epic_image_ex", "epic_image_efield", "epic_efield_floats", "epic_measure_peak", "epic_autotune", "epic_solve_gains", "epic_image_series_ex", "epic_image_host", "epic_image_host_async", "epic_host_wait", "epic_out_floats", "epic_status",
            "epic_set_profiling", "epic_stage_times", "epic_image_static", "epic_image_series", "epic_destroy",
            "epic_strerror", "epic_search_plan", "epic_search_info", "epic_dedisperse", "epic_single_pulse",
            "epic_search_status", "epic_search_destroy")
@@ -89,6 +89,10 @@ def load():
     L.epic_image_series.argtypes = [vp, vp, vp, i, i, vp, vp]
     L.epic_image_series.restype = i
     L.epic_image_host.restype = i
+    L.epic_image_host_async.argtypes = [vp, vp, vp, i, vp, vp]
+    L.epic_image_host_async.restype = i
+    L.epic_host_wait.argtypes = [vp]
+    L.epic_host_wait.restype = i
     L.epic_image_ex.argtypes = [vp, vp, vp, vp, i, vp, vp]
     L.epic_image_ex.restype = i
     L.epic_autotune.argtypes = [vp, i, vp]
@@ -307,6 +311,26 @@ class Plan:
                                     int(v.shape[0]), out.data_ptr(), self._stream(stream))
         _check(rc, "epic_image_host")
         return out
+
+    def image_host_async(self, v, gains=None, out=None, stream=None):
+        """Pipelined host-buffer variant (epic_image_host_async): queues upload,
+        imaging and download and returns at once; call host_wait() before reading
+        `out` or changing the inputs.  Host tensors should be pinned."""
+        import torch
+        self._check_inputs(v, gains, device=False)
+        if out is None:
+            out = torch.empty(self.out_floats // 2, dtype=torch.complex64).pin_memory()
+        elif out.dtype != torch.complex64 or out.numel() * 2 != self.out_floats or not out.is_contiguous() \
+                or out.is_cuda:
+            raise ValueError("out must be a contiguous host complex64 tensor of the plan's output size")
+        rc = load().epic_image_host_async(self._h, v.data_ptr(), gains.data_ptr() if gains is not None else None,
+                                          int(v.shape[0]), out.data_ptr(), self._stream(stream))
+        _check(rc, "epic_image_host_async")
+        return out
+
+    def host_wait(self):
+        """Block until every queued image_host_async call's copies have finished."""
+        _check(load().epic_host_wait(self._h), "epic_host_wait")
 
     def split(self, flat):
         """Per-channel [NP][N][N] views of a packed output."""
