@@ -30,6 +30,14 @@ __device__ __forceinline__ float2 ci4_decode(uint32_t b)
     return make_float2(static_cast<float>(re), static_cast<float>(im));
 }
 
+// How the pair kernel's lists are dealt (build_pair_tables): the 8 TMEM warps start with
+// tmem_load work units (~37 cycles each) for their conversion and products, and a TMEM warp's
+// share is split so that about first_pct percent is gridded under class 0's column stage.
+struct PairSchedule {
+    int tmem_load = 90;
+    int first_pct = 80;
+};
+
 struct GroupCfg {
     int N = 0, M = 0, Q1 = 1, Q = 1;
     int n_chan = 0;
@@ -71,8 +79,13 @@ struct GroupCfg {
     short2 *d_j0 = nullptr;            // device: [n_chan] first occupied alias block (x, y)
     uint32_t *d_bseg = nullptr;        // device: footprint rows (a << 8 | dyi) per (channel, 8-row band)
     int *d_boff = nullptr;             // device: [n_chan * 8 + 1] offsets into d_bseg
-    // grid side 128 in a tensor plan: the pair kernel (tc_pair128.cu), two pixel classes per CTA
+    // grid sides 128 and 64 in a tensor plan: the pair kernel (tc_pair128.cu)
     bool pair = false;
+    PairSchedule psched;               // how its lists are dealt to the warps (epic_autotune measures a few)
+    std::vector<uint32_t> h_tab32;     // host: the FP32 gather table of the group (kept to re-deal the lists)
+    std::vector<int4> h_idx32;
+    std::vector<int2> h_chan32;
+    size_t ptab_n = 0, pidx_n = 0;     // sizes of the device lists and warp offsets
     int launch_items = 0;              // CTAs per time chunk (n_items, or n_chan * 2 for the pair kernel)
     int pwords = 0;                    // largest channel block of the pair lists (16-bit words)
     uint16_t *d_ptab = nullptr;        // device: pair-kernel gather lists (build_pair_tables)
@@ -131,6 +144,7 @@ struct epic_plan_s {
     void *g_out = nullptr;
     int g_T = -1;
     bool g_prof = false;
+    std::vector<short2> h_cells;       // host copy of the cell map, kept when a group uses the pair kernel
     // host-buffer entry point staging (allocated on first use)
     uint8_t *d_stage_v = nullptr;
     float *d_stage_g = nullptr;
@@ -188,11 +202,12 @@ int launch_tc_dual_fold(epic_plan_s *plan, const GroupCfg &g, const float2 *gain
                         bool accumulate, cudaStream_t stream);
 int launch_tc_dual(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,
                    cudaStream_t stream);
-// grid side 128: two pixel classes per CTA from one gridding (tc_pair128.cu)
+// grid sides 128 and 64: the gather-gridding pair kernel (tc_pair128.cu)
 int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
                       const std::vector<uint32_t> &tab32, const std::vector<int4> &idx32,
                       const std::vector<int2> &chan32, std::vector<uint16_t> &tab, std::vector<int4> &idx,
-                      std::vector<int2> &chan, std::vector<unsigned long long> &upper);
+                      std::vector<int2> &chan, std::vector<unsigned long long> &upper,
+                      const PairSchedule &sched = PairSchedule());
 size_t tc_pair_smem_bytes(int A, int K, int words);
 int prepare_tc_pair(const epic_plan_s *plan, size_t smem);
 int launch_tc_pair(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,

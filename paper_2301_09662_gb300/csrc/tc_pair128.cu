@@ -666,12 +666,13 @@ const void *pair_kernel(int cls)
 // zero).  The
 // batches are dealt to the kernel's gridding warps longest first, each to the
 // warp with the least work so far (a batch costs 4 d + 6, about 37 cycles a
-// unit): the 8 TMEM warps start with kTmemLoad units for their conversions and
-// products, the gridding-only warps with none.  A TMEM warp's batches are split
-// in two parts for the two gridding phases of an iteration, about four fifths
-// of the work in the first (it overlaps class 0's column stage, the second
-// only part of class 1's, after class 0's products); a gridding-only warp has
-// one list.  idx[ci * kPairGatherWarps + w]
+// unit): the 8 TMEM warps start with sched.tmem_load units for their
+// conversions and products, the gridding-only warps with none.  A TMEM warp's
+// batches are split in two parts for the two gridding phases of an iteration,
+// about sched.first_pct percent of the work in the first (it overlaps class 0's
+// column stage, the second only part of class 1's, after class 0's products); a
+// gridding-only warp has one list.  The defaults (90 units, 80 %) are the
+// measured best on the LWA-like layout; epic_autotune measures a few others.  idx[ci * kPairGatherWarps + w]
 // = (first half's offset, its batches, second half's offset, its batches),
 // offsets in words from the channel block's start; chan[ci] = (block start,
 // block words).  The upper mask of a channel lists the folded rows whose cells
@@ -680,11 +681,12 @@ const void *pair_kernel(int cls)
 int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
                       const std::vector<uint32_t> &tab32, const std::vector<int4> &idx32,
                       const std::vector<int2> &chan32, std::vector<uint16_t> &tab, std::vector<int4> &idx,
-                      std::vector<int2> &chan, std::vector<unsigned long long> &upper)
+                      std::vector<int2> &chan, std::vector<unsigned long long> &upper, const PairSchedule &sched)
 {
     constexpr int M = 64, S = M + 1, W32 = 8, W = kPairGatherWarps, kWindow = 96;
-    constexpr long long kTmemLoad = 90;
-    if (A > 1024 || K * (K + 1) > 63) return EPIC_ERR_UNSUPPORTED;
+    const long long kTmemLoad = sched.tmem_load;
+    if (A > 1024 || K * (K + 1) > 63 || sched.tmem_load < 0 || sched.first_pct < 0 || sched.first_pct > 100)
+        return EPIC_ERR_UNSUPPORTED;
     const int nc = static_cast<int>(chans.size()), h = (K - 1) / 2;
     tab.clear();
     idx.assign(static_cast<size_t>(nc) * W, make_int4(0, 0, 0, 0));
@@ -818,10 +820,10 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
             for (int b : per[w]) total += 4LL * blen[b] + 6;
             size_t split = per[w].size();   // gridding-only warps: one list
             if (w < 8) {
-                // the prefix closest to four fifths of the warp's gridding
+                // the prefix closest to first_pct percent of the warp's gridding
                 long long run = 0, best = -1;
                 for (size_t i = 0; i <= per[w].size(); i++) {
-                    const long long dev = std::llabs(5 * run - 4 * total);
+                    const long long dev = std::llabs(100 * run - sched.first_pct * total);
                     if (best < 0 || dev < best) {
                         best = dev;
                         split = i;

@@ -196,8 +196,29 @@ int main(int argc, char **argv)
         std::vector<unsigned long long> r32, upper;
         std::vector<uint16_t> ptab;
         CHECK(epic::build_gather_table(band, A, K, M, P, chans, t32, i32, c32, r32) == EPIC_OK, "band table");
-        CHECK(epic::build_pair_tables(band, A, K, chans, t32, i32, c32, ptab, pidx, pchan, upper) == EPIC_OK,
-              "pair lists build failed");
+        // every schedule the autotuner tries deals the same batches: same sizes, same per-channel blocks
+        const epic::PairSchedule scheds[] = {{90, 80}, {0, 0}, {150, 67}, {60, 100}};
+        for (const epic::PairSchedule &ps : scheds) {
+            std::vector<int4> pidx_s;
+            std::vector<int2> pchan_s;
+            std::vector<unsigned long long> upper_s;
+            std::vector<uint16_t> ptab_s;
+            CHECK(epic::build_pair_tables(band, A, K, chans, t32, i32, c32, ptab_s, pidx_s, pchan_s, upper_s, ps) ==
+                      EPIC_OK,
+                  "pair lists build failed (schedule %d/%d)", ps.tmem_load, ps.first_pct);
+            if (ps.tmem_load == 90 && ps.first_pct == 80) {
+                ptab = ptab_s;
+                pidx = pidx_s;
+                pchan = pchan_s;
+                upper = upper_s;
+                continue;
+            }
+            bool same = ptab_s.size() == ptab.size() && pidx_s.size() == pidx.size() && upper_s == upper;
+            for (size_t i = 0; same && i < pchan.size(); i++) same = pchan_s[i].x == pchan[i].x && pchan_s[i].y == pchan[i].y;
+            std::multiset<uint16_t> a(ptab.begin(), ptab.end()), b(ptab_s.begin(), ptab_s.end());
+            CHECK(same && a == b, "schedule %d/%d changes the lists' sizes or content", ps.tmem_load, ps.first_pct);
+        }
+        CHECK(!ptab.empty(), "pair lists build failed");
         for (int ci = 0; ci < C && g_bad == 0; ci++) {
             unsigned long long up = 0;
             for (int a = 0; a < A; a++)

