@@ -401,7 +401,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         const int htid = tid - kSimtP;                  // helpers: 0 .. 32 kPairHelpers - 1
         // a3: gather gridding of n batches from offset `at` (u16 units) straight into G16.  A
         // batch is [d][32 G16 byte offsets of the lanes' cell pairs (pol 0, Re, hi part), or
-        // 0xFFFF][d x 32 entries tp << 10 | a]; empty steps name the zero tap slot and antenna 0.
+        // 0xFFFF][d x 32 entries tp << 10 | a]; empty steps name the zero tap slot.
         auto gather = [&](int at, int n, int t) {
             const uint16_t *bt = stab + at;
             const float4 *es4 = reinterpret_cast<const float4 *>(es + (t & 1) * AP);
@@ -662,8 +662,9 @@ const void *pair_kernel(int cls)
 // a mod 8, as far as the lists allow.  Storage: [list length d][32 G16 byte
 // offsets k_off(y, 2 xp) of the pairs (0xFFFF: an empty lane)][d x 32 entries
 // tp << 10 | a] in 16-bit words, an empty step naming tap slot K (K + 1)
-// (zeros) and antenna 0; no zero lists (G16 keeps the cells no list names at
-// zero).  The
+// (zeros) and an antenna its step loads anyway; no zero lists (G16 keeps the
+// cells no list names at zero).  The greedy step order is then improved by a
+// local search (swaps within a lane's list) on the voltage loads' wavefronts.  The
 // batches are dealt to the kernel's gridding warps longest first, each to the
 // warp with the least work so far (a batch costs 4 d + 6, about 37 cycles a
 // unit): the 8 TMEM warps start with sched.tmem_load units for their
@@ -761,7 +762,8 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
             for (int q : bt) d = std::max(d, static_cast<int>(pairs[q].second.size()));
             blen[b] = d;
             auto &wd = words[b];
-            const uint16_t empty = static_cast<uint16_t>((K * (K + 1)) << 10);   // zero tap slot, antenna 0
+            const int empty_tp = K * (K + 1);                                    // the zero tap slot
+            const uint16_t empty = static_cast<uint16_t>(empty_tp << 10);
             wd.assign(1 + 32 + static_cast<size_t>(d) * 32, empty);
             wd[0] = static_cast<uint16_t>(d);
             for (int l = 0; l < 32; l++) {
@@ -799,6 +801,49 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
                         slot[(e & 1023) & 7] = e & 1023;
                         wd[1 + 32 + static_cast<size_t>(j) * 32 + g0 + l] = e;
                     }
+                }
+                // then a local search over each lane's order (two of its steps swapped, empty ones
+                // included) while the group's voltage loads need fewer wavefronts: a step costs the
+                // most distinct antennas any 16-byte bank group (a mod 8) receives
+                auto at = [&](int j, int l) -> uint16_t & { return wd[1 + 32 + static_cast<size_t>(j) * 32 + g0 + l]; };
+                auto step_cost = [&](int j) {
+                    int seen[8], ns = 0, cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0}, mx = 1;
+                    for (int l = 0; l < 8; l++) {
+                        const uint16_t e = at(j, l);
+                        if ((e >> 10) == empty_tp) continue;
+                        const int a = e & 1023;
+                        bool dup = false;
+                        for (int q = 0; q < ns; q++) dup = dup || seen[q] == a;
+                        if (dup) continue;
+                        seen[ns++] = a;
+                        mx = std::max(mx, ++cnt[a & 7]);
+                    }
+                    return mx;
+                };
+                bool improved = true;
+                for (int pass = 0; pass < 8 && improved; pass++) {
+                    improved = false;
+                    for (int l = 0; l < 8; l++)
+                        for (int j1 = 0; j1 < d; j1++)
+                            for (int j2 = j1 + 1; j2 < d; j2++) {
+                                uint16_t &x = at(j1, l), &y = at(j2, l);
+                                if (x == y) continue;
+                                const int before = step_cost(j1) + step_cost(j2);
+                                std::swap(x, y);
+                                if (step_cost(j1) + step_cost(j2) < before) improved = true;
+                                else std::swap(x, y);
+                            }
+                }
+                // an empty step loads an antenna its step loads anyway (its tap pair is zero)
+                for (int j = 0; j < d; j++) {
+                    int a0 = 0;
+                    for (int l = 0; l < 8; l++)
+                        if ((at(j, l) >> 10) != empty_tp) {
+                            a0 = at(j, l) & 1023;
+                            break;
+                        }
+                    for (int l = 0; l < 8; l++)
+                        if ((at(j, l) >> 10) == empty_tp) at(j, l) = static_cast<uint16_t>((empty_tp << 10) | a0);
                 }
             }
         }

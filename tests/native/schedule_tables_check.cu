@@ -268,10 +268,7 @@ int main(int argc, char **argv)
                                 const uint16_t e = pb[off + 33 + 32LL * j + l];
                                 const long long a = e & 1023, tp = e >> 10;
                                 CHECK(a < A && tp <= K * (K + 1), "channel %d: entry out of range", ci);
-                                if (tp == K * (K + 1)) {   // an empty step: the zero tap slot, antenna 0
-                                    CHECK(a == 0, "channel %d: empty step with an antenna", ci);
-                                    continue;
-                                }
+                                if (tp == K * (K + 1)) continue;   // an empty step: the zero tap slot (any antenna)
                                 CHECK(lane_ok, "channel %d: entry under an empty or bad lane offset", ci);
                                 const long long pos = y * 32 + k / 2;
                                 got.insert((pos << 24) | (a << 8) | tp);
