@@ -295,7 +295,8 @@ int build_reg64_schedule(const std::vector<short2> &cells, int A, int K, int M, 
 // list).  Within each group of lanes that one shared-memory request serves (8
 // for the 16-byte dual-polarisation voltage loads, 16 for the 8-byte
 // single-polarisation ones) the list order is chosen greedily so that one step
-// reads distinct banks.  Cells of touched rows that no listed pair writes get
+// reads distinct banks (a greedy order, then a local search of swaps within a
+// lane's list on the wavefronts).  Cells of touched rows that no listed pair writes get
 // zeros, from per-warp lists of 32 cells per step; rows nobody touches are
 // skipped by the transform and need nothing.  Batches go to the warps longest
 // first, each to the warp with the least work so far, then the zero steps.
@@ -391,6 +392,38 @@ int build_gather_table(const std::vector<short2> &cells, int A, int K, int M, in
                         slot[static_cast<int>(e >> 8) % grp] = static_cast<int>(e >> 8);
                         words[1 + 32 + static_cast<size_t>(j) * 32 + g0 + l] = e;
                     }
+                }
+                // then a local search over each lane's order (two of its steps swapped, empty ones
+                // included) while the group's voltage loads need fewer wavefronts: a step costs the
+                // most distinct antennas any bank slot (a mod grp) receives
+                auto at = [&](int j, int l) -> uint32_t & { return words[1 + 32 + static_cast<size_t>(j) * 32 + g0 + l]; };
+                auto step_cost = [&](int j) {
+                    int seen[16], ns = 0, cnt[16] = {}, mx = 0;
+                    for (int l = 0; l < grp; l++) {
+                        const uint32_t e = at(j, l);
+                        if (e == ~0u) continue;
+                        const int a = static_cast<int>(e >> 8);
+                        bool dup = false;
+                        for (int q = 0; q < ns; q++) dup = dup || seen[q] == a;
+                        if (dup) continue;
+                        seen[ns++] = a;
+                        mx = std::max(mx, ++cnt[a % grp]);
+                    }
+                    return mx;
+                };
+                bool improved = d <= 24;   // (bounded: plan time grows as d^2 per pass)
+                for (int pass = 0; pass < 4 && improved; pass++) {
+                    improved = false;
+                    for (int l = 0; l < grp; l++)
+                        for (int j1 = 0; j1 < d; j1++)
+                            for (int j2 = j1 + 1; j2 < d; j2++) {
+                                uint32_t &x = at(j1, l), &y = at(j2, l);
+                                if (x == y) continue;
+                                const int before = step_cost(j1) + step_cost(j2);
+                                std::swap(x, y);
+                                if (step_cost(j1) + step_cost(j2) < before) improved = true;
+                                else std::swap(x, y);
+                            }
                 }
             }
             batches.push_back(std::move(words));

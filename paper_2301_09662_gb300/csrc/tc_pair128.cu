@@ -820,8 +820,8 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
                     }
                     return mx;
                 };
-                bool improved = true;
-                for (int pass = 0; pass < 8 && improved; pass++) {
+                bool improved = d <= 24;   // (bounded: plan time grows as d^2 per pass)
+                for (int pass = 0; pass < 4 && improved; pass++) {
                     improved = false;
                     for (int l = 0; l < 8; l++)
                         for (int j1 = 0; j1 < d; j1++)
