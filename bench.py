@@ -325,7 +325,9 @@ def tensor_roofline(wl, form, img_ms, peaks, pair=True):
     ach = flops / (img_ms / 1e3) / 1e12
     peak = float(peaks.get("bf16_tflops", 1892.1))
     alg = sum(fp32_flops_per_spectrum(wl.A, wl.K, int(n)) for n in wl.grid_n) * wl.T * wl.n_pol
+    sustained = float(peaks.get("bf16_tflops_sustained", 0.0)) or None
     return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "frac_of_sustained": (ach / sustained) if sustained else None,
             "traffic": None, "executed_flops_per_launch": flops, "ms_per_launch": img_ms,
             "stage_gemms_per_class_and_sample": stages / max(1, sum((int(n) // 64) ** 2 for n in wl.grid_n)),
             "algorithmic_flops_per_launch": alg, "algorithmic_tflops": alg / (img_ms / 1e3) / 1e12,
@@ -799,6 +801,10 @@ def run_ours(args):
         line["workloads"] = time_workloads(flush, args, stream)
     if not args.no_peaks and world == 1:
         line["peaks_measured"] = measure_pipe_peaks()
+        tc_probe = line["peaks_measured"].get("fp16_tc")
+        if roofline.get("bound") == "tensor" and isinstance(tc_probe, float) and tc_probe > 0:
+            # the same achieved rate against this run's own back-to-back 128 x 256 x 16 FP16 MMA probe
+            roofline["frac_of_fp16_mma_probe"] = roofline["achieved"] / tc_probe
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     if rank == 0:
