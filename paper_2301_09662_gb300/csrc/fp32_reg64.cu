@@ -135,7 +135,10 @@ __device__ __forceinline__ void transform_store(float2 *G, unsigned long long ro
         const int pos = e % (M * M), plane = e / (M * M), ts = plane / P, p = plane % P;
         if (t + ts >= t1) continue;
         const int my = pos / M, mx = pos % M;
-        const int i = (Q1 * my + hy + N / 2) % N, j = (Q1 * mx + hx + N / 2) % N;
+        // shifted row and column: Q1 m + h + N/2 lies in [0, 2N), so one conditional subtraction
+        int i = Q1 * my + hy + N / 2, j = Q1 * mx + hx + N / 2;
+        i -= i >= N ? N : 0;
+        j -= j >= N ? N : 0;
         out[static_cast<long long>(t + ts) * stride + off_c + p * NN + static_cast<long long>(i) * N + j] =
             G[plane * BUF + my * S + mx];
     }
