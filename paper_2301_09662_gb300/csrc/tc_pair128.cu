@@ -420,6 +420,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 const uint32_t e0 = d > 0 ? ent[0] : empty;
                 float4 ww = tw8[(e0 >> 10) << 3];
                 float4 ee = es4[e0 & 1023u];
+#pragma unroll 2
                 for (int j = 0; j < d; j++) {
                     const uint32_t en2 = j + 2 < d ? ent[(j + 2) * 32] : empty;
                     const float4 wwn = tw8[(en1 >> 10) << 3];
