@@ -664,8 +664,10 @@ const void *pair_kernel(int cls)
 // offsets k_off(y, 2 xp) of the pairs (0xFFFF: an empty lane)][d x 32 entries
 // tp << 10 | a] in 16-bit words, an empty step naming tap slot K (K + 1)
 // (zeros) and an antenna its step loads anyway; no zero lists (G16 keeps the
-// cells no list names at zero).  The greedy step order is then improved by a
-// local search (swaps within a lane's list) on the voltage loads' wavefronts.  The
+// cells no list names at zero).  Before that a batch's lists are grouped into
+// the four 8-lane groups so that each group's antennas spread over the bank
+// slots, and the greedy step order is then improved by a local search (swaps
+// within a lane's list) on the voltage loads' wavefronts.  The
 // batches are dealt to the kernel's gridding warps longest first, each to the
 // warp with the least work so far (a batch costs 4 d + 6, about 37 cycles a
 // unit): the 8 TMEM warps start with sched.tmem_load units for their
@@ -758,9 +760,80 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
         std::vector<std::vector<uint16_t>> words(batches.size());
         std::vector<int> blen(batches.size());
         for (size_t b = 0; b < batches.size(); b++) {
-            const auto &bt = batches[b];
+            auto &bt = batches[b];
+            // the batch's lanes into 4 groups of 8 (one 16-byte voltage request each) so that a
+            // group's antennas spread over the 8 bank slots a mod 8: a group needs at least
+            // max(its longest list, the most distinct antennas on one slot) wavefronts per
+            // sample; lists go longest first to the group that bound grows least for, then
+            // swaps of two lists between groups while the sum falls (the store banks do not
+            // depend on the lane)
+            if (bt.size() > 8) {
+                const int nq = static_cast<int>(bt.size());
+                std::vector<int> ord(nq);
+                for (int i = 0; i < nq; i++) ord[i] = i;
+                std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) {
+                    return pairs[bt[u]].second.size() > pairs[bt[v]].second.size();
+                });
+                auto bound = [&](const int *lanes, int n) {
+                    uint64_t seen[16] = {};          // antennas < 1024
+                    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0}, mx = 0, dl = 0;
+                    for (int k = 0; k < n; k++) {
+                        const auto &lst = pairs[bt[lanes[k]]].second;
+                        dl = std::max(dl, static_cast<int>(lst.size()));
+                        for (uint16_t e : lst) {
+                            const int a = e & 1023;
+                            const uint64_t bit = 1ull << (a & 63);
+                            if (seen[a >> 6] & bit) continue;
+                            seen[a >> 6] |= bit;
+                            mx = std::max(mx, ++cnt[a & 7]);
+                        }
+                    }
+                    return std::max(dl, mx);
+                };
+                int grp[4][8], gn[4] = {0, 0, 0, 0};
+                for (int i : ord) {
+                    int best_g = -1, best_inc = 0;
+                    for (int g = 0; g < 4; g++) {
+                        if (gn[g] >= 8) continue;
+                        const int before = bound(grp[g], gn[g]);
+                        grp[g][gn[g]] = i;
+                        const int inc = bound(grp[g], gn[g] + 1) - before;
+                        if (best_g < 0 || inc < best_inc) {
+                            best_g = g;
+                            best_inc = inc;
+                        }
+                    }
+                    grp[best_g][gn[best_g]++] = i;
+                }
+                int cost[4];
+                for (int g = 0; g < 4; g++) cost[g] = bound(grp[g], gn[g]);
+                bool better = true;
+                for (int pass = 0; pass < 4 && better; pass++) {
+                    better = false;
+                    for (int g1 = 0; g1 < 4; g1++)
+                        for (int g2 = g1 + 1; g2 < 4; g2++)
+                            for (int i1 = 0; i1 < gn[g1]; i1++)
+                                for (int i2 = 0; i2 < gn[g2]; i2++) {
+                                    std::swap(grp[g1][i1], grp[g2][i2]);
+                                    const int c1 = bound(grp[g1], gn[g1]), c2 = bound(grp[g2], gn[g2]);
+                                    if (c1 + c2 < cost[g1] + cost[g2]) {
+                                        cost[g1] = c1;
+                                        cost[g2] = c2;
+                                        better = true;
+                                    } else {
+                                        std::swap(grp[g1][i1], grp[g2][i2]);
+                                    }
+                                }
+                }
+                // every group at its own 8-lane slot (a group of fewer than 8 leaves empty lanes, -1)
+                std::vector<int> placed(32, -1);
+                for (int g = 0; g < 4; g++)
+                    for (int k = 0; k < gn[g]; k++) placed[8 * g + k] = bt[grp[g][k]];
+                bt = placed;
+            }
             int d = 0;
-            for (int q : bt) d = std::max(d, static_cast<int>(pairs[q].second.size()));
+            for (int q : bt)
+                if (q >= 0) d = std::max(d, static_cast<int>(pairs[q].second.size()));
             blen[b] = d;
             auto &wd = words[b];
             const int empty_tp = K * (K + 1);                                    // the zero tap slot
@@ -768,7 +841,7 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
             wd.assign(1 + 32 + static_cast<size_t>(d) * 32, empty);
             wd[0] = static_cast<uint16_t>(d);
             for (int l = 0; l < 32; l++) {
-                if (l >= static_cast<int>(bt.size())) {
+                if (l >= static_cast<int>(bt.size()) || bt[l] < 0) {
                     wd[1 + l] = 0xFFFFu;
                     continue;
                 }
@@ -778,7 +851,7 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
             for (int g0 = 0; g0 < 32; g0 += 8) {
                 std::vector<std::vector<uint16_t>> rem(8);
                 for (int l = 0; l < 8; l++)
-                    if (g0 + l < static_cast<int>(bt.size())) rem[l] = pairs[bt[g0 + l]].second;
+                    if (g0 + l < static_cast<int>(bt.size()) && bt[g0 + l] >= 0) rem[l] = pairs[bt[g0 + l]].second;
                 for (int j = 0; j < d; j++) {
                     std::vector<int> order(8);
                     for (int l = 0; l < 8; l++) order[l] = l;
