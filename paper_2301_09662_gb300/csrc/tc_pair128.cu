@@ -63,6 +63,7 @@
 // status word and stops the CTA.  Twelve warps cost no registers over nine: a
 // scheduler holding three warps already limits a thread to 168.
 #include <algorithm>
+#include <array>
 #include <cstdlib>
 
 #include "dft_small.cuh"
@@ -754,6 +755,47 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
                 }
             while (first < pairs.size() && taken[first]) first++;
             batches.push_back(std::move(bt));
+        }
+        // repair store-bank conflicts: a pair whose bank its batch already uses is exchanged with a
+        // pair of another batch whose bank is free there, when its own bank is free in the other
+        // batch and neither batch's longest list grows (so no batch gains steps)
+        {
+            auto bank_of = [&](int q) { const int pos = pairs[q].first; return 4 * ((pos >> 5) & 7) + (pos & 3); };
+            const int nb = static_cast<int>(batches.size());
+            std::vector<std::array<int, 32>> cnt(nb);
+            std::vector<size_t> dmax(nb, 0);
+            for (int b = 0; b < nb; b++) {
+                cnt[b].fill(0);
+                for (int q : batches[b]) {
+                    cnt[b][bank_of(q)]++;
+                    dmax[b] = std::max(dmax[b], pairs[q].second.size());
+                }
+            }
+            for (int pass = 0; pass < 3; pass++) {
+                bool moved = false;
+                for (int b1 = 0; b1 < nb; b1++)
+                    for (size_t i1 = 0; i1 < batches[b1].size(); i1++) {
+                        const int q1 = batches[b1][i1], r1 = bank_of(q1);
+                        if (cnt[b1][r1] < 2) continue;
+                        const size_t len = pairs[q1].second.size();
+                        bool done = false;
+                        for (int b2 = 0; b2 < nb && !done; b2++) {
+                            if (b2 == b1 || cnt[b2][r1] > 0 || len > dmax[b2]) continue;   // r1 free in b2
+                            for (size_t i2 = 0; i2 < batches[b2].size() && !done; i2++) {
+                                const int q2 = batches[b2][i2], r2 = bank_of(q2);
+                                if (pairs[q2].second.size() > dmax[b1] || cnt[b1][r2] > 0) continue;   // r2 free in b1
+                                batches[b1][i1] = q2;
+                                batches[b2][i2] = q1;
+                                cnt[b1][r1]--;
+                                cnt[b1][r2]++;
+                                cnt[b2][r2]--;
+                                cnt[b2][r1]++;
+                                done = moved = true;
+                            }
+                        }
+                    }
+                if (!moved) break;
+            }
         }
         // each batch as words: length, positions, then the steps with distinct voltage banks per
         // group of 8 lanes where possible
