@@ -126,20 +126,24 @@ def test_mixed_grid_sides_in_a_tensor_plan(precision, tol):
 # ---- grid side 128: two pixel classes per CTA from one gridding (the pair kernel)
 
 PAIR_CASES = [
-    # A,  C, T,  K
-    (64, 2, 9, 5),
-    (256, 2, 6, 5),
-    (100, 3, 13, 3),     # A * P not a multiple of 32: partial bank groups
-    (256, 1, 7, 7),
-    (120, 2, 5, 1),      # point kernel
+    # A,  C, T,  K,  N
+    (64, 2, 9, 5, 128),
+    (256, 2, 6, 5, 128),
+    (100, 3, 13, 3, 128),    # A * P not a multiple of 32: partial bank groups
+    (256, 1, 7, 7, 128),
+    (120, 2, 5, 1, 128),     # point kernel
+    (480, 1, 4, 5, 128),     # lists and voltages too large for the pair kernel: the two-stage kernel
+    (64, 2, 9, 5, 64),       # side 64: the pair kernel's one-class form
+    (100, 3, 13, 3, 64),
+    (60, 2, 5, 7, 64),
 ]
 
 
-@pytest.mark.parametrize("A,C,T,K", PAIR_CASES)
+@pytest.mark.parametrize("A,C,T,K,N", PAIR_CASES)
 @pytest.mark.parametrize("precision,tol", [(epic.EPIC_TC_SPLIT_FP16, SPLIT_TOL), (epic.EPIC_TC_FP16, FP16_TOL),
                                            (epic.EPIC_TC_SPLIT_BF16, BF16_TOL)])
-def test_pair_kernel_matches_oracle(A, C, T, K, precision, tol):
-    wl = synth.random_small(A=A, P=2, C=C, T=T, N=128, K=K, seed=600 + A + K + T)
+def test_pair_kernel_matches_oracle(A, C, T, K, N, precision, tol):
+    wl = synth.random_small(A=A, P=2, C=C, T=T, N=N, K=K, seed=600 + A + K + T + N)
     assert _cmp(wl, precision).max() < tol
 
 
