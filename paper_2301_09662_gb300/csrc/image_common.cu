@@ -85,7 +85,7 @@ epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N
     const bool autosub = !(flags & EPIC_NO_AUTOSUB);
 
     // A_pq(c) in FP64, reduced in a fixed order (deterministic)
-    __shared__ double red[kThreads][6];
+    __shared__ double red[kThreads / 32][6];
     __shared__ double apq[6];   // XX, YY, Re XY, Im XY (YX = conj XY)
     const bool ant_kernels = Yauto != nullptr;   // auto image from the per-antenna auto-correlation grid
     if (autosub && !ant_kernels) {
@@ -112,11 +112,17 @@ epilogue_kernel(const float *__restrict__ partial, int n_tau, int n_items, int N
                 s[3] += pr * ia[3] + pi * ia[2];
             }
         }
-        for (int k = 0; k < 4; k++) red[threadIdx.x][k] = s[k];
+        // fixed-order tree: within each warp by shuffles, then the warps' sums by thread 0..3
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_down_sync(0xffffffffu, s[k], o);
+        if ((threadIdx.x & 31) == 0)
+            for (int k = 0; k < 4; k++) red[threadIdx.x >> 5][k] = s[k];
         __syncthreads();
         if (threadIdx.x < 4) {
             double tot = 0;
-            for (int i = 0; i < kThreads; i++) tot += red[i][threadIdx.x];
+            for (int i = 0; i < kThreads / 32; i++) tot += red[i][threadIdx.x];
             apq[threadIdx.x] = tot;
         }
         __syncthreads();
@@ -283,7 +289,8 @@ int launch_epi(epic_plan_s *plan, const GroupCfg &g, const float2 *gains, int T,
                cudaStream_t stream)
 {
     const int NN = g.N * g.N;
-    const int tiles = (NN + kThreads * 4 - 1) / (kThreads * 4);
+    // 8 pixels a thread: fewer blocks, each reducing the channel's auto-power sums once
+    const int tiles = (NN + kThreads * 8 - 1) / (kThreads * 8);
     const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(g.n_chan));
     epilogue_kernel<M, P><<<grid, kThreads, 0, stream>>>(g.d_partial, n_tau, g.n_items, g.N, g.Q1, g.R1, g.R2,
                                                          g.d_chans,
