@@ -280,3 +280,18 @@ def test_autotuned_tensor_plan_keeps_parity():
     ref = oracle.workload_image(wl)
     assert peak_rel_err(out.cpu().numpy().astype(np.complex128), ref, wl.grid_n, 2).max() < SPLIT_TOL
     p.close()
+
+
+@pytest.mark.parametrize("N", [128, 64])
+def test_pair_kernel_empty_integration_is_zero(N):
+    """n_spectra = 0 through a pair-kernel plan: an all-zero image, status OK."""
+    import torch
+    wl = synth.random_small(A=48, P=2, C=2, T=4, N=N, K=5, seed=1300 + N)
+    p = epic.Plan.from_workload(wl, precision=epic.EPIC_TC_SPLIT_FP16)
+    v = torch.from_numpy(wl.v[:0].copy()).cuda()
+    g = torch.from_numpy(wl.gains).cuda()
+    out = p.image(v, g)
+    torch.cuda.synchronize()
+    assert p.status() == epic.EPIC_OK
+    assert torch.count_nonzero(out) == 0
+    p.close()
