@@ -115,6 +115,7 @@ struct epic_plan_s {
     size_t out_floats = 0;
     long long ef_stride = 0;           // E-field images: complex elements per sample (sum_c P N_c^2)
     uint8_t *d_dft = nullptr;          // tensor form: the 64-point DFT operand (hi, lo parts)
+    uint8_t *d_dft48 = nullptr;        // the 48-point DFT in the same 128 x 128 operands (grid side 96)
     short2 *d_cells = nullptr;         // [C][A]
     float2 *d_kernel = nullptr;        // [K*K]
     int *d_autoint = nullptr;          // [C][A][4] exact integer auto sums
@@ -194,7 +195,7 @@ int launch_imaging(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
                    cudaStream_t stream);
 
 // tensor-core form, both 64-point DFT stages on tcgen05 (tc_dual64.cu)
-void build_dft_operand(bool bf16, std::vector<uint16_t> &words);
+void build_dft_operand(bool bf16, std::vector<uint16_t> &words, int M = 64);
 size_t tc_dual_smem_bytes(int A, int K);
 int prepare_tc_dual(const epic_plan_s *plan, size_t smem);
 size_t tc_dual_fold_smem_bytes();
@@ -207,7 +208,7 @@ int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std:
                       const std::vector<uint32_t> &tab32, const std::vector<int4> &idx32,
                       const std::vector<int2> &chan32, std::vector<uint16_t> &tab, std::vector<int4> &idx,
                       std::vector<int2> &chan, std::vector<unsigned long long> &upper,
-                      const PairSchedule &sched = PairSchedule());
+                      const PairSchedule &sched = PairSchedule(), int M = 64);
 size_t tc_pair_smem_bytes(int A, int K, int words);
 int prepare_tc_pair(const epic_plan_s *plan, size_t smem);
 int launch_tc_pair(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const float2 *gains, int T, int *n_tau,

@@ -64,6 +64,7 @@ void free_plan(epic_plan_s *p)
     cudaFree(p->d_cells);
     cudaFree(p->d_kernel);
     cudaFree(p->d_dft);
+    cudaFree(p->d_dft48);
     cudaFree(p->d_bauto);
     cudaFree(p->d_autoint);
     cudaFree(p->d_status);
@@ -608,10 +609,12 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
     const bool tensor = precision != EPIC_FP32;
     if (tensor) {
         // the tensor form runs on 64-point transforms: sides 64, 128, 256, 512 fold to them and
-        // side 32 is transformed zero-padded; channel groups of side 96 in the same plan run the
-        // FP32 kernel, but at least one group must be of another side
+        // side 32 is transformed zero-padded; side 96 (48-point transforms in the same operands)
+        // only on the dual-polarisation pair kernel, else it runs the FP32 kernel in the same
+        // plan, and then at least one group must be of another side (checked again once the
+        // groups are built)
         if ((n_ant * n_pol) % 4 != 0) return EPIC_ERR_UNSUPPORTED;
-        bool any = false;
+        bool any = n_pol == 2 && !ant_kernels;
         for (int c = 0; c < n_chan; c++) any = any || grid_n[c] != 96;
         if (!any) return EPIC_ERR_UNSUPPORTED;
     }
@@ -840,25 +843,30 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                 }
             }
             if (rc == EPIC_OK && g.tensor && !g.tc_regular && !g.alias) rc = EPIC_ERR_UNSUPPORTED;
-            // grid side 128 in a tensor plan: two pixel classes per CTA from one gridding when the
-            // aperture's rows fold without overlap and the lists fit in shared memory; grid side 64:
-            // the same kernel with its one class
-            if (rc == EPIC_OK && g.tensor && (g.N == 128 || g.N == 64) && n_pol == 2 && p->nker == 1 &&
-                !(diag & EPIC_DIAG_NO_PAIR)) {
+            // grid sides 128 and 96 in a tensor plan: two pixel classes per CTA from one gridding when
+            // the aperture's rows fold without overlap and the lists fit in shared memory (side 96:
+            // 48-point DFTs in the 64-point operands; without the pair kernel it stays on the FP32
+            // kernel); grid side 64: the same kernel with its one class
+            const bool pair_side = (g.tensor && (g.N == 128 || g.N == 64)) || (tensor && g.N == 96 && g.reg64);
+            if (rc == EPIC_OK && pair_side && n_pol == 2 && p->nker == 1 && !(diag & EPIC_DIAG_NO_PAIR)) {
                 std::vector<uint32_t> tab32;
                 std::vector<int4> idx32, pidx;
                 std::vector<int2> chan32, pchan;
                 std::vector<unsigned long long> rows32, upper;
                 std::vector<uint16_t> ptab;
-                if (epic::build_gather_table(cells, n_ant, p->K, 64, 2, g.chans, tab32, idx32, chan32, rows32) ==
+                if (epic::build_gather_table(cells, n_ant, p->K, g.M, 2, g.chans, tab32, idx32, chan32, rows32) ==
                         EPIC_OK &&
                     epic::build_pair_tables(cells, n_ant, p->K, g.chans, tab32, idx32, chan32, ptab, pidx, pchan,
-                                            upper) == EPIC_OK) {
+                                            upper, epic::PairSchedule(), g.M) == EPIC_OK) {
                     int words = 0;
                     for (const int2 &ch : pchan) words = std::max(words, ch.y);
                     if (epic::tc_pair_smem_bytes(n_ant, p->K, words) + 2048 <= static_cast<size_t>(smem_optin)) {
                         g.pair = true;
                         g.pwords = words;
+                        if (g.M == 48) {   // side 96 leaves the FP32 kernel for the pair kernel
+                            g.tensor = true;
+                            g.tc_regular = true;
+                        }
                         g.h_tab32 = std::move(tab32);
                         g.h_idx32 = std::move(idx32);
                         g.h_chan32 = std::move(chan32);
@@ -873,7 +881,7 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                 }
             }
         }
-        g.launch_items = g.pair ? g.n_chan * (g.N == 128 ? 2 : 1) : g.n_items;
+        g.launch_items = g.pair ? g.n_chan * (g.Q1 == 2 ? 2 : 1) : g.n_items;
         if (g.pair) g.tau_cap = std::max(g.tau_cap, epic::fp32_pick_tau(g.launch_items, max_spectra, p->sm_count));
         if (rc == EPIC_OK) rc = dev_upload(&g.d_chans, g.chans.data(), g.chans.size());
         if (rc == EPIC_OK) rc = dev_upload(&g.d_out_off, offs.data(), offs.size());
@@ -900,6 +908,11 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
                             static_cast<size_t>(g.tau_cap) * g.n_items * g.M * g.M * npf);
         p->groups.push_back(g);
     }
+    if (rc == EPIC_OK && tensor) {   // a tensor plan runs at least one group on the tensor cores
+        bool any = false;
+        for (const auto &g : p->groups) any = any || g.tensor;
+        if (!any) rc = EPIC_ERR_UNSUPPORTED;
+    }
     // exact auto sums: one set per image of a series batch (slot 0 for epic_image)
     p->series_cap = epic::kMaxTau;
     for (const auto &g : p->groups) p->series_cap = std::min(p->series_cap, g.tau_cap);
@@ -912,14 +925,20 @@ int epic_plan(epic_plan_t *out, const double *ant_xy_m, int n_ant, int n_pol,
         std::vector<uint16_t> ops;
         epic::build_dft_operand(precision == EPIC_TC_SPLIT_BF16, ops);
         rc = dev_upload(&p->d_dft, reinterpret_cast<const uint8_t *>(ops.data()), ops.size() * 2);
+        bool side48 = false;
+        for (const auto &g : p->groups) side48 = side48 || (g.pair && g.M == 48);
+        if (rc == EPIC_OK && side48) {
+            epic::build_dft_operand(precision == EPIC_TC_SPLIT_BF16, ops, 48);
+            rc = dev_upload(&p->d_dft48, reinterpret_cast<const uint8_t *>(ops.data()), ops.size() * 2);
+        }
         // the dual kernel's dynamic shared memory: the largest any of its groups needs (a
         // large side on the fold path needs the operands and the grid only)
         size_t dual = 0;
         for (const auto &g : p->groups)
-            if (g.tensor)
+            if (g.tensor && !g.pair)
                 dual = std::max(dual, g.tc_regular ? epic::tc_dual_smem_bytes(n_ant, p->K)
                                                    : epic::tc_dual_fold_smem_bytes());
-        if (rc == EPIC_OK) rc = epic::prepare_tc_dual(p, dual);
+        if (rc == EPIC_OK && dual) rc = epic::prepare_tc_dual(p, dual);
         size_t pair = 0;
         for (const auto &g : p->groups)
             if (g.pair) pair = std::max(pair, epic::tc_pair_smem_bytes(n_ant, p->K, g.pwords));
@@ -1011,7 +1030,7 @@ int repack_pair(epic_plan_s *plan, epic::GroupCfg &g, const epic::PairSchedule &
     std::vector<unsigned long long> upper;
     std::vector<uint16_t> ptab;
     int rc = epic::build_pair_tables(plan->h_cells, plan->A, plan->K, g.chans, g.h_tab32, g.h_idx32, g.h_chan32,
-                                     ptab, pidx, pchan, upper, ps);
+                                     ptab, pidx, pchan, upper, ps, g.M);
     if (rc != EPIC_OK) return rc;
     if (ptab.size() != g.ptab_n || pidx.size() != g.pidx_n) return EPIC_ERR_UNSUPPORTED;
     if (cudaStreamSynchronize(s) != cudaSuccess ||

@@ -590,11 +590,12 @@ int launch_tc_dual(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
     });
 }
 
-// The 64-point DFT X[r][k] in real 2 x 2 block form, hi and lo parts, K-major:
-// row r = 32 q + l -> (my = 16 q + l mod 16, part = l / 16), column k = 64 part' + j,
-// X = exp(+2 pi i j my / 64) as [[cos, -sin], [sin, cos]] over (part, part').
-// The lo part is what the hi part leaves of the FP64 value, rounded once more.
-void build_dft_operand(bool bf16, std::vector<uint16_t> &words)
+// The M-point DFT X[r][k] (M = 64, or 48 in the first 48 of the 64 frequencies and inputs, the
+// rest zero) in real 2 x 2 block form, hi and lo parts, K-major: row r = 32 q + l -> (my = 16 q
+// + l mod 16, part = l / 16), column k = 64 part' + j, X = exp(+2 pi i j my / M) as
+// [[cos, -sin], [sin, cos]] over (part, part').  The lo part is what the hi part leaves of the
+// FP64 value, rounded once more.
+void build_dft_operand(bool bf16, std::vector<uint16_t> &words, int M)
 {
     words.assign(2 * kPart / 2, 0);
     auto to16 = [bf16](double x, double &back) -> uint16_t {
@@ -613,11 +614,13 @@ void build_dft_operand(bool bf16, std::vector<uint16_t> &words)
         for (int k = 0; k < 128; k++) {
             const int j = k % 64;
             const bool im_in = k >= 64;
-            const long e = (static_cast<long>(j) * my) % 64;
-            const double th = 2.0 * M_PI * static_cast<double>(e) / 64.0;
+            // an M-point DFT (M = 64, or 48 in the first 48 rows and columns, the rest zero)
+            const long e = (static_cast<long>(j) * my) % M;
+            const double th = 2.0 * M_PI * static_cast<double>(e) / M;
             double a;
             if (part == 0) a = im_in ? -std::sin(th) : std::cos(th);
             else a = im_in ? std::cos(th) : std::sin(th);
+            if (j >= M || my >= M) a = 0.0;
             double hi_back = 0, lo_back = 0;
             const uint16_t hi = to16(a, hi_back);
             const uint16_t lo = to16(a - hi_back, lo_back);

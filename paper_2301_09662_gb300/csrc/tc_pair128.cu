@@ -157,7 +157,7 @@ __device__ __forceinline__ void products(uint32_t lane_addr, uint32_t d2, int hh
 // lane l reads copy l mod 8, so the eight lanes of one 16-byte request never
 // share a bank group; the last slot is zero, for the lists' empty steps),
 // stage [(A*P + 3) / 4] (u32), the channel's lists [words] (u16).
-template <int VAR, int CLS>
+template <int VAR, int CLS, int MF>
 __global__ void __launch_bounds__(kPairThreads, 1)
 tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gains,
                   const short2 *__restrict__ cells, const float2 *__restrict__ kern, int K,
@@ -169,7 +169,11 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                   const float *__restrict__ dfreq, const float4 *__restrict__ dtab)
 {
     constexpr int P = 2;
-    constexpr int N = CLS == 2 ? 128 : 64;   // grid side: two classes of side 128, or side 64 unfolded
+    // grid side: two classes of folded side MF (128 or 96), or side 64 unfolded; a 48-point DFT
+    // sits in the 64-point operands' first 48 rows and columns (the rest zero)
+    constexpr int N = CLS == 2 ? 2 * MF : MF;
+    static_assert(MF == 64 || (MF == 48 && CLS == 2), "folded sides 64 and 48");
+    auto wrap = [](int x) { return ((x % N) + N) % N; };
     constexpr bool kBF16 = VAR == 2;
     constexpr bool kSplit = VAR != 1;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -227,7 +231,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     for (int a = simt ? tid : A; a < A; a += kGath) {
         const short2 k = cells[static_cast<size_t>(c) * A + a];
         if (k.x < hk || k.x >= N - hk || k.y < hk || k.y >= N - hk) atomicOr(status, kStatusDevice);
-        const float2 ph = twN[(k.x * hx) & (N - 1)];
+        const float2 ph = twN[wrap(k.x * hx)];
         for (int p = 0; p < P; p++) {
             const float2 g = gains ? gains[(static_cast<size_t>(c) * A + a) * P + p] : make_float2(1.f, 0.f);
             const float2 gg = cmul(g, ph);
@@ -241,7 +245,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         float2 w[2];
         for (int u = 0; u < 2; u++) {
             const int dx = j - 1 + u;
-            w[u] = (tp < TPN && dx >= 0 && dx < K) ? cmul(kern[dyi * K + dx], twN[((dx - hk) * hx) & (N - 1)])
+            w[u] = (tp < TPN && dx >= 0 && dx < K) ? cmul(kern[dyi * K + dx], twN[wrap((dx - hk) * hx)])
                                                    : make_float2(0.f, 0.f);
         }
         tw2[i] = make_float4(w[0].x, w[0].y, w[1].x, w[1].y);
@@ -279,8 +283,8 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
         tc::tmem_st32_issue(acc, z);
         tc::tmem_st32_issue(acc + 32, z);
         // the column-stage operand of class hy = 1 (A operand in TMEM): X with input row jy
-        // turned by w_128^{ky}, ky = jy + 64 [row listed as upper], i.e. the rotation by
-        // w_128^{2 jy my + ky} in real 2 x 2 form.  Lane = output (my, part), columns k / 2 of
+        // turned by w_N^{ky}, ky = jy + MF [row listed as upper], i.e. the rotation by
+        // w_N^{2 jy my + ky} in real 2 x 2 form (N = 2 MF).  Lane = output (my, part), columns k / 2 of
         // k = 64 im_in + jy (hi, then lo 64 columns on); warp half w / 4 = im_in.
         const int myo = 16 * (warp & 3) + (lane & 15), prt = lane >> 4, imin = warp >> 2;
         const unsigned long long up = upper[ci];
@@ -291,9 +295,10 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
 #pragma unroll
             for (int u = 0; u < 2; u++) {
                 const int j = 2 * w + u;
-                const int kyj = j + (((up >> j) & 1ull) ? 64 : 0);
-                const float2 e = twN[(2 * j * myo + kyj) & (N - 1)];
+                const int kyj = j + (((up >> j) & 1ull) ? MF : 0);
+                const float2 e = twN[wrap(2 * j * myo + kyj)];
                 a2[u] = prt == 0 ? (imin ? -e.y : e.x) : (imin ? e.x : e.y);
+                if (MF < 64 && (j >= MF || myo >= MF)) a2[u] = 0.f;   // outside the 48-point DFT
             }
             split_pair<kBF16, kSplit>(a2[0], a2[1], xh[w], xl[w]);
         }
@@ -325,6 +330,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 if (!withhold_mma) {
 #pragma unroll
                     for (int kb = 0; kb < 8; kb++) {
+                        if (MF < 64 && (kb & 3) * 16 >= MF) continue;   // k beyond the folded side: zeros
                         const uint64_t g_hi = tc::smem_desc(g_base + kb * 256, kLBO, kSBO);
                         const uint64_t x_hi = tc::smem_desc(x_base + kb * 256, kLBO, kSBO);
                         tc::mma_f16(taddr + col_r(t), g_hi, x_hi, idesc_row, kb > 0 ? 1u : 0u);
@@ -351,6 +357,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                         const uint32_t d2 = taddr + (hy ? col_r(t) : col_a(t));
 #pragma unroll
                         for (int kb = 0; kb < 8; kb++) {
+                            if (MF < 64 && (kb & 3) * 16 >= MF) continue;
                             const uint64_t h_hi = tc::smem_desc(h_base + kb * 256, kLBO, kSBO);
                             const uint64_t h_lo = tc::smem_desc(h_base + kPart + kb * 256, kLBO, kSBO);
                             if (hy == 0) {
@@ -383,6 +390,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
     } else {
         const int m = 32 * (warp & 3) + lane;          // TMEM warps: lane m = (pol, jy) in D1, (my, part) in D2
         const int hp = (warp >> 2) & 1;                 // which half of the columns
+        const bool prod_rows = 16 * (warp & 3) < MF;    // the warp's pixel rows my = 16 (w mod 4) .. exist
         const int part = lane >> 4;
         const int pol = m >> 6, jy = m & 63;
         const int4 my_idx = pidx[ci * kGathW + warp];   // (first batch, batches in half 1, second half's start, batches in half 2)
@@ -540,7 +548,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                     if (!tc::mbar_wait(&bar_m2[0], p2, wait_budget)) fail();
                     else {
                         tc::fence_after_sync();
-                        products<true>(lane_addr, col_a(t), hp, part, acc0);
+                        if (prod_rows) products<true>(lane_addr, col_a(t), hp, part, acc0);
                         tc::fence_before_sync();
                         tc::mbar_arrive(&bar_fa);
                     }
@@ -565,7 +573,7 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                 if (!tc::mbar_wait(&bar_m2[1], p2, wait_budget)) fail();
                 else {
                     tc::fence_after_sync();
-                    products<false>(lane_addr, col_r(t), hp, part, acc0);
+                    if (prod_rows) products<false>(lane_addr, col_r(t), hp, part, acc0);
                     tc::fence_before_sync();
                     tc::mbar_arrive(&bar_fb);
                 }
@@ -584,13 +592,14 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             const int my = 16 * (warp & 3) + (lane & 15);
             // items: channel ci's classes h = 2 hy + hx (side 128), or channel ci (side 64)
             float4 *dst0 = reinterpret_cast<float4 *>(partial) +
-                           (static_cast<size_t>(tau) * n_items_out + (CLS == 2 ? ci * 4 + hx : ci)) * (64 * 64);
+                           (static_cast<size_t>(tau) * n_items_out + (CLS == 2 ? ci * 4 + hx : ci)) * (MF * MF);
             float4 *dst1 = reinterpret_cast<float4 *>(partial) +
-                           (static_cast<size_t>(tau) * n_items_out + ci * 4 + 2 + hx) * (64 * 64);
+                           (static_cast<size_t>(tau) * n_items_out + ci * 4 + 2 + hx) * (MF * MF);
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 const int mx = 32 * hp + 16 * part + j;
-                dst0[my * 64 + mx] = make_float4(acc0[j].x * inv, acc0[j].y * inv, acc0[j].z * inv, acc0[j].w * inv_im);
+                if (my < MF && mx < MF)
+                    dst0[my * MF + mx] = make_float4(acc0[j].x * inv, acc0[j].y * inv, acc0[j].z * inv, acc0[j].w * inv_im);
             }
 #pragma unroll
             for (int half = 0; half < (CLS == 2 ? 2 : 0); half++) {
@@ -601,9 +610,10 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
 #pragma unroll
                 for (int jj = 0; jj < 8; jj++) {
                     const int mx = 32 * hp + 16 * part + 8 * half + jj;
-                    dst1[my * 64 + mx] = make_float4(__uint_as_float(s[4 * jj]) * inv, __uint_as_float(s[4 * jj + 1]) * inv,
-                                                     __uint_as_float(s[4 * jj + 2]) * inv,
-                                                     __uint_as_float(s[4 * jj + 3]) * inv_im);
+                    if (my < MF && mx < MF)
+                        dst1[my * MF + mx] = make_float4(__uint_as_float(s[4 * jj]) * inv, __uint_as_float(s[4 * jj + 1]) * inv,
+                                                         __uint_as_float(s[4 * jj + 2]) * inv,
+                                                         __uint_as_float(s[4 * jj + 3]) * inv_im);
                 }
             }
         }
@@ -642,11 +652,14 @@ int pair_dispatch(int precision, F &&f)
     }
 }
 
+// the instantiation for a group: two classes of folded side 64 (grid side 128) or 48 (96), or one
+// class of side 64
 template <int VAR>
-const void *pair_kernel(int cls)
+const void *pair_kernel(int cls, int mf)
 {
-    return cls == 2 ? reinterpret_cast<const void *>(tc_pair128_kernel<VAR, 2>)
-                    : reinterpret_cast<const void *>(tc_pair128_kernel<VAR, 1>);
+    if (cls == 1) return reinterpret_cast<const void *>(tc_pair128_kernel<VAR, 1, 64>);
+    return mf == 48 ? reinterpret_cast<const void *>(tc_pair128_kernel<VAR, 2, 48>)
+                    : reinterpret_cast<const void *>(tc_pair128_kernel<VAR, 2, 64>);
 }
 
 }  // namespace
@@ -686,11 +699,14 @@ const void *pair_kernel(int cls)
 int build_pair_tables(const std::vector<short2> &cells, int A, int K, const std::vector<int> &chans,
                       const std::vector<uint32_t> &tab32, const std::vector<int4> &idx32,
                       const std::vector<int2> &chan32, std::vector<uint16_t> &tab, std::vector<int4> &idx,
-                      std::vector<int2> &chan, std::vector<unsigned long long> &upper, const PairSchedule &sched)
+                      std::vector<int2> &chan, std::vector<unsigned long long> &upper, const PairSchedule &sched,
+                      int M)
 {
-    constexpr int M = 64, S = M + 1, W32 = 8, W = kPairGatherWarps, kWindow = 96;
+    constexpr int W32 = 8, W = kPairGatherWarps, kWindow = 96;
+    const int S = M + 1;
     const long long kTmemLoad = sched.tmem_load;
-    if (A > 1024 || K * (K + 1) > 63 || sched.tmem_load < 0 || sched.first_pct < 0 || sched.first_pct > 100)
+    if (A > 1024 || K * (K + 1) > 63 || sched.tmem_load < 0 || sched.first_pct < 0 || sched.first_pct > 100 ||
+        (M != 64 && M != 48))
         return EPIC_ERR_UNSUPPORTED;
     const int nc = static_cast<int>(chans.size()), h = (K - 1) / 2;
     tab.clear();
@@ -1019,8 +1035,10 @@ size_t tc_pair_smem_bytes(int A, int K, int words) { return pair_smem(A, K, word
 int prepare_tc_pair(const epic_plan_s *plan, size_t smem)
 {
     return pair_dispatch(plan->precision, [&](auto vv) {
-        const int rc = raise_dyn_smem_cap(pair_kernel<decltype(vv)::value>(2), smem);
-        return rc != EPIC_OK ? rc : raise_dyn_smem_cap(pair_kernel<decltype(vv)::value>(1), smem);
+        constexpr int V = decltype(vv)::value;
+        int rc = raise_dyn_smem_cap(pair_kernel<V>(2, 64), smem);
+        if (rc == EPIC_OK) rc = raise_dyn_smem_cap(pair_kernel<V>(1, 64), smem);
+        return rc != EPIC_OK ? rc : raise_dyn_smem_cap(pair_kernel<V>(2, 48), smem);
     });
 }
 
@@ -1030,15 +1048,16 @@ int launch_tc_pair(epic_plan_s *plan, const GroupCfg &g, const uint8_t *v, const
     int n_tau = choose_tau(plan, g, T);
     if (n_tau > g.tau_cap) n_tau = g.tau_cap;
     *n_tau_out = n_tau;
-    const int cls = g.N == 128 ? 2 : 1;
+    const int cls = g.Q1 == 2 ? 2 : 1;
     const dim3 grid(static_cast<unsigned>(g.n_chan * cls * n_tau));
     const size_t smem = pair_smem(plan->A, plan->K, g.pwords);
+    const uint8_t *dft = g.M == 48 ? plan->d_dft48 : plan->d_dft;
     return pair_dispatch(plan->precision, [&](auto vv) {
         constexpr int V = decltype(vv)::value;
-        auto kfn = cls == 2 ? tc_pair128_kernel<V, 2> : tc_pair128_kernel<V, 1>;
+        auto kfn = cls == 1 ? tc_pair128_kernel<V, 1, 64> : g.M == 48 ? tc_pair128_kernel<V, 2, 48> : tc_pair128_kernel<V, 2, 64>;
         kfn<<<grid, kPairThreads, smem, stream>>>(
             v, gains, plan->d_cells, plan->d_kernel, plan->K, g.d_chans, g.d_twN, g.d_ptab, g.d_pchan, g.d_pidx,
-            g.d_upper, plan->d_dft, plan->A, plan->C, T, g.n_items, n_tau, g.d_partial, plan->d_status,
+            g.d_upper, dft, plan->A, plan->C, T, g.n_items, n_tau, g.d_partial, plan->d_status,
             plan->wait_budget, plan->test_withhold_mma, plan->d_dfreq, plan->delays ? plan->d_dtab : nullptr);
         return cudaGetLastError() == cudaSuccess ? EPIC_OK : EPIC_ERR_CUDA;
     });

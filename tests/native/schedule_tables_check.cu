@@ -187,9 +187,11 @@ int main(int argc, char **argv)
     // each warp's batches split in two halves that cover them once, offsets inside the block, the
     // upper-row mask, and no list for a layout whose rows overlap after folding
     long long pair_words = -1;
-    if (N == 128 && P == 2 && K * (K + 1) <= 63 && A <= 1024) {
+    if ((N == 128 || N == 96) && P == 2 && K * (K + 1) <= 63 && A <= 1024) {
+        // the pair kernel's lists (folded side M = 64 or 48): an aperture band of M - 4 rows
+        const int span = M - 4;
         std::vector<short2> band(cells);
-        for (auto &c : band) c.y = static_cast<short>(N / 2 - 30 + ((c.y - h) % (60 - 2 * h)) + h);
+        for (auto &c : band) c.y = static_cast<short>(M - span / 2 + ((c.y - h) % (span - 2 * h)) + h);
         std::vector<uint32_t> t32;
         std::vector<int4> i32, pidx;
         std::vector<int2> c32, pchan;
@@ -203,7 +205,7 @@ int main(int argc, char **argv)
             std::vector<int2> pchan_s;
             std::vector<unsigned long long> upper_s;
             std::vector<uint16_t> ptab_s;
-            CHECK(epic::build_pair_tables(band, A, K, chans, t32, i32, c32, ptab_s, pidx_s, pchan_s, upper_s, ps) ==
+            CHECK(epic::build_pair_tables(band, A, K, chans, t32, i32, c32, ptab_s, pidx_s, pchan_s, upper_s, ps, M) ==
                       EPIC_OK,
                   "pair lists build failed (schedule %d/%d)", ps.tmem_load, ps.first_pct);
             if (ps.tmem_load == 90 && ps.first_pct == 80) {
@@ -224,7 +226,7 @@ int main(int argc, char **argv)
             for (int a = 0; a < A; a++)
                 for (int dy = -h; dy <= h; dy++) {
                     const int ky = band[static_cast<size_t>(ci) * A + a].y + dy;
-                    if (ky >= 64) up |= 1ull << (ky - 64);
+                    if (ky >= M) up |= 1ull << (ky - M);
                 }
             CHECK(up == upper[ci], "channel %d: upper-row mask", ci);
             std::multiset<long long> want, got;
@@ -262,7 +264,7 @@ int main(int argc, char **argv)
                             const uint16_t go = pb[off + 1 + l];
                             const int y = (go / 2048) * 8 + (go % 128) / 16;
                             const int k = ((go % 2048) / 128) * 8 + (go % 16) / 2;
-                            const bool lane_ok = go != 0xFFFFu && y < 64 && k < 64 && k % 2 == 0 &&
+                            const bool lane_ok = go != 0xFFFFu && y < M && k < M && k % 2 == 0 &&
                                                  epic::tcc::k_off(y, k) == go;
                             for (int j = 0; j < d; j++) {
                                 const uint16_t e = pb[off + 33 + 32LL * j + l];
@@ -287,7 +289,7 @@ int main(int argc, char **argv)
             std::vector<short2> wide(band);
             for (int ci = 0; ci < C; ci++) {
                 wide[static_cast<size_t>(ci) * A].y = static_cast<short>(h);
-                wide[static_cast<size_t>(ci) * A + 1].y = static_cast<short>(64 + h);
+                wide[static_cast<size_t>(ci) * A + 1].y = static_cast<short>(M + h);
             }
             std::vector<uint32_t> t2;
             std::vector<int4> i2, pidx2;
@@ -295,7 +297,7 @@ int main(int argc, char **argv)
             std::vector<unsigned long long> r2, up2;
             std::vector<uint16_t> pt2;
             CHECK(epic::build_gather_table(wide, A, K, M, P, chans, t2, i2, c2, r2) == EPIC_OK, "wide table");
-            CHECK(epic::build_pair_tables(wide, A, K, chans, t2, i2, c2, pt2, pidx2, pchan2, up2) ==
+            CHECK(epic::build_pair_tables(wide, A, K, chans, t2, i2, c2, pt2, pidx2, pchan2, up2, epic::PairSchedule(), M) ==
                       EPIC_ERR_UNSUPPORTED,
                   "rows that overlap after folding were accepted");
         }

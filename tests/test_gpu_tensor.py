@@ -80,8 +80,8 @@ def test_tensor_lwa_full_size_sampled_channels(precision, tol):
 def test_tensor_uneven_workload_full_size_sampled_channels(precision, tol):
     """The full uneven band (192 channels over 30-80 MHz, grid sides 64/96/128,
     1000 spectra) in one tensor plan: side 64 on the pair kernel's one-class form,
-    96 on the FP32 register kernel, 128 on the pair kernel; one channel of each
-    group against the oracle."""
+    96 and 128 on its two-class forms; one channel of each group against the
+    oracle."""
     wl = synth.uneven()
     chans = [0, 100, 191]
     assert sorted(set(int(wl.grid_n[c]) for c in chans)) == [64, 96, 128]
@@ -116,8 +116,9 @@ def test_two_stage_form_sample_counts(T):
 
 @pytest.mark.parametrize("precision,tol", [(epic.EPIC_TC_SPLIT_FP16, SPLIT_TOL), (epic.EPIC_TC_SPLIT_BF16, BF16_TOL)])
 def test_mixed_grid_sides_in_a_tensor_plan(precision, tol):
-    """Channel groups of sides 64, 96 and 128 in one tensor plan: 64 and 128 fold to the
-    tensor kernel, 96 runs the FP32 kernel; every channel meets the form's bound."""
+    """Channel groups of sides 64, 96 and 128 in one tensor plan, every one on the
+    tensor cores (side 96 through 48-point DFTs); every channel meets the form's
+    bound."""
     wl = synth.random_small(A=40, P=2, C=3, T=17, N=64, K=5, seed=350)
     wl.grid_n = np.array([64, 96, 128], np.int32)
     assert _cmp(wl, precision).max() < tol
@@ -136,6 +137,9 @@ PAIR_CASES = [
     (64, 2, 9, 5, 64),       # side 64: the pair kernel's one-class form
     (100, 3, 13, 3, 64),
     (60, 2, 5, 7, 64),
+    (96, 2, 9, 5, 96),       # side 96: 48-point DFTs in the 64-point operands
+    (100, 2, 7, 3, 96),
+    (200, 1, 5, 7, 96),
 ]
 
 
@@ -147,21 +151,25 @@ def test_pair_kernel_matches_oracle(A, C, T, K, N, precision, tol):
     assert _cmp(wl, precision).max() < tol
 
 
-@pytest.mark.parametrize("N", [128, 64])
+@pytest.mark.parametrize("N", [128, 96, 64])
 def test_pair_kernel_agrees_with_single_class_kernel(N):
-    """The gather-gridding pair kernel (two classes per CTA at side 128, its
-    one-class form at side 64) and the older one-class kernel (EPIC_DIAG_NO_PAIR)
-    compute the same images up to FP32 rounding of different summation orders."""
+    """The gather-gridding pair kernel (two classes per CTA at sides 128 and 96,
+    its one-class form at side 64) and the form EPIC_DIAG_NO_PAIR selects (the
+    two-stage kernel; at side 96, which has no other tensor kernel, the FP32 form)
+    compute the same images up to rounding of different summation orders."""
     wl = synth.random_small(A=200 if N == 128 else 90, P=2, C=2, T=11, N=N, K=5, seed=610 + N)
     a, pa = run_gpu(wl, precision=epic.EPIC_TC_SPLIT_FP16)
-    b, pb = run_gpu(wl, precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_DIAG_NO_PAIR)
+    if N == 96:   # a tensor plan of side 96 alone has no other tensor kernel: the FP32 form
+        b, pb = run_gpu(wl, precision=epic.EPIC_FP32)
+    else:
+        b, pb = run_gpu(wl, precision=epic.EPIC_TC_SPLIT_FP16, flags=epic.EPIC_DIAG_NO_PAIR)
     pa.close()
     pb.close()
     assert peak_rel_err(a, b, wl.grid_n, 2).max() < 5e-6
     assert peak_rel_err(a, oracle.workload_image(wl), wl.grid_n, 2).max() < SPLIT_TOL
 
 
-@pytest.mark.parametrize("N", [128, 64])
+@pytest.mark.parametrize("N", [128, 96, 64])
 @pytest.mark.parametrize("T", [1, 2, 3, 64])
 def test_pair_kernel_sample_counts(T, N):
     """One sample (prologue only), two, three, and many over several time chunks:

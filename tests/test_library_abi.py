@@ -92,10 +92,11 @@ def _seven_antennas():
     return synth.random_small(A=8, P=2, C=2, T=4, N=32, K=3, seed=1).ant_xy[:7]
 
 
-@pytest.mark.parametrize("bad", [dict(grid_n=np.array([96, 96], np.int32)),
+@pytest.mark.parametrize("bad", [dict(grid_n=np.array([96, 96], np.int32), n_pol=1),
                                  dict(n_pol=1, ant_xy=_seven_antennas())])
 def test_tensor_form_rejects_unsupported_shapes_on_host(lib, bad):
-    # every channel on side 96 (no 64-point transform), or n_ant * n_pol not a multiple of 4
+    # every channel on side 96 with single polarisation (side 96 is on the tensor cores only
+    # through the dual-polarisation pair kernel), or n_ant * n_pol not a multiple of 4
     rc, h = epic.make_plan_raw(**_geom(precision=epic.EPIC_TC_SPLIT_FP16, **bad))
     assert rc == epic.EPIC_ERR_UNSUPPORTED and not h.value
 
