@@ -75,17 +75,20 @@ enum {
     EPIC_TC_SPLIT_BF16 = 3      /* tensor cores, two-part BF16 split (hi + lo, 3 MMAs per k-block): about
                                    16 significant bits, bounded by 1e-4 of the peak, not 1e-5 */
 };
-/* The tensor-core forms run both 64-point DFT stages of every pixel class as
- * tcgen05 GEMMs (the complex DFT in real 2 x 2 block form, FP32 accumulation
- * in tensor memory; a 32 side as the 64-point DFT of the zero-padded grid).
- * Grid sides 128 and 64 with dual polarisation and one shared kernel run the
- * gather-gridding kernel (gridding straight into the FP16 operand; two pixel
- * classes per CTA from one gridding at side 128) when the channel's lists fit
- * in shared memory and no folded row holds cells of both aperture halves;
- * otherwise, and for sides 32, 256 and 512 or single polarisation, the
- * two-stage kernel (one class per CTA).  Side 96 (folded side 48) runs the
- * FP32 kernel inside a tensor plan.  Accuracy: split FP16 within 1e-5 of the
- * channel peak, single FP16 within 2e-3. */
+/* The tensor-core forms run both DFT stages of every pixel class as tcgen05
+ * GEMMs (the complex DFT in real 2 x 2 block form, FP32 accumulation in tensor
+ * memory; 64-point, a 32 side as the 64-point DFT of the zero-padded grid, a 96
+ * side's 48-point DFTs in the first 48 rows and columns of the same operands).
+ * Grid sides 128, 96 and 64 with dual polarisation and one shared kernel run
+ * the gather-gridding kernel (gridding straight into the FP16 operand; two
+ * pixel classes per CTA from one gridding at sides 128 and 96) when the
+ * channel's lists fit in shared memory and no folded row holds cells of both
+ * aperture halves; otherwise, and for sides 32, 256 and 512 or single
+ * polarisation, the two-stage kernel (one class per CTA) — except side 96,
+ * which then runs the FP32 kernel inside the tensor plan (a tensor plan must
+ * run at least one group on the tensor cores, else EPIC_ERR_UNSUPPORTED).
+ * Accuracy: split FP16 within 1e-5 of the channel peak, single FP16 within
+ * 2e-3. */
 
 /* flags */
 #define EPIC_MEAN        1u     /* divide the sum over time by n_spectra */
