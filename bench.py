@@ -311,16 +311,20 @@ def run_reference(args):
 def tensor_roofline(wl, form, img_ms, peaks, pair=True):
     """Executed tensor FLOPs of the tensor-core imaging launch over its time.
     Each 64-point DFT stage of one sample is 8 k-blocks x terms MMAs of
-    128 x 128 x 16.  Grid side 128 runs two pixel classes per CTA from one row
-    stage (pair kernel): 3 stage GEMMs per two classes; other sides (and
-    side 128 with EPIC_DIAG_NO_PAIR): 2 per class.  Also the method's
-    algorithmic FLOPs (the FP32 FFT form's count) over the same time."""
+    128 x 128 x 16 (a side-96 48-point stage skips 2 of the 8 k-blocks).
+    Grid sides 128 and 96 run two pixel classes per CTA from one row stage
+    (pair kernel): 3 stage GEMMs per two classes; other sides (and these with
+    EPIC_DIAG_NO_PAIR): 2 per class.  Also the method's algorithmic FLOPs (the
+    FP32 FFT form's count) over the same time."""
     terms = 1 if form == "tc_fp16" else 3
-    stage = 8 * terms * 2.0 * 128 * 128 * 16
+    stage = 8 * terms * 2.0 * 128 * 128 * 16          # one 64-point stage: 8 k-blocks x terms MMAs
     stages = 0.0
     for n in wl.grid_n:
-        classes = (int(n) // 64) ** 2
-        stages += classes * (1.5 if (pair and int(n) == 128) else 2.0)
+        n = int(n)
+        fold = 48 if n == 96 else 64                    # side 96: 48-point DFTs, 6 of the 8 k-blocks
+        classes = max(1, n // fold) ** 2
+        per_class = 1.5 if (pair and n in (128, 96)) else 2.0
+        stages += classes * per_class * (6.0 / 8.0 if n == 96 else 1.0)
     flops = stages * wl.T * stage
     ach = flops / (img_ms / 1e3) / 1e12
     peak = float(peaks.get("bf16_tflops", 1892.1))
@@ -510,18 +514,16 @@ def time_workloads(flush, args, stream):
             stages = p.stage_times()
             entry = {"value": wl.spectra / (step / 1e3), "unit": UNIT, "ms_per_step": step, "stages_ms_last": stages}
             if fname.startswith("tc_"):
-                # the longest launch that runs on the tensor cores (side 96 runs the FP32 kernel inside a
-                # tensor plan); the groups' launches overlap in the graph, so a stage's time includes
-                # sharing the GPU with the others
-                tc_stages = [k for k in stages if k.startswith("image[") and int(k[8:-1]) != 96]
+                # the longest launch (every side runs on the tensor cores in a tensor plan)
+                tc_stages = [k for k in stages if k.startswith("image[")]
                 img_stage = max(tc_stages, key=lambda k: stages[k])
                 side = int(img_stage[8:-1])
                 sub = copy_with_side(wl, side)
                 entry["roofline"] = tensor_roofline(sub, fname, stages[img_stage], peaks)
                 entry["roofline"]["kernel"] = f"tensor-core imaging launch {img_stage}"
-                if any(int(k[8:-1]) == 96 for k in stages if k.startswith("image[")):
-                    entry["roofline"]["note"] = ("grid side 96 runs the FP32 kernel in this plan; the side groups' "
-                                                 "launches overlap, so this launch's time includes sharing the GPU")
+                if len(tc_stages) > 1:
+                    entry["roofline"]["note"] = ("the side groups' launches overlap in one graph, so this launch's "
+                                                 "time includes sharing the GPU with the others")
             else:
                 entry["roofline"] = fp32_roofline(wl, stages, peaks, sm_count)
             lines[fname] = entry
