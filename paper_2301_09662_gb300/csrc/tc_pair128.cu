@@ -59,8 +59,12 @@
 // between a row stage and the next gridding.  Warp 11 issues, in order, the
 // row stage of t after bar_g (and, from the second sample on, bar_fa of
 // t - 1), then after bar_h (and bar_fb of t - 1) the column stages of classes
-// 0 and 1, each committed to its own mbarrier.  Every wait is bounded; a timeout is recorded in the plan's
-// status word and stops the CTA.  Twelve warps cost no registers over nine: a
+// 0 and 1, each committed to its own mbarrier.  Each of its waits costs a
+// shared-memory round trip of a few hundred cycles under the gridding's load,
+// so it waits first for the barrier that is usually complete (bar_fa, bar_fb)
+// and last for the one on the path (bar_g, bar_h), and reads the abort flag
+// once a sample while the row stage runs.  Every wait is bounded; a timeout is
+// recorded in the plan's status word and stops the CTA.  Twelve warps cost no registers over nine: a
 // scheduler holding three warps already limits a thread to 168.
 #include <algorithm>
 #include <array>
@@ -321,10 +325,10 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             bool ok = tc::mbar_wait(&bar_x, 0, wait_budget);
             uint32_t pg = 0, ph = 0, pf = 0;
             for (int t = t0; t < t1 && ok; t++) {
-                ok = tc::mbar_wait(&bar_g, pg, wait_budget) && !abort_flag;
+                if (t > t0)   // R(t) = A(t - 1): the products of (t - 1, 0) have read it
+                    ok = tc::mbar_wait(&bar_fa, pf, wait_budget);
+                ok = ok && tc::mbar_wait(&bar_g, pg, wait_budget);
                 pg ^= 1u;
-                if (ok && t > t0)   // R(t) = A(t - 1): the products of (t - 1, 0) have read it
-                    ok = tc::mbar_wait(&bar_fa, pf, wait_budget) && !abort_flag;
                 if (!ok) break;
                 tc::fence_after_sync();
                 if (!withhold_mma) {
@@ -343,10 +347,14 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                     }
                     tc::mma_commit(&bar_m1);
                 }
-                ok = tc::mbar_wait(&bar_h, ph, wait_budget) && !abort_flag;
+                if (abort_flag) {
+                    ok = false;
+                    break;
+                }
+                if (CLS == 2 && t > t0)   // A(t) = R(t - 1): the products of (t - 1, 1) have read it
+                    ok = tc::mbar_wait(&bar_fb, pf, wait_budget);
+                ok = ok && tc::mbar_wait(&bar_h, ph, wait_budget);
                 ph ^= 1u;
-                if (CLS == 2 && ok && t > t0)   // A(t) = R(t - 1): the products of (t - 1, 1) have read it
-                    ok = tc::mbar_wait(&bar_fb, pf, wait_budget) && !abort_flag;
                 if (t > t0) pf ^= 1u;
                 if (!ok) break;
                 tc::fence_after_sync();
