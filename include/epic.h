@@ -127,10 +127,11 @@ enum {
                                                 EPIC_ERR_TIMEOUT; the context stays usable */
 #define EPIC_DIAG_ALIAS_BATCH(n) ((((unsigned)(n)) & 255u) << 16)   /* fold path: at most n (1..255) samples
                                                                         per time batch */
-#define EPIC_DIAG_NO_PAIR        (1u << 12)  /* tensor form, grid sides 128 and 64: the two-stage kernel of
-                                                every side (one pixel class per CTA, scheduled gridding)
-                                                instead of the gather-gridding pair kernel (two classes
-                                                from one gridding at side 128, its one class at 64) */
+#define EPIC_DIAG_NO_PAIR        (1u << 12)  /* tensor form without the gather-gridding pair kernel (two
+                                                classes from one gridding at sides 128 and 96, its one
+                                                class at 64): sides 128 and 64 run the two-stage kernel
+                                                of the other sides (one pixel class per CTA, scheduled
+                                                gridding), side 96 the FP32 register kernel */
 
 /*
  * epic_plan -- validate the array geometry and build every table the imaging
