@@ -424,20 +424,33 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
             const float4 *es4 = reinterpret_cast<const float4 *>(es + (t & 1) * AP);
             const float4 *tw8 = tw2 + (lane & 7);
             const uint32_t empty = static_cast<uint32_t>(TPN) << 10;
+            // the next batch's header and first entry are loaded a batch ahead (every batch has d >= 1)
+            int d = 0;
+            uint32_t off = kNone, e0 = empty;
+            if (n > 0) {
+                d = bt[0];
+                off = bt[1 + lane];
+                e0 = bt[33 + lane];
+            }
             for (int b = 0; b < n; b++) {
-                const int d = bt[0];
-                const uint32_t off = bt[1 + lane];
                 const uint16_t *ent = bt + 33 + lane;
+                const uint16_t *nbt = bt + 33 + 32 * d;
+                int dn = 0;
+                uint32_t offn = kNone, e0n = empty;
+                if (b + 1 < n) {
+                    dn = nbt[0];
+                    offn = nbt[1 + lane];
+                    e0n = nbt[33 + lane];
+                }
                 float2 acc[P][2];
 #pragma unroll
                 for (int p = 0; p < P; p++) acc[p][0] = acc[p][1] = make_float2(0.f, 0.f);
                 // software-pipelined: the entry two steps ahead and the taps and voltages one step
-                // ahead are in flight while the current step's multiply-adds run
+                // ahead are in flight while the current step's multiply-adds run (unrolled by four)
                 uint32_t en1 = d > 1 ? ent[32] : empty;
-                const uint32_t e0 = d > 0 ? ent[0] : empty;
                 float4 ww = tw8[(e0 >> 10) << 3];
                 float4 ee = es4[e0 & 1023u];
-#pragma unroll 2
+#pragma unroll 4
                 for (int j = 0; j < d; j++) {
                     const uint32_t en2 = j + 2 < d ? ent[(j + 2) * 32] : empty;
                     const float4 wwn = tw8[(en1 >> 10) << 3];
@@ -472,7 +485,10 @@ tc_pair128_kernel(const uint8_t *__restrict__ v, const float2 *__restrict__ gain
                         }
                     }
                 }
-                bt += 33 + 32 * d;
+                bt = nbt;
+                d = dn;
+                off = offn;
+                e0 = e0n;
             }
         };
         // D1 (row transform of the sample) -> H16, shared by both classes (class hy = 1's turn is in
